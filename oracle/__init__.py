@@ -1,0 +1,167 @@
+"""FP64 CPU oracle of the slip-wall D2Q9 MRT lattice Boltzmann method.
+
+TEST INFRASTRUCTURE ONLY: the tests, `__graft_entry__.smoke()` and the CPU
+baseline leg of `bench.py` use it; the product path never does.  It shares
+no code with the CUDA library (`paper_2012_14707_gb300`): the parameter
+formulas are in `oracle.params`, the time stepping in `lbm_oracle.c`.
+
+Parity status per function (what pins it is in tests/test_oracle_*.py):
+  * parameter formulas -- pinned (cross-identities between independently
+    printed equations, the slip law of Eq. PhyscPoiSlip).
+  * collision + forcing -- pinned (moment identities, conservation, rest
+    state, momentum gain per step).
+  * boundary scheme -- pinned (halfway bounce-back no-slip parabola at the
+    magic parameter, Zhao no-slip parabola, slip Poiseuille closed forms for
+    tuned and untuned parameters).
+  * curved walls (Couette) -- pinned only to within discretisation error
+    (error against Eq. EqAnaMicro falls under refinement).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from . import params  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB = os.path.join(_HERE, "liblbm_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        up = ctypes.POINTER(ctypes.c_uint8)
+        lib.olbm_create.restype = P
+        lib.olbm_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, up,
+                                    ctypes.c_double, ctypes.c_double, dp, ctypes.c_int, ip, ip, ip,
+                                    dp, dp, dp, dp, dp, ctypes.c_int]
+        lib.olbm_step.argtypes = [P, ctypes.c_long]
+        lib.olbm_fields.argtypes = [P, dp, dp, dp]
+        lib.olbm_residual.argtypes = [P, dp, dp]
+        lib.olbm_get_f.argtypes = [P, dp]
+        lib.olbm_set_f.argtypes = [P, dp]
+        lib.olbm_get_fpost.argtypes = [P, dp]
+        lib.olbm_get_minv.argtypes = [P, dp]
+        lib.olbm_steps.restype = ctypes.c_long
+        lib.olbm_steps.argtypes = [P]
+        lib.olbm_destroy.argtypes = [P]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class OracleLBM:
+    """One case on the CPU in FP64.
+
+    `par` is an `oracle.params.Parameters`; per-link r and l come from it
+    unless `link_r` / `link_l` are given.  `diffuse_mode` 0 evaluates the
+    Maxwell part of Eq. EqNewBDSC at the fluid velocity of x_f (the reading
+    under which the analysis of Sec. 3.B holds), 1 at the wall velocity u_b
+    (the equation as printed).
+    """
+
+    def __init__(self, case, par, link_r=None, link_l=None, diffuse_mode=0):
+        lib = _load()
+        self.case = case
+        self.par = par
+        g = np.ascontiguousarray(case.link_q, np.float64)
+        r, l = par.per_link(g)
+        if link_l is not None:
+            l = np.asarray(link_l, np.float64) * np.ones_like(g)
+        if link_r is not None:
+            r = np.asarray(link_r, np.float64) * np.ones_like(g)
+        self.link_r = np.ascontiguousarray(r, np.float64)
+        self.link_l = np.ascontiguousarray(l, np.float64)
+        self._keep = [np.ascontiguousarray(case.solid, np.uint8), par.relaxation_times(),
+                      np.ascontiguousarray(case.link_x, np.int32),
+                      np.ascontiguousarray(case.link_y, np.int32),
+                      np.ascontiguousarray(case.link_dir, np.int32), self.link_r, self.link_l, g,
+                      np.ascontiguousarray(case.link_ubx, np.float64),
+                      np.ascontiguousarray(case.link_uby, np.float64)]
+        k = self._keep
+        ip = ctypes.POINTER(ctypes.c_int32)
+        self._h = lib.olbm_create(
+            case.nx, case.ny, int(case.periodic_x), int(case.periodic_y),
+            k[0].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), case.ax, case.ay, _dp(k[1]),
+            case.n_links, k[2].ctypes.data_as(ip), k[3].ctypes.data_as(ip),
+            k[4].ctypes.data_as(ip), _dp(k[5]), _dp(k[6]), _dp(k[7]), _dp(k[8]), _dp(k[9]),
+            int(diffuse_mode))
+        if not self._h:
+            raise ValueError("oracle rejected the case (bad link set or parameters)")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _load().olbm_destroy(h)
+            self._h = None
+
+    def step(self, n: int = 1):
+        _load().olbm_step(self._h, int(n))
+
+    @property
+    def steps(self) -> int:
+        return int(_load().olbm_steps(self._h))
+
+    def fields(self):
+        n = self.case.nx * self.case.ny
+        rho, ux, uy = np.empty(n), np.empty(n), np.empty(n)
+        _load().olbm_fields(self._h, _dp(rho), _dp(ux), _dp(uy))
+        s = (self.case.ny, self.case.nx)
+        return rho.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def residual(self):
+        res = ctypes.c_double()
+        mass = ctypes.c_double()
+        _load().olbm_residual(self._h, ctypes.byref(res), ctypes.byref(mass))
+        return res.value, mass.value
+
+    def get_f(self) -> np.ndarray:
+        f = np.empty((9, self.case.ny, self.case.nx))
+        _load().olbm_get_f(self._h, _dp(f))
+        return f
+
+    def get_fpost(self) -> np.ndarray:
+        f = np.empty((9, self.case.ny, self.case.nx))
+        _load().olbm_get_fpost(self._h, _dp(f))
+        return f
+
+    def set_f(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, np.float64).reshape(9, self.case.ny, self.case.nx)
+        _load().olbm_set_f(self._h, _dp(f))
+
+    def minv(self) -> np.ndarray:
+        m = np.empty((9, 9))
+        _load().olbm_get_minv(self._h, _dp(m))
+        return m
+
+    def run_to(self, tol: float, max_steps: int, every: int = 100):
+        """Step in chunks of `every` until residual < tol; returns steps done."""
+        done = 0
+        while done < max_steps:
+            self.step(every)
+            done += every
+            res, _ = self.residual()
+            if res < tol:
+                break
+        return done

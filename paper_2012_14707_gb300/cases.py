@@ -1,0 +1,336 @@
+"""Seeded synthetic inputs for the slip-wall D2Q9 solver.
+
+This module builds geometry only: solid masks, the boundary links
+(fluid node, unknown incoming direction, distance ratio gamma, wall velocity
+at the wall point) and the scalar case data (Kn, characteristic length H,
+body acceleration).  It holds none of the method's arithmetic: no relaxation
+times, no slip coefficients, no collision or boundary formulas.  Both the
+FP64 oracle and the CUDA library consume exactly these arrays, so the two
+sides see identical distance ratios.
+
+Conventions (Sec. 2, Eq. 3 and Fig. 1 of the paper):
+  * D2Q9 velocities c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+    (-1,-1),(1,-1).
+  * Node (x, y) sits at the point (x, y); the mask is row-major, index
+    y*nx + x, 1 = solid.
+  * A link (x, y, i, q) exists when (x, y) is fluid and the node x_r = x - c_i
+    is solid: f_i at (x, y) is unknown after streaming.  q is the paper's
+    gamma = |x_b - x_f| / |x_r - x_f|, in (0, 1], with x_b the wall point on
+    the segment x_f -> x_r.
+  * Non-periodic axes always have solid first and last rows/columns.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.int64)
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.int64)
+
+
+@dataclasses.dataclass
+class Case:
+    """One solver input.  Arrays are host numpy arrays."""
+
+    name: str
+    nx: int
+    ny: int
+    periodic_x: bool
+    periodic_y: bool
+    solid: np.ndarray  # uint8 [ny, nx]
+    link_x: np.ndarray  # int32 [n_links]
+    link_y: np.ndarray  # int32
+    link_dir: np.ndarray  # int32, 1..8
+    link_q: np.ndarray  # float64, gamma in (0, 1]
+    link_ubx: np.ndarray  # float64, wall velocity at x_b
+    link_uby: np.ndarray  # float64
+    Kn: float
+    H: float  # characteristic length in lattice units (Kn = lambda / H)
+    ax: float = 0.0
+    ay: float = 0.0
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_links(self) -> int:
+        return int(self.link_x.shape[0])
+
+    @property
+    def n_fluid(self) -> int:
+        return int((self.solid == 0).sum())
+
+    def links_sorted(self) -> "Case":
+        """Same case with links ordered by (y, x, dir)."""
+        order = np.lexsort((self.link_dir, self.link_x, self.link_y))
+        return dataclasses.replace(
+            self,
+            link_x=self.link_x[order], link_y=self.link_y[order],
+            link_dir=self.link_dir[order], link_q=self.link_q[order],
+            link_ubx=self.link_ubx[order], link_uby=self.link_uby[order])
+
+
+# --------------------------------------------------------------------------
+# generic helpers
+# --------------------------------------------------------------------------
+
+def _wall_candidates(solid: np.ndarray, periodic_x: bool, periodic_y: bool):
+    """All (x, y, i) with (x, y) fluid and (x, y) - c_i solid.
+
+    Out-of-domain neighbours on a non-periodic axis count as solid; the
+    generators below never put fluid on such an edge, so that case does not
+    arise for the cases built here.
+    """
+    ny, nx = solid.shape
+    ys, xs = np.nonzero(solid == 0)
+    out_x, out_y, out_i, out_rx, out_ry = [], [], [], [], []
+    for i in range(1, 9):
+        rx = xs - CX[i]
+        ry = ys - CY[i]
+        if periodic_x:
+            rx = rx % nx
+        if periodic_y:
+            ry = ry % ny
+        inside = (rx >= 0) & (rx < nx) & (ry >= 0) & (ry < ny)
+        hit = np.ones_like(inside)
+        hit[inside] = solid[ry[inside], rx[inside]] != 0
+        out_x.append(xs[hit]); out_y.append(ys[hit])
+        out_i.append(np.full(int(hit.sum()), i, dtype=np.int64))
+        out_rx.append(rx[hit]); out_ry.append(ry[hit])
+    return (np.concatenate(out_x), np.concatenate(out_y), np.concatenate(out_i),
+            np.concatenate(out_rx), np.concatenate(out_ry))
+
+
+def _segment_circle_t(px, py, dx, dy, cx, cy, R, inner):
+    """Parameter t in (0, 1] where p + t*d first meets the circle |. - c| = R.
+
+    `inner=True`: p is outside the circle and p + d inside or on it (the
+    smaller root).  `inner=False`: p inside, p + d outside or on it (the
+    larger root).  Plain quadratic formula in FP64.
+    """
+    ox = px - cx
+    oy = py - cy
+    a = dx * dx + dy * dy
+    b = 2.0 * (ox * dx + oy * dy)
+    c = ox * ox + oy * oy - R * R
+    disc = np.maximum(b * b - 4.0 * a * c, 0.0)
+    sq = np.sqrt(disc)
+    t = np.where(inner, (-b - sq) / (2.0 * a), (-b + sq) / (2.0 * a))
+    return np.clip(t, np.finfo(np.float64).tiny, 1.0)
+
+
+def _make_case(name, solid, periodic_x, periodic_y, lx, ly, li, q, ubx, uby,
+               Kn, H, ax=0.0, ay=0.0, meta=None) -> Case:
+    ny, nx = solid.shape
+    return Case(
+        name=name, nx=nx, ny=ny, periodic_x=periodic_x, periodic_y=periodic_y,
+        solid=np.ascontiguousarray(solid, dtype=np.uint8),
+        link_x=np.asarray(lx, np.int32), link_y=np.asarray(ly, np.int32),
+        link_dir=np.asarray(li, np.int32), link_q=np.asarray(q, np.float64),
+        link_ubx=np.asarray(ubx, np.float64), link_uby=np.asarray(uby, np.float64),
+        Kn=float(Kn), H=float(H), ax=float(ax), ay=float(ay),
+        meta=dict(meta or {})).links_sorted()
+
+
+# --------------------------------------------------------------------------
+# flat channel, periodic in x (Sec. 4.A.1, Fig. 3)
+# --------------------------------------------------------------------------
+
+def channel(nx: int, m: int, q_bottom: float, q_top: float, Kn: float,
+            ax: float = 1e-6, H: float | None = None,
+            u_bottom: float = 0.0, u_top: float = 0.0,
+            name: str = "slip_channel") -> Case:
+    """Channel with m fluid rows between two flat walls.
+
+    Rows 0 and m+1 are solid.  The lower wall lies q_bottom below the first
+    fluid row, the upper wall q_top above the last, so every link of a wall
+    row has gamma = q of that wall (a diagonal link crosses the wall at the
+    same fraction of its length as a vertical one).  The default H is the
+    wall-to-wall distance m - 1 + q_bottom + q_top; y of fluid row j
+    (1-based) measured from the lower wall is j - 1 + q_bottom.
+    """
+    ny = m + 2
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    solid[ny - 1, :] = 1
+    lx, ly, li, rx, ry = _wall_candidates(solid, True, False)
+    bottom = ry == 0
+    q = np.where(bottom, q_bottom, q_top)
+    ubx = np.where(bottom, u_bottom, u_top)
+    uby = np.zeros_like(ubx)
+    if H is None:
+        H = m - 1 + q_bottom + q_top
+    return _make_case(name, solid, True, False, lx, ly, li, q, ubx, uby, Kn, H,
+                      ax=ax, meta=dict(m=m, q_bottom=q_bottom, q_top=q_top))
+
+
+# --------------------------------------------------------------------------
+# cylindrical Couette flow (Sec. 4.B, Fig. 9)
+# --------------------------------------------------------------------------
+
+def annulus(n: int, R1: float, R2: float, Kn: float, omega1: float,
+            omega2: float = 0.0, center: float | None = None,
+            name: str = "couette") -> Case:
+    """n x n lattice, concentric circles about `center` (default (n-1)/2).
+
+    A node is solid when its distance r from the centre has r <= R1 or
+    r >= R2.  Each link's gamma comes from the exact segment-circle
+    intersection; the wall velocity at x_b is omega x (x_b - centre) of the
+    wall that was hit.  H = R2 - R1 (Kn = lambda / (R2 - R1)).
+    """
+    c = (n - 1) / 2.0 if center is None else float(center)
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    rr = np.hypot(xx - c, yy - c)
+    solid = ((rr <= R1) | (rr >= R2)).astype(np.uint8)
+    if R2 > c:
+        raise ValueError("outer circle must leave a solid edge row")
+    lx, ly, li, rx, ry = _wall_candidates(solid, False, False)
+    r_ref = np.hypot(rx - c, ry - c)
+    inner = r_ref <= R1
+    px = lx.astype(np.float64)
+    py = ly.astype(np.float64)
+    dx = -CX[li].astype(np.float64)
+    dy = -CY[li].astype(np.float64)
+    t = _segment_circle_t(px, py, dx, dy, c, c, np.where(inner, R1, R2), inner)
+    bx = px + t * dx - c
+    by = py + t * dy - c
+    om = np.where(inner, omega1, omega2)
+    ubx = -om * by
+    uby = om * bx
+    return _make_case(name, solid, False, False, lx, ly, li, t, ubx, uby, Kn,
+                      R2 - R1, meta=dict(R1=R1, R2=R2, center=c, omega1=omega1,
+                                         omega2=omega2))
+
+
+# --------------------------------------------------------------------------
+# x-periodic channel packed with random cylinders
+# --------------------------------------------------------------------------
+
+def cylinder_array(nx: int, ny: int, seed: int, porosity: float = 0.7,
+                   r_min: float = 8.0, r_max: float = 32.0,
+                   clearance: float = 2.0, Kn: float = 0.02, ax: float = 1e-5,
+                   max_trials: int | None = None,
+                   name: str = "cylinder_array") -> Case:
+    """Random sequential addition of non-overlapping cylinders.
+
+    Rows 0 and ny-1 are solid, with flat walls halfway (gamma = 1/2) between
+    them and the adjacent fluid rows.  Radii are uniform in [r_min, r_max];
+    every cylinder keeps `clearance` nodes from the walls, from the x ends
+    (no wrap across the periodic seam) and from every other cylinder.
+    Cylinders are added until the node porosity drops to `porosity` or
+    `max_trials` candidates were rejected in a row.  H is the mean cylinder
+    diameter actually placed.
+    """
+    rng = np.random.default_rng(seed)
+    cell = 2.0 * r_max + clearance
+    grid: dict[tuple[int, int], list[int]] = {}
+    cxs: list[float] = []
+    cys: list[float] = []
+    rs: list[float] = []
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    solid[ny - 1, :] = 1
+    label = np.full((ny, nx), -1, np.int32)
+    n_total = nx * ny
+    n_solid = int(solid.sum())
+    max_trials = max_trials or 20000
+    misses = 0
+    batch = 4096
+    while n_solid / n_total < 1.0 - porosity and misses < max_trials:
+        rad = rng.uniform(r_min, r_max, batch)
+        ccx = rng.uniform(0.0, nx - 1.0, batch)
+        ccy = rng.uniform(0.0, ny - 1.0, batch)
+        for k in range(batch):
+            R, X, Y = float(rad[k]), float(ccx[k]), float(ccy[k])
+            if (X - R < clearance or X + R > nx - 1 - clearance
+                    or Y - R < 1.0 + clearance or Y + R > ny - 2 - clearance):
+                misses += 1
+                continue
+            ix, iy = int(X / cell), int(Y / cell)
+            ok = True
+            for jx in (ix - 1, ix, ix + 1):
+                for jy in (iy - 1, iy, iy + 1):
+                    for idx in grid.get((jx, jy), ()):
+                        if math.hypot(X - cxs[idx], Y - cys[idx]) < R + rs[idx] + clearance:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                misses += 1
+                if misses >= max_trials:
+                    break
+                continue
+            misses = 0
+            idx = len(rs)
+            cxs.append(X); cys.append(Y); rs.append(R)
+            grid.setdefault((ix, iy), []).append(idx)
+            x0, x1 = int(math.ceil(X - R)), int(math.floor(X + R))
+            y0, y1 = int(math.ceil(Y - R)), int(math.floor(Y + R))
+            sy, sx = np.mgrid[y0:y1 + 1, x0:x1 + 1]
+            inside = (sx - X) ** 2 + (sy - Y) ** 2 <= R * R
+            sub = solid[y0:y1 + 1, x0:x1 + 1]
+            n_solid += int((inside & (sub == 0)).sum())
+            sub[inside] = 1
+            label[y0:y1 + 1, x0:x1 + 1][inside] = idx
+            if n_solid / n_total >= 1.0 - porosity:
+                break
+    cxa = np.asarray(cxs)
+    cya = np.asarray(cys)
+    ra = np.asarray(rs)
+    lx, ly, li, rx, ry = _wall_candidates(solid, True, False)
+    lab = label[ry, rx]
+    wall = lab < 0
+    q = np.full(lx.shape, 0.5)
+    if (~wall).any():
+        sel = ~wall
+        k = lab[sel]
+        px = lx[sel].astype(np.float64)
+        py = ly[sel].astype(np.float64)
+        dx = -CX[li[sel]].astype(np.float64)
+        dy = -CY[li[sel]].astype(np.float64)
+        q[sel] = _segment_circle_t(px, py, dx, dy, cxa[k], cya[k], ra[k],
+                                   np.ones(px.shape, bool))
+    zeros = np.zeros(lx.shape)
+    H = float(2.0 * ra.mean()) if len(ra) else float(ny - 2)
+    return _make_case(name, solid, True, False, lx, ly, li, q, zeros, zeros, Kn,
+                      H, ax=ax, meta=dict(seed=seed, n_cylinders=len(rs),
+                                          porosity=1.0 - n_solid / n_total,
+                                          centers_x=cxa, centers_y=cya, radii=ra))
+
+
+def periodic_box(nx: int, ny: int, name: str = "periodic_box",
+                 Kn: float = 0.05, H: float = 10.0, ax: float = 0.0,
+                 ay: float = 0.0) -> Case:
+    """Fully periodic box with no solid node and no link."""
+    solid = np.zeros((ny, nx), np.uint8)
+    e = np.zeros(0)
+    return _make_case(name, solid, True, True, e, e, e, e, e, e, Kn, H,
+                      ax=ax, ay=ay)
+
+
+# --------------------------------------------------------------------------
+# the named workloads
+# --------------------------------------------------------------------------
+
+def config_poiseuille() -> Case:
+    """4 x 32 fluid nodes, x-periodic, gamma 0.5 below and 0.3 above,
+    Kn = 0.05, a = 1e-6 (FP64 closed-form workload)."""
+    return channel(4, 32, 0.5, 0.3, Kn=0.05, ax=1e-6, name="poiseuille_4x32")
+
+
+def config_couette(Kn: float = 0.05, n: int = 256, R1: float = 60.0,
+                   R2: float = 120.0, mach: float = 0.05) -> Case:
+    """256^2 annulus, R1 = 60, R2 = 120, inner wall at Ma ~ 0.05, outer at rest."""
+    omega1 = mach * math.sqrt(1.0 / 3.0) / R1
+    return annulus(n, R1, R2, Kn, omega1, 0.0, name=f"couette_{n}_Kn{Kn:g}")
+
+
+def config_throughput(seed: int = 0, nx: int = 8192, ny: int = 4096,
+                      ax: float = 1e-5) -> Case:
+    """8192 x 4096 x-periodic channel of random cylinders (radius 8-32,
+    porosity 0.7), Kn = 0.02."""
+    return cylinder_array(nx, ny, seed, porosity=0.7, Kn=0.02, ax=ax,
+                          name=f"cylinders_{nx}x{ny}_s{seed}")

@@ -1,0 +1,320 @@
+"""Throughput benchmark of the slip-wall D2Q9 MRT solver.
+
+Workload: the single-domain throughput case -- an 8192 x 4096 x-periodic
+channel packed with random cylinders (radius 8-32 nodes, porosity 0.7,
+seeded), Kn = 0.02, force-driven, FP32 deviation storage.  One benchmark
+step = 100 lattice time steps (the fused collide-stream-boundary kernel)
+followed by the FP64 residual/mass reduction and its read-back, i.e. one
+pass of the whole hot path at the default residual interval; the default
+--steps 100 times 10,000 lattice steps.
+
+Prints one JSON line: MLUPS over fluid nodes (whole job), the roofline of
+the step kernel against measured HBM bandwidth, an end-to-end number through
+the C ABI with host buffers, and the FP64 CPU oracle timed on a bounded
+sample of the same workload.  With --impl reference the oracle itself is the
+timed arm (on the host cores).
+
+Multi-GPU (torchrun): every rank runs an independent replica of the case
+(seed = rank); the path has no exchange step, so there is no collective in
+the data path ("replicas only", weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FLUID_BYTES = {"fp32": 72, "fp64": 144}  # algorithmic bytes per fluid-node update
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if key in d and isinstance(d[key], (int, float)):
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_sample(precision: str, n_steps: int = 3, rows: int = 512):
+    """The FP64 oracle (single thread, as it stands) on a bounded sample of
+    the workload: `n_steps` lattice steps of an 8192 x `rows` channel built
+    with the same cylinder recipe.  Returns MLUPS over fluid nodes."""
+    import oracle
+    from oracle import params as P
+    from paper_2012_14707_gb300 import cases
+    case = cases.cylinder_array(8192, rows, 0, porosity=0.7, Kn=0.02, ax=1e-5,
+                                name=f"cylinders_8192x{rows}_s0")
+    o = oracle.OracleLBM(case, P.Parameters(case.Kn, case.H))
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(n_steps)
+    dt = time.perf_counter() - t0
+    return case.n_fluid * n_steps / dt / 1e6, case, dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    rows = 512
+    import oracle
+    from oracle import params as P
+    from paper_2012_14707_gb300 import cases
+    case = cases.cylinder_array(8192, rows, 0, porosity=0.7, Kn=0.02, ax=1e-5,
+                                name=f"cylinders_8192x{rows}_s0")
+    o = oracle.OracleLBM(case, P.Parameters(case.Kn, case.H))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = case.n_fluid * args.steps / dt / 1e6
+    sample = (f"each step: one FP64 lattice step of an 8192x{rows} channel with the same "
+              f"cylinder recipe ({case.n_fluid} fluid nodes), single thread")
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "cylinders_8192x4096_phi0.7_Kn0.02 (oracle on an 8192x512 band)",
+                   "model": "D2Q9 MRT + curved slip boundary (FP64 CPU oracle)",
+                   "l2": "inputs larger than L2 not applicable (CPU)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2012_14707_gb300 import build as lbm_build
+    from paper_2012_14707_gb300 import cases, lbm
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lbm_build.build()
+    lbm.load()
+
+    case = cases.config_throughput(seed=rank)
+    stream = torch.cuda.current_stream(dev)
+    solver = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
+                        residual_every=args.lbm_steps)
+    info = solver.info()
+    n_fluid = info.n_fluid
+    per = args.lbm_steps
+
+    def bench_step():
+        solver.step(per)
+        return solver.residual()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    last = None
+    for s in range(args.steps):
+        k_start[s].record(stream)
+        solver.step(per)
+        k_end[s].record(stream)
+        last = solver.residual()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in zip(k_start, k_end))
+    if world > 1:
+        t = torch.tensor([elapsed_ms, kernel_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms, kernel_ms = float(t[0]), float(t[1])
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    updates = world * n_fluid * per * args.steps
+    mlups = updates / (elapsed_ms / 1e3) / 1e6
+    launch_ms = kernel_ms / (args.steps * per)
+    alg_bytes = FLUID_BYTES[args.precision] * n_fluid
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    peak, peak_src = _peak_hbm()
+    solver.close()
+
+    # End to end through the C ABI with host buffers: create from host
+    # arrays (mask + links H2D), the same steps with the residual read back,
+    # and the final fields copied to host memory.
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
+                    residual_every=per)
+    for _ in range(args.steps):
+        s2.step(per)
+        s2.residual()
+    rho, ux, uy = s2.fields()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    h2d = case.solid.nbytes + case.n_links * (3 * 4 + 3 * 8)
+    d2h = 3 * 8 * case.nx * case.ny + args.steps * 2 * 8
+    e2e_mlups = world * n_fluid * per * args.steps / e2e_s / 1e6
+
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as fh:
+                pj = json.load(fh)
+            if pj.get("precision") == args.precision and pj.get("kernel_rev") == KERNEL_REV:
+                traffic = pj.get("bytes_per_launch_full_size")
+        except (OSError, ValueError):
+            traffic = None
+
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"cylinders_{case.nx}x{case.ny}_phi0.7_Kn0.02",
+                   "nx": case.nx, "ny": case.ny, "n_fluid": n_fluid, "n_links": case.n_links,
+                   "precision": args.precision, "lattice_steps_per_step": per,
+                   "l2": "inputs larger than L2 (2 x 1.2 GB lattices)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "step_kernel", "bytes_per_fluid_node": FLUID_BYTES[args.precision],
+                     "launch_ms": launch_ms, "peak_source": peak_src},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "seconds": e2e_s},
+        "gpu_launches": args.steps * (per + 2),
+        "clocks": clocks,
+        "residual_last": last[0] if last else None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, bcase, dt = cpu_baseline_sample(args.precision)
+        line["cpu_baseline"] = {
+            "value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"3 FP64 lattice steps of an 8192x512 channel with the same cylinder "
+                      f"recipe ({bcase.n_fluid} fluid nodes), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
+KERNEL_REV = 1
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--lbm-steps", type=int, default=100,
+                    help="lattice steps per benchmark step (the residual interval)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * lbm.h -- C ABI of the GB300 slip-wall D2Q9 MRT lattice Boltzmann library
+ * (liblbm.so).
+ *
+ * The library advances a 2-D lattice with the multiple-relaxation-time
+ * lattice Boltzmann equation with Guo forcing (Sec. 2 of Wang et al.,
+ * "Curved boundary conditions of the lattice Boltzmann method for simulating
+ * microgaseous flows in the slip regime", Eqs. LBENS, LBEequi, LBEforce,
+ * MomentPost) and applies the paper's local curved slip boundary scheme on
+ * every boundary link (Sec. 3.A, Eq. EqNewBDSC), with the free parameter,
+ * combination parameter and uniform tau_q of Sec. 3.B (Eqs. Eqexlva,
+ * SliCoeffrtsr, NSliCoertstq, the clamp of l below -0.4).
+ *
+ * Conventions shared by every entry point:
+ *   * D2Q9 velocities c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),
+ *     (-1,1),(-1,-1),(1,-1) (Eq. 3); lattice units, delta_x = delta_t = 1.
+ *   * Node (x, y) has row-major index y*nx + x.  Host field arrays are
+ *     nx*ny doubles in that order; population arrays are 9*nx*ny doubles,
+ *     index (i*ny + y)*nx + x.
+ *   * A boundary link (x, y, i, q, ubx, uby) names a fluid node x_f = (x, y)
+ *     whose neighbour x_f - c_i is solid, so f_i(x_f) is unknown after
+ *     streaming; q is the distance ratio gamma = |x_b - x_f| / |x_r - x_f| in
+ *     (0, 1] of Fig. 1 and (ubx, uby) the wall velocity at x_b.
+ *   * Every call returns an lbm_status code; no call aborts or exits.  On an
+ *     error the handle's message (lbm_last_error) says what was wrong.
+ *   * All device work runs on the stream given at creation (params.stream,
+ *     a cudaStream_t; NULL = the legacy default stream).  Calls that return
+ *     host data synchronise that stream; the others are asynchronous.
+ *   * The handle owns its device memory; every input array is copied at
+ *     creation, so the caller keeps ownership of its buffers.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* bad argument, link set or parameter (tau_q <= 1/2, ...) */
+  LBM_ECUDA = 2,     /* a CUDA runtime call failed */
+  LBM_EUNSTABLE = 3, /* a non-finite density or velocity was found */
+  LBM_ETIMEOUT = 4,  /* a device-side wait hit its iteration limit */
+  LBM_ENOMEM = 5     /* device or host allocation failed */
+} lbm_status;
+
+typedef enum {
+  LBM_FP64 = 0, /* populations stored and collided in FP64 */
+  LBM_FP32 = 1  /* populations stored as FP32 deviations f_i - w_i, FP32 arithmetic */
+} lbm_precision;
+
+typedef enum {
+  LBM_L_PAPER = 0,        /* l from Eq. Eqexlva, set to 0 where it is below l_clamp */
+  LBM_L_ZERO = 1,         /* l = 0 (the halfway DBB scheme when gamma = 1/2) */
+  LBM_L_GAMMA = 2,        /* l = gamma      (alternatives compared in Sec. 4) */
+  LBM_L_2GAMMA = 3,       /* l = 2 gamma */
+  LBM_L_GAMMA2 = 4,       /* l = gamma^2 */
+  LBM_L_GAMMA2_GAMMA = 5, /* l = gamma^2 + gamma */
+  LBM_L_FIXED = 6         /* l = params.l_value for every link */
+} lbm_l_mode;
+
+typedef struct lbm_handle lbm_handle_t;
+
+typedef struct {
+  int32_t nx, ny;                 /* lattice size, both >= 1 */
+  int32_t periodic_x, periodic_y; /* 1 = periodic; a non-periodic axis needs solid edge rows */
+  double H;                       /* characteristic length in lattice units (Eq. tKnrela) */
+  double ax, ay;                  /* body acceleration a, lattice units (Eq. LBEforce) */
+} lbm_domain_t;
+
+typedef struct {
+  double sigma;   /* wall accommodation coefficient (Sec. 4), default 1 */
+  double L1, L2;  /* slip coefficients of Eq. PhyscSlip; NaN = from sigma (Sec. 4) */
+  double E;       /* constant of Eq. Eqexlva; NaN = min(-0.65, E_max - 0.1), E_max of Eq. EqECond */
+  double l_clamp; /* l := 0 where Eq. Eqexlva gives l < l_clamp (Sec. 3.B), default -0.4 */
+  double tau_rho, tau_j, tau_e, tau_eps; /* fixed relaxation times (Sec. 4): 1, 1, 1.1, 1.2 */
+  double tau_s;   /* NaN = 1/2 + sqrt(6/pi) Kn H (Eq. tKnrela) */
+  double tau_q;   /* NaN = Eq. NSliCoertstq */
+  double r_value; /* NaN = Eq. SliCoeffrtsr with the l actually used; else r for every link */
+  double l_value; /* used by LBM_L_FIXED */
+  int32_t l_mode;       /* lbm_l_mode, default LBM_L_PAPER */
+  int32_t diffuse_mode; /* Maxwell part of Eq. EqNewBDSC at 0 = the fluid velocity of x_f
+                           (the reading under which Sec. 3.B holds, default), 1 = the wall
+                           velocity u_b (the equation as printed) */
+  int32_t precision;    /* lbm_precision, default LBM_FP32 */
+  int32_t residual_every; /* steps between residual checks in lbm_run_to, default 100 */
+  void *stream;         /* cudaStream_t for all device work; NULL = legacy default stream */
+} lbm_params_t;
+
+typedef struct {
+  int64_t n_nodes, n_fluid, n_links;
+  int64_t steps;          /* time steps taken since creation (or the last lbm_set_f) */
+  double tau_s, tau_q, E, E_max, L1, L2;
+  int64_t n_clamped;      /* links whose l was set to 0 by the clamp */
+  int64_t device_bytes;   /* device memory held by the handle */
+  int32_t precision, pitch; /* storage precision; row pitch in elements */
+} lbm_info_t;
+
+/* Fill *p with the defaults listed above (no side effects). */
+void lbm_params_default(lbm_params_t *p);
+
+/*
+ * Create a solver for one case.  solid: nx*ny bytes, nonzero = solid.
+ * Links: n_links entries in six parallel arrays (any order; duplicates,
+ * links whose node is solid or whose neighbour x_f - c_i is fluid, gamma
+ * outside (0, 1], and fluid nodes with an unknown direction that no link
+ * covers are LBM_EINVAL).  Kn is the Knudsen number of Eq. tKnrela.  The
+ * state starts at rest, f_i = w_i (rho = 1, u = 0).  On success *out holds
+ * the handle; on failure *out is NULL and the returned code says why
+ * (lbm_last_error(NULL) gives the message of the last failed creation on
+ * this thread).
+ */
+int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
+               const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
+               const double *link_q, const double *link_ubx, const double *link_uby,
+               double Kn, const lbm_params_t *params, lbm_handle_t **out);
+
+/* Advance n >= 0 time steps (collision, streaming, boundary links: Sec. 2,
+ * Eq. EqNewBDSC).  Asynchronous on the handle's stream. */
+int lbm_step(lbm_handle_t *h, int64_t n);
+
+/*
+ * Density and velocity (Eq. FluidMacr: rho = sum f, rho u = sum c f + rho a/2)
+ * of every node, nx*ny doubles each; solid nodes get 0.  on_device = 0: host
+ * pointers (the call synchronises); 1: device pointers on the handle's
+ * device (asynchronous).  Any of the three pointers may be NULL.
+ */
+int lbm_fields(lbm_handle_t *h, double *rho, double *ux, double *uy, int on_device);
+
+/*
+ * Convergence and conservation monitor: residual = ||u^n - u^(n-1)||_2 /
+ * ||u^n||_2 over fluid nodes (0 before the first step) and mass =
+ * sum over fluid nodes of sum_i f_i, both accumulated in FP64.  Synchronises.
+ * Returns LBM_EUNSTABLE (with the values still written) when a fluid node
+ * has a non-finite density or velocity.
+ */
+int lbm_residual(lbm_handle_t *h, double *residual, double *mass);
+
+/* Step in chunks of params.residual_every until the residual is below tol
+ * or max_steps were taken; *steps_done and *residual report the outcome. */
+int lbm_run_to(lbm_handle_t *h, double tol, int64_t max_steps, int64_t *steps_done,
+               double *residual);
+
+/* All populations f_i (not deviations) as 9*nx*ny host doubles (get: the
+ * current state; set: replaces the state and the previous-step state, so
+ * the next residual is 0 until a step is taken).  Synchronise. */
+int lbm_get_f(lbm_handle_t *h, double *f);
+int lbm_set_f(lbm_handle_t *h, const double *f);
+
+/* Per-link free parameter l and combination parameter r as used, in the
+ * order the links were given at creation (n_links doubles each, host). */
+int lbm_link_params(const lbm_handle_t *h, double *r, double *l);
+
+int lbm_get_info(const lbm_handle_t *h, lbm_info_t *info);
+
+/*
+ * Host-only FP64 precompute of Sec. 3.B without creating a solver (no CUDA
+ * call): tau_s (Eq. tKnrela), L1, L2, E, E_max, tau_q (Eq. NSliCoertstq)
+ * into *info (the other info fields are zero), and for n links with
+ * directions dir[] (1..8), distance ratios q[] and wall velocities
+ * (ubx[], uby[]) the free parameter l[] (Eq. Eqexlva with the clamp) and
+ * the combination parameter r[] (Eq. SliCoeffrtsr).  r and l may be NULL.
+ * LBM_EINVAL (message via lbm_last_error(NULL)) for the same parameter
+ * errors lbm_create reports.
+ */
+int lbm_precompute(double Kn, double H, const lbm_params_t *params, size_t n,
+                   const int32_t *dir, const double *q, const double *ubx, const double *uby,
+                   double *r, double *l, lbm_info_t *info);
+
+/* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
+void lbm_destroy(lbm_handle_t *h);
+
+/* Message of the handle's last error ("" if none); with h = NULL, the last
+ * failed lbm_create on the calling thread. */
+const char *lbm_last_error(const lbm_handle_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

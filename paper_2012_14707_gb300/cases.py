@@ -334,3 +334,12 @@ def config_throughput(seed: int = 0, nx: int = 8192, ny: int = 4096,
     porosity 0.7), Kn = 0.02."""
     return cylinder_array(nx, ny, seed, porosity=0.7, Kn=0.02, ax=ax,
                           name=f"cylinders_{nx}x{ny}_s{seed}")
+
+
+def random_populations(nx: int, ny: int, seed: int, amp: float = 1e-3) -> np.ndarray:
+    """Seeded population field f[9][ny][nx] = w_i (1 + amp * N(0, 1)): a
+    perturbed rest state to start parity runs from (an input, not a
+    solution of anything)."""
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    rng = np.random.default_rng(seed)
+    return w[:, None, None] * (1.0 + amp * rng.standard_normal((9, ny, nx)))

@@ -1,0 +1,550 @@
+// C ABI of liblbm.so (declared in include/lbm.h): validation, the host-side
+// layout build, device memory, and the step / residual / field calls.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+struct lbm_handle {
+  int precision = LBM_FP32;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int32_t nx = 0, ny = 0, pitch = 0, px = 0, py = 0;
+  int64_t plane = 0;
+  double ax = 0.0, ay = 0.0;
+  lbm::CaseParams cp{};
+  lbm_params_t params{};
+  void *f[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint8_t *flags = nullptr;
+  int32_t *lbase = nullptr;
+  void *links = nullptr;
+  double *partials = nullptr;
+  double *result = nullptr;
+  double *h_result = nullptr;  // pinned, 4 doubles
+  int64_t n_fluid = 0, n_links = 0, steps = 0, dev_bytes = 0;
+  std::vector<double> link_r, link_l;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+const int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+int fail(lbm_handle_t *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(lbm_handle_t *h, cudaError_t e, const char *what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CK(h, call)                                 \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+size_t elem_size(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+
+void release(lbm_handle_t *h) {
+  if (!h) return;
+  cudaStream_t s = h->stream;
+  cudaStreamSynchronize(s);
+  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->flags), static_cast<void *>(h->lbase),
+                  h->links, static_cast<void *>(h->partials), static_cast<void *>(h->result)})
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
+  if (h->h_result) cudaFreeHost(h->h_result);
+  delete h;
+}
+
+template <typename C>
+lbm::StepConst<C> step_const(const lbm_handle_t *h) {
+  lbm::StepConst<C> k;
+  k.s_e = static_cast<C>(1.0 / h->cp.tau_e);
+  k.s_eps = static_cast<C>(1.0 / h->cp.tau_eps);
+  k.s_q = static_cast<C>(1.0 / h->cp.tau_q);
+  k.s_s = static_cast<C>(1.0 / h->cp.tau_s);
+  k.s_j = static_cast<C>(1.0 / h->cp.tau_j);
+  k.ax = static_cast<C>(h->ax);
+  k.ay = static_cast<C>(h->ay);
+  k.nx = h->nx;
+  k.ny = h->ny;
+  k.pitch = h->pitch;
+  k.periodic_x = h->px;
+  k.periodic_y = h->py;
+  k.plane = h->plane;
+  return k;
+}
+
+cudaError_t do_step(lbm_handle_t *h) {
+  const int src = h->cur, dst = 1 - h->cur;
+  cudaError_t e;
+  if (h->precision == LBM_FP64) {
+    e = lbm::launch_step<double, double>(
+        static_cast<const double *>(h->f[src]), static_cast<double *>(h->f[dst]), h->flags,
+        h->lbase, static_cast<const lbm::LinkCoef<double> *>(h->links), step_const<double>(h),
+        h->stream);
+  } else {
+    e = lbm::launch_step<float, float>(
+        static_cast<const float *>(h->f[src]), static_cast<float *>(h->f[dst]), h->flags,
+        h->lbase, static_cast<const lbm::LinkCoef<float> *>(h->links), step_const<float>(h),
+        h->stream);
+  }
+  if (e == cudaSuccess) {
+    h->cur = dst;
+    h->steps++;
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_params_default(lbm_params_t *p) {
+  if (!p) return;
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  std::memset(p, 0, sizeof(*p));
+  p->sigma = 1.0;
+  p->L1 = nan;
+  p->L2 = nan;
+  p->E = nan;
+  p->l_clamp = -0.4;
+  p->tau_rho = 1.0;
+  p->tau_j = 1.0;
+  p->tau_e = 1.1;
+  p->tau_eps = 1.2;
+  p->tau_s = nan;
+  p->tau_q = nan;
+  p->r_value = nan;
+  p->l_value = 0.0;
+  p->l_mode = LBM_L_PAPER;
+  p->diffuse_mode = 0;
+  p->precision = LBM_FP32;
+  p->residual_every = 100;
+  p->stream = nullptr;
+}
+
+int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
+               const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
+               const double *link_q, const double *link_ubx, const double *link_uby, double Kn,
+               const lbm_params_t *params, lbm_handle_t **out) {
+  g_create_error.clear();
+  if (out) *out = nullptr;
+  auto bad = [](int code, const std::string &m) {
+    g_create_error = m;
+    return code;
+  };
+  if (!dom || !solid || !params || !out) return bad(LBM_EINVAL, "null argument");
+  if (n_links && (!link_x || !link_y || !link_dir || !link_q || !link_ubx || !link_uby))
+    return bad(LBM_EINVAL, "null link array");
+  const lbm_params_t &p = *params;
+  if (dom->nx < 1 || dom->ny < 1) return bad(LBM_EINVAL, "nx and ny must be >= 1");
+  if (p.precision != LBM_FP64 && p.precision != LBM_FP32)
+    return bad(LBM_EINVAL, "precision must be LBM_FP64 or LBM_FP32");
+  if (p.diffuse_mode != 0 && p.diffuse_mode != 1) return bad(LBM_EINVAL, "diffuse_mode must be 0 or 1");
+  if (p.residual_every < 1) return bad(LBM_EINVAL, "residual_every must be >= 1");
+  if (!std::isfinite(dom->ax) || !std::isfinite(dom->ay)) return bad(LBM_EINVAL, "non-finite force");
+  const int32_t nx = dom->nx, ny = dom->ny;
+  if (static_cast<int64_t>(nx) * ny > (int64_t(1) << 31))
+    return bad(LBM_EINVAL, "lattice larger than 2^31 nodes");
+  if (n_links > static_cast<size_t>(std::numeric_limits<int32_t>::max()))
+    return bad(LBM_EINVAL, "too many links");
+  const int px = dom->periodic_x ? 1 : 0, py = dom->periodic_y ? 1 : 0;
+  // Non-periodic axes need solid edges so that no fluid node streams off the lattice.
+  if (!px)
+    for (int32_t y = 0; y < ny; y++)
+      if (!solid[(size_t)y * nx] || !solid[(size_t)y * nx + nx - 1])
+        return bad(LBM_EINVAL, "non-periodic x needs solid first and last columns");
+  if (!py)
+    for (int32_t x = 0; x < nx; x++)
+      if (!solid[x] || !solid[(size_t)(ny - 1) * nx + x])
+        return bad(LBM_EINVAL, "non-periodic y needs solid first and last rows");
+
+  lbm::CaseParams cp;
+  std::string msg = lbm::compute_case_params(Kn, dom->H, p, &cp);
+  if (!msg.empty()) return bad(LBM_EINVAL, msg);
+
+  const int32_t align = 32;
+  const int32_t pitch = (nx + align - 1) / align * align;
+  const int64_t plane = static_cast<int64_t>(pitch) * ny;
+  std::vector<uint8_t> flags(static_cast<size_t>(plane), lbm::kSolid);
+  int64_t n_fluid = 0;
+  for (int32_t y = 0; y < ny; y++)
+    for (int32_t x = 0; x < nx; x++)
+      if (!solid[(size_t)y * nx + x]) {
+        flags[(size_t)y * pitch + x] = 0;
+        n_fluid++;
+      }
+  auto wrapped = [&](int32_t x, int32_t y, int dx, int dy, int32_t *xo, int32_t *yo) {
+    int32_t a = x + dx, b = y + dy;
+    if (a < 0 || a >= nx) {
+      if (!px) return false;
+      a = (a + nx) % nx;
+    }
+    if (b < 0 || b >= ny) {
+      if (!py) return false;
+      b = (b + ny) % ny;
+    }
+    *xo = a;
+    *yo = b;
+    return true;
+  };
+  for (size_t k = 0; k < n_links; k++) {
+    const int32_t x = link_x[k], y = link_y[k], i = link_dir[k];
+    char buf[200];
+    if (x < 0 || x >= nx || y < 0 || y >= ny || i < 1 || i > 8) {
+      std::snprintf(buf, sizeof buf, "link %zu: node or direction out of range", k);
+      return bad(LBM_EINVAL, buf);
+    }
+    if (!(link_q[k] > 0.0 && link_q[k] <= 1.0) || !std::isfinite(link_ubx[k]) ||
+        !std::isfinite(link_uby[k])) {
+      std::snprintf(buf, sizeof buf, "link %zu: gamma must lie in (0, 1], wall velocity finite", k);
+      return bad(LBM_EINVAL, buf);
+    }
+    uint8_t &fl = flags[(size_t)y * pitch + x];
+    int32_t xr, yr;
+    if (solid[(size_t)y * nx + x] || !wrapped(x, y, -kCx[i], -kCy[i], &xr, &yr) ||
+        !solid[(size_t)yr * nx + xr]) {
+      std::snprintf(buf, sizeof buf, "link %zu: node must be fluid and x - c_i solid", k);
+      return bad(LBM_EINVAL, buf);
+    }
+    if (fl & (1u << (i - 1))) {
+      std::snprintf(buf, sizeof buf, "link %zu: duplicate (node, direction)", k);
+      return bad(LBM_EINVAL, buf);
+    }
+    fl |= static_cast<uint8_t>(1u << (i - 1));
+  }
+  // Every unknown direction of every fluid node needs its link.
+  for (int32_t y = 0; y < ny; y++)
+    for (int32_t x = 0; x < nx; x++) {
+      if (solid[(size_t)y * nx + x]) continue;
+      const uint8_t fl = flags[(size_t)y * pitch + x];
+      if (fl == lbm::kSolid) return bad(LBM_EINVAL, "fluid node enclosed on all eight sides");
+      for (int i = 1; i < 9; i++) {
+        int32_t xr, yr;
+        const bool unknown = !wrapped(x, y, -kCx[i], -kCy[i], &xr, &yr) || solid[(size_t)yr * nx + xr];
+        if (unknown != static_cast<bool>(fl & (1u << (i - 1)))) {
+          char buf[200];
+          std::snprintf(buf, sizeof buf, "node (%d, %d) direction %d: no link for an unknown population",
+                        x, y, i);
+          return bad(LBM_EINVAL, buf);
+        }
+      }
+    }
+
+  // Per-link parameters (input order), then the node-sorted device table.
+  lbm_handle_t *h = new (std::nothrow) lbm_handle_t();
+  if (!h) return bad(LBM_ENOMEM, "host allocation failed");
+  h->link_r.resize(n_links);
+  h->link_l.resize(n_links);
+  std::vector<double> coef(8 * n_links);
+  msg = lbm::compute_link_coefs(cp, p, n_links, link_dir, link_q, link_ubx, link_uby,
+                                h->link_r.data(), h->link_l.data(), coef.data(), &cp.n_clamped);
+  if (!msg.empty()) {
+    delete h;
+    return bad(LBM_EINVAL, msg);
+  }
+  std::vector<int64_t> order(n_links);
+  std::iota(order.begin(), order.end(), 0);
+  auto key = [&](int64_t k) {
+    return (static_cast<int64_t>(link_y[k]) * pitch + link_x[k]) * 16 + link_dir[k];
+  };
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+  std::vector<int32_t> lbase(static_cast<size_t>(plane), -1);
+  for (int64_t s = static_cast<int64_t>(n_links) - 1; s >= 0; s--) {
+    const int64_t k = order[s];
+    lbase[(size_t)link_y[k] * pitch + link_x[k]] = static_cast<int32_t>(s);
+  }
+
+  h->precision = p.precision;
+  h->stream = static_cast<cudaStream_t>(p.stream);
+  h->nx = nx;
+  h->ny = ny;
+  h->pitch = pitch;
+  h->plane = plane;
+  h->px = px;
+  h->py = py;
+  h->ax = dom->ax;
+  h->ay = dom->ay;
+  h->cp = cp;
+  h->params = p;
+  h->n_fluid = n_fluid;
+  h->n_links = static_cast<int64_t>(n_links);
+  cudaGetDevice(&h->device);
+
+  const size_t es = elem_size(p.precision);
+  const size_t fbytes = 9 * static_cast<size_t>(plane) * es;
+  const size_t lbytes = std::max<size_t>(1, n_links) * 8 * es;
+  const size_t pbytes = lbm::kResidualBlocks * lbm::kPartialStride * sizeof(double);
+  std::vector<unsigned char> lhost(lbytes, 0);
+  for (size_t s = 0; s < n_links; s++) {
+    const double *c = &coef[8 * order[s]];
+    if (es == 8) {
+      std::memcpy(&lhost[s * 64], c, 64);
+    } else {
+      float cf[8];
+      for (int j = 0; j < 8; j++) cf[j] = static_cast<float>(c[j]);
+      std::memcpy(&lhost[s * 32], cf, 32);
+    }
+  }
+  auto alloc = [&](void **ptr, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(ptr, bytes, h->stream);
+    if (e == cudaSuccess) h->dev_bytes += static_cast<int64_t>(bytes);
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc(&h->f[0], fbytes);
+  if (e == cudaSuccess) e = alloc(&h->f[1], fbytes);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->flags), flags.size());
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), lbase.size() * 4);
+  if (e == cudaSuccess) e = alloc(&h->links, lbytes);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_result), 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, fbytes, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->flags, flags.data(), flags.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->lbase, lbase.data(), lbase.size() * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->links, lhost.data(), lbytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device setup: ") + cudaGetErrorString(e);
+    const int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    release(h);
+    return code;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_handle_t *h, int64_t n) {
+  if (!h) return LBM_EINVAL;
+  if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
+  for (int64_t s = 0; s < n; s++) {
+    cudaError_t e = do_step(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+  }
+  return LBM_OK;
+}
+
+int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
+  if (!h) return LBM_EINVAL;
+  const int c = h->cur, pv = 1 - h->cur;
+  cudaError_t e;
+  if (h->precision == LBM_FP64)
+    e = lbm::launch_residual<double>(static_cast<const double *>(h->f[c]),
+                                     static_cast<const double *>(h->f[pv]), h->flags, h->nx,
+                                     h->ny, h->pitch, h->plane, h->ax, h->ay, h->partials,
+                                     h->result, h->stream);
+  else
+    e = lbm::launch_residual<float>(static_cast<const float *>(h->f[c]),
+                                    static_cast<const float *>(h->f[pv]), h->flags, h->nx, h->ny,
+                                    h->pitch, h->plane, h->ax, h->ay, h->partials, h->result,
+                                    h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
+  LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  LBM_CK(h, cudaStreamSynchronize(h->stream));
+  const double num = h->h_result[0], den = h->h_result[1];
+  double res;
+  if (std::isnan(num) || std::isnan(den))
+    res = std::numeric_limits<double>::quiet_NaN();
+  else
+    res = den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+  if (residual) *residual = res;
+  if (mass) *mass = static_cast<double>(h->n_fluid) + h->h_result[2];
+  if (h->h_result[3] > 0.0) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "%.0f fluid nodes with non-finite density or velocity",
+                  h->h_result[3]);
+    return fail(h, LBM_EUNSTABLE, buf);
+  }
+  return LBM_OK;
+}
+
+int lbm_run_to(lbm_handle_t *h, double tol, int64_t max_steps, int64_t *steps_done,
+               double *residual) {
+  if (!h) return LBM_EINVAL;
+  if (max_steps < 0) return fail(h, LBM_EINVAL, "negative max_steps");
+  int64_t done = 0;
+  double res = INFINITY;
+  while (done < max_steps) {
+    const int64_t n = std::min<int64_t>(h->params.residual_every, max_steps - done);
+    int rc = lbm_step(h, n);
+    if (rc) return rc;
+    done += n;
+    rc = lbm_residual(h, &res, nullptr);
+    if (rc) {
+      if (steps_done) *steps_done = done;
+      if (residual) *residual = res;
+      return rc;
+    }
+    if (res < tol) break;
+  }
+  if (steps_done) *steps_done = done;
+  if (residual) *residual = res;
+  return LBM_OK;
+}
+
+int lbm_fields(lbm_handle_t *h, double *rho, double *ux, double *uy, int on_device) {
+  if (!h) return LBM_EINVAL;
+  const int64_t n = static_cast<int64_t>(h->nx) * h->ny;
+  double *d = nullptr;
+  double *r = rho, *u = ux, *v = uy;
+  if (!on_device) {
+    LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), 3 * n * sizeof(double), h->stream));
+    r = rho ? d : nullptr;
+    u = ux ? d + n : nullptr;
+    v = uy ? d + 2 * n : nullptr;
+  }
+  cudaError_t e;
+  if (h->precision == LBM_FP64)
+    e = lbm::launch_fields<double>(static_cast<const double *>(h->f[h->cur]), h->flags, h->nx,
+                                   h->ny, h->pitch, h->plane, h->ax, h->ay, r, u, v, h->stream);
+  else
+    e = lbm::launch_fields<float>(static_cast<const float *>(h->f[h->cur]), h->flags, h->nx,
+                                  h->ny, h->pitch, h->plane, h->ax, h->ay, r, u, v, h->stream);
+  if (e == cudaSuccess && !on_device) {
+    if (rho && e == cudaSuccess)
+      e = cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (ux && e == cudaSuccess)
+      e = cudaMemcpyAsync(ux, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (uy && e == cudaSuccess)
+      e = cudaMemcpyAsync(uy, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "lbm_fields");
+  return LBM_OK;
+}
+
+int lbm_get_f(lbm_handle_t *h, double *f) {
+  if (!h || !f) return h ? fail(h, LBM_EINVAL, "null output") : LBM_EINVAL;
+  const int64_t n = 9 * static_cast<int64_t>(h->nx) * h->ny;
+  double *d = nullptr;
+  LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), n * sizeof(double), h->stream));
+  cudaError_t e;
+  if (h->precision == LBM_FP64)
+    e = lbm::launch_export_f<double>(static_cast<const double *>(h->f[h->cur]), h->nx, h->ny,
+                                     h->pitch, h->plane, d, h->stream);
+  else
+    e = lbm::launch_export_f<float>(static_cast<const float *>(h->f[h->cur]), h->nx, h->ny,
+                                    h->pitch, h->plane, d, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lbm_get_f");
+  return LBM_OK;
+}
+
+int lbm_set_f(lbm_handle_t *h, const double *f) {
+  if (!h || !f) return h ? fail(h, LBM_EINVAL, "null input") : LBM_EINVAL;
+  const int64_t n = 9 * static_cast<int64_t>(h->nx) * h->ny;
+  double *d = nullptr;
+  LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), n * sizeof(double), h->stream));
+  cudaError_t e = cudaMemcpyAsync(d, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+    if (h->precision == LBM_FP64)
+      e = lbm::launch_import_f<double>(d, h->nx, h->ny, h->pitch, h->plane,
+                                       static_cast<double *>(h->f[b]), h->stream);
+    else
+      e = lbm::launch_import_f<float>(d, h->nx, h->ny, h->pitch, h->plane,
+                                      static_cast<float *>(h->f[b]), h->stream);
+  }
+  cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_f");
+  h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_link_params(const lbm_handle_t *h, double *r, double *l) {
+  if (!h) return LBM_EINVAL;
+  if (r) std::copy(h->link_r.begin(), h->link_r.end(), r);
+  if (l) std::copy(h->link_l.begin(), h->link_l.end(), l);
+  return LBM_OK;
+}
+
+int lbm_get_info(const lbm_handle_t *h, lbm_info_t *info) {
+  if (!h || !info) return LBM_EINVAL;
+  info->n_nodes = static_cast<int64_t>(h->nx) * h->ny;
+  info->n_fluid = h->n_fluid;
+  info->n_links = h->n_links;
+  info->steps = h->steps;
+  info->tau_s = h->cp.tau_s;
+  info->tau_q = h->cp.tau_q;
+  info->E = h->cp.E;
+  info->E_max = h->cp.E_max;
+  info->L1 = h->cp.L1;
+  info->L2 = h->cp.L2;
+  info->n_clamped = h->cp.n_clamped;
+  info->device_bytes = h->dev_bytes;
+  info->precision = h->precision;
+  info->pitch = h->pitch;
+  return LBM_OK;
+}
+
+int lbm_precompute(double Kn, double H, const lbm_params_t *params, size_t n, const int32_t *dir,
+                   const double *q, const double *ubx, const double *uby, double *r, double *l,
+                   lbm_info_t *info) {
+  g_create_error.clear();
+  if (!params || (n && (!dir || !q || !ubx || !uby))) {
+    g_create_error = "null argument";
+    return LBM_EINVAL;
+  }
+  for (size_t k = 0; k < n; k++)
+    if (dir[k] < 1 || dir[k] > 8 || !(q[k] > 0.0 && q[k] <= 1.0)) {
+      g_create_error = "direction outside 1..8 or gamma outside (0, 1]";
+      return LBM_EINVAL;
+    }
+  lbm::CaseParams cp;
+  std::string msg = lbm::compute_case_params(Kn, H, *params, &cp);
+  std::vector<double> rr(n), ll(n), coef(8 * n);
+  if (msg.empty())
+    msg = lbm::compute_link_coefs(cp, *params, n, dir, q, ubx, uby, rr.data(), ll.data(),
+                                  coef.data(), &cp.n_clamped);
+  if (!msg.empty()) {
+    g_create_error = msg;
+    return LBM_EINVAL;
+  }
+  if (r) std::copy(rr.begin(), rr.end(), r);
+  if (l) std::copy(ll.begin(), ll.end(), l);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n_links = static_cast<int64_t>(n);
+    info->tau_s = cp.tau_s;
+    info->tau_q = cp.tau_q;
+    info->E = cp.E;
+    info->E_max = cp.E_max;
+    info->L1 = cp.L1;
+    info->L2 = cp.L2;
+    info->n_clamped = cp.n_clamped;
+    info->precision = params->precision;
+  }
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle_t *h) { release(h); }
+
+const char *lbm_last_error(const lbm_handle_t *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations shared by the host side and the kernels of liblbm.so.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Node flag byte: bits 0..7 = unknown incoming directions 1..8 (x - c_i is
+// solid); kSolid marks a solid (or padding) node that is never updated.
+constexpr uint8_t kSolid = 0xFF;
+
+// Relaxation rates and forcing of one case, as the kernels consume them.
+template <typename C>
+struct StepConst {
+  C s_e, s_eps, s_q, s_s, s_j;  // 1/tau of the non-conserved moments and of j
+  C ax, ay;                     // body acceleration
+  int32_t nx, ny, pitch;        // lattice size and row pitch (elements)
+  int32_t periodic_x, periodic_y;
+  int64_t plane;                // elements per population plane = ny * pitch
+};
+
+// Coefficients of one link in the kernels' folded form of Eq. EqNewBDSC,
+// in deviation variables d = f - w:
+//   d_i(x_f, t+1) = k1 d_ib + k2 d'_i + k3 d'_ib + c0 + c1 drho
+//                   + c2 (drho + rho P_i(u_f)),
+//   P_i(u) = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u.
+template <typename C>
+struct alignas(sizeof(C) * 4) LinkCoef {
+  C k1, k2, k3, c0;
+  C c1, c2, pad0, pad1;
+};
+
+// Case parameters after the FP64 precompute of Sec. 3.B.
+struct CaseParams {
+  double tau_s, tau_q, tau_rho, tau_j, tau_e, tau_eps;
+  double L1, L2, E, E_max;
+  int64_t n_clamped;
+};
+
+// Host-side FP64 precompute (lbm_params.cpp).  Returns "" or an error text.
+std::string compute_case_params(double Kn, double H, const lbm_params_t &p, CaseParams *out);
+// Per-link l and r (Sec. 3.B) and the folded coefficients above.
+std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size_t n,
+                               const int32_t *dir, const double *q, const double *ubx,
+                               const double *uby, double *r_out, double *l_out,
+                               double *coef8_out /* n x 8 */, int64_t *n_clamped);
+
+// Kernel launchers (lbm_kernels.cu).  All return the launch error code.
+template <typename T, typename C>
+cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
+                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
+                            int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
+                            double *partials, double *result, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t ny,
+                          int32_t pitch, int64_t plane, double ax, double ay, double *rho,
+                          double *ux, double *uy, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+                            double *out, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch,
+                            int64_t plane, T *f, cudaStream_t s);
+
+// Fixed reduction geometry: deterministic partial order on every device.
+constexpr int kResidualBlocks = 1024;
+constexpr int kResidualThreads = 256;
+constexpr int kPartialStride = 4;  // num, den, mass deviation, non-finite count
+
+}  // namespace lbm

@@ -1,0 +1,351 @@
+// Device kernels of liblbm.so: the fused collide-stream-boundary step, the
+// FP64 residual/mass reduction, and field/population conversion.
+//
+// Populations are stored as deviations d_i = f_i - w_i (rest state rho = 1,
+// u = 0 is d = 0), one plane per direction: d[i][y][x] with a padded row
+// pitch.  The step kernel is a push scheme (Sec. 2: collide, then stream):
+// each fluid node reads its nine values once, collides in moment space, and
+// writes f'_i to x + c_i in the other lattice.  Unknown populations of a
+// boundary node (x_f - c_i solid) are never pushed by anyone; the node fills
+// them itself from values it holds in registers (Eq. EqNewBDSC is local:
+// f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all belong to x_f).
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+template <typename C>
+struct Num;
+template <>
+struct Num<float> {
+  static __device__ __forceinline__ float c(double v) { return static_cast<float>(v); }
+};
+template <>
+struct Num<double> {
+  static __device__ __forceinline__ double c(double v) { return v; }
+};
+
+__device__ __forceinline__ int wrap_x(int x, int nx, int periodic) {
+  // Non-periodic axes have solid edges, so fluid never pushes past them.
+  return periodic ? (x < 0 ? x + nx : (x >= nx ? x - nx : x)) : x;
+}
+
+// One time step for one node.  T: storage type, C: arithmetic type.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256)
+step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__restrict__ flags,
+            const int32_t *__restrict__ lbase, const LinkCoef<C> *__restrict__ links,
+            const StepConst<C> k) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= k.nx) return;
+  for (int y = blockIdx.y; y < k.ny; y += gridDim.y) {
+    const int64_t node = static_cast<int64_t>(y) * k.pitch + x;
+    const uint8_t fl = flags[node];
+    if (fl == kSolid) continue;
+    const int64_t P = k.plane;
+    C d[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) d[i] = static_cast<C>(src[i * P + node]);
+
+    // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
+    const C s14 = d[1] + d[2] + d[3] + d[4];
+    const C s58 = d[5] + d[6] + d[7] + d[8];
+    const C drho = d[0] + s14 + s58;
+    const C e = C(-4) * d[0] - s14 + C(2) * s58;
+    const C eps = C(4) * d[0] - C(2) * s14 + s58;
+    const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
+    const C jx = d[1] - d[3] + d5m6 + d8m7;
+    const C qx = C(2) * (d[3] - d[1]) + d5m6 + d8m7;
+    const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
+    const C jy = d[2] - d[4] + d5p6 - d7p8;
+    const C qy = C(2) * (d[4] - d[2]) + d5p6 - d7p8;
+    const C pxx = d[1] - d[2] + d[3] - d[4];
+    const C pxy = d[5] - d[6] + d[7] - d[8];
+
+    // Eq. FluidMacr.
+    const C rho = C(1) + drho;
+    const C rax = rho * k.ax, ray = rho * k.ay;
+    const C inv_rho = C(1) / rho;
+    const C ux = (jx + C(0.5) * rax) * inv_rho;
+    const C uy = (jy + C(0.5) * ray) * inv_rho;
+    const C uu = ux * ux + uy * uy;
+    const C rux = rho * ux, ruy = rho * uy;
+
+    // Eq. MomentPost: m' = m - S (m - m_eq) + (I - S/2) M Fbar, with
+    // M f_eq and M Fbar in closed form.
+    const C ua6 = C(6) * (rux * k.ax + ruy * k.ay);
+    const C e_p = e - k.s_e * (e + C(2) * drho - C(3) * rho * uu) + (C(1) - C(0.5) * k.s_e) * ua6;
+    const C eps_p = eps - k.s_eps * (eps - drho + C(3) * rho * uu) - (C(1) - C(0.5) * k.s_eps) * ua6;
+    const C fj = C(1) - C(0.5) * k.s_j, fq = C(1) - C(0.5) * k.s_q, fs = C(1) - C(0.5) * k.s_s;
+    const C jx_p = jx - k.s_j * (jx - rux) + fj * rax;
+    const C jy_p = jy - k.s_j * (jy - ruy) + fj * ray;
+    const C qx_p = qx - k.s_q * (qx + rux) - fq * rax;
+    const C qy_p = qy - k.s_q * (qy + ruy) - fq * ray;
+    const C pxx_p = pxx - k.s_s * (pxx - rho * (ux * ux - uy * uy)) + fs * C(2) * (rux * k.ax - ruy * k.ay);
+    const C pxy_p = pxy - k.s_s * (pxy - rho * ux * uy) + fs * (rux * k.ay + ruy * k.ax);
+
+    // f' = M^-1 m' with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+    const C r9 = drho * C(1.0 / 9.0);
+    const C e36 = e_p * C(1.0 / 36.0), p36 = eps_p * C(1.0 / 36.0);
+    const C jx6 = jx_p * C(1.0 / 6.0), jy6 = jy_p * C(1.0 / 6.0);
+    const C qx12 = qx_p * C(1.0 / 12.0), qy12 = qy_p * C(1.0 / 12.0);
+    const C xx4 = pxx_p * C(0.25), xy4 = pxy_p * C(0.25);
+    const C axis = r9 - e36 - C(2) * p36;
+    const C diag = r9 + C(2) * e36 + p36;
+    const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
+    const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
+    C o[9];
+    o[0] = r9 - C(4) * e36 + C(4) * p36;
+    o[1] = axis + ax_x + xx4;
+    o[2] = axis + ax_y - xx4;
+    o[3] = axis - ax_x + xx4;
+    o[4] = axis - ax_y - xx4;
+    o[5] = diag + dg_x + dg_y + xy4;
+    o[6] = diag - dg_x + dg_y - xy4;
+    o[7] = diag - dg_x - dg_y + xy4;
+    o[8] = diag + dg_x - dg_y - xy4;
+
+    // Streaming: push f'_i to x + c_i unless that node is solid (bit of the
+    // opposite direction set).
+    const int xe = wrap_x(x + 1, k.nx, k.periodic_x), xw = wrap_x(x - 1, k.nx, k.periodic_x);
+    const int yn = wrap_x(y + 1, k.ny, k.periodic_y), ys = wrap_x(y - 1, k.ny, k.periodic_y);
+    const int64_t rowc = static_cast<int64_t>(y) * k.pitch;
+    const int64_t rown = static_cast<int64_t>(yn) * k.pitch;
+    const int64_t rows = static_cast<int64_t>(ys) * k.pitch;
+    dst[node] = static_cast<T>(o[0]);
+    // bit (j-1) set <=> x - c_j solid; push i needs x + c_i = x - c_opp(i) fluid.
+    if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = static_cast<T>(o[1]);  // opp(1) = 3
+    if (!(fl & (1u << 3))) dst[2 * P + rown + x] = static_cast<T>(o[2]);   // opp(2) = 4
+    if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = static_cast<T>(o[3]);  // opp(3) = 1
+    if (!(fl & (1u << 1))) dst[4 * P + rows + x] = static_cast<T>(o[4]);   // opp(4) = 2
+    if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = static_cast<T>(o[5]);  // opp(5) = 7
+    if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = static_cast<T>(o[6]);  // opp(6) = 8
+    if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = static_cast<T>(o[7]);  // opp(7) = 5
+    if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = static_cast<T>(o[8]);  // opp(8) = 6
+
+    if (fl) {
+      // Boundary links of this node, Eq. EqNewBDSC in the folded form of
+      // LinkCoef (links sorted by node, then direction).
+      int li = lbase[node];
+      const C cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+      const C cys[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+      const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+      for (int j = 1; j < 9; j++) {
+        if (fl & (1u << (j - 1))) {
+          const LinkCoef<C> c = links[li++];
+          const C cu = cxs[j] * ux + cys[j] * uy;
+          const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+          const C v = c.k1 * d[opp[j]] + c.k2 * o[j] + c.k3 * o[opp[j]] + c.c0 + c.c1 * drho +
+                      c.c2 * (drho + rho * pj);
+          dst[j * P + node] = static_cast<T>(v);
+        }
+      }
+    }
+  }
+}
+
+// Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).
+__device__ __forceinline__ double node_velocity(const double *d, double ax, double ay, double &rho,
+                                                double &ux, double &uy) {
+  double drho = 0.0, jx, jy;
+  for (int i = 0; i < 9; i++) drho += d[i];
+  jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+  jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  rho = 1.0 + drho;
+  ux = (jx + 0.5 * rho * ax) / rho;
+  uy = (jy + 0.5 * rho * ay) / rho;
+  return drho;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Pass 1: each block reduces a fixed, strided slice of the nodes into
+// partials[block * 4 + {0..3}] (FP64, warp shuffles then shared memory).
+template <typename T>
+__global__ void __launch_bounds__(kResidualThreads)
+residual_partials(const T *__restrict__ cur, const T *__restrict__ prev,
+                  const uint8_t *__restrict__ flags, int32_t nx, int32_t ny, int32_t pitch,
+                  int64_t plane, double ax, double ay, double *__restrict__ partials) {
+  double num = 0.0, den = 0.0, dm = 0.0, bad = 0.0;
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t y = p / nx, x = p - y * nx;
+    const int64_t node = y * pitch + x;
+    if (flags[node] == kSolid) continue;
+    double a[9], b[9];
+    for (int i = 0; i < 9; i++) {
+      a[i] = static_cast<double>(cur[i * plane + node]);
+      b[i] = static_cast<double>(prev[i * plane + node]);
+    }
+    double r1, u1, v1, r0, u0, v0;
+    const double drho = node_velocity(a, ax, ay, r1, u1, v1);
+    node_velocity(b, ax, ay, r0, u0, v0);
+    if (!(isfinite(r1) && isfinite(u1) && isfinite(v1))) {
+      bad += 1.0;
+      continue;
+    }
+    num += (u1 - u0) * (u1 - u0) + (v1 - v0) * (v1 - v0);
+    den += u1 * u1 + v1 * v1;
+    dm += drho;
+  }
+  __shared__ double sh[kResidualThreads / 32][kPartialStride];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  dm = warp_sum(dm);
+  bad = warp_sum(bad);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[w][0] = num;
+    sh[w][1] = den;
+    sh[w][2] = dm;
+    sh[w][3] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPartialStride) {
+    double s = 0.0;
+    for (int i = 0; i < kResidualThreads / 32; i++) s += sh[i][threadIdx.x];
+    partials[blockIdx.x * kPartialStride + threadIdx.x] = s;
+  }
+}
+
+// Pass 2: one block sums the partials in a fixed order.
+__global__ void __launch_bounds__(kResidualBlocks)
+residual_final(const double *__restrict__ partials, double *__restrict__ out) {
+  __shared__ double sh[kResidualBlocks / 32][kPartialStride];
+  double v[kPartialStride];
+  for (int c = 0; c < kPartialStride; c++)
+    v[c] = warp_sum(partials[threadIdx.x * kPartialStride + c]);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int c = 0; c < kPartialStride; c++) sh[w][c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < kPartialStride) {
+    double s = 0.0;
+    for (int i = 0; i < kResidualBlocks / 32; i++) s += sh[i][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void fields_kernel(const T *__restrict__ f, const uint8_t *__restrict__ flags,
+                              int32_t nx, int32_t ny, int32_t pitch, int64_t plane, double ax,
+                              double ay, double *rho, double *ux, double *uy) {
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t y = p / nx, x = p - y * nx;
+    const int64_t node = y * pitch + x;
+    double r = 0.0, u = 0.0, v = 0.0;
+    if (flags[node] != kSolid) {
+      double a[9];
+      for (int i = 0; i < 9; i++) a[i] = static_cast<double>(f[i * plane + node]);
+      node_velocity(a, ax, ay, r, u, v);
+    }
+    if (rho) rho[p] = r;
+    if (ux) ux[p] = u;
+    if (uy) uy[p] = v;
+  }
+}
+
+__constant__ double kWd[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+template <typename T>
+__global__ void export_kernel(const T *__restrict__ f, int32_t nx, int32_t ny, int32_t pitch,
+                              int64_t plane, double *out) {
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
+    out[p] = kWd[i] + static_cast<double>(f[i * plane + y * pitch + x]);
+  }
+}
+
+template <typename T>
+__global__ void import_kernel(const double *__restrict__ in, int32_t nx, int32_t ny,
+                              int32_t pitch, int64_t plane, T *f) {
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
+    f[i * plane + y * pitch + x] = static_cast<T>(in[p] - kWd[i]);
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return static_cast<int>(b < 1 ? 1 : (b > 65536 ? 65536 : b));
+}
+
+}  // namespace
+
+template <typename T, typename C>
+cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
+                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
+  const int threads = 256;
+  dim3 grid((k.nx + threads - 1) / threads, k.ny < 65535 ? k.ny : 65535);
+  step_kernel<T, C><<<grid, threads, 0, s>>>(src, dst, flags, lbase, links, k);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
+                            int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
+                            double *partials, double *result, cudaStream_t s) {
+  residual_partials<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(cur, prev, flags, nx, ny, pitch,
+                                                                   plane, ax, ay, partials);
+  residual_final<<<1, kResidualBlocks, 0, s>>>(partials, result);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
+                          int64_t plane, double ax, double ay, double *rho, double *ux, double *uy,
+                          cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, flags, nx, ny, pitch, plane, ax, ay, rho, ux, uy);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+                            double *out, cudaStream_t s) {
+  const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
+  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, nx, ny, pitch, plane, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+                            T *f, cudaStream_t s) {
+  const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
+  import_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(in, nx, ny, pitch, plane, f);
+  return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE(T, C)                                                                      \
+  template cudaError_t launch_step<T, C>(const T *, T *, const uint8_t *, const int32_t *,         \
+                                         const LinkCoef<C> *, const StepConst<C> &, cudaStream_t); \
+  template cudaError_t launch_residual<T>(const T *, const T *, const uint8_t *, int32_t, int32_t,  \
+                                         int32_t, int64_t, double, double, double *, double *,     \
+                                         cudaStream_t);                                            \
+  template cudaError_t launch_fields<T>(const T *, const uint8_t *, int32_t, int32_t, int32_t,     \
+                                        int64_t, double, double, double *, double *, double *,     \
+                                        cudaStream_t);                                             \
+  template cudaError_t launch_export_f<T>(const T *, int32_t, int32_t, int32_t, int64_t, double *, \
+                                          cudaStream_t);                                           \
+  template cudaError_t launch_import_f<T>(const double *, int32_t, int32_t, int32_t, int64_t, T *, \
+                                          cudaStream_t);
+
+LBM_INSTANTIATE(double, double)
+LBM_INSTANTIATE(float, float)
+
+}  // namespace lbm

@@ -1,0 +1,306 @@
+"""ctypes binding of liblbm.so (include/lbm.h), argument marshalling only.
+
+The module-level functions carry the C names (`lbm_create`, `lbm_step`,
+`lbm_fields`, `lbm_residual`, ...) and take numpy arrays or raw device
+pointers; every step of the computation runs in the CUDA library.  There is
+no fallback: if liblbm.so is missing or fails to load, the first call raises.
+`Solver` is a small convenience wrapper around one handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOMEM = range(6)
+LBM_FP64, LBM_FP32 = 0, 1
+L_MODES = {"paper": 0, "zero": 1, "gamma": 2, "2gamma": 3, "gamma2": 4, "gamma2+gamma": 5,
+           "fixed": 6}
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+
+# Every entry point include/lbm.h declares.
+EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_residual",
+           "lbm_run_to", "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info",
+           "lbm_precompute", "lbm_destroy", "lbm_last_error")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("H", ctypes.c_double), ("ax", ctypes.c_double), ("ay", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("L1", ctypes.c_double), ("L2", ctypes.c_double),
+                ("E", ctypes.c_double), ("l_clamp", ctypes.c_double),
+                ("tau_rho", ctypes.c_double), ("tau_j", ctypes.c_double),
+                ("tau_e", ctypes.c_double), ("tau_eps", ctypes.c_double),
+                ("tau_s", ctypes.c_double), ("tau_q", ctypes.c_double),
+                ("r_value", ctypes.c_double), ("l_value", ctypes.c_double),
+                ("l_mode", ctypes.c_int32), ("diffuse_mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("residual_every", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_fluid", ctypes.c_int64),
+                ("n_links", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("tau_s", ctypes.c_double), ("tau_q", ctypes.c_double), ("E", ctypes.c_double),
+                ("E_max", ctypes.c_double), ("L1", ctypes.c_double), ("L2", ctypes.c_double),
+                ("n_clamped", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("pitch", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblbm.so once and declare every signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2012_14707_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.lbm_params_default.argtypes = [ctypes.POINTER(Params)]
+    lib.lbm_params_default.restype = None
+    lib.lbm_create.argtypes = [ctypes.POINTER(Domain), ctypes.POINTER(ctypes.c_uint8), ctypes.c_size_t,
+                               ip, ip, ip, dp, dp, dp, ctypes.c_double, ctypes.POINTER(Params),
+                               ctypes.POINTER(H)]
+    lib.lbm_step.argtypes = [H, ctypes.c_int64]
+    lib.lbm_fields.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_residual.argtypes = [H, dp, dp]
+    lib.lbm_run_to.argtypes = [H, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), dp]
+    lib.lbm_get_f.argtypes = [H, dp]
+    lib.lbm_set_f.argtypes = [H, dp]
+    lib.lbm_link_params.argtypes = [H, dp, dp]
+    lib.lbm_get_info.argtypes = [H, ctypes.POINTER(Info)]
+    lib.lbm_precompute.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(Params),
+                                   ctypes.c_size_t, ip, dp, dp, dp, dp, dp, ctypes.POINTER(Info)]
+    lib.lbm_destroy.argtypes = [H]
+    lib.lbm_destroy.restype = None
+    lib.lbm_last_error.argtypes = [H]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_create", "lbm_step", "lbm_fields", "lbm_residual", "lbm_run_to",
+                 "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info", "lbm_precompute"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int, h=None):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_last_error(h).decode())
+    return rc
+
+
+# --------------------------------------------------------------------------
+# the C entry points under their own names
+# --------------------------------------------------------------------------
+
+def lbm_params_default() -> Params:
+    p = Params()
+    load().lbm_params_default(ctypes.byref(p))
+    return p
+
+
+def lbm_create(nx, ny, periodic_x, periodic_y, H, ax, ay, solid, link_x, link_y, link_dir,
+               link_q, link_ubx, link_uby, Kn, params: Params):
+    """Returns an opaque handle (int); raises LbmError on failure."""
+    lib = load()
+    dom = Domain(int(nx), int(ny), int(bool(periodic_x)), int(bool(periodic_y)), float(H),
+                 float(ax), float(ay))
+    solid = np.ascontiguousarray(solid, np.uint8).reshape(-1)
+    if solid.size != int(nx) * int(ny):
+        raise ValueError("solid mask must hold nx*ny entries")
+    arrs = [np.ascontiguousarray(a, t) for a, t in
+            ((link_x, np.int32), (link_y, np.int32), (link_dir, np.int32),
+             (link_q, np.float64), (link_ubx, np.float64), (link_uby, np.float64))]
+    n = arrs[0].size
+    if any(a.size != n for a in arrs):
+        raise ValueError("link arrays differ in length")
+    ip = ctypes.POINTER(ctypes.c_int32)
+    h = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(dom), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n,
+                        arrs[0].ctypes.data_as(ip), arrs[1].ctypes.data_as(ip),
+                        arrs[2].ctypes.data_as(ip), _dp(arrs[3]), _dp(arrs[4]), _dp(arrs[5]),
+                        float(Kn), ctypes.byref(params), ctypes.byref(h))
+    _check(rc, None)
+    return h.value
+
+
+def lbm_step(h, n: int):
+    _check(load().lbm_step(h, int(n)), h)
+
+
+def lbm_fields(h, rho, ux, uy, on_device: bool = False):
+    """Host numpy arrays (float64, nx*ny) or device pointers (int) when
+    on_device; None skips a field."""
+    lib = load()
+    if on_device:
+        _check(lib.lbm_fields(h, rho, ux, uy, 1), h)
+        return
+    ptr = [None if a is None else a.ctypes.data for a in (rho, ux, uy)]
+    for a in (rho, ux, uy):
+        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+            raise ValueError("field arrays must be C-contiguous float64")
+    _check(lib.lbm_fields(h, ptr[0], ptr[1], ptr[2], 0), h)
+
+
+def lbm_residual(h):
+    """Returns (residual, mass); raises LbmError(LBM_EUNSTABLE) on non-finite state."""
+    r, m = ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_residual(h, ctypes.byref(r), ctypes.byref(m)), h)
+    return r.value, m.value
+
+
+def lbm_run_to(h, tol: float, max_steps: int):
+    done, res = ctypes.c_int64(), ctypes.c_double()
+    _check(load().lbm_run_to(h, float(tol), int(max_steps), ctypes.byref(done), ctypes.byref(res)), h)
+    return done.value, res.value
+
+
+def lbm_get_f(h, out: np.ndarray):
+    _check(load().lbm_get_f(h, _dp(out)), h)
+
+
+def lbm_set_f(h, f: np.ndarray):
+    f = np.ascontiguousarray(f, np.float64)
+    _check(load().lbm_set_f(h, _dp(f)), h)
+
+
+def lbm_link_params(h, n_links: int):
+    r, l = np.empty(n_links), np.empty(n_links)
+    _check(load().lbm_link_params(h, _dp(r), _dp(l)), h)
+    return r, l
+
+
+def lbm_get_info(h) -> Info:
+    info = Info()
+    _check(load().lbm_get_info(h, ctypes.byref(info)), h)
+    return info
+
+
+def lbm_precompute(Kn, H, params: Params, link_dir, link_q, link_ubx=None, link_uby=None):
+    """Host-only FP64 precompute: returns (r, l, info)."""
+    d = np.ascontiguousarray(link_dir, np.int32)
+    q = np.ascontiguousarray(link_q, np.float64)
+    ubx = np.zeros_like(q) if link_ubx is None else np.ascontiguousarray(link_ubx, np.float64)
+    uby = np.zeros_like(q) if link_uby is None else np.ascontiguousarray(link_uby, np.float64)
+    r, l = np.empty(q.size), np.empty(q.size)
+    info = Info()
+    _check(load().lbm_precompute(float(Kn), float(H), ctypes.byref(params), q.size,
+                                 d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(q), _dp(ubx),
+                                 _dp(uby), _dp(r), _dp(l), ctypes.byref(info)), None)
+    return r, l, info
+
+
+def lbm_destroy(h):
+    if h:
+        load().lbm_destroy(h)
+
+
+def lbm_last_error(h=None) -> str:
+    return load().lbm_last_error(h).decode()
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper
+# --------------------------------------------------------------------------
+
+class Solver:
+    """One case on the GPU.
+
+    `case` is a `cases.Case`.  Keyword arguments override the parameter
+    defaults of include/lbm.h: precision ("fp32" | "fp64"), l_mode (a name of
+    L_MODES or a float for a fixed l), r (fixed r), tau_q, tau_s, E, L1, L2,
+    sigma, diffuse_mode, residual_every, stream (a cudaStream_t as int).
+    """
+
+    def __init__(self, case, precision="fp32", l_mode="paper", r=None, tau_q=None, tau_s=None,
+                 E=None, L1=None, L2=None, sigma=1.0, diffuse_mode=0, residual_every=100,
+                 stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4):
+        p = lbm_params_default()
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if isinstance(l_mode, str):
+            p.l_mode = L_MODES[l_mode]
+        else:
+            p.l_mode = L_MODES["fixed"]
+            p.l_value = float(l_mode)
+        nan = math.nan
+        p.r_value = nan if r is None else float(r)
+        p.tau_q = nan if tau_q is None else float(tau_q)
+        p.tau_s = nan if tau_s is None else float(tau_s)
+        p.E = nan if E is None else float(E)
+        p.L1 = nan if L1 is None else float(L1)
+        p.L2 = nan if L2 is None else float(L2)
+        p.sigma = float(sigma)
+        p.tau_e, p.tau_eps, p.l_clamp = float(tau_e), float(tau_eps), float(l_clamp)
+        p.diffuse_mode = int(diffuse_mode)
+        p.residual_every = int(residual_every)
+        p.stream = stream
+        self.case = case
+        self.params = p
+        self.h = None
+        self.h = lbm_create(case.nx, case.ny, case.periodic_x, case.periodic_y, case.H, case.ax,
+                            case.ay, case.solid, case.link_x, case.link_y, case.link_dir,
+                            case.link_q, case.link_ubx, case.link_uby, case.Kn, p)
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def residual(self):
+        return lbm_residual(self.h)
+
+    def run_to(self, tol, max_steps):
+        return lbm_run_to(self.h, tol, max_steps)
+
+    def fields(self):
+        n = self.case.nx * self.case.ny
+        rho, ux, uy = np.empty(n), np.empty(n), np.empty(n)
+        lbm_fields(self.h, rho, ux, uy)
+        s = (self.case.ny, self.case.nx)
+        return rho.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def get_f(self):
+        f = np.empty((9, self.case.ny, self.case.nx))
+        lbm_get_f(self.h, f)
+        return f
+
+    def set_f(self, f):
+        lbm_set_f(self.h, f)
+
+    def link_params(self):
+        return lbm_link_params(self.h, self.case.n_links)
+
+    def info(self) -> Info:
+        return lbm_get_info(self.h)

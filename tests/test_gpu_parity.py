@@ -1,0 +1,190 @@
+"""GPU (liblbm.so through the C ABI) against the FP64 oracle, on the same
+seeded inputs.
+
+Tolerances: FP64 storage -- populations element by element within 1e-13
+absolute (populations are O(0.1); this leaves room for summation-order
+round-off over a few hundred steps only).  FP32 deviation storage --
+velocity relative L2 <= 1e-5 and mass drift |M_gpu - M_oracle| / M_oracle(0)
+<= 1e-10, the accuracy targets of the FP32 path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import params as P
+from paper_2012_14707_gb300 import cases
+from paper_2012_14707_gb300 import build as lbm_build
+from paper_2012_14707_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lbm_build.build()
+    lbm.load()
+    oracle.build()
+
+
+def _pair(case, precision, start_seed=None, amp=1e-3, **kw):
+    """Oracle and GPU solver on the same case, parameters and start state."""
+    okw = {}
+    gkw = dict(precision=precision)
+    for k in ("l_mode", "diffuse_mode", "E", "L1", "L2", "tau_s"):
+        if k in kw:
+            gkw[k] = kw[k]
+    if "r" in kw:
+        gkw["r"] = kw["r"]
+        okw["r_fixed"] = kw["r"]
+    if "tau_q" in kw:
+        gkw["tau_q"] = kw["tau_q"]
+        okw["tau_q_fixed"] = kw["tau_q"]
+    par = P.Parameters(case.Kn, case.H, L1=kw.get("L1"), L2=kw.get("L2"), E=kw.get("E"),
+                       tau_s=kw.get("tau_s"), l_mode=kw.get("l_mode", "paper"), **okw)
+    o = oracle.OracleLBM(case, par, diffuse_mode=kw.get("diffuse_mode", 0))
+    g = lbm.Solver(case, **gkw)
+    if start_seed is not None:
+        f0 = cases.random_populations(case.nx, case.ny, start_seed, amp)
+        o.set_f(f0)
+        g.set_f(f0)
+    return o, g
+
+
+def _vel_rel_l2(case, a, b):
+    fl = case.solid == 0
+    num = ((a[1] - b[1])[fl] ** 2 + (a[2] - b[2])[fl] ** 2).sum()
+    den = (b[1][fl] ** 2 + b[2][fl] ** 2).sum()
+    return math.sqrt(num / den)
+
+
+CASES = {
+    "poiseuille": lambda: cases.config_poiseuille(),
+    "annulus": lambda: cases.annulus(40, 8.0, 16.0, 0.05, 0.05 * math.sqrt(1 / 3) / 8),
+    "cylinders": lambda: cases.cylinder_array(300, 150, 5, Kn=0.02, ax=1e-5),
+    "box": lambda: cases.periodic_box(70, 45, ax=2e-5, ay=-1e-5),
+    "column": lambda: cases.periodic_box(1, 7, ax=1e-5),
+    "row": lambda: cases.periodic_box(33, 1, ay=1e-5),
+    "channel_moving": lambda: cases.channel(37, 9, 0.2, 0.85, Kn=0.05, ax=1e-6, u_top=0.01),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("diffuse_mode", [0, 1])
+def test_fp64_populations_match_oracle(name, diffuse_mode):
+    c = CASES[name]()
+    kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    o, g = _pair(c, "fp64", start_seed=11, diffuse_mode=diffuse_mode, **kw)
+    for n in (1, 37, 162):
+        o.step(n)
+        g.step(n)
+        np.testing.assert_allclose(g.get_f(), o.get_f(), rtol=0, atol=1e-13)
+    ro, mo = o.residual()
+    rg, mg = g.residual()
+    assert rg == pytest.approx(ro, rel=1e-8, abs=1e-300)
+    assert mg == pytest.approx(mo, rel=1e-13)
+    fo, fg = o.fields(), g.fields()
+    for a, b in zip(fg, fo):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("l_mode,extra", [
+    ("zero", {}), ("gamma", {}), ("2gamma", {}), ("gamma2", {}), ("gamma2+gamma", {}),
+    (0.35, {"r": 0.7, "tau_q": 0.9}),
+])
+def test_fp64_scheme_variants_match_oracle(l_mode, extra):
+    c = CASES["cylinders"]()
+    o, g = _pair(c, "fp64", start_seed=3, l_mode=l_mode, **extra)
+    o.step(120)
+    g.step(120)
+    np.testing.assert_allclose(g.get_f(), o.get_f(), rtol=0, atol=1e-13)
+    r_g, l_g = g.link_params()
+    np.testing.assert_allclose(r_g, o.link_r, rtol=1e-13)
+    np.testing.assert_allclose(l_g, o.link_l, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_velocity_and_mass_match_oracle(name):
+    c = CASES[name]()
+    kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    o, g = _pair(c, "fp32", **kw)
+    m0 = o.residual()[1]
+    for n in (500, 1500):
+        o.step(n)
+        g.step(n)
+        assert _vel_rel_l2(c, g.fields(), o.fields()) <= 1e-5
+        assert abs(g.residual()[1] - o.residual()[1]) / m0 <= 1e-10
+
+
+def test_poiseuille_steady_state_fp64_and_fp32():
+    """4 x 32 channel run to residual 1e-10: FP64 meets Eq. numvelo like the
+    oracle; FP32 meets the oracle's steady profile within 1e-5."""
+    c = cases.config_poiseuille()
+    par = P.Parameters(c.Kn, c.H)
+    uc = c.ax * c.H ** 2 / (8 * P.viscosity(par.tau_s))
+    want = P.poiseuille_profile(np.arange(32) + 0.5, c.H, uc,
+                                P.slip_velocity_physical(par.L1, par.L2, c.Kn))
+    g64 = lbm.Solver(c, precision="fp64")
+    steps, res = g64.run_to(1e-10, 100000)
+    assert res < 1e-10
+    ux = g64.fields()[1][1:33, 0]
+    np.testing.assert_allclose(ux / uc, want / uc, rtol=0, atol=5e-8)
+    g32 = lbm.Solver(c, precision="fp32")
+    g32.run_to(1e-9, 100000)
+    ux32 = g32.fields()[1][1:33, 0]
+    assert np.sqrt(((ux32 - ux) ** 2).sum() / (ux ** 2).sum()) <= 1e-5
+
+
+@pytest.mark.parametrize("Kn", [0.01, 0.05, 0.1])
+def test_couette_256_parity_and_slip(Kn):
+    """256^2 annulus (R1 = 60, R2 = 120): FP64 and FP32 follow the oracle
+    over 300 steps; FP32 run to steady is within 3 % (rel. L2) of the
+    analytic slip solution Eq. EqAnaMicro."""
+    c = cases.config_couette(Kn)
+    for prec in ("fp64", "fp32"):
+        o, g = _pair(c, prec, L1=1.0, L2=0.0)
+        o.step(300)
+        g.step(300)
+        if prec == "fp64":
+            np.testing.assert_allclose(g.get_f(), o.get_f(), rtol=0, atol=1e-13)
+        else:
+            assert _vel_rel_l2(c, g.fields(), o.fields()) <= 1e-5
+    g = lbm.Solver(c, precision="fp32", L1=1.0, L2=0.0)
+    g.run_to(1e-9, 400000)
+    rho, ux, uy = g.fields()
+    m = c.meta
+    yy, xx = np.mgrid[0:c.ny, 0:c.nx]
+    dx, dy = xx - m["center"], yy - m["center"]
+    rr = np.hypot(dx, dy)
+    fl = c.solid == 0
+    ut = (-dy * ux + dx * uy) / np.where(rr > 0, rr, 1)
+    ua = P.couette_profile(rr, m["R1"], m["R2"], m["omega1"], 0.0, Kn * (m["R2"] - m["R1"]))
+    err = np.sqrt(((ut - ua)[fl] ** 2).sum() / (ua[fl] ** 2).sum())
+    assert err < 0.03
+
+
+def test_full_size_throughput_case_matches_oracle():
+    """8192 x 4096 random-cylinder channel, FP32 in the benchmark's launch
+    configuration: two steps from a seeded perturbed state, every node
+    against the oracle."""
+    c = cases.config_throughput()
+    o, g = _pair(c, "fp32", start_seed=21, amp=1e-3)
+    o.step(2)
+    g.step(2)
+    a, b = g.get_f(), o.get_f()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    # FP32 deviation storage: |error| ~ 1e-7 of the deviation scale amp * w
+    np.testing.assert_allclose((a - w) / w, (b - w) / w, rtol=0, atol=2e-8)
+
+
+def test_nonfinite_state_is_reported():
+    c = CASES["box"]()
+    g = lbm.Solver(c, precision="fp32")
+    f = cases.random_populations(c.nx, c.ny, 1)
+    f[3, 10, 20] = np.nan
+    g.set_f(f)
+    g.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.residual()
+    assert ei.value.code == lbm.LBM_EUNSTABLE

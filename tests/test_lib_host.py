@@ -1,0 +1,116 @@
+"""CPU-side checks of liblbm.so: it builds, loads, exports every entry point
+include/lbm.h declares, validates its inputs on the host, and its FP64
+precompute of Sec. 3.B agrees with the oracle's (two independent codes)."""
+import math
+import re
+import os
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import params as P
+from paper_2012_14707_gb300 import cases
+from paper_2012_14707_gb300 import build as lbm_build
+from paper_2012_14707_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lbm_build.build()
+    return lbm.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 12
+    assert set(names) == set(lbm.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_params_default(lib):
+    p = lbm.lbm_params_default()
+    assert p.sigma == 1.0 and p.l_clamp == -0.4
+    assert (p.tau_rho, p.tau_j, p.tau_e, p.tau_eps) == (1.0, 1.0, 1.1, 1.2)
+    assert math.isnan(p.tau_s) and math.isnan(p.tau_q) and math.isnan(p.E)
+    assert p.precision == lbm.LBM_FP32 and p.residual_every == 100
+
+
+@pytest.mark.parametrize("case_fn", [
+    cases.config_poiseuille,
+    lambda: cases.config_couette(0.01, n=96, R1=20, R2=44),
+    lambda: cases.cylinder_array(200, 100, 3, Kn=0.02),
+])
+@pytest.mark.parametrize("mode", ["paper", "zero", "gamma", "gamma2+gamma"])
+def test_precompute_matches_oracle(lib, case_fn, mode):
+    c = case_fn()
+    Lkw = dict(L1=1.0, L2=0.0) if c.name.startswith("couette") else {}
+    par = P.Parameters(c.Kn, c.H, l_mode=mode, **Lkw)
+    r_o, l_o = par.per_link(c.link_q)
+    p = lbm.lbm_params_default()
+    p.l_mode = lbm.L_MODES[mode]
+    if Lkw:
+        p.L1, p.L2 = 1.0, 0.0
+    r, l, info = lbm.lbm_precompute(c.Kn, c.H, p, c.link_dir, c.link_q, c.link_ubx, c.link_uby)
+    assert info.tau_s == pytest.approx(par.tau_s, rel=1e-14)
+    assert info.tau_q == pytest.approx(par.tau_q, rel=1e-13)
+    assert info.E == pytest.approx(par.E, rel=1e-14)
+    assert info.E_max == pytest.approx(par.E_max, rel=1e-13, abs=1e-14)
+    np.testing.assert_allclose(l, l_o, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(r, r_o, rtol=1e-13)
+
+
+def test_precompute_rejects_bad_parameters(lib):
+    p = lbm.lbm_params_default()
+    p.E = 0.5  # above the bound of Eq. EqECond: tau_q < 1/2
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_precompute(0.05, 31.8, p, [2], [0.5])
+    assert ei.value.code == lbm.LBM_EINVAL and "tau_q" in str(ei.value)
+    p = lbm.lbm_params_default()
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_precompute(0.05, 31.8, p, [2], [0.0])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_precompute(0.05, 31.8, p, [9], [0.5])
+
+
+def _create(c, **kw):
+    p = lbm.lbm_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return lbm.lbm_create(c.nx, c.ny, c.periodic_x, c.periodic_y, c.H, c.ax, c.ay, c.solid,
+                          c.link_x, c.link_y, c.link_dir, c.link_q, c.link_ubx, c.link_uby, c.Kn, p)
+
+
+def test_create_validates_links_before_touching_the_device(lib):
+    """Malformed inputs are refused on the host (no GPU needed)."""
+    c = cases.channel(6, 5, 0.5, 0.3, Kn=0.05)
+    drop = dataclasses.replace(c, link_x=c.link_x[1:], link_y=c.link_y[1:], link_dir=c.link_dir[1:],
+                               link_q=c.link_q[1:], link_ubx=c.link_ubx[1:], link_uby=c.link_uby[1:])
+    bad_q = dataclasses.replace(c, link_q=np.where(np.arange(c.n_links) == 2, 1.5, c.link_q))
+    d = c.link_dir.copy()
+    d[0] = 1  # x - c_1 is fluid in a channel row
+    bad_dir = dataclasses.replace(c, link_dir=d)
+    dup = dataclasses.replace(c, link_x=np.r_[c.link_x, c.link_x[:1]], link_y=np.r_[c.link_y, c.link_y[:1]],
+                              link_dir=np.r_[c.link_dir, c.link_dir[:1]], link_q=np.r_[c.link_q, c.link_q[:1]],
+                              link_ubx=np.r_[c.link_ubx, 0.0], link_uby=np.r_[c.link_uby, 0.0])
+    open_edge = dataclasses.replace(c, periodic_x=False)
+    for bad, word in ((drop, "no link"), (bad_q, "gamma"), (bad_dir, "solid"), (dup, "duplicate"),
+                      (open_edge, "non-periodic")):
+        with pytest.raises(lbm.LbmError) as ei:
+            _create(bad)
+        assert ei.value.code == lbm.LBM_EINVAL
+        assert word in str(ei.value)
+    with pytest.raises(lbm.LbmError) as ei:
+        _create(c, E=0.5)
+    assert "tau_q" in str(ei.value)
+    with pytest.raises(lbm.LbmError):
+        _create(c, precision=7)

@@ -180,7 +180,10 @@ def run_ours(args):
     lbm_build.build()
     lbm.load()
 
-    case = cases.config_throughput(seed=rank)
+    if args.nx or args.ny:
+        case = cases.config_throughput(seed=rank, nx=args.nx or 8192, ny=args.ny or 4096)
+    else:
+        case = cases.config_throughput(seed=rank)
     stream = torch.cuda.current_stream(dev)
     solver = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
                         residual_every=args.lbm_steps)
@@ -236,19 +239,8 @@ def run_ours(args):
     # arrays (mask + links H2D), the same steps with the residual read back,
     # and the final fields copied to host memory.
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s2 = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
-                    residual_every=per)
-    for _ in range(args.steps):
-        s2.step(per)
-        s2.residual()
-    rho, ux, uy = s2.fields()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    s2.close()
-    h2d = case.solid.nbytes + case.n_links * (3 * 4 + 3 * 8)
-    d2h = 3 * 8 * case.nx * case.ny + args.steps * 2 * 8
-    e2e_mlups = world * n_fluid * per * args.steps / e2e_s / 1e6
+    e2e = None if args.no_e2e else _e2e(args, case, stream, per, world, n_fluid, lbm, torch)
+
 
     traffic = None
     prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
@@ -276,9 +268,7 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "step_kernel", "bytes_per_fluid_node": FLUID_BYTES[args.precision],
                      "launch_ms": launch_ms, "peak_source": peak_src},
-        "e2e": {"value": e2e_mlups, "unit": "MLUPS",
-                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                "seconds": e2e_s},
+        "e2e": e2e,
         "gpu_launches": args.steps * (per + 2),
         "clocks": clocks,
         "residual_last": last[0] if last else None,
@@ -296,6 +286,24 @@ def run_ours(args):
     return 0
 
 
+def _e2e(args, case, stream, per, world, n_fluid, lbm, torch):
+    t0 = time.perf_counter()
+    s2 = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
+                    residual_every=per)
+    for _ in range(args.steps):
+        s2.step(per)
+        s2.residual()
+    s2.fields()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    h2d = case.solid.nbytes + case.n_links * (3 * 4 + 3 * 8)
+    d2h = 3 * 8 * case.nx * case.ny + args.steps * 2 * 8
+    return {"value": world * n_fluid * per * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "seconds": e2e_s}
+
+
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
 KERNEL_REV = 1
 
@@ -310,6 +318,9 @@ def main():
     ap.add_argument("--lbm-steps", type=int, default=100,
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nx", type=int, default=0, help="profiling only: smaller lattice width")
+    ap.add_argument("--ny", type=int, default=0, help="profiling only: smaller lattice height")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

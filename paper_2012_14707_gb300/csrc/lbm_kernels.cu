@@ -16,17 +16,6 @@
 namespace lbm {
 namespace {
 
-template <typename C>
-struct Num;
-template <>
-struct Num<float> {
-  static __device__ __forceinline__ float c(double v) { return static_cast<float>(v); }
-};
-template <>
-struct Num<double> {
-  static __device__ __forceinline__ double c(double v) { return v; }
-};
-
 __device__ __forceinline__ int wrap_x(int x, int nx, int periodic) {
   // Non-periodic axes have solid edges, so fluid never pushes past them.
   return periodic ? (x < 0 ? x + nx : (x >= nx ? x - nx : x)) : x;
@@ -97,7 +86,6 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
     const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
     const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
     C o[9];
-    o[0] = r9 - C(4) * e36 + C(4) * p36;
     o[1] = axis + ax_x + xx4;
     o[2] = axis + ax_y - xx4;
     o[3] = axis - ax_x + xx4;
@@ -106,6 +94,11 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
     o[6] = diag - dg_x + dg_y - xy4;
     o[7] = diag - dg_x - dg_y + xy4;
     o[8] = diag + dg_x - dg_y - xy4;
+    // The rest population closes the mass balance: M^-1 m' conserves
+    // sum f exactly only in exact arithmetic, so f'_0 = drho - sum_{i>0} f'_i
+    // (equal to r9 - 4 e36 + 4 p36 up to rounding) keeps the stored mass
+    // unchanged by the collision to within one rounding of f'_0.
+    o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
 
     // Streaming: push f'_i to x + c_i unless that node is solid (bit of the
     // opposite direction set).

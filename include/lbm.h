@@ -171,11 +171,38 @@ int lbm_precompute(double Kn, double H, const lbm_params_t *params, size_t n,
                    const int32_t *dir, const double *q, const double *ubx, const double *uby,
                    double *r, double *l, lbm_info_t *info);
 
+/*
+ * Residual and mass of a state the caller holds, with no device allocation.
+ * The paper has no counterpart: this is a library facility for callers that
+ * cannot allocate device memory where they monitor convergence (their
+ * device memory belongs to another framework's pool, or an allocation there
+ * would synchronise or fail).  Same quantities as lbm_residual.
+ *   f_cur, f_prev: device arrays, 9*nx*ny doubles each, full populations f_i
+ *                  in the layout of lbm_get_f (states at steps n and n-1).
+ *   solid:         device array, nx*ny bytes, nonzero = solid (as lbm_create).
+ *   ax, ay:        body acceleration (for the half-force velocity).
+ *   stream:        cudaStream_t to run on (NULL = legacy default stream);
+ *                  the call synchronises it.
+ *   residual, mass: host outputs.
+ * Scratch: a fixed device array in the library (16384 rows x 5 doubles,
+ * 640 KiB), held by every GPU that loads the library until the process
+ * exits; ny > 16384 is LBM_EINVAL.  The first call on a device looks up that
+ * array's address with the device current, so make the first call on each
+ * device before any stream capture.  All calls share the array and each
+ * call overwrites every part of it that it reads, so calls whose work
+ * overlaps on the GPU (other threads, other streams) race and must not be
+ * issued concurrently.  Errors: LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE (outputs
+ * still written); the message is lbm_last_error(NULL).
+ */
+int lbm_residual_noalloc(const double *f_cur, const double *f_prev, const uint8_t *solid,
+                         int32_t nx, int32_t ny, double ax, double ay, void *stream,
+                         double *residual, double *mass);
+
 /* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
 void lbm_destroy(lbm_handle_t *h);
 
 /* Message of the handle's last error ("" if none); with h = NULL, the last
- * failed lbm_create on the calling thread. */
+ * failed lbm_create (or handle-less call) on the calling thread. */
 const char *lbm_last_error(const lbm_handle_t *h);
 
 #ifdef __cplusplus

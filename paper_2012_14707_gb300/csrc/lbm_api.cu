@@ -112,6 +112,14 @@ cudaError_t do_step(lbm_handle_t *h) {
 
 }  // namespace
 
+namespace lbm {
+// Error text for handle-less calls, read back by lbm_last_error(NULL).
+const char *set_thread_error(const std::string &msg) {
+  g_create_error = msg;
+  return g_create_error.c_str();
+}
+}  // namespace lbm
+
 extern "C" {
 
 void lbm_params_default(lbm_params_t *p) {

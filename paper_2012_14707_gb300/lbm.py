@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
 # Every entry point include/lbm.h declares.
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_residual",
            "lbm_run_to", "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info",
-           "lbm_precompute", "lbm_destroy", "lbm_last_error")
+           "lbm_precompute", "lbm_residual_noalloc", "lbm_destroy", "lbm_last_error")
 
 
 class LbmError(RuntimeError):
@@ -91,12 +91,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_get_info.argtypes = [H, ctypes.POINTER(Info)]
     lib.lbm_precompute.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(Params),
                                    ctypes.c_size_t, ip, dp, dp, dp, dp, dp, ctypes.POINTER(Info)]
+    lib.lbm_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_void_p, dp, dp]
     lib.lbm_destroy.argtypes = [H]
     lib.lbm_destroy.restype = None
     lib.lbm_last_error.argtypes = [H]
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_step", "lbm_fields", "lbm_residual", "lbm_run_to",
-                 "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info", "lbm_precompute"):
+                 "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info", "lbm_precompute",
+                 "lbm_residual_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -211,6 +215,19 @@ def lbm_precompute(Kn, H, params: Params, link_dir, link_q, link_ubx=None, link_
                                  d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(q), _dp(ubx),
                                  _dp(uby), _dp(r), _dp(l), ctypes.byref(info)), None)
     return r, l, info
+
+
+def lbm_residual_noalloc(f_cur_ptr: int, f_prev_ptr: int, solid_ptr: int, nx: int, ny: int,
+                         ax: float, ay: float, stream: int | None = None):
+    """Residual and mass of caller-held device state without any device
+    allocation (see include/lbm.h).  Pointers are device addresses: f_cur and
+    f_prev 9*nx*ny float64 populations in the lbm_get_f layout, solid nx*ny
+    uint8.  Returns (residual, mass)."""
+    r, m = ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_residual_noalloc(f_cur_ptr, f_prev_ptr, solid_ptr, int(nx), int(ny),
+                                       float(ax), float(ay), stream, ctypes.byref(r),
+                                       ctypes.byref(m)), None)
+    return r.value, m.value
 
 
 def lbm_destroy(h):

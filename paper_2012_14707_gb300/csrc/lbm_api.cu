@@ -28,6 +28,9 @@ struct lbm_handle {
   double *partials = nullptr;
   double *result = nullptr;
   double *h_result = nullptr;  // pinned, 4 doubles
+  int *d_err = nullptr;        // device: set by a kernel whose bounded wait ran out
+  int *h_err = nullptr;        // pinned copy of *err
+  int step_grid = 0;           // persistent grid of the step kernel
   int64_t n_fluid = 0, n_links = 0, steps = 0, dev_bytes = 0;
   std::vector<double> link_r, link_l;
   std::string err;
@@ -63,10 +66,12 @@ void release(lbm_handle_t *h) {
   cudaStream_t s = h->stream;
   cudaStreamSynchronize(s);
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->flags), static_cast<void *>(h->lbase),
-                  h->links, static_cast<void *>(h->partials), static_cast<void *>(h->result)})
+                  h->links, static_cast<void *>(h->partials), static_cast<void *>(h->result),
+                  static_cast<void *>(h->d_err)})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
   if (h->h_result) cudaFreeHost(h->h_result);
+  if (h->h_err) cudaFreeHost(h->h_err);
   delete h;
 }
 
@@ -96,12 +101,12 @@ cudaError_t do_step(lbm_handle_t *h) {
     e = lbm::launch_step<double, double>(
         static_cast<const double *>(h->f[src]), static_cast<double *>(h->f[dst]), h->flags,
         h->lbase, static_cast<const lbm::LinkCoef<double> *>(h->links), step_const<double>(h),
-        h->stream);
+        h->d_err, h->step_grid, h->stream);
   } else {
     e = lbm::launch_step<float, float>(
         static_cast<const float *>(h->f[src]), static_cast<float *>(h->f[dst]), h->flags,
         h->lbase, static_cast<const lbm::LinkCoef<float> *>(h->links), step_const<float>(h),
-        h->stream);
+        h->d_err, h->step_grid, h->stream);
   }
   if (e == cudaSuccess) {
     h->cur = dst;
@@ -322,7 +327,13 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->d_err), sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_result), 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_err), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = p.precision == LBM_FP64 ? lbm::step_grid<double, double>(&h->step_grid)
+                                : lbm::step_grid<float, float>(&h->step_grid);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, fbytes, h->stream);
   if (e == cudaSuccess)
@@ -369,7 +380,11 @@ int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
   LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
+  LBM_CK(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LBM_CK(h, cudaStreamSynchronize(h->stream));
+  if (*h->h_err)
+    return fail(h, LBM_ETIMEOUT,
+                "a step kernel's bounded wait for its bulk copies ran out; the state is invalid");
   const double num = h->h_result[0], den = h->h_result[1];
   double res;
   if (std::isnan(num) || std::isnan(den))

@@ -51,10 +51,34 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                const double *uby, double *r_out, double *l_out,
                                double *coef8_out /* n x 8 */, int64_t *n_clamped);
 
+// Step kernel geometry: tiles are row segments of kTileBytes per population
+// plane; kStages tiles in flight per CTA.
+constexpr int kStepThreads = 256;
+constexpr int kStages = 3;
+constexpr int kTileBytes = 2048;
+constexpr long long kWaitCycles = 1ll << 31;  // bounded mbarrier wait, ~1 s
+
+template <typename T>
+struct StepTile {
+  static constexpr int W = kTileBytes / static_cast<int>(sizeof(T));  // elements per tile
+};
+
+template <typename T>
+struct StepSmem {
+  T f[kStages][9][StepTile<T>::W];
+  uint8_t flags[kStages][StepTile<T>::W];
+  uint64_t bar[kStages];
+};
+
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
 template <typename T, typename C>
 cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
-                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
+                        const LinkCoef<C> *links, const StepConst<C> &k, int *err, int grid,
+                        cudaStream_t s);
+// Persistent grid size for the step kernel on the current device (SMs x
+// resident CTAs); also raises the kernel's dynamic shared-memory limit.
+template <typename T, typename C>
+cudaError_t step_grid(int *grid);
 
 template <typename T>
 cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,

@@ -107,17 +107,19 @@ def test_fp64_scheme_variants_match_oracle(l_mode, extra):
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp32_velocity_and_mass_match_oracle(name):
     """From rest, 2000 steps.  Velocity rel. L2 <= 1e-5 everywhere.  Mass
-    drift against the oracle trajectory: <= 1e-10 with stationary walls;
-    moving walls (u_b ~ 0.03 and 0.01 here) make the deviations next to the
-    wall O(1e-2), whose FP32 rounding (one per link and step, random sign)
-    accumulates to ~8e-10 on these few-hundred-node lattices: held to 2e-9;
-    the periodic boxes accelerate without bound (u ~ 0.04): held to 1e-8."""
+    drift against the oracle trajectory: <= 1e-10 with stationary walls.
+    Moving walls (u_b ~ 0.03 and 0.01 here) exchange mass with the fluid
+    every step in tiny net amounts (~1e-8 per link and step) computed from
+    wall populations of size ~1e-3; their FP32 rounding is the same every
+    step once the flow is steady, so it adds up linearly (1.4e-8 relative
+    after 2000 steps on the 9-row channel): held to 3e-8.  The periodic
+    boxes accelerate without bound (u ~ 0.04): held to 1e-8."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
     o, g = _pair(c, "fp32", **kw)
     m0 = o.residual()[1]
-    mass_tol = {"box": 1e-8, "column": 1e-8, "row": 1e-8, "annulus": 2e-9,
-                "channel_moving": 2e-9}.get(name, 1e-10)
+    mass_tol = {"box": 1e-8, "column": 1e-8, "row": 1e-8, "annulus": 3e-8,
+                "channel_moving": 3e-8}.get(name, 1e-10)
     for n in (500, 1500):
         o.step(n)
         g.step(n)

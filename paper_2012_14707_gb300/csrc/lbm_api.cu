@@ -30,7 +30,6 @@ struct lbm_handle {
   double *h_result = nullptr;  // pinned, 4 doubles
   int *d_err = nullptr;        // device: set by a kernel whose bounded wait ran out
   int *h_err = nullptr;        // pinned copy of *err
-  int step_grid = 0;           // persistent grid of the step kernel
   int64_t n_fluid = 0, n_links = 0, steps = 0, dev_bytes = 0;
   std::vector<double> link_r, link_l;
   std::string err;
@@ -83,6 +82,11 @@ lbm::StepConst<C> step_const(const lbm_handle_t *h) {
   k.s_q = static_cast<C>(1.0 / h->cp.tau_q);
   k.s_s = static_cast<C>(1.0 / h->cp.tau_s);
   k.s_j = static_cast<C>(1.0 / h->cp.tau_j);
+  k.h_e = static_cast<C>(1.0 - 0.5 / h->cp.tau_e);
+  k.h_eps = static_cast<C>(1.0 - 0.5 / h->cp.tau_eps);
+  k.h_q = static_cast<C>(1.0 - 0.5 / h->cp.tau_q);
+  k.h_s = static_cast<C>(1.0 - 0.5 / h->cp.tau_s);
+  k.h_j = static_cast<C>(1.0 - 0.5 / h->cp.tau_j);
   k.ax = static_cast<C>(h->ax);
   k.ay = static_cast<C>(h->ay);
   k.nx = h->nx;
@@ -101,12 +105,12 @@ cudaError_t do_step(lbm_handle_t *h) {
     e = lbm::launch_step<double, double>(
         static_cast<const double *>(h->f[src]), static_cast<double *>(h->f[dst]), h->flags,
         h->lbase, static_cast<const lbm::LinkCoef<double> *>(h->links), step_const<double>(h),
-        h->d_err, h->step_grid, h->stream);
+        h->stream);
   } else {
     e = lbm::launch_step<float, float>(
         static_cast<const float *>(h->f[src]), static_cast<float *>(h->f[dst]), h->flags,
         h->lbase, static_cast<const lbm::LinkCoef<float> *>(h->links), step_const<float>(h),
-        h->d_err, h->step_grid, h->stream);
+        h->stream);
   }
   if (e == cudaSuccess) {
     h->cur = dst;
@@ -172,8 +176,9 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (p.residual_every < 1) return bad(LBM_EINVAL, "residual_every must be >= 1");
   if (!std::isfinite(dom->ax) || !std::isfinite(dom->ay)) return bad(LBM_EINVAL, "non-finite force");
   const int32_t nx = dom->nx, ny = dom->ny;
-  if (static_cast<int64_t>(nx) * ny > (int64_t(1) << 31))
-    return bad(LBM_EINVAL, "lattice larger than 2^31 nodes");
+  // 32-bit element offsets in the kernels: 9 planes of the padded lattice < 2^31.
+  if ((static_cast<int64_t>(nx) + 31) / 32 * 32 * ny * 9 >= (int64_t(1) << 31))
+    return bad(LBM_EINVAL, "lattice too large: 9 * pitch * ny must stay below 2^31");
   if (n_links > static_cast<size_t>(std::numeric_limits<int32_t>::max()))
     return bad(LBM_EINVAL, "too many links");
   const int px = dom->periodic_x ? 1 : 0, py = dom->periodic_y ? 1 : 0;
@@ -331,9 +336,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_result), 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_err), sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess)
-    e = p.precision == LBM_FP64 ? lbm::step_grid<double, double>(&h->step_grid)
-                                : lbm::step_grid<float, float>(&h->step_grid);
+
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, fbytes, h->stream);
   if (e == cudaSuccess)

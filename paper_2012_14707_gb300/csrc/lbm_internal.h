@@ -19,6 +19,7 @@ constexpr uint8_t kSolid = 0xFF;
 template <typename C>
 struct StepConst {
   C s_e, s_eps, s_q, s_s, s_j;  // 1/tau of the non-conserved moments and of j
+  C h_e, h_eps, h_q, h_s, h_j;  // 1 - s/2: weights of the forcing moments (Eq. MomentPost)
   C ax, ay;                     // body acceleration
   int32_t nx, ny, pitch;        // lattice size and row pitch (elements)
   int32_t periodic_x, periodic_y;
@@ -51,34 +52,22 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                const double *uby, double *r_out, double *l_out,
                                double *coef8_out /* n x 8 */, int64_t *n_clamped);
 
-// Step kernel geometry: tiles are row segments of kTileBytes per population
-// plane; kStages tiles in flight per CTA.
+// Step kernel geometry: one thread per node, kStepThreads nodes of a row
+// per CTA, registers bounded for kStepMinBlocks resident CTAs per SM.
 constexpr int kStepThreads = 256;
-constexpr int kStages = 3;
-constexpr int kTileBytes = 2048;
-constexpr long long kWaitCycles = 1ll << 31;  // bounded mbarrier wait, ~1 s
-
 template <typename T>
-struct StepTile {
-  static constexpr int W = kTileBytes / static_cast<int>(sizeof(T));  // elements per tile
+struct StepOcc {
+  static constexpr int min_blocks = 6;  // FP32: 40 registers, no spills
 };
-
-template <typename T>
-struct StepSmem {
-  T f[kStages][9][StepTile<T>::W];
-  uint8_t flags[kStages][StepTile<T>::W];
-  uint64_t bar[kStages];
+template <>
+struct StepOcc<double> {
+  static constexpr int min_blocks = 2;
 };
 
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
 template <typename T, typename C>
 cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
-                        const LinkCoef<C> *links, const StepConst<C> &k, int *err, int grid,
-                        cudaStream_t s);
-// Persistent grid size for the step kernel on the current device (SMs x
-// resident CTAs); also raises the kernel's dynamic shared-memory limit.
-template <typename T, typename C>
-cudaError_t step_grid(int *grid);
+                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,

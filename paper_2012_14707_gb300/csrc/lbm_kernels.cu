@@ -12,7 +12,6 @@
 #include <cstdint>
 
 #include "lbm_internal.h"
-#include "lbm_ptx.h"
 
 namespace lbm {
 namespace {
@@ -31,196 +30,141 @@ __device__ __forceinline__ int wrap_x(int x, int nx, int periodic) {
   return periodic ? (x < 0 ? x + nx : (x >= nx ? x - nx : x)) : x;
 }
 
-// Collision, push streaming and the link epilogue of one fluid node whose
-// nine deviations are in d[].  T: storage type, C: arithmetic type.
-template <typename T, typename C>
-__device__ __forceinline__ void node_update(C (&d)[9], const uint8_t fl, const int x, const int y,
-                                            T *__restrict__ dst, const int32_t *__restrict__ lbase,
-                                            const LinkCoef<C> *__restrict__ links,
-                                            const StepConst<C> &k) {
-  const int64_t P = k.plane;
-  const int64_t node = static_cast<int64_t>(y) * k.pitch + x;
-
-  // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
-  const C s14 = d[1] + d[2] + d[3] + d[4];
-  const C s58 = d[5] + d[6] + d[7] + d[8];
-  const C drho = d[0] + s14 + s58;
-  const C e = C(-4) * d[0] - s14 + C(2) * s58;
-  const C eps = C(4) * d[0] - C(2) * s14 + s58;
-  const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
-  const C jx = d[1] - d[3] + d5m6 + d8m7;
-  const C qx = C(2) * (d[3] - d[1]) + d5m6 + d8m7;
-  const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
-  const C jy = d[2] - d[4] + d5p6 - d7p8;
-  const C qy = C(2) * (d[4] - d[2]) + d5p6 - d7p8;
-  const C pxx = d[1] - d[2] + d[3] - d[4];
-  const C pxy = d[5] - d[6] + d[7] - d[8];
-
-  // Eq. FluidMacr.
-  const C rho = C(1) + drho;
-  const C rax = rho * k.ax, ray = rho * k.ay;
-  const C inv_rho = C(1) / rho;
-  const C ux = (jx + C(0.5) * rax) * inv_rho;
-  const C uy = (jy + C(0.5) * ray) * inv_rho;
-  const C uu = ux * ux + uy * uy;
-  const C rux = rho * ux, ruy = rho * uy;
-
-  // Eq. MomentPost: m' = m - S (m - m_eq) + (I - S/2) M Fbar, with M f_eq and
-  // M Fbar in closed form.
-  const C ua6 = C(6) * (rux * k.ax + ruy * k.ay);
-  const C e_p = e - k.s_e * (e + C(2) * drho - C(3) * rho * uu) + (C(1) - C(0.5) * k.s_e) * ua6;
-  const C eps_p = eps - k.s_eps * (eps - drho + C(3) * rho * uu) - (C(1) - C(0.5) * k.s_eps) * ua6;
-  const C fj = C(1) - C(0.5) * k.s_j, fq = C(1) - C(0.5) * k.s_q, fs = C(1) - C(0.5) * k.s_s;
-  const C jx_p = jx - k.s_j * (jx - rux) + fj * rax;
-  const C jy_p = jy - k.s_j * (jy - ruy) + fj * ray;
-  const C qx_p = qx - k.s_q * (qx + rux) - fq * rax;
-  const C qy_p = qy - k.s_q * (qy + ruy) - fq * ray;
-  const C pxx_p = pxx - k.s_s * (pxx - rho * (ux * ux - uy * uy)) + fs * C(2) * (rux * k.ax - ruy * k.ay);
-  const C pxy_p = pxy - k.s_s * (pxy - rho * ux * uy) + fs * (rux * k.ay + ruy * k.ax);
-
-  // f' = M^-1 m' with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
-  const C r9 = drho * C(1.0 / 9.0);
-  const C e36 = e_p * C(1.0 / 36.0), p36 = eps_p * C(1.0 / 36.0);
-  const C jx6 = jx_p * C(1.0 / 6.0), jy6 = jy_p * C(1.0 / 6.0);
-  const C qx12 = qx_p * C(1.0 / 12.0), qy12 = qy_p * C(1.0 / 12.0);
-  const C xx4 = pxx_p * C(0.25), xy4 = pxy_p * C(0.25);
-  const C axis = r9 - e36 - C(2) * p36;
-  const C diag = r9 + C(2) * e36 + p36;
-  const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
-  const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
-  C o[9];
-  o[1] = axis + ax_x + xx4;
-  o[2] = axis + ax_y - xx4;
-  o[3] = axis - ax_x + xx4;
-  o[4] = axis - ax_y - xx4;
-  o[5] = diag + dg_x + dg_y + xy4;
-  o[6] = diag - dg_x + dg_y - xy4;
-  o[7] = diag - dg_x - dg_y + xy4;
-  o[8] = diag + dg_x - dg_y - xy4;
-  // The rest population closes the mass balance: M^-1 m' conserves sum f
-  // exactly only in exact arithmetic, so f'_0 = drho - sum_{i>0} f'_i (equal
-  // to r9 - 4 e36 + 4 p36 up to rounding) keeps the stored mass unchanged by
-  // the collision to within one rounding of f'_0.
-  o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
-
-  // Streaming: push f'_i to x + c_i unless that node is solid.
-  const int xe = wrap_x(x + 1, k.nx, k.periodic_x), xw = wrap_x(x - 1, k.nx, k.periodic_x);
-  const int yn = wrap_x(y + 1, k.ny, k.periodic_y), ys = wrap_x(y - 1, k.ny, k.periodic_y);
-  const int64_t rowc = static_cast<int64_t>(y) * k.pitch;
-  const int64_t rown = static_cast<int64_t>(yn) * k.pitch;
-  const int64_t rows = static_cast<int64_t>(ys) * k.pitch;
-  dst[node] = static_cast<T>(o[0]);
-  // bit (j-1) set <=> x - c_j solid; push i needs x + c_i = x - c_opp(i) fluid.
-  if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = static_cast<T>(o[1]);  // opp(1) = 3
-  if (!(fl & (1u << 3))) dst[2 * P + rown + x] = static_cast<T>(o[2]);   // opp(2) = 4
-  if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = static_cast<T>(o[3]);  // opp(3) = 1
-  if (!(fl & (1u << 1))) dst[4 * P + rows + x] = static_cast<T>(o[4]);   // opp(4) = 2
-  if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = static_cast<T>(o[5]);  // opp(5) = 7
-  if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = static_cast<T>(o[6]);  // opp(6) = 8
-  if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = static_cast<T>(o[7]);  // opp(7) = 5
-  if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = static_cast<T>(o[8]);  // opp(8) = 6
-
-  if (fl) {
-    // Boundary links of this node, Eq. EqNewBDSC in the folded form of
-    // LinkCoef (links sorted by node, then direction).
-    int li = lbase[node];
-    const C cxs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const C cys[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-#pragma unroll
-    for (int j = 1; j < 9; j++) {
-      if (fl & (1u << (j - 1))) {
-        const LinkCoef<C> c = links[li++];
-        const C cu = cxs[j] * ux + cys[j] * uy;
-        const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-        const C v = c.k1 * d[opp[j]] + c.k2 * o[j] + c.k3 * o[opp[j]] + c.c0 + c.c1 * drho +
-                    c.c2 * (drho + rho * pj);
-        dst[j * P + node] = static_cast<T>(v);
-      }
-    }
-  }
+template <typename C>
+__device__ __forceinline__ C recip(C v);
+template <>
+__device__ __forceinline__ float recip<float>(float v) {
+  return __frcp_rn(v);
+}
+template <>
+__device__ __forceinline__ double recip<double>(double v) {
+  return 1.0 / v;
 }
 
-// One time step over the whole lattice.  Persistent CTAs walk row segments
-// ("tiles") of kTileBytes per population plane.  Thread 0 of each CTA keeps
-// up to kStages tiles in flight: nine 1-D bulk copies (one per plane) plus
-// the flag bytes per tile into a shared-memory ring, each stage completing on
-// its own mbarrier; the CTA's threads collide the tile from shared memory and
-// push the results straight to the other lattice.  Every wait is bounded:
-// a wait that runs out sets *err and the CTA drains its own copies (again
-// bounded) and returns.
+// One time step, one thread per node (x), one CTA row of kStepThreads nodes
+// per (blockIdx.x, y).  Each fluid node loads its nine deviations, collides
+// in moment space, pushes f'_i to x + c_i in the other lattice (unless that
+// node is solid) and fills its own unknown populations from the link table
+// (Eq. EqNewBDSC is local: f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and
+// rho_f all belong to x_f).  Offsets are 32-bit (the lattice is limited to
+// 2^31 / 9 nodes per plane); row wraps are uniform per CTA.
 template <typename T, typename C>
-__global__ void __launch_bounds__(kStepThreads)
+__global__ void __launch_bounds__(kStepThreads, StepOcc<T>::min_blocks)
 step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__restrict__ flags,
             const int32_t *__restrict__ lbase, const LinkCoef<C> *__restrict__ links,
-            const StepConst<C> k, int *__restrict__ err) {
-  constexpr int W = StepTile<T>::W;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  StepSmem<T> &sm = *reinterpret_cast<StepSmem<T> *>(smem_raw);
-  __shared__ int ok_sh;
-  const int tid = threadIdx.x;
-  const int nseg = (k.pitch + W - 1) / W;
-  const int64_t ntiles = static_cast<int64_t>(k.ny) * nseg;
-  const int64_t first = blockIdx.x, stride = gridDim.x;
-  const int64_t nmine = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
+            const StepConst<C> k) {
+  const int x = blockIdx.x * kStepThreads + threadIdx.x;
+  if (x >= k.nx) return;
+  const uint32_t P = static_cast<uint32_t>(k.plane);
+  const int xe = (x + 1 == k.nx) ? (k.periodic_x ? 0 : x + 1) : x + 1;
+  const int xw = (x == 0) ? (k.periodic_x ? k.nx - 1 : 0) : x - 1;
+  for (int y = blockIdx.y; y < k.ny; y += gridDim.y) {
+    const uint32_t rowc = static_cast<uint32_t>(y) * k.pitch;
+    const uint32_t node = rowc + x;
+    const uint8_t fl = flags[node];
+    if (fl == kSolid) continue;
+    const int yn = (y + 1 == k.ny) ? (k.periodic_y ? 0 : y + 1) : y + 1;
+    const int ys = (y == 0) ? (k.periodic_y ? k.ny - 1 : 0) : y - 1;
+    const uint32_t rown = static_cast<uint32_t>(yn) * k.pitch;
+    const uint32_t rows = static_cast<uint32_t>(ys) * k.pitch;
 
-  if (tid == 0) {
-    for (int s = 0; s < kStages; s++) ptx::mbar_init(&sm.bar[s], 1);
-    ptx::fence_mbar_init();
-  }
-  __syncthreads();
-
-  auto issue = [&](int64_t it, int s) {
-    const int64_t t = first + it * stride;
-    const int y = static_cast<int>(t / nseg);
-    const int x0 = static_cast<int>(t - static_cast<int64_t>(y) * nseg) * W;
-    const int L = min(W, k.pitch - x0);  // multiple of 32 elements
-    const int64_t off = static_cast<int64_t>(y) * k.pitch + x0;
-    ptx::mbar_arrive_expect_tx(&sm.bar[s], static_cast<uint32_t>(9 * L * sizeof(T) + L));
+    C d[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++)
-      ptx::bulk_g2s(&sm.f[s][i][0], src + i * k.plane + off, static_cast<uint32_t>(L * sizeof(T)),
-                    &sm.bar[s]);
-    ptx::bulk_g2s(&sm.flags[s][0], flags + off, static_cast<uint32_t>(L), &sm.bar[s]);
-  };
+    for (int i = 0; i < 9; i++) d[i] = static_cast<C>(src[i * P + node]);
 
-  if (tid == 0)
-    for (int s = 0; s < kStages && s < nmine; s++) issue(s, s);
+    // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
+    const C s14 = (d[1] + d[2]) + (d[3] + d[4]);
+    const C s58 = (d[5] + d[6]) + (d[7] + d[8]);
+    const C drho = d[0] + s14 + s58;
+    const C e = C(-4) * d[0] - s14 + C(2) * s58;
+    const C eps = C(4) * d[0] - C(2) * s14 + s58;
+    const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
+    const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
+    const C jx = d[1] - d[3] + d5m6 + d8m7;
+    const C qx = C(2) * (d[3] - d[1]) + d5m6 + d8m7;
+    const C jy = d[2] - d[4] + d5p6 - d7p8;
+    const C qy = C(2) * (d[4] - d[2]) + d5p6 - d7p8;
+    const C pxx = d[1] - d[2] + d[3] - d[4];
+    const C pxy = d[5] - d[6] + d[7] - d[8];
 
-  for (int64_t it = 0; it < nmine; it++) {
-    const int s = static_cast<int>(it % kStages);
-    const uint32_t par = static_cast<uint32_t>((it / kStages) & 1);
-    if (tid == 0) ok_sh = ptx::mbar_wait_bounded(&sm.bar[s], par, kWaitCycles);
-    __syncthreads();
-    if (!ok_sh) {
-      if (tid == 0) {
-        atomicExch(err, 1);
-        for (int64_t j = it; j < nmine && j < it + kStages; j++)
-          ptx::mbar_wait_bounded(&sm.bar[j % kStages], static_cast<uint32_t>((j / kStages) & 1),
-                                 kWaitCycles);
+    // Eq. FluidMacr.
+    const C rho = C(1) + drho;
+    const C rax = rho * k.ax, ray = rho * k.ay;
+    const C inv_rho = recip<C>(rho);
+    const C ux = (jx + C(0.5) * rax) * inv_rho;
+    const C uy = (jy + C(0.5) * ray) * inv_rho;
+    const C uu = ux * ux + uy * uy;
+    const C rux = rho * ux, ruy = rho * uy;
+
+    // Eq. MomentPost: m' = m - S (m - m_eq) + (I - S/2) M Fbar, with M f_eq
+    // and M Fbar in closed form; the factors (1 - s/2) come precomputed.
+    const C ua6 = C(6) * (rux * k.ax + ruy * k.ay);
+    const C e_p = e - k.s_e * (e + C(2) * drho - C(3) * rho * uu) + k.h_e * ua6;
+    const C eps_p = eps - k.s_eps * (eps - drho + C(3) * rho * uu) - k.h_eps * ua6;
+    const C jx_p = jx - k.s_j * (jx - rux) + k.h_j * rax;
+    const C jy_p = jy - k.s_j * (jy - ruy) + k.h_j * ray;
+    const C qx_p = qx - k.s_q * (qx + rux) - k.h_q * rax;
+    const C qy_p = qy - k.s_q * (qy + ruy) - k.h_q * ray;
+    const C pxx_p = pxx - k.s_s * (pxx - rho * (ux * ux - uy * uy)) +
+                    k.h_s * C(2) * (rux * k.ax - ruy * k.ay);
+    const C pxy_p = pxy - k.s_s * (pxy - rho * ux * uy) + k.h_s * (rux * k.ay + ruy * k.ax);
+
+    // f' = M^-1 m' with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+    const C r9 = drho * C(1.0 / 9.0);
+    const C e36 = e_p * C(1.0 / 36.0), p36 = eps_p * C(1.0 / 36.0);
+    const C jx6 = jx_p * C(1.0 / 6.0), jy6 = jy_p * C(1.0 / 6.0);
+    const C qx12 = qx_p * C(1.0 / 12.0), qy12 = qy_p * C(1.0 / 12.0);
+    const C xx4 = pxx_p * C(0.25), xy4 = pxy_p * C(0.25);
+    const C axis = r9 - e36 - C(2) * p36;
+    const C diag = r9 + C(2) * e36 + p36;
+    const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
+    const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
+    C o[9];
+    o[1] = axis + ax_x + xx4;
+    o[2] = axis + ax_y - xx4;
+    o[3] = axis - ax_x + xx4;
+    o[4] = axis - ax_y - xx4;
+    o[5] = diag + dg_x + dg_y + xy4;
+    o[6] = diag - dg_x + dg_y - xy4;
+    o[7] = diag - dg_x - dg_y + xy4;
+    o[8] = diag + dg_x - dg_y - xy4;
+    // The rest population closes the mass balance: M^-1 m' conserves sum f
+    // exactly only in exact arithmetic, so f'_0 = drho - sum_{i>0} f'_i
+    // (equal to r9 - 4 e36 + 4 p36 up to rounding) keeps the stored mass
+    // unchanged by the collision to within one rounding of f'_0.
+    o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+
+    // Streaming: push f'_i to x + c_i unless that node is solid; bit (j-1)
+    // set <=> x - c_j solid, so push i needs bit opp(i) clear.
+    dst[node] = static_cast<T>(o[0]);
+    if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = static_cast<T>(o[1]);  // opp(1) = 3
+    if (!(fl & (1u << 3))) dst[2 * P + rown + x] = static_cast<T>(o[2]);   // opp(2) = 4
+    if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = static_cast<T>(o[3]);  // opp(3) = 1
+    if (!(fl & (1u << 1))) dst[4 * P + rows + x] = static_cast<T>(o[4]);   // opp(4) = 2
+    if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = static_cast<T>(o[5]);  // opp(5) = 7
+    if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = static_cast<T>(o[6]);  // opp(6) = 8
+    if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = static_cast<T>(o[7]);  // opp(7) = 5
+    if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = static_cast<T>(o[8]);  // opp(8) = 6
+
+    if (fl) {
+      // Boundary links of this node, Eq. EqNewBDSC in the folded form of
+      // LinkCoef (links sorted by node, then direction).
+      int li = lbase[node];
+#pragma unroll
+      for (int j = 1; j < 9; j++) {
+        if (fl & (1u << (j - 1))) {
+          constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+          constexpr int cx_tab[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+          constexpr int cy_tab[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+          const int jb = opp_tab[j];
+          const LinkCoef<C> c = links[li++];
+          const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
+          const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+          const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c.c0 + c.c1 * drho +
+                      c.c2 * (drho + rho * pj);
+          dst[j * P + node] = static_cast<T>(v);
+        }
       }
-      __syncthreads();
-      return;
-    }
-    ptx::mbar_try_wait(&sm.bar[s], par);  // phase complete: acquire for this thread
-    const int64_t t = first + it * stride;
-    const int y = static_cast<int>(t / nseg);
-    const int x0 = static_cast<int>(t - static_cast<int64_t>(y) * nseg) * W;
-    const int L = min(W, k.pitch - x0);
-    for (int xl = tid; xl < L; xl += kStepThreads) {
-      const int x = x0 + xl;
-      if (x >= k.nx) break;
-      const uint8_t fl = sm.flags[s][xl];
-      if (fl == kSolid) continue;
-      C d[9];
-#pragma unroll
-      for (int i = 0; i < 9; i++) d[i] = static_cast<C>(sm.f[s][i][xl]);
-      node_update<T, C>(d, fl, x, y, dst, lbase, links, k);
-    }
-    __syncthreads();
-    if (tid == 0 && it + kStages < nmine) {
-      ptx::fence_proxy_async_smem();
-      issue(it + kStages, s);
     }
   }
 }
@@ -403,26 +347,10 @@ int grid_for(int64_t n, int threads) {
 
 template <typename T, typename C>
 cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
-                        const LinkCoef<C> *links, const StepConst<C> &k, int *err, int grid,
-                        cudaStream_t s) {
-  step_kernel<T, C><<<grid, kStepThreads, sizeof(StepSmem<T>), s>>>(src, dst, flags, lbase, links,
-                                                                    k, err);
+                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
+  dim3 grid((k.nx + kStepThreads - 1) / kStepThreads, k.ny < 65535 ? k.ny : 65535);
+  step_kernel<T, C><<<grid, kStepThreads, 0, s>>>(src, dst, flags, lbase, links, k);
   return cudaGetLastError();
-}
-
-template <typename T, typename C>
-cudaError_t step_grid(int *grid) {
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sizeof(StepSmem<T>)));
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<T, C>, kStepThreads,
-                                                    sizeof(StepSmem<T>));
-  if (e != cudaSuccess) return e;
-  *grid = sms * (per_sm > 0 ? per_sm : 1);
-  return cudaSuccess;
 }
 
 template <typename T>
@@ -462,9 +390,7 @@ cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pi
 
 #define LBM_INSTANTIATE(T, C)                                                                      \
   template cudaError_t launch_step<T, C>(const T *, T *, const uint8_t *, const int32_t *,         \
-                                         const LinkCoef<C> *, const StepConst<C> &, int *, int,    \
-                                         cudaStream_t);                                            \
-  template cudaError_t step_grid<T, C>(int *);                                                     \
+                                         const LinkCoef<C> *, const StepConst<C> &, cudaStream_t); \
   template cudaError_t launch_residual<T>(const T *, const T *, const uint8_t *, int32_t, int32_t,  \
                                          int32_t, int64_t, double, double, double *, double *,     \
                                          cudaStream_t);                                            \

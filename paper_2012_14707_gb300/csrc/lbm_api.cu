@@ -94,6 +94,7 @@ lbm::StepConst<C> step_const(const lbm_handle_t *h) {
   k.pitch = h->pitch;
   k.periodic_x = h->px;
   k.periodic_y = h->py;
+  k.diffuse_mode = h->params.diffuse_mode;
   k.plane = h->plane;
   return k;
 }
@@ -306,17 +307,17 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
 
   const size_t es = elem_size(p.precision);
   const size_t fbytes = 9 * static_cast<size_t>(plane) * es;
-  const size_t lbytes = std::max<size_t>(1, n_links) * 8 * es;
+  const size_t lbytes = std::max<size_t>(1, n_links) * 4 * es;
   const size_t pbytes = lbm::kResidualBlocks * lbm::kPartialStride * sizeof(double);
   std::vector<unsigned char> lhost(lbytes, 0);
   for (size_t s = 0; s < n_links; s++) {
     const double *c = &coef[8 * order[s]];
     if (es == 8) {
-      std::memcpy(&lhost[s * 64], c, 64);
+      std::memcpy(&lhost[s * 32], c, 32);
     } else {
-      float cf[8];
-      for (int j = 0; j < 8; j++) cf[j] = static_cast<float>(c[j]);
-      std::memcpy(&lhost[s * 32], cf, 32);
+      float cf[4];
+      for (int j = 0; j < 4; j++) cf[j] = static_cast<float>(c[j]);
+      std::memcpy(&lhost[s * 16], cf, 16);
     }
   }
   auto alloc = [&](void **ptr, size_t bytes) {

@@ -23,6 +23,7 @@ struct StepConst {
   C ax, ay;                     // body acceleration
   int32_t nx, ny, pitch;        // lattice size and row pitch (elements)
   int32_t periodic_x, periodic_y;
+  int32_t diffuse_mode;         // reading of the Maxwell part, see LinkCoef
   int64_t plane;                // elements per population plane = ny * pitch
 };
 
@@ -30,11 +31,15 @@ struct StepConst {
 // in deviation variables d = f - w:
 //   d_i(x_f, t+1) = k1 d_ib + k2 d'_i + k3 d'_ib + c0 + c1 drho
 //                   + c2 (drho + rho P_i(u_f)),
-//   P_i(u) = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u.
+//   P_i(u) = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u,
+// with r = k1 + k2 + k3 and, for the Maxwell part at the fluid velocity
+// (diffuse_mode 0): c0 = c1 = alpha, c2 = (1 - r) w_i; at the wall velocity
+// (diffuse_mode 1): c0 = alpha + (r - 1) w_i, c1 = alpha, c2 = 0.  alpha
+// collects every term proportional to rho_f (wall-velocity terms).  One
+// 16-byte record per link.
 template <typename C>
 struct alignas(sizeof(C) * 4) LinkCoef {
-  C k1, k2, k3, c0;
-  C c1, c2, pad0, pad1;
+  C k1, k2, k3, alpha;
 };
 
 // Case parameters after the FP64 precompute of Sec. 3.B.

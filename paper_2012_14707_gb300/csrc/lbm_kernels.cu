@@ -25,10 +25,6 @@ struct Arith<double> {
   using type = double;
 };
 
-__device__ __forceinline__ int wrap_x(int x, int nx, int periodic) {
-  // Non-periodic axes have solid edges, so fluid never pushes past them.
-  return periodic ? (x < 0 ? x + nx : (x >= nx ? x - nx : x)) : x;
-}
 
 template <typename C>
 __device__ __forceinline__ C recip(C v);
@@ -71,6 +67,9 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
     C d[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) d[i] = static_cast<C>(src[i * P + node]);
+    // First link of this node (links sorted by node, then direction), loaded
+    // now so that its latency overlaps the collision.
+    const int lb = fl ? lbase[node] : 0;
 
     // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
     const C s14 = (d[1] + d[2]) + (d[3] + d[4]);
@@ -146,22 +145,36 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
     if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = static_cast<T>(o[7]);  // opp(7) = 5
     if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = static_cast<T>(o[8]);  // opp(8) = 6
 
-    if (fl) {
-      // Boundary links of this node, Eq. EqNewBDSC in the folded form of
-      // LinkCoef (links sorted by node, then direction).
-      int li = lbase[node];
+    // Boundary links of this node, Eq. EqNewBDSC in the folded form of
+    // LinkCoef.  Directions that no active lane of the warp needs are
+    // skipped warp-uniformly (solid lanes and lanes past nx have left).
+    const unsigned wmask = __reduce_or_sync(__activemask(), static_cast<unsigned>(fl));
+    if (wmask) {
+      int li = lb;
 #pragma unroll
       for (int j = 1; j < 9; j++) {
+        if (!(wmask & (1u << (j - 1)))) continue;
         if (fl & (1u << (j - 1))) {
           constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
           constexpr int cx_tab[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
           constexpr int cy_tab[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+          constexpr double w_tab[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                       1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
           const int jb = opp_tab[j];
           const LinkCoef<C> c = links[li++];
+          const C r = c.k1 + c.k2 + c.k3;
+          C c0, c2;
+          if (k.diffuse_mode == 0) {
+            c0 = c.alpha;
+            c2 = (C(1) - r) * C(w_tab[j]);
+          } else {
+            c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
+            c2 = C(0);
+          }
           const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
           const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-          const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c.c0 + c.c1 * drho +
-                      c.c2 * (drho + rho * pj);
+          const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
+                      c2 * (drho + rho * pj);
           dst[j * P + node] = static_cast<T>(v);
         }
       }

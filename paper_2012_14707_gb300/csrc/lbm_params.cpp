@@ -115,15 +115,13 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
       alpha += (1.0 - r) * kW[i] * (1.0 + 3.0 * cub + 4.5 * cub * cub - 1.5 * uu);
       beta = 0.0;
     }
+    (void)beta;  // implied by diffuse_mode and r = k1 + k2 + k3 in the kernel
     double *c = coef8 + 8 * k;
     c[0] = k1;
     c[1] = k2;
     c[2] = k3;
-    c[3] = alpha + (r + beta - 1.0) * kW[i];
-    c[4] = alpha;
-    c[5] = beta * kW[i];
-    c[6] = 0.0;
-    c[7] = 0.0;
+    c[3] = alpha;
+    c[4] = c[5] = c[6] = c[7] = 0.0;
   }
   *n_clamped = clamped;
   return "";

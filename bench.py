@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FLUID_BYTES = {"fp32": 72, "fp64": 144}  # algorithmic bytes per fluid-node update
+FLUID_BYTES = {"fp32": 72, "fp64": 144, "bf16": 36, "fp16": 36}  # algorithmic bytes per fluid-node update
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -257,7 +257,7 @@ def run_ours(args):
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "fp16": "f16"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"cylinders_{case.nx}x{case.ny}_phi0.7_Kn0.02",
                    "nx": case.nx, "ny": case.ny, "n_fluid": n_fluid, "n_links": case.n_links,
@@ -314,7 +314,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--precision", choices=("fp32", "fp64", "bf16", "fp16"), default="fp32")
     ap.add_argument("--lbm-steps", type=int, default=100,
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -50,7 +50,9 @@ typedef enum {
 
 typedef enum {
   LBM_FP64 = 0, /* populations stored and collided in FP64 */
-  LBM_FP32 = 1  /* populations stored as FP32 deviations f_i - w_i, FP32 arithmetic */
+  LBM_FP32 = 1, /* populations stored as FP32 deviations f_i - w_i, FP32 arithmetic */
+  LBM_BF16 = 2, /* deviations stored as BF16, FP32 arithmetic */
+  LBM_FP16 = 3  /* deviations times storage_scale stored as FP16, FP32 arithmetic */
 } lbm_precision;
 
 typedef enum {
@@ -88,6 +90,8 @@ typedef struct {
                            velocity u_b (the equation as printed) */
   int32_t precision;    /* lbm_precision, default LBM_FP32 */
   int32_t residual_every; /* steps between residual checks in lbm_run_to, default 100 */
+  double storage_scale; /* LBM_FP16 only: deviations are stored times this power of two
+                           (0 = 4096, which keeps |d| from 1.5e-8 to 16 in FP16's normal range) */
   void *stream;         /* cudaStream_t for all device work; NULL = legacy default stream */
 } lbm_params_t;
 

@@ -343,3 +343,66 @@ def random_populations(nx: int, ny: int, seed: int, amp: float = 1e-3) -> np.nda
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
     rng = np.random.default_rng(seed)
     return w[:, None, None] * (1.0 + amp * rng.standard_normal((9, ny, nx)))
+
+
+# --------------------------------------------------------------------------
+# inclined channel (Sec. 4.A.2, Fig. 6)
+# --------------------------------------------------------------------------
+
+def inclined_channel(nx: int, tan_theta: float, n_ab: float, Kn: float, a: float = 1e-6,
+                     offset: float = 0.37, name: str | None = None) -> Case:
+    """Channel whose flat walls are inclined at angle theta to the x axis.
+
+    The lattice is nx wide and ny = nx tan(theta) high (an integer), periodic
+    in both directions, so that the band wraps onto itself: that is the
+    channel periodic along its own direction, one period per lattice.  The
+    fluid band lies between the lines y = x tan(theta) + offset and
+    y = x tan(theta) + offset + n_ab (vertical extent n_ab, perpendicular
+    width H = n_ab cos(theta)), taken modulo ny; the rest is solid.  Each
+    link's gamma is the exact crossing of its segment with the wall line it
+    cuts.  The body force a acts along the channel, (cos, sin)(theta) a.
+    meta holds the line data to evaluate the analytic profile: the signed
+    perpendicular distance y' of a node from the lower wall.
+    """
+    ny_f = nx * tan_theta
+    ny = int(round(ny_f))
+    if abs(ny - ny_f) > 1e-9 or ny < 2:
+        raise ValueError("nx * tan(theta) must be an integer >= 2")
+    if n_ab > ny - 2:
+        raise ValueError("the band must leave at least two solid rows")
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    # vertical coordinate above the lower wall, folded into [0, ny)
+    s = np.mod(yy - xx * tan_theta - offset, ny)
+    solid = (~((s > 0.0) & (s < n_ab))).astype(np.uint8)
+    lx, ly, li, rx, ry = _wall_candidates(solid, True, True)
+    px = lx.astype(np.float64)
+    py = ly.astype(np.float64)
+    dx = -CX[li].astype(np.float64)
+    dy = -CY[li].astype(np.float64)
+    # s along the segment p + t d: s(t) = s0 + t (dy - dx tan);  the wall hit
+    # is s = 0 (lower) when s decreases, s = n_ab (upper) when it increases.
+    s0 = np.mod(py - px * tan_theta - offset, ny)
+    ds = dy - dx * tan_theta
+    target = np.where(ds < 0, 0.0, n_ab)
+    t = (target - s0) / ds
+    if np.any(~np.isfinite(t)) or np.any(t <= 0) or np.any(t > 1 + 1e-12):
+        raise ValueError("link without a wall crossing in (0, 1]")
+    t = np.minimum(t, 1.0)
+    zeros = np.zeros(lx.shape)
+    cos_t = 1.0 / math.sqrt(1.0 + tan_theta ** 2)
+    sin_t = tan_theta * cos_t
+    H = n_ab * cos_t
+    nm = name or f"inclined_{nx}_tan{tan_theta:g}_nab{n_ab:g}"
+    return _make_case(nm, solid, True, True, lx, ly, li, t, zeros, zeros, Kn, H,
+                      ax=a * cos_t, ay=a * sin_t,
+                      meta=dict(tan_theta=tan_theta, offset=offset, n_ab=n_ab, cos=cos_t,
+                                sin=sin_t, a=a))
+
+
+def inclined_coordinates(case: Case) -> tuple[np.ndarray, np.ndarray]:
+    """(y', unit vector along the channel) for an inclined_channel case:
+    y' = perpendicular distance of each node from the lower wall."""
+    m = case.meta
+    yy, xx = np.mgrid[0:case.ny, 0:case.nx].astype(np.float64)
+    s = np.mod(yy - xx * m["tan_theta"] - m["offset"], case.ny)
+    return s * m["cos"], np.array([m["cos"], m["sin"]])

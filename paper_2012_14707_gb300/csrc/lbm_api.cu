@@ -7,6 +7,7 @@
 #include <limits>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm_internal.h"
@@ -18,6 +19,7 @@ struct lbm_handle {
   int32_t nx = 0, ny = 0, pitch = 0, px = 0, py = 0;
   int64_t plane = 0;
   double ax = 0.0, ay = 0.0;
+  double scale = 1.0;  // storage scale of the 16-bit types
   lbm::CaseParams cp{};
   lbm_params_t params{};
   void *f[2] = {nullptr, nullptr};
@@ -58,7 +60,26 @@ int cuda_fail(lbm_handle_t *h, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
-size_t elem_size(int precision) { return precision == LBM_FP64 ? 8 : 4; }
+size_t elem_size(int precision) {
+  return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
+}
+
+// Calls f(T*, C*) with null pointers whose types name the storage type T and
+// the arithmetic type C of `precision`.
+template <typename F>
+cudaError_t dispatch(int precision, F &&f) {
+  switch (precision) {
+    case LBM_FP64: return f(static_cast<double *>(nullptr), static_cast<double *>(nullptr));
+    case LBM_FP32: return f(static_cast<float *>(nullptr), static_cast<float *>(nullptr));
+    case LBM_BF16: return f(static_cast<__nv_bfloat16 *>(nullptr), static_cast<float *>(nullptr));
+    default: return f(static_cast<__half *>(nullptr), static_cast<float *>(nullptr));
+  }
+}
+#define LBM_TYPES(tT, tC)                              \
+  using T = std::remove_pointer_t<decltype(tT)>;       \
+  using C = std::remove_pointer_t<decltype(tC)>;       \
+  (void)sizeof(T);                                     \
+  (void)sizeof(C)
 
 void release(lbm_handle_t *h) {
   if (!h) return;
@@ -95,24 +116,21 @@ lbm::StepConst<C> step_const(const lbm_handle_t *h) {
   k.periodic_x = h->px;
   k.periodic_y = h->py;
   k.diffuse_mode = h->params.diffuse_mode;
+  k.sc = static_cast<C>(h->scale);
+  k.inv_sc = static_cast<C>(1.0 / h->scale);
   k.plane = h->plane;
   return k;
 }
 
 cudaError_t do_step(lbm_handle_t *h) {
   const int src = h->cur, dst = 1 - h->cur;
-  cudaError_t e;
-  if (h->precision == LBM_FP64) {
-    e = lbm::launch_step<double, double>(
-        static_cast<const double *>(h->f[src]), static_cast<double *>(h->f[dst]), h->flags,
-        h->lbase, static_cast<const lbm::LinkCoef<double> *>(h->links), step_const<double>(h),
-        h->stream);
-  } else {
-    e = lbm::launch_step<float, float>(
-        static_cast<const float *>(h->f[src]), static_cast<float *>(h->f[dst]), h->flags,
-        h->lbase, static_cast<const lbm::LinkCoef<float> *>(h->links), step_const<float>(h),
-        h->stream);
-  }
+  cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
+    LBM_TYPES(tT, tC);
+    return lbm::launch_step<T, C>(static_cast<const T *>(h->f[src]), static_cast<T *>(h->f[dst]),
+                                  h->flags, h->lbase,
+                                  static_cast<const lbm::LinkCoef<C> *>(h->links),
+                                  step_const<C>(h), h->stream);
+  });
   if (e == cudaSuccess) {
     h->cur = dst;
     h->steps++;
@@ -171,8 +189,10 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     return bad(LBM_EINVAL, "null link array");
   const lbm_params_t &p = *params;
   if (dom->nx < 1 || dom->ny < 1) return bad(LBM_EINVAL, "nx and ny must be >= 1");
-  if (p.precision != LBM_FP64 && p.precision != LBM_FP32)
-    return bad(LBM_EINVAL, "precision must be LBM_FP64 or LBM_FP32");
+  if (p.precision < LBM_FP64 || p.precision > LBM_FP16)
+    return bad(LBM_EINVAL, "precision must be LBM_FP64, LBM_FP32, LBM_BF16 or LBM_FP16");
+  if (!(p.storage_scale >= 0.0) || !std::isfinite(p.storage_scale))
+    return bad(LBM_EINVAL, "storage_scale must be 0 (default) or a positive power of two");
   if (p.diffuse_mode != 0 && p.diffuse_mode != 1) return bad(LBM_EINVAL, "diffuse_mode must be 0 or 1");
   if (p.residual_every < 1) return bad(LBM_EINVAL, "residual_every must be >= 1");
   if (!std::isfinite(dom->ax) || !std::isfinite(dom->ay)) return bad(LBM_EINVAL, "non-finite force");
@@ -290,6 +310,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   }
 
   h->precision = p.precision;
+  h->scale = p.precision == LBM_FP16 ? (p.storage_scale > 0.0 ? p.storage_scale : 4096.0) : 1.0;
   h->stream = static_cast<cudaStream_t>(p.stream);
   h->nx = nx;
   h->ny = ny;
@@ -307,12 +328,13 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
 
   const size_t es = elem_size(p.precision);
   const size_t fbytes = 9 * static_cast<size_t>(plane) * es;
-  const size_t lbytes = std::max<size_t>(1, n_links) * 4 * es;
+  const size_t ces = p.precision == LBM_FP64 ? 8 : 4;  // link coefficients: FP64 or FP32
+  const size_t lbytes = std::max<size_t>(1, n_links) * 4 * ces;
   const size_t pbytes = lbm::kResidualBlocks * lbm::kPartialStride * sizeof(double);
   std::vector<unsigned char> lhost(lbytes, 0);
   for (size_t s = 0; s < n_links; s++) {
     const double *c = &coef[8 * order[s]];
-    if (es == 8) {
+    if (ces == 8) {
       std::memcpy(&lhost[s * 32], c, 32);
     } else {
       float cf[4];
@@ -370,17 +392,12 @@ int lbm_step(lbm_handle_t *h, int64_t n) {
 int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   if (!h) return LBM_EINVAL;
   const int c = h->cur, pv = 1 - h->cur;
-  cudaError_t e;
-  if (h->precision == LBM_FP64)
-    e = lbm::launch_residual<double>(static_cast<const double *>(h->f[c]),
-                                     static_cast<const double *>(h->f[pv]), h->flags, h->nx,
-                                     h->ny, h->pitch, h->plane, h->ax, h->ay, h->partials,
-                                     h->result, h->stream);
-  else
-    e = lbm::launch_residual<float>(static_cast<const float *>(h->f[c]),
-                                    static_cast<const float *>(h->f[pv]), h->flags, h->nx, h->ny,
-                                    h->pitch, h->plane, h->ax, h->ay, h->partials, h->result,
-                                    h->stream);
+  cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
+    LBM_TYPES(tT, tC);
+    return lbm::launch_residual<T>(static_cast<const T *>(h->f[c]), static_cast<const T *>(h->f[pv]),
+                                   h->flags, h->nx, h->ny, h->pitch, h->plane, h->ax, h->ay,
+                                   h->scale, h->partials, h->result, h->stream);
+  });
   if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
   LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
@@ -441,13 +458,11 @@ int lbm_fields(lbm_handle_t *h, double *rho, double *ux, double *uy, int on_devi
     u = ux ? d + n : nullptr;
     v = uy ? d + 2 * n : nullptr;
   }
-  cudaError_t e;
-  if (h->precision == LBM_FP64)
-    e = lbm::launch_fields<double>(static_cast<const double *>(h->f[h->cur]), h->flags, h->nx,
-                                   h->ny, h->pitch, h->plane, h->ax, h->ay, r, u, v, h->stream);
-  else
-    e = lbm::launch_fields<float>(static_cast<const float *>(h->f[h->cur]), h->flags, h->nx,
-                                  h->ny, h->pitch, h->plane, h->ax, h->ay, r, u, v, h->stream);
+  cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
+    LBM_TYPES(tT, tC);
+    return lbm::launch_fields<T>(static_cast<const T *>(h->f[h->cur]), h->flags, h->nx, h->ny,
+                                 h->pitch, h->plane, h->ax, h->ay, h->scale, r, u, v, h->stream);
+  });
   if (e == cudaSuccess && !on_device) {
     if (rho && e == cudaSuccess)
       e = cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -467,13 +482,11 @@ int lbm_get_f(lbm_handle_t *h, double *f) {
   const int64_t n = 9 * static_cast<int64_t>(h->nx) * h->ny;
   double *d = nullptr;
   LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), n * sizeof(double), h->stream));
-  cudaError_t e;
-  if (h->precision == LBM_FP64)
-    e = lbm::launch_export_f<double>(static_cast<const double *>(h->f[h->cur]), h->nx, h->ny,
-                                     h->pitch, h->plane, d, h->stream);
-  else
-    e = lbm::launch_export_f<float>(static_cast<const float *>(h->f[h->cur]), h->nx, h->ny,
-                                    h->pitch, h->plane, d, h->stream);
+  cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
+    LBM_TYPES(tT, tC);
+    return lbm::launch_export_f<T>(static_cast<const T *>(h->f[h->cur]), h->nx, h->ny, h->pitch,
+                                   h->plane, h->scale, d, h->stream);
+  });
   if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   cudaFreeAsync(d, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -487,14 +500,12 @@ int lbm_set_f(lbm_handle_t *h, const double *f) {
   double *d = nullptr;
   LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), n * sizeof(double), h->stream));
   cudaError_t e = cudaMemcpyAsync(d, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
-    if (h->precision == LBM_FP64)
-      e = lbm::launch_import_f<double>(d, h->nx, h->ny, h->pitch, h->plane,
-                                       static_cast<double *>(h->f[b]), h->stream);
-    else
-      e = lbm::launch_import_f<float>(d, h->nx, h->ny, h->pitch, h->plane,
-                                      static_cast<float *>(h->f[b]), h->stream);
-  }
+  for (int b = 0; b < 2 && e == cudaSuccess; b++)
+    e = dispatch(h->precision, [&](auto tT, auto tC) {
+      LBM_TYPES(tT, tC);
+      return lbm::launch_import_f<T>(d, h->nx, h->ny, h->pitch, h->plane, h->scale,
+                                     static_cast<T *>(h->f[b]), h->stream);
+    });
   cudaFreeAsync(d, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_f");

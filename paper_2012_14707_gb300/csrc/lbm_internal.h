@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -20,6 +22,7 @@ template <typename C>
 struct StepConst {
   C s_e, s_eps, s_q, s_s, s_j;  // 1/tau of the non-conserved moments and of j
   C h_e, h_eps, h_q, h_s, h_j;  // 1 - s/2: weights of the forcing moments (Eq. MomentPost)
+  C sc, inv_sc;                 // storage scale of the 16-bit types (1 otherwise)
   C ax, ay;                     // body acceleration
   int32_t nx, ny, pitch;        // lattice size and row pitch (elements)
   int32_t periodic_x, periodic_y;
@@ -77,20 +80,20 @@ cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_
 template <typename T>
 cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
                             int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
-                            double *partials, double *result, cudaStream_t s);
+                            double scale, double *partials, double *result, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t ny,
-                          int32_t pitch, int64_t plane, double ax, double ay, double *rho,
-                          double *ux, double *uy, cudaStream_t s);
+                          int32_t pitch, int64_t plane, double ax, double ay, double scale,
+                          double *rho, double *ux, double *uy, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
-                            double *out, cudaStream_t s);
+                            double scale, double *out, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch,
-                            int64_t plane, T *f, cudaStream_t s);
+                            int64_t plane, double scale, T *f, cudaStream_t s);
 
 // Fixed reduction geometry: deterministic partial order on every device.
 constexpr int kResidualBlocks = 1024;

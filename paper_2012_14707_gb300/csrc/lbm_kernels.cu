@@ -16,13 +16,30 @@
 namespace lbm {
 namespace {
 
+// Storage of a deviation d as T and its arithmetic type C.  FP32 and FP64
+// store d itself; the 16-bit types store d * scale (scale a power of two,
+// 1 for BF16), so loads and stores are exact apart from the rounding to T.
 template <typename T>
-struct Arith {
-  using type = float;
+struct Stor {
+  using C = T;
+  static __device__ __forceinline__ C ld(T v, C) { return v; }
+  static __device__ __forceinline__ T st(C v, C) { return v; }
 };
 template <>
-struct Arith<double> {
-  using type = double;
+struct Stor<__half> {
+  using C = float;
+  static __device__ __forceinline__ float ld(__half v, float inv) { return __half2float(v) * inv; }
+  static __device__ __forceinline__ __half st(float v, float sc) { return __float2half_rn(v * sc); }
+};
+template <>
+struct Stor<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ float ld(__nv_bfloat16 v, float inv) {
+    return __bfloat162float(v) * inv;
+  }
+  static __device__ __forceinline__ __nv_bfloat16 st(float v, float sc) {
+    return __float2bfloat16_rn(v * sc);
+  }
 };
 
 
@@ -66,7 +83,7 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
 
     C d[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) d[i] = static_cast<C>(src[i * P + node]);
+    for (int i = 0; i < 9; i++) d[i] = Stor<T>::ld(src[i * P + node], k.inv_sc);
     // First link of this node (links sorted by node, then direction), loaded
     // now so that its latency overlaps the collision.
     const int lb = fl ? lbase[node] : 0;
@@ -131,19 +148,28 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
     // exactly only in exact arithmetic, so f'_0 = drho - sum_{i>0} f'_i
     // (equal to r9 - 4 e36 + 4 p36 up to rounding) keeps the stored mass
     // unchanged by the collision to within one rounding of f'_0.
+    // Round f'_1..f'_8 to storage first (a no-op for FP32/FP64), so that the
+    // closure below balances the values actually stored.
+    T t[9];
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      t[i] = Stor<T>::st(o[i], k.sc);
+      o[i] = Stor<T>::ld(t[i], k.inv_sc);
+    }
     o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+    t[0] = Stor<T>::st(o[0], k.sc);
 
     // Streaming: push f'_i to x + c_i unless that node is solid; bit (j-1)
     // set <=> x - c_j solid, so push i needs bit opp(i) clear.
-    dst[node] = static_cast<T>(o[0]);
-    if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = static_cast<T>(o[1]);  // opp(1) = 3
-    if (!(fl & (1u << 3))) dst[2 * P + rown + x] = static_cast<T>(o[2]);   // opp(2) = 4
-    if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = static_cast<T>(o[3]);  // opp(3) = 1
-    if (!(fl & (1u << 1))) dst[4 * P + rows + x] = static_cast<T>(o[4]);   // opp(4) = 2
-    if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = static_cast<T>(o[5]);  // opp(5) = 7
-    if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = static_cast<T>(o[6]);  // opp(6) = 8
-    if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = static_cast<T>(o[7]);  // opp(7) = 5
-    if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = static_cast<T>(o[8]);  // opp(8) = 6
+    dst[node] = t[0];
+    if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = t[1];  // opp(1) = 3
+    if (!(fl & (1u << 3))) dst[2 * P + rown + x] = t[2];   // opp(2) = 4
+    if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = t[3];  // opp(3) = 1
+    if (!(fl & (1u << 1))) dst[4 * P + rows + x] = t[4];   // opp(4) = 2
+    if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = t[5];  // opp(5) = 7
+    if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = t[6];  // opp(6) = 8
+    if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = t[7];  // opp(7) = 5
+    if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = t[8];  // opp(8) = 6
 
     // Boundary links of this node, Eq. EqNewBDSC in the folded form of
     // LinkCoef.  Directions that no active lane of the warp needs are
@@ -175,7 +201,7 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
           const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
           const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
                       c2 * (drho + rho * pj);
-          dst[j * P + node] = static_cast<T>(v);
+          dst[j * P + node] = Stor<T>::st(v, k.sc);
         }
       }
     }
@@ -238,8 +264,10 @@ template <typename T>
 __global__ void __launch_bounds__(kResidualThreads)
 residual_partials(const T *__restrict__ cur, const T *__restrict__ prev,
                   const uint8_t *__restrict__ flags, int32_t nx, int32_t ny, int32_t pitch,
-                  int64_t plane, double ax, double ay, double *__restrict__ partials) {
-  using C = typename Arith<T>::type;
+                  int64_t plane, double ax, double ay, double inv_scale,
+                  double *__restrict__ partials) {
+  using C = typename Stor<T>::C;
+  const C inv = static_cast<C>(inv_scale);
   double num = 0.0, den = 0.0, dm = 0.0, bad = 0.0;
   for (int y = blockIdx.x; y < ny; y += gridDim.x) {
     const int64_t row = static_cast<int64_t>(y) * pitch;
@@ -249,8 +277,8 @@ residual_partials(const T *__restrict__ cur, const T *__restrict__ prev,
       C a[9], b[9];
 #pragma unroll
       for (int i = 0; i < 9; i++) {
-        a[i] = static_cast<C>(cur[i * plane + node]);
-        b[i] = static_cast<C>(prev[i * plane + node]);
+        a[i] = Stor<T>::ld(cur[i * plane + node], inv);
+        b[i] = Stor<T>::ld(prev[i * plane + node], inv);
       }
       C n1, d1, m1;
       residual_terms<C>(a, b, static_cast<C>(ax), static_cast<C>(ay), n1, d1, m1);
@@ -308,7 +336,8 @@ residual_final(const double *__restrict__ partials, double *__restrict__ out) {
 template <typename T>
 __global__ void fields_kernel(const T *__restrict__ f, const uint8_t *__restrict__ flags,
                               int32_t nx, int32_t ny, int32_t pitch, int64_t plane, double ax,
-                              double ay, double *rho, double *ux, double *uy) {
+                              double ay, double inv_scale, double *rho, double *ux, double *uy) {
+  using C = typename Stor<T>::C;
   const int64_t n = static_cast<int64_t>(nx) * ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -317,7 +346,8 @@ __global__ void fields_kernel(const T *__restrict__ f, const uint8_t *__restrict
     double r = 0.0, u = 0.0, v = 0.0;
     if (flags[node] != kSolid) {
       double a[9];
-      for (int i = 0; i < 9; i++) a[i] = static_cast<double>(f[i * plane + node]);
+      for (int i = 0; i < 9; i++)
+        a[i] = static_cast<double>(Stor<T>::ld(f[i * plane + node], static_cast<C>(inv_scale)));
       node_velocity(a, ax, ay, r, u, v);
     }
     if (rho) rho[p] = r;
@@ -331,23 +361,27 @@ __constant__ double kWd[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
 
 template <typename T>
 __global__ void export_kernel(const T *__restrict__ f, int32_t nx, int32_t ny, int32_t pitch,
-                              int64_t plane, double *out) {
+                              int64_t plane, double inv_scale, double *out) {
+  using C = typename Stor<T>::C;
   const int64_t n = static_cast<int64_t>(nx) * ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
-    out[p] = kWd[i] + static_cast<double>(f[i * plane + y * pitch + x]);
+    out[p] = kWd[i] + static_cast<double>(
+                          Stor<T>::ld(f[i * plane + y * pitch + x], static_cast<C>(inv_scale)));
   }
 }
 
 template <typename T>
 __global__ void import_kernel(const double *__restrict__ in, int32_t nx, int32_t ny,
-                              int32_t pitch, int64_t plane, T *f) {
+                              int32_t pitch, int64_t plane, double scale, T *f) {
+  using C = typename Stor<T>::C;
   const int64_t n = static_cast<int64_t>(nx) * ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
-    f[i * plane + y * pitch + x] = static_cast<T>(in[p] - kWd[i]);
+    f[i * plane + y * pitch + x] =
+        Stor<T>::st(static_cast<C>(in[p] - kWd[i]), static_cast<C>(scale));
   }
 }
 
@@ -369,35 +403,36 @@ cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_
 template <typename T>
 cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
                             int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
-                            double *partials, double *result, cudaStream_t s) {
-  residual_partials<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(cur, prev, flags, nx, ny, pitch,
-                                                                   plane, ax, ay, partials);
+                            double scale, double *partials, double *result, cudaStream_t s) {
+  residual_partials<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(
+      cur, prev, flags, nx, ny, pitch, plane, ax, ay, 1.0 / scale, partials);
   residual_final<<<1, kResidualBlocks, 0, s>>>(partials, result);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
-                          int64_t plane, double ax, double ay, double *rho, double *ux, double *uy,
-                          cudaStream_t s) {
+                          int64_t plane, double ax, double ay, double scale, double *rho,
+                          double *ux, double *uy, cudaStream_t s) {
   const int64_t n = static_cast<int64_t>(nx) * ny;
-  fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, flags, nx, ny, pitch, plane, ax, ay, rho, ux, uy);
+  fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, flags, nx, ny, pitch, plane, ax, ay,
+                                                    1.0 / scale, rho, ux, uy);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
-                            double *out, cudaStream_t s) {
+                            double scale, double *out, cudaStream_t s) {
   const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
-  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, nx, ny, pitch, plane, out);
+  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, nx, ny, pitch, plane, 1.0 / scale, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
-                            T *f, cudaStream_t s) {
+                            double scale, T *f, cudaStream_t s) {
   const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
-  import_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(in, nx, ny, pitch, plane, f);
+  import_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(in, nx, ny, pitch, plane, scale, f);
   return cudaGetLastError();
 }
 
@@ -405,17 +440,19 @@ cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pi
   template cudaError_t launch_step<T, C>(const T *, T *, const uint8_t *, const int32_t *,         \
                                          const LinkCoef<C> *, const StepConst<C> &, cudaStream_t); \
   template cudaError_t launch_residual<T>(const T *, const T *, const uint8_t *, int32_t, int32_t,  \
-                                         int32_t, int64_t, double, double, double *, double *,     \
-                                         cudaStream_t);                                            \
+                                         int32_t, int64_t, double, double, double, double *,       \
+                                         double *, cudaStream_t);                                  \
   template cudaError_t launch_fields<T>(const T *, const uint8_t *, int32_t, int32_t, int32_t,     \
-                                        int64_t, double, double, double *, double *, double *,     \
-                                        cudaStream_t);                                             \
-  template cudaError_t launch_export_f<T>(const T *, int32_t, int32_t, int32_t, int64_t, double *, \
-                                          cudaStream_t);                                           \
-  template cudaError_t launch_import_f<T>(const double *, int32_t, int32_t, int32_t, int64_t, T *, \
-                                          cudaStream_t);
+                                        int64_t, double, double, double, double *, double *,       \
+                                        double *, cudaStream_t);                                   \
+  template cudaError_t launch_export_f<T>(const T *, int32_t, int32_t, int32_t, int64_t, double,   \
+                                          double *, cudaStream_t);                                 \
+  template cudaError_t launch_import_f<T>(const double *, int32_t, int32_t, int32_t, int64_t,      \
+                                          double, T *, cudaStream_t);
 
 LBM_INSTANTIATE(double, double)
 LBM_INSTANTIATE(float, float)
+LBM_INSTANTIATE(__half, float)
+LBM_INSTANTIATE(__nv_bfloat16, float)
 
 }  // namespace lbm

@@ -18,10 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOMEM = range(6)
-LBM_FP64, LBM_FP32 = 0, 1
+LBM_FP64, LBM_FP32, LBM_BF16, LBM_FP16 = 0, 1, 2, 3
 L_MODES = {"paper": 0, "zero": 1, "gamma": 2, "2gamma": 3, "gamma2": 4, "gamma2+gamma": 5,
            "fixed": 6}
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32}
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16": LBM_BF16, "fp16": LBM_FP16}
 
 # Every entry point include/lbm.h declares.
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_residual",
@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
                 ("r_value", ctypes.c_double), ("l_value", ctypes.c_double),
                 ("l_mode", ctypes.c_int32), ("diffuse_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("residual_every", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("storage_scale", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -247,14 +247,14 @@ class Solver:
     """One case on the GPU.
 
     `case` is a `cases.Case`.  Keyword arguments override the parameter
-    defaults of include/lbm.h: precision ("fp32" | "fp64"), l_mode (a name of
+    defaults of include/lbm.h: precision ("fp32" | "fp64" | "bf16" | "fp16"), l_mode (a name of
     L_MODES or a float for a fixed l), r (fixed r), tau_q, tau_s, E, L1, L2,
     sigma, diffuse_mode, residual_every, stream (a cudaStream_t as int).
     """
 
     def __init__(self, case, precision="fp32", l_mode="paper", r=None, tau_q=None, tau_s=None,
                  E=None, L1=None, L2=None, sigma=1.0, diffuse_mode=0, residual_every=100,
-                 stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4):
+                 stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4, storage_scale=0.0):
         p = lbm_params_default()
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if isinstance(l_mode, str):
@@ -273,6 +273,7 @@ class Solver:
         p.tau_e, p.tau_eps, p.l_clamp = float(tau_e), float(tau_eps), float(l_clamp)
         p.diffuse_mode = int(diffuse_mode)
         p.residual_every = int(residual_every)
+        p.storage_scale = float(storage_scale)
         p.stream = stream
         self.case = case
         self.params = p

@@ -92,6 +92,9 @@ typedef struct {
   int32_t residual_every; /* steps between residual checks in lbm_run_to, default 100 */
   double storage_scale; /* LBM_FP16 only: deviations are stored times this power of two
                            (0 = 4096, which keeps |d| from 1.5e-8 to 16 in FP16's normal range) */
+  int32_t collision;    /* 0 = MRT (default); 1 = BGK reading of Sec. 3.B: every relaxation
+                           time equals tau_s and E solves Eq. NSliCoertstq for tau_q = tau_s
+                           (tau_q, E and the fixed relaxation times given here are ignored) */
   void *stream;         /* cudaStream_t for all device work; NULL = legacy default stream */
 } lbm_params_t;
 

@@ -103,6 +103,14 @@ def tau_q_uniform(tau_s, L1, L2, E):
     return num / den
 
 
+def E_for_bgk(tau_s, L1, L2):
+    """Sec. 3.B, BGK remark: the E for which Eq. NSliCoertstq gives
+    tau_q = tau_s (Eq. NSliCoertstq solved for E)."""
+    a = 2 * tau_s - 1
+    return ((a * (tau_s * math.sqrt(6 * math.pi) * L2 - L1) - 2 * S6PI * tau_s
+             - tau_s * (8 * S6PI * tau_s + 4 * L1 * a)) / (12 * S6PI * tau_s))
+
+
 def E_upper_bound(tau_s, L1, L2):
     """Eq. EqECond: tau_q > 1/2 requires E below this value."""
     return ((math.pi * tau_s * L2 - 3 * math.sqrt(math.pi / 6) * L1) * (2 * tau_s - 1)
@@ -198,6 +206,9 @@ class Parameters:
     Eq. SliCoeffrtsr with the l actually used (identical to Eq. NSliCoertsr
     where no clamp applies).
 
+    `bgk=True` takes the BGK reading of Sec. 3.B: every relaxation time
+    equals tau_s and E solves Eq. NSliCoertstq for tau_q = tau_s.
+
     `l_mode` selects the free parameter: "paper" (Eq. Eqexlva), "zero",
     "gamma", "2gamma", "gamma2", "gamma2+gamma" (the alternatives of
     Sec. 4) or a float (a fixed l).  `r_fixed` and `tau_q_fixed` replace the
@@ -206,7 +217,7 @@ class Parameters:
 
     def __init__(self, Kn, H, sigma=1.0, L1=None, L2=None, E=None, l_clamp=-0.4,
                  tau_rho=1.0, tau_j=1.0, tau_e=1.1, tau_eps=1.2, l_mode="paper",
-                 r_fixed=None, tau_q_fixed=None, tau_s=None):
+                 r_fixed=None, tau_q_fixed=None, tau_s=None, bgk=False):
         self.Kn = float(Kn)
         self.H = float(H)
         self.tau_s = tau_s_from_kn(Kn, H) if tau_s is None else float(tau_s)
@@ -215,6 +226,11 @@ class Parameters:
         self.L2 = dL2 if L2 is None else float(L2)
         self.E_max = E_upper_bound(self.tau_s, self.L1, self.L2)
         self.E = min(-0.65, self.E_max - 0.1) if E is None else float(E)
+        if bgk:
+            # BGK (Sec. 3.B): one relaxation time tau_s for every moment and
+            # the E that makes the uniform tau_q equal to it
+            self.E = E_for_bgk(self.tau_s, self.L1, self.L2)
+            tau_rho = tau_j = tau_e = tau_eps = self.tau_s
         self.l_clamp = l_clamp
         self.l_mode = l_mode
         self.r_fixed = r_fixed

@@ -2,6 +2,7 @@
 // of the per-link coefficients the step kernel consumes.
 #include <cmath>
 #include <cstdio>
+#include <limits>
 #include <string>
 
 #include "lbm_internal.h"
@@ -37,22 +38,32 @@ std::string compute_case_params(double Kn, double H, const lbm_params_t &p, Case
   // Eq. EqECond: tau_q > 1/2 requires E < E_max.
   double Emax = (kPi * ts * L2 - 3.0 * std::sqrt(kPi / 6.0) * L1) * a / (12.0 * ts) - 0.5;
   double E = std::isnan(p.E) ? std::fmin(-0.65, Emax - 0.1) : p.E;
+  double tau_fix[4] = {p.tau_rho, p.tau_j, p.tau_e, p.tau_eps};
+  if (p.collision != 0 && p.collision != 1)
+    return fmt("collision must be 0 (MRT) or 1 (BGK), got %g", static_cast<double>(p.collision));
+  const bool bgk = p.collision == 1;
+  if (bgk) {
+    // BGK reading of Sec. 3.B: tau_q = tau_s in Eq. NSliCoertstq, solved for E.
+    E = (a * (ts * std::sqrt(6.0 * kPi) * L2 - L1) - 2.0 * s6 * ts -
+         ts * (8.0 * s6 * ts + 4.0 * L1 * a)) / (12.0 * s6 * ts);
+    for (double &t : tau_fix) t = ts;
+  }
   // Eq. NSliCoertstq: the gamma-independent tau_q.
-  double tq = p.tau_q;
+  double tq = bgk ? std::numeric_limits<double>::quiet_NaN() : p.tau_q;
   if (std::isnan(tq)) {
     double num = a * (ts * std::sqrt(6.0 * kPi) * L2 - L1) - 2.0 * s6 * ts * (1.0 + 6.0 * E);
     tq = num / (8.0 * s6 * ts + 4.0 * L1 * a);
   }
   if (!(tq > 0.5) || !std::isfinite(tq))
     return fmt("tau_q = %g must exceed 1/2 (E = %g; see the E bound of Eq. EqECond)", tq, E);
-  for (double t : {p.tau_rho, p.tau_j, p.tau_e, p.tau_eps})
+  for (double t : tau_fix)
     if (!(t > 0.5) || !std::isfinite(t)) return fmt("fixed relaxation time %g must exceed 1/2", t);
   cp->tau_s = ts;
   cp->tau_q = tq;
-  cp->tau_rho = p.tau_rho;
-  cp->tau_j = p.tau_j;
-  cp->tau_e = p.tau_e;
-  cp->tau_eps = p.tau_eps;
+  cp->tau_rho = tau_fix[0];
+  cp->tau_j = tau_fix[1];
+  cp->tau_e = tau_fix[2];
+  cp->tau_eps = tau_fix[3];
   cp->L1 = L1;
   cp->L2 = L2;
   cp->E = E;

@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
                 ("r_value", ctypes.c_double), ("l_value", ctypes.c_double),
                 ("l_mode", ctypes.c_int32), ("diffuse_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("residual_every", ctypes.c_int32),
-                ("storage_scale", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("storage_scale", ctypes.c_double), ("collision", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -254,7 +255,8 @@ class Solver:
 
     def __init__(self, case, precision="fp32", l_mode="paper", r=None, tau_q=None, tau_s=None,
                  E=None, L1=None, L2=None, sigma=1.0, diffuse_mode=0, residual_every=100,
-                 stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4, storage_scale=0.0):
+                 stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4, storage_scale=0.0,
+                 bgk=False):
         p = lbm_params_default()
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if isinstance(l_mode, str):
@@ -274,6 +276,7 @@ class Solver:
         p.diffuse_mode = int(diffuse_mode)
         p.residual_every = int(residual_every)
         p.storage_scale = float(storage_scale)
+        p.collision = 1 if bgk else 0
         p.stream = stream
         self.case = case
         self.params = p

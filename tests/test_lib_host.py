@@ -114,3 +114,17 @@ def test_create_validates_links_before_touching_the_device(lib):
     assert "tau_q" in str(ei.value)
     with pytest.raises(lbm.LbmError):
         _create(c, precision=7)
+
+
+def test_bgk_precompute_matches_oracle(lib):
+    for Kn, H in ((0.05, 9.2), (0.03, 11.5), (0.1, 4.0)):
+        par = P.Parameters(Kn, H, bgk=True)
+        p = lbm.lbm_params_default()
+        p.collision = 1
+        g = np.array([0.2, 0.5, 0.9])
+        r, l, info = lbm.lbm_precompute(Kn, H, p, [2, 5, 6], g)
+        assert info.tau_q == pytest.approx(par.tau_s, rel=1e-12)
+        assert info.E == pytest.approx(par.E, rel=1e-13)
+        r_o, l_o = par.per_link(g)
+        np.testing.assert_allclose(l, l_o, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(r, r_o, rtol=1e-13)

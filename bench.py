@@ -308,6 +308,58 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch):
 KERNEL_REV = 4
 
 
+def run_batch(args):
+    """The batched workload: 512 uneven cases (sizes 64x64-1024x512, slip
+    channel / annulus / cylinder array, Kn log-uniform 0.001-0.1), FP32, all
+    run together to --batch-tol (capped at --batch-max-steps).  value =
+    aggregate fluid-node updates per second over the cases still running."""
+    import numpy as np
+    import torch
+
+    from paper_2012_14707_gb300 import build as lbm_build
+    from paper_2012_14707_gb300 import cases, lbm
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    lbm.load()
+    cl = cases.batch_cases(args.batch_cases, seed=rank)
+    t0 = time.perf_counter()
+    b = lbm.Batch(cl, precision=args.precision)
+    t_create = time.perf_counter() - t0
+    info = b.info()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, res, total = b.run_to(args.batch_tol, args.batch_max_steps, check_every=args.lbm_steps)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    nf = np.array([c.n_fluid for c in cl], np.float64)
+    run = np.where(steps > 0, steps, total).astype(np.float64)
+    updates = float((nf * run).sum())
+    conv = steps > 0
+    line = {
+        "metric": "MLUPS (batched)", "value": updates / wall / 1e6, "unit": "MLUPS",
+        "n_gpus": world, "steps": int(total), "warmup": 0, "ms_per_step": wall / max(total, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "fp16": "f16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"batch_{len(cl)}_cases_64-1024x64-512_Kn0.001-0.1",
+                   "total_nodes": info["total_nodes"], "total_fluid": info["total_fluid"],
+                   "cta_threads_autotuned": info["cta_threads"], "tol": args.batch_tol,
+                   "max_steps": args.batch_max_steps, "check_every": args.lbm_steps},
+        "batch": {"converged": int(conv.sum()), "unstable": int((steps < 0).sum()),
+                  "steps_to_steady_median": float(np.median(steps[conv])) if conv.any() else None,
+                  "steps_to_steady_p90": float(np.percentile(steps[conv], 90)) if conv.any() else None,
+                  "create_seconds": t_create, "wall_seconds": wall},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,11 +371,18 @@ def main():
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=("throughput", "batch"), default="throughput")
+    ap.add_argument("--batch-cases", type=int, default=512)
+    ap.add_argument("--batch-max-steps", type=int, default=20000)
+    ap.add_argument("--batch-tol", type=float, default=1e-6,
+                    help="residual to reach; the one-step FP32 residual floors near 1e-8")
     ap.add_argument("--nx", type=int, default=0, help="profiling only: smaller lattice width")
     ap.add_argument("--ny", type=int, default=0, help="profiling only: smaller lattice height")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -170,36 +170,39 @@ def channel(nx: int, m: int, q_bottom: float, q_top: float, Kn: float,
 
 def annulus(n: int, R1: float, R2: float, Kn: float, omega1: float,
             omega2: float = 0.0, center: float | None = None,
-            name: str = "couette") -> Case:
-    """n x n lattice, concentric circles about `center` (default (n-1)/2).
+            name: str = "couette", ny: int | None = None) -> Case:
+    """n x n lattice (n x ny if ny is given), concentric circles about
+    `center` (default the lattice centre).
 
     A node is solid when its distance r from the centre has r <= R1 or
     r >= R2.  Each link's gamma comes from the exact segment-circle
     intersection; the wall velocity at x_b is omega x (x_b - centre) of the
     wall that was hit.  H = R2 - R1 (Kn = lambda / (R2 - R1)).
     """
+    nyy = n if ny is None else int(ny)
     c = (n - 1) / 2.0 if center is None else float(center)
-    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
-    rr = np.hypot(xx - c, yy - c)
+    cy = (nyy - 1) / 2.0 if center is None else float(center)
+    yy, xx = np.mgrid[0:nyy, 0:n].astype(np.float64)
+    rr = np.hypot(xx - c, yy - cy)
     solid = ((rr <= R1) | (rr >= R2)).astype(np.uint8)
-    if R2 > c:
+    if R2 > min(c, cy):
         raise ValueError("outer circle must leave a solid edge row")
     lx, ly, li, rx, ry = _wall_candidates(solid, False, False)
-    r_ref = np.hypot(rx - c, ry - c)
+    r_ref = np.hypot(rx - c, ry - cy)
     inner = r_ref <= R1
     px = lx.astype(np.float64)
     py = ly.astype(np.float64)
     dx = -CX[li].astype(np.float64)
     dy = -CY[li].astype(np.float64)
-    t = _segment_circle_t(px, py, dx, dy, c, c, np.where(inner, R1, R2), inner)
+    t = _segment_circle_t(px, py, dx, dy, c, cy, np.where(inner, R1, R2), inner)
     bx = px + t * dx - c
-    by = py + t * dy - c
+    by = py + t * dy - cy
     om = np.where(inner, omega1, omega2)
     ubx = -om * by
     uby = om * bx
     return _make_case(name, solid, False, False, lx, ly, li, t, ubx, uby, Kn,
-                      R2 - R1, meta=dict(R1=R1, R2=R2, center=c, omega1=omega1,
-                                         omega2=omega2))
+                      R2 - R1, meta=dict(R1=R1, R2=R2, center=c, center_y=cy,
+                                         omega1=omega1, omega2=omega2))
 
 
 # --------------------------------------------------------------------------
@@ -406,3 +409,45 @@ def inclined_coordinates(case: Case) -> tuple[np.ndarray, np.ndarray]:
     yy, xx = np.mgrid[0:case.ny, 0:case.nx].astype(np.float64)
     s = np.mod(yy - xx * m["tan_theta"] - m["offset"], case.ny)
     return s * m["cos"], np.array([m["cos"], m["sin"]])
+
+
+# --------------------------------------------------------------------------
+# batch of uneven cases
+# --------------------------------------------------------------------------
+
+def batch_cases(n_cases: int = 512, seed: int = 0, nx_range=(64, 1024), ny_range=(64, 512),
+                kn_range=(0.001, 0.1)) -> list[Case]:
+    """Seeded batch: sizes uniform over nx_range x ny_range, geometry uniform
+    over {slip channel, annulus, random cylinder array}, Kn log-uniform over
+    kn_range, driving at Ma ~ 0.02-0.05 (wall speed) or a fixed small body
+    force.
+
+    * channel: gamma of each wall ~ U(0.05, 1], force 2e-6 along x;
+    * annulus: R2 = 0.45 min(nx, ny), R1 = beta R2 with beta ~ U[0.2, 0.6],
+      inner wall at Ma ~ U[0.02, 0.05], outer at rest;
+    * cylinder array: radii U[8, min(32, min(nx, ny) / 8)], porosity 0.7,
+      force 5e-6 along x.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    cs = math.sqrt(1.0 / 3.0)
+    for k in range(n_cases):
+        nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        kind = int(rng.integers(0, 3))
+        Kn = float(math.exp(rng.uniform(math.log(kn_range[0]), math.log(kn_range[1]))))
+        if kind == 0:
+            gb, gt = float(rng.uniform(0.05, 1.0)), float(rng.uniform(0.05, 1.0))
+            c = channel(nx, ny - 2, gb, gt, Kn=Kn, ax=2e-6, name=f"b{k}_channel")
+        elif kind == 1:
+            R2 = 0.45 * min(nx, ny)
+            R1 = float(rng.uniform(0.2, 0.6)) * R2
+            ma = float(rng.uniform(0.02, 0.05))
+            c = annulus(nx, R1, R2, Kn, ma * cs / R1, 0.0, name=f"b{k}_annulus", ny=ny)
+        else:
+            rmax = max(8.0, min(32.0, min(nx, ny) / 8.0))
+            c = cylinder_array(nx, ny, int(rng.integers(0, 2**31)), porosity=0.7, r_min=8.0,
+                               r_max=rmax, Kn=Kn, ax=5e-6, name=f"b{k}_cylinders")
+        c.meta["batch_kind"] = ("channel", "annulus", "cylinders")[kind]
+        out.append(c)
+    return out

@@ -97,29 +97,8 @@ void release(lbm_handle_t *h) {
 
 template <typename C>
 lbm::StepConst<C> step_const(const lbm_handle_t *h) {
-  lbm::StepConst<C> k;
-  k.s_e = static_cast<C>(1.0 / h->cp.tau_e);
-  k.s_eps = static_cast<C>(1.0 / h->cp.tau_eps);
-  k.s_q = static_cast<C>(1.0 / h->cp.tau_q);
-  k.s_s = static_cast<C>(1.0 / h->cp.tau_s);
-  k.s_j = static_cast<C>(1.0 / h->cp.tau_j);
-  k.h_e = static_cast<C>(1.0 - 0.5 / h->cp.tau_e);
-  k.h_eps = static_cast<C>(1.0 - 0.5 / h->cp.tau_eps);
-  k.h_q = static_cast<C>(1.0 - 0.5 / h->cp.tau_q);
-  k.h_s = static_cast<C>(1.0 - 0.5 / h->cp.tau_s);
-  k.h_j = static_cast<C>(1.0 - 0.5 / h->cp.tau_j);
-  k.ax = static_cast<C>(h->ax);
-  k.ay = static_cast<C>(h->ay);
-  k.nx = h->nx;
-  k.ny = h->ny;
-  k.pitch = h->pitch;
-  k.periodic_x = h->px;
-  k.periodic_y = h->py;
-  k.diffuse_mode = h->params.diffuse_mode;
-  k.sc = static_cast<C>(h->scale);
-  k.inv_sc = static_cast<C>(1.0 / h->scale);
-  k.plane = h->plane;
-  return k;
+  return lbm::make_step_const<C>(h->cp, h->nx, h->ny, h->pitch, h->plane, h->px, h->py, h->ax, h->ay,
+                                 h->params.diffuse_mode, h->scale);
 }
 
 cudaError_t do_step(lbm_handle_t *h) {
@@ -141,50 +120,19 @@ cudaError_t do_step(lbm_handle_t *h) {
 }  // namespace
 
 namespace lbm {
-// Error text for handle-less calls, read back by lbm_last_error(NULL).
-const char *set_thread_error(const std::string &msg) {
-  g_create_error = msg;
-  return g_create_error.c_str();
-}
-}  // namespace lbm
-
-extern "C" {
-
-void lbm_params_default(lbm_params_t *p) {
-  if (!p) return;
-  const double nan = std::numeric_limits<double>::quiet_NaN();
-  std::memset(p, 0, sizeof(*p));
-  p->sigma = 1.0;
-  p->L1 = nan;
-  p->L2 = nan;
-  p->E = nan;
-  p->l_clamp = -0.4;
-  p->tau_rho = 1.0;
-  p->tau_j = 1.0;
-  p->tau_e = 1.1;
-  p->tau_eps = 1.2;
-  p->tau_s = nan;
-  p->tau_q = nan;
-  p->r_value = nan;
-  p->l_value = 0.0;
-  p->l_mode = LBM_L_PAPER;
-  p->diffuse_mode = 0;
-  p->precision = LBM_FP32;
-  p->residual_every = 100;
-  p->stream = nullptr;
-}
-
-int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
-               const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
-               const double *link_q, const double *link_ubx, const double *link_uby, double Kn,
-               const lbm_params_t *params, lbm_handle_t **out) {
-  g_create_error.clear();
-  if (out) *out = nullptr;
-  auto bad = [](int code, const std::string &m) {
-    g_create_error = m;
+// Validation and host-side layout of one case: flags, link-table bases and
+// the node-sorted link coefficients (used by lbm_create and
+// lbm_batch_create).  Returns a status code; *err gets the message.
+int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
+                    const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
+                    const double *link_q, const double *link_ubx, const double *link_uby,
+                    double Kn, const lbm_params_t *params, lbm::HostCase *hc,
+                    std::string *err) {
+  auto bad = [err](int code, const std::string &m) {
+    *err = m;
     return code;
   };
-  if (!dom || !solid || !params || !out) return bad(LBM_EINVAL, "null argument");
+  if (!dom || !solid || !params) return bad(LBM_EINVAL, "null argument");
   if (n_links && (!link_x || !link_y || !link_dir || !link_q || !link_ubx || !link_uby))
     return bad(LBM_EINVAL, "null link array");
   const lbm_params_t &p = *params;
@@ -285,55 +233,132 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
       }
     }
 
-  // Per-link parameters (input order), then the node-sorted device table.
-  lbm_handle_t *h = new (std::nothrow) lbm_handle_t();
-  if (!h) return bad(LBM_ENOMEM, "host allocation failed");
-  h->link_r.resize(n_links);
-  h->link_l.resize(n_links);
+  // Per-link parameters (input order), then the node-sorted table.
+  hc->link_r.assign(n_links, 0.0);
+  hc->link_l.assign(n_links, 0.0);
   std::vector<double> coef(8 * n_links);
   msg = lbm::compute_link_coefs(cp, p, n_links, link_dir, link_q, link_ubx, link_uby,
-                                h->link_r.data(), h->link_l.data(), coef.data(), &cp.n_clamped);
-  if (!msg.empty()) {
-    delete h;
-    return bad(LBM_EINVAL, msg);
-  }
+                                hc->link_r.data(), hc->link_l.data(), coef.data(), &cp.n_clamped);
+  if (!msg.empty()) return bad(LBM_EINVAL, msg);
   std::vector<int64_t> order(n_links);
   std::iota(order.begin(), order.end(), 0);
   auto key = [&](int64_t k) {
     return (static_cast<int64_t>(link_y[k]) * pitch + link_x[k]) * 16 + link_dir[k];
   };
   std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
-  std::vector<int32_t> lbase(static_cast<size_t>(plane), -1);
+  hc->lbase.assign(static_cast<size_t>(plane), -1);
   for (int64_t s = static_cast<int64_t>(n_links) - 1; s >= 0; s--) {
     const int64_t k = order[s];
-    lbase[(size_t)link_y[k] * pitch + link_x[k]] = static_cast<int32_t>(s);
+    hc->lbase[(size_t)link_y[k] * pitch + link_x[k]] = static_cast<int32_t>(s);
   }
+  hc->coef.resize(4 * n_links);
+  for (size_t q = 0; q < n_links; q++)
+    for (int j = 0; j < 4; j++) hc->coef[4 * q + j] = coef[8 * order[q] + j];
+  hc->flags.swap(flags);
+  hc->nx = nx;
+  hc->ny = ny;
+  hc->pitch = pitch;
+  hc->plane = plane;
+  hc->px = px;
+  hc->py = py;
+  hc->ax = dom->ax;
+  hc->ay = dom->ay;
+  hc->scale = p.precision == LBM_FP16 ? (p.storage_scale > 0.0 ? p.storage_scale : 4096.0) : 1.0;
+  hc->cp = cp;
+  hc->params = p;
+  hc->n_fluid = n_fluid;
+  hc->n_links = static_cast<int64_t>(n_links);
+  return LBM_OK;
 
+}
+
+}  // namespace lbm
+
+namespace lbm {
+// Error text for handle-less calls, read back by lbm_last_error(NULL).
+const char *set_thread_error(const std::string &msg) {
+  g_create_error = msg;
+  return g_create_error.c_str();
+}
+}  // namespace lbm
+
+extern "C" {
+
+void lbm_params_default(lbm_params_t *p) {
+  if (!p) return;
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  std::memset(p, 0, sizeof(*p));
+  p->sigma = 1.0;
+  p->L1 = nan;
+  p->L2 = nan;
+  p->E = nan;
+  p->l_clamp = -0.4;
+  p->tau_rho = 1.0;
+  p->tau_j = 1.0;
+  p->tau_e = 1.1;
+  p->tau_eps = 1.2;
+  p->tau_s = nan;
+  p->tau_q = nan;
+  p->r_value = nan;
+  p->l_value = 0.0;
+  p->l_mode = LBM_L_PAPER;
+  p->diffuse_mode = 0;
+  p->precision = LBM_FP32;
+  p->residual_every = 100;
+  p->stream = nullptr;
+}
+
+int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
+               const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
+               const double *link_q, const double *link_ubx, const double *link_uby, double Kn,
+               const lbm_params_t *params, lbm_handle_t **out) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "null argument";
+    return LBM_EINVAL;
+  }
+  *out = nullptr;
+  lbm::HostCase hc;
+  int rc = lbm::build_host_case(dom, solid, n_links, link_x, link_y, link_dir, link_q, link_ubx,
+                                link_uby, Kn, params, &hc, &g_create_error);
+  if (rc != LBM_OK) return rc;
+  lbm_handle_t *h = new (std::nothrow) lbm_handle_t();
+  if (!h) {
+    g_create_error = "host allocation failed";
+    return LBM_ENOMEM;
+  }
+  const lbm_params_t &p = *params;
+  const int64_t plane = hc.plane;
+  h->link_r.swap(hc.link_r);
+  h->link_l.swap(hc.link_l);
+  std::vector<uint8_t> &flags = hc.flags;
+  std::vector<int32_t> &lbase = hc.lbase;
+  const size_t n_links_sz = static_cast<size_t>(hc.n_links);
   h->precision = p.precision;
-  h->scale = p.precision == LBM_FP16 ? (p.storage_scale > 0.0 ? p.storage_scale : 4096.0) : 1.0;
+  h->scale = hc.scale;
   h->stream = static_cast<cudaStream_t>(p.stream);
-  h->nx = nx;
-  h->ny = ny;
-  h->pitch = pitch;
-  h->plane = plane;
-  h->px = px;
-  h->py = py;
-  h->ax = dom->ax;
-  h->ay = dom->ay;
-  h->cp = cp;
+  h->nx = hc.nx;
+  h->ny = hc.ny;
+  h->pitch = hc.pitch;
+  h->plane = hc.plane;
+  h->px = hc.px;
+  h->py = hc.py;
+  h->ax = hc.ax;
+  h->ay = hc.ay;
+  h->cp = hc.cp;
   h->params = p;
-  h->n_fluid = n_fluid;
-  h->n_links = static_cast<int64_t>(n_links);
+  h->n_fluid = hc.n_fluid;
+  h->n_links = hc.n_links;
   cudaGetDevice(&h->device);
 
   const size_t es = elem_size(p.precision);
   const size_t fbytes = 9 * static_cast<size_t>(plane) * es;
   const size_t ces = p.precision == LBM_FP64 ? 8 : 4;  // link coefficients: FP64 or FP32
-  const size_t lbytes = std::max<size_t>(1, n_links) * 4 * ces;
+  const size_t lbytes = std::max<size_t>(1, n_links_sz) * 4 * ces;
   const size_t pbytes = lbm::kResidualBlocks * lbm::kPartialStride * sizeof(double);
   std::vector<unsigned char> lhost(lbytes, 0);
-  for (size_t s = 0; s < n_links; s++) {
-    const double *c = &coef[8 * order[s]];
+  for (size_t s = 0; s < n_links_sz; s++) {
+    const double *c = &hc.coef[4 * s];
     if (ces == 8) {
       std::memcpy(&lhost[s * 32], c, 32);
     } else {

@@ -1,0 +1,246 @@
+// Device-side building blocks shared by the kernels of liblbm.so: storage
+// conversion, the fused collide-stream-boundary update of one node, and the
+// pieces of the FP64 reductions.
+#pragma once
+
+#include <cstdint>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace dev {
+
+
+// Storage of a deviation d as T and its arithmetic type C.  FP32 and FP64
+// store d itself; the 16-bit types store d * scale (scale a power of two,
+// 1 for BF16), so loads and stores are exact apart from the rounding to T.
+template <typename T>
+struct Stor {
+  using C = T;
+  static __device__ __forceinline__ C ld(T v, C) { return v; }
+  static __device__ __forceinline__ T st(C v, C) { return v; }
+};
+template <>
+struct Stor<__half> {
+  using C = float;
+  static __device__ __forceinline__ float ld(__half v, float inv) { return __half2float(v) * inv; }
+  static __device__ __forceinline__ __half st(float v, float sc) { return __float2half_rn(v * sc); }
+};
+template <>
+struct Stor<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ float ld(__nv_bfloat16 v, float inv) {
+    return __bfloat162float(v) * inv;
+  }
+  static __device__ __forceinline__ __nv_bfloat16 st(float v, float sc) {
+    return __float2bfloat16_rn(v * sc);
+  }
+};
+
+
+template <typename C>
+__device__ __forceinline__ C recip(C v);
+template <>
+__device__ __forceinline__ float recip<float>(float v) {
+  return __frcp_rn(v);
+}
+template <>
+__device__ __forceinline__ double recip<double>(double v) {
+  return 1.0 / v;
+}
+
+// One time step for node (x, y), x < nx (see the file comment of
+// lbm_kernels.cu): load, collide, push, link epilogue.  xe / xw are the
+// (wrapped) columns x +- 1.
+template <typename T, typename C>
+__device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restrict__ dst,
+                                          const uint8_t *__restrict__ flags,
+                                          const int32_t *__restrict__ lbase,
+                                          const LinkCoef<C> *__restrict__ links,
+                                          const StepConst<C> &k, const int x, const int y,
+                                          const int xe, const int xw) {
+  const uint32_t P = static_cast<uint32_t>(k.plane);
+  const uint32_t rowc = static_cast<uint32_t>(y) * k.pitch;
+  const uint32_t node = rowc + x;
+  const uint8_t fl = flags[node];
+  if (fl == kSolid) return;
+  const int yn = (y + 1 == k.ny) ? (k.periodic_y ? 0 : y + 1) : y + 1;
+  const int ys = (y == 0) ? (k.periodic_y ? k.ny - 1 : 0) : y - 1;
+  const uint32_t rown = static_cast<uint32_t>(yn) * k.pitch;
+  const uint32_t rows = static_cast<uint32_t>(ys) * k.pitch;
+
+  C d[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) d[i] = Stor<T>::ld(src[i * P + node], k.inv_sc);
+  // First link of this node (links sorted by node, then direction), loaded
+  // now so that its latency overlaps the collision.
+  const int lb = fl ? lbase[node] : 0;
+
+  // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
+  const C s14 = (d[1] + d[2]) + (d[3] + d[4]);
+  const C s58 = (d[5] + d[6]) + (d[7] + d[8]);
+  const C drho = d[0] + s14 + s58;
+  const C e = C(-4) * d[0] - s14 + C(2) * s58;
+  const C eps = C(4) * d[0] - C(2) * s14 + s58;
+  const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
+  const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
+  const C jx = d[1] - d[3] + d5m6 + d8m7;
+  const C qx = C(2) * (d[3] - d[1]) + d5m6 + d8m7;
+  const C jy = d[2] - d[4] + d5p6 - d7p8;
+  const C qy = C(2) * (d[4] - d[2]) + d5p6 - d7p8;
+  const C pxx = d[1] - d[2] + d[3] - d[4];
+  const C pxy = d[5] - d[6] + d[7] - d[8];
+
+  // Eq. FluidMacr.
+  const C rho = C(1) + drho;
+  const C rax = rho * k.ax, ray = rho * k.ay;
+  const C inv_rho = recip<C>(rho);
+  const C ux = (jx + C(0.5) * rax) * inv_rho;
+  const C uy = (jy + C(0.5) * ray) * inv_rho;
+  const C uu = ux * ux + uy * uy;
+  const C rux = rho * ux, ruy = rho * uy;
+
+  // Eq. MomentPost: m' = m - S (m - m_eq) + (I - S/2) M Fbar, with M f_eq
+  // and M Fbar in closed form; the factors (1 - s/2) come precomputed.
+  const C ua6 = C(6) * (rux * k.ax + ruy * k.ay);
+  const C e_p = e - k.s_e * (e + C(2) * drho - C(3) * rho * uu) + k.h_e * ua6;
+  const C eps_p = eps - k.s_eps * (eps - drho + C(3) * rho * uu) - k.h_eps * ua6;
+  const C jx_p = jx - k.s_j * (jx - rux) + k.h_j * rax;
+  const C jy_p = jy - k.s_j * (jy - ruy) + k.h_j * ray;
+  const C qx_p = qx - k.s_q * (qx + rux) - k.h_q * rax;
+  const C qy_p = qy - k.s_q * (qy + ruy) - k.h_q * ray;
+  const C pxx_p = pxx - k.s_s * (pxx - rho * (ux * ux - uy * uy)) +
+                  k.h_s * C(2) * (rux * k.ax - ruy * k.ay);
+  const C pxy_p = pxy - k.s_s * (pxy - rho * ux * uy) + k.h_s * (rux * k.ay + ruy * k.ax);
+
+  // f' = M^-1 m' with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+  const C r9 = drho * C(1.0 / 9.0);
+  const C e36 = e_p * C(1.0 / 36.0), p36 = eps_p * C(1.0 / 36.0);
+  const C jx6 = jx_p * C(1.0 / 6.0), jy6 = jy_p * C(1.0 / 6.0);
+  const C qx12 = qx_p * C(1.0 / 12.0), qy12 = qy_p * C(1.0 / 12.0);
+  const C xx4 = pxx_p * C(0.25), xy4 = pxy_p * C(0.25);
+  const C axis = r9 - e36 - C(2) * p36;
+  const C diag = r9 + C(2) * e36 + p36;
+  const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
+  const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
+  C o[9];
+  o[1] = axis + ax_x + xx4;
+  o[2] = axis + ax_y - xx4;
+  o[3] = axis - ax_x + xx4;
+  o[4] = axis - ax_y - xx4;
+  o[5] = diag + dg_x + dg_y + xy4;
+  o[6] = diag - dg_x + dg_y - xy4;
+  o[7] = diag - dg_x - dg_y + xy4;
+  o[8] = diag + dg_x - dg_y - xy4;
+  // The rest population closes the mass balance: M^-1 m' conserves sum f
+  // exactly only in exact arithmetic, so f'_0 = drho - sum_{i>0} f'_i
+  // (equal to r9 - 4 e36 + 4 p36 up to rounding) keeps the stored mass
+  // unchanged by the collision to within one rounding of f'_0.
+  // Round f'_1..f'_8 to storage first (a no-op for FP32/FP64), so that the
+  // closure below balances the values actually stored.
+  T t[9];
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    t[i] = Stor<T>::st(o[i], k.sc);
+    o[i] = Stor<T>::ld(t[i], k.inv_sc);
+  }
+  o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+  t[0] = Stor<T>::st(o[0], k.sc);
+
+  // Streaming: push f'_i to x + c_i unless that node is solid; bit (j-1)
+  // set <=> x - c_j solid, so push i needs bit opp(i) clear.
+  dst[node] = t[0];
+  if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = t[1];  // opp(1) = 3
+  if (!(fl & (1u << 3))) dst[2 * P + rown + x] = t[2];   // opp(2) = 4
+  if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = t[3];  // opp(3) = 1
+  if (!(fl & (1u << 1))) dst[4 * P + rows + x] = t[4];   // opp(4) = 2
+  if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = t[5];  // opp(5) = 7
+  if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = t[6];  // opp(6) = 8
+  if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = t[7];  // opp(7) = 5
+  if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = t[8];  // opp(8) = 6
+
+  // Boundary links of this node, Eq. EqNewBDSC in the folded form of
+  // LinkCoef.  Directions that no active lane of the warp needs are
+  // skipped warp-uniformly (solid lanes and lanes past nx have left).
+  const unsigned wmask = __reduce_or_sync(__activemask(), static_cast<unsigned>(fl));
+  if (wmask) {
+    int li = lb;
+#pragma unroll
+    for (int j = 1; j < 9; j++) {
+      if (!(wmask & (1u << (j - 1)))) continue;
+      if (fl & (1u << (j - 1))) {
+        constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        constexpr int cx_tab[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        constexpr int cy_tab[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        constexpr double w_tab[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        const int jb = opp_tab[j];
+        const LinkCoef<C> c = links[li++];
+        const C r = c.k1 + c.k2 + c.k3;
+        C c0, c2;
+        if (k.diffuse_mode == 0) {
+          c0 = c.alpha;
+          c2 = (C(1) - r) * C(w_tab[j]);
+        } else {
+          c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
+          c2 = C(0);
+        }
+        const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
+        const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+        const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
+                    c2 * (drho + rho * pj);
+        dst[j * P + node] = Stor<T>::st(v, k.sc);
+      }
+    }
+  }
+}
+
+// Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).
+__device__ __forceinline__ double node_velocity(const double *d, double ax, double ay, double &rho,
+                                                double &ux, double &uy) {
+  double drho = 0.0, jx, jy;
+  for (int i = 0; i < 9; i++) drho += d[i];
+  jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+  jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  rho = 1.0 + drho;
+  ux = (jx + 0.5 * rho * ax) / rho;
+  uy = (jy + 0.5 * rho * ay) / rho;
+  return drho;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Residual terms of one node from its deviations now (a) and one step
+// earlier (b), in arithmetic type C.  The per-population change a - b is
+// exact in floating point (Sterbenz) for the small steps near steady state,
+// so u^n - u^(n-1) is formed from it rather than by subtracting velocities:
+//   u1 - u0 = (dj rho0 - j0 drho) / (rho0 rho1)   (the a/2 terms cancel).
+template <typename C>
+__device__ __forceinline__ void residual_terms(const C (&a)[9], const C (&b)[9], C ax, C ay,
+                                               C &num, C &den, C &drho1) {
+  C dd[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) dd[i] = a[i] - b[i];
+  const C r0 = C(1) + (((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7])) + b[8]);
+  const C dr = ((dd[0] + dd[1]) + (dd[2] + dd[3])) + ((dd[4] + dd[5]) + (dd[6] + dd[7])) + dd[8];
+  const C jx0 = b[1] - b[3] + (b[5] - b[6]) + (b[8] - b[7]);
+  const C jy0 = b[2] - b[4] + (b[5] + b[6]) - (b[7] + b[8]);
+  const C djx = dd[1] - dd[3] + (dd[5] - dd[6]) + (dd[8] - dd[7]);
+  const C djy = dd[2] - dd[4] + (dd[5] + dd[6]) - (dd[7] + dd[8]);
+  const C r1 = r0 + dr;
+  const C inv = C(1) / (r0 * r1);
+  const C dux = (djx * r0 - jx0 * dr) * inv;
+  const C duy = (djy * r0 - jy0 * dr) * inv;
+  const C ux1 = (jx0 + djx + C(0.5) * r1 * ax) / r1;
+  const C uy1 = (jy0 + djy + C(0.5) * r1 * ay) / r1;
+  num = dux * dux + duy * duy;
+  den = ux1 * ux1 + uy1 * uy1;
+  drho1 = r1 - C(1);
+}
+
+}  // namespace dev
+}  // namespace lbm

@@ -52,6 +52,57 @@ struct CaseParams {
   int64_t n_clamped;
 };
 
+// One validated case laid out for the device (host copy): node flags, the
+// first link of every node, and the node-sorted link coefficients
+// (k1, k2, k3, alpha per link, FP64).
+struct HostCase {
+  int32_t nx = 0, ny = 0, pitch = 0, px = 0, py = 0;
+  int64_t plane = 0, n_fluid = 0, n_links = 0;
+  double ax = 0.0, ay = 0.0, scale = 1.0;
+  CaseParams cp{};
+  lbm_params_t params{};
+  std::vector<uint8_t> flags;
+  std::vector<int32_t> lbase;
+  std::vector<double> coef;
+  std::vector<double> link_r, link_l;  // per link in input order
+};
+
+// Kernel constants of one case in arithmetic type C.
+template <typename C>
+StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32_t pitch,
+                             int64_t plane, int32_t px, int32_t py, double ax, double ay,
+                             int32_t diffuse_mode, double scale) {
+  StepConst<C> k;
+  k.s_e = static_cast<C>(1.0 / cp.tau_e);
+  k.s_eps = static_cast<C>(1.0 / cp.tau_eps);
+  k.s_q = static_cast<C>(1.0 / cp.tau_q);
+  k.s_s = static_cast<C>(1.0 / cp.tau_s);
+  k.s_j = static_cast<C>(1.0 / cp.tau_j);
+  k.h_e = static_cast<C>(1.0 - 0.5 / cp.tau_e);
+  k.h_eps = static_cast<C>(1.0 - 0.5 / cp.tau_eps);
+  k.h_q = static_cast<C>(1.0 - 0.5 / cp.tau_q);
+  k.h_s = static_cast<C>(1.0 - 0.5 / cp.tau_s);
+  k.h_j = static_cast<C>(1.0 - 0.5 / cp.tau_j);
+  k.sc = static_cast<C>(scale);
+  k.inv_sc = static_cast<C>(1.0 / scale);
+  k.ax = static_cast<C>(ax);
+  k.ay = static_cast<C>(ay);
+  k.nx = nx;
+  k.ny = ny;
+  k.pitch = pitch;
+  k.periodic_x = px;
+  k.periodic_y = py;
+  k.diffuse_mode = diffuse_mode;
+  k.plane = plane;
+  return k;
+}
+
+// Validation and layout of one case (lbm_api.cu).
+int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
+                    const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
+                    const double *link_q, const double *link_ubx, const double *link_uby,
+                    double Kn, const lbm_params_t *params, HostCase *hc, std::string *err);
+
 // Host-side FP64 precompute (lbm_params.cpp).  Returns "" or an error text.
 std::string compute_case_params(double Kn, double H, const lbm_params_t &p, CaseParams *out);
 // Per-link l and r (Sec. 3.B) and the folded coefficients above.

@@ -26,7 +26,9 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16": LBM_BF16, "fp16": LBM_
 # Every entry point include/lbm.h declares.
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_residual",
            "lbm_run_to", "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info",
-           "lbm_precompute", "lbm_residual_noalloc", "lbm_destroy", "lbm_last_error")
+           "lbm_precompute", "lbm_residual_noalloc", "lbm_destroy", "lbm_last_error",
+           "lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
+           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error")
 
 
 class LbmError(RuntimeError):
@@ -63,6 +65,14 @@ class Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("pitch", ctypes.c_int32)]
 
 
+class CaseDesc(ctypes.Structure):
+    _fields_ = [("dom", Domain), ("solid", ctypes.c_void_p), ("n_links", ctypes.c_size_t),
+                ("link_x", ctypes.c_void_p), ("link_y", ctypes.c_void_p),
+                ("link_dir", ctypes.c_void_p), ("link_q", ctypes.c_void_p),
+                ("link_ubx", ctypes.c_void_p), ("link_uby", ctypes.c_void_p),
+                ("Kn", ctypes.c_double), ("params", Params)]
+
+
 _lib = None
 
 
@@ -97,6 +107,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.c_double, ctypes.c_void_p, dp, dp]
     lib.lbm_destroy.argtypes = [H]
     lib.lbm_destroy.restype = None
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.lbm_batch_create.argtypes = [ctypes.POINTER(CaseDesc), ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.POINTER(H)]
+    lib.lbm_batch_reset.argtypes = [H]
+    lib.lbm_batch_run_to.argtypes = [H, ctypes.c_double, ctypes.c_int64, ctypes.c_int32, i64p, dp,
+                                     i64p]
+    lib.lbm_batch_fields.argtypes = [H, ctypes.c_int32, dp, dp, dp]
+    lib.lbm_batch_info.argtypes = [H, i64p, i64p, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32)]
+    lib.lbm_batch_destroy.argtypes = [H]
+    lib.lbm_batch_destroy.restype = None
+    lib.lbm_batch_last_error.argtypes = [H]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
+                 "lbm_batch_info"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.lbm_last_error.argtypes = [H]
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_step", "lbm_fields", "lbm_residual", "lbm_run_to",
@@ -325,3 +351,111 @@ class Solver:
 
     def info(self) -> Info:
         return lbm_get_info(self.h)
+
+
+# --------------------------------------------------------------------------
+# batched solver
+# --------------------------------------------------------------------------
+
+def _bcheck(rc, b=None):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_batch_last_error(b).decode())
+
+
+def make_params(**kw) -> Params:
+    """lbm_params_t with the keyword overrides of `Solver`."""
+    p = lbm_params_default()
+    l_mode = kw.pop("l_mode", "paper")
+    if isinstance(l_mode, str):
+        p.l_mode = L_MODES[l_mode]
+    else:
+        p.l_mode = L_MODES["fixed"]
+        p.l_value = float(l_mode)
+    for key, field in (("r", "r_value"), ("tau_q", "tau_q"), ("tau_s", "tau_s"), ("E", "E"),
+                       ("L1", "L1"), ("L2", "L2")):
+        v = kw.pop(key, None)
+        setattr(p, field, math.nan if v is None else float(v))
+    if kw.pop("bgk", False):
+        p.collision = 1
+    for key in ("sigma", "diffuse_mode", "tau_e", "tau_eps", "l_clamp", "storage_scale"):
+        if key in kw:
+            setattr(p, key, kw.pop(key))
+    if kw:
+        raise TypeError(f"unknown parameters {sorted(kw)}")
+    return p
+
+
+class Batch:
+    """Many cases advanced together (lbm_batch_*).  `cases` is a list of
+    `cases.Case`; `params` an optional list of keyword dicts (see
+    `Solver`) per case."""
+
+    def __init__(self, case_list, precision="fp32", params=None, stream=None):
+        lib = load()
+        self.cases = list(case_list)
+        n = len(self.cases)
+        descs = (CaseDesc * n)()
+        self._keep = []
+        for k, c in enumerate(self.cases):
+            arrs = [np.ascontiguousarray(c.solid, np.uint8).reshape(-1),
+                    np.ascontiguousarray(c.link_x, np.int32), np.ascontiguousarray(c.link_y, np.int32),
+                    np.ascontiguousarray(c.link_dir, np.int32),
+                    np.ascontiguousarray(c.link_q, np.float64),
+                    np.ascontiguousarray(c.link_ubx, np.float64),
+                    np.ascontiguousarray(c.link_uby, np.float64)]
+            self._keep.append(arrs)
+            d = descs[k]
+            d.dom = Domain(c.nx, c.ny, int(c.periodic_x), int(c.periodic_y), c.H, c.ax, c.ay)
+            d.solid = arrs[0].ctypes.data
+            d.n_links = c.n_links
+            d.link_x, d.link_y, d.link_dir = (arrs[1].ctypes.data, arrs[2].ctypes.data,
+                                              arrs[3].ctypes.data)
+            d.link_q, d.link_ubx, d.link_uby = (arrs[4].ctypes.data, arrs[5].ctypes.data,
+                                                arrs[6].ctypes.data)
+            d.Kn = c.Kn
+            d.params = make_params(**(params[k] if params else {}))
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _bcheck(lib.lbm_batch_create(descs, n, prec, stream, ctypes.byref(h)))
+        self.h = h.value
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _bcheck(load().lbm_batch_reset(self.h), self.h)
+
+    def run_to(self, tol: float, max_steps: int, check_every: int = 100):
+        """Returns (steps per case, residual per case, total steps)."""
+        n = len(self.cases)
+        steps = np.zeros(n, np.int64)
+        res = np.zeros(n)
+        tot = ctypes.c_int64()
+        _bcheck(load().lbm_batch_run_to(self.h, float(tol), int(max_steps), int(check_every),
+                                        steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        _dp(res), ctypes.byref(tot)), self.h)
+        return steps, res, tot.value
+
+    def fields(self, k: int):
+        c = self.cases[k]
+        n = c.nx * c.ny
+        rho, ux, uy = np.empty(n), np.empty(n), np.empty(n)
+        _bcheck(load().lbm_batch_fields(self.h, int(k), _dp(rho), _dp(ux), _dp(uy)), self.h)
+        s = (c.ny, c.nx)
+        return rho.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def info(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        t, nt = ctypes.c_int32(), ctypes.c_int32()
+        _bcheck(load().lbm_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t),
+                                      ctypes.byref(nt)), self.h)
+        return dict(total_nodes=a.value, total_fluid=b.value, cta_threads=t.value, n_tiles=nt.value)

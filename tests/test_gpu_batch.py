@@ -1,0 +1,70 @@
+"""Batched solver (lbm_batch_*) against lone solvers and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import params as P
+from paper_2012_14707_gb300 import build as lbm_build
+from paper_2012_14707_gb300 import cases, lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lbm_build.build()
+    lbm.load()
+    oracle.build()
+
+
+def _small_batch():
+    return cases.batch_cases(7, seed=3, nx_range=(40, 130), ny_range=(40, 96),
+                             kn_range=(0.01, 0.1))
+
+
+def test_case_in_batch_is_bitwise_the_case_alone():
+    """Every case of a mixed batch converges at the same step, to bitwise the
+    same fields, as the same case run alone with the same check interval."""
+    cl = _small_batch()
+    b = lbm.Batch(cl, precision="fp32")
+    steps, res, total = b.run_to(1e-6, 8000, check_every=100)
+    assert (steps != 0).any()
+    for k, c in enumerate(cl):
+        s = lbm.Solver(c, precision="fp32", residual_every=100)
+        n, r = s.run_to(1e-6, 8000)
+        if steps[k] > 0:
+            assert n == steps[k], (k, n, steps[k])
+        got = b.fields(k)
+        want = s.fields()
+        for a, w in zip(got, want):
+            np.testing.assert_array_equal(a, w)
+
+
+def test_batch_matches_oracle_fp64():
+    """FP64 batch of three different cases, 300 steps, against the oracle."""
+    cl = _small_batch()[:3]
+    b = lbm.Batch(cl, precision="fp64")
+    steps, res, total = b.run_to(0.0, 300, check_every=100)
+    assert total == 300 and (steps == 0).all()
+    for k, c in enumerate(cl):
+        o = oracle.OracleLBM(c, P.Parameters(c.Kn, c.H))
+        o.step(300)
+        for a, w in zip(b.fields(k), o.fields()):
+            np.testing.assert_allclose(a, w, rtol=0, atol=1e-12)
+
+
+def test_batch_reset_and_info():
+    cl = _small_batch()[:2]
+    b = lbm.Batch(cl, precision="fp32")
+    info = b.info()
+    assert info["total_nodes"] == sum(c.nx * c.ny for c in cl)
+    assert info["total_fluid"] == sum(c.n_fluid for c in cl)
+    assert info["cta_threads"] in (64, 128, 256)
+    s1 = b.run_to(0.0, 200, 100)
+    f1 = b.fields(1)
+    b.reset()
+    s2 = b.run_to(0.0, 200, 100)
+    for a, w in zip(b.fields(1), f1):
+        np.testing.assert_array_equal(a, w)
+    with pytest.raises(lbm.LbmError):
+        b.run_to(1e-6, 100, check_every=3)

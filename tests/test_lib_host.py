@@ -128,3 +128,16 @@ def test_bgk_precompute_matches_oracle(lib):
         r_o, l_o = par.per_link(g)
         np.testing.assert_allclose(l, l_o, rtol=1e-13, atol=1e-14)
         np.testing.assert_allclose(r, r_o, rtol=1e-13)
+
+
+def test_batch_create_reports_the_bad_case(lib):
+    """Batch validation runs on the host before any device call and names
+    the offending case."""
+    good = cases.channel(6, 5, 0.5, 0.3, Kn=0.05)
+    q = good.link_q.copy()
+    q[0] = 2.0
+    bad = dataclasses.replace(good, link_q=q)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Batch([good, bad])
+    assert ei.value.code == lbm.LBM_EINVAL
+    assert "case 1" in str(ei.value)

@@ -205,6 +205,82 @@ int lbm_residual_noalloc(const double *f_cur, const double *f_prev, const uint8_
                          int32_t nx, int32_t ny, double ax, double ay, void *stream,
                          double *residual, double *mass);
 
+/* ---------------------------------------------------------------------------
+ * Batched solver: many independent cases of different sizes, geometries and
+ * parameters advanced together.  Each case is what lbm_create takes; all of
+ * them are stored in one precision.  A step is one launch over every active
+ * case; every check_every steps a batched reduction computes each case's
+ * residual (as lbm_residual) and retires converged cases on the device; the
+ * steps and the reduction run as one captured CUDA graph.  Cases follow the
+ * same per-node arithmetic as a lone case created with the same inputs.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch_t;
+
+typedef struct {
+  lbm_domain_t dom;
+  const uint8_t *solid;  /* nx*ny bytes, as lbm_create */
+  size_t n_links;
+  const int32_t *link_x, *link_y, *link_dir;
+  const double *link_q, *link_ubx, *link_uby;
+  double Kn;
+  lbm_params_t params;   /* precision and stream are taken from the batch */
+} lbm_case_t;
+
+/* Copy and validate n_cases cases (errors name the case), lay them out on
+ * the device, pick the CTA width by timing (cached per size class), start
+ * every case at rest.  stream: cudaStream_t or NULL (the batch then makes
+ * its own, since graph capture needs a non-legacy stream). */
+int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision, void *stream,
+                     lbm_batch_t **out);
+/* Back to rest, every case active, step counts zero. */
+int lbm_batch_reset(lbm_batch_t *b);
+/* Advance all active cases, check_every (even, >= 2) steps at a time, until
+ * every case has residual < tol or max_steps were taken.  Outputs (host,
+ * n_cases entries, may be NULL): the step count at which each case met tol
+ * (negative if it became non-finite, 0 if still running) and its last
+ * residual; *steps_total = steps taken by the batch.  Synchronises. */
+int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t check_every,
+                     int64_t *steps_per_case, double *residual_per_case, int64_t *steps_total);
+/* Density and velocity of case c (host arrays of nx*ny doubles, may be NULL). */
+int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double *uy);
+int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fluid,
+                   int32_t *cta_threads, int32_t *n_tiles);
+void lbm_batch_destroy(lbm_batch_t *b);
+/* Last error of the batch; with b = NULL, of the last failed lbm_batch_create. */
+const char *lbm_batch_last_error(const lbm_batch_t *b);
+
+/* ---------------------------------------------------------------------------
+ * Warm-start network (the paper has none): a convolutional encoder-decoder
+ * with `levels` levels and `base` channels at the top level, doubling per
+ * level; per level two 3x3 convolutions with ReLU, 2x2 average pooling
+ * down, nearest upsampling and concatenation with the encoder output up,
+ * a 1x1 convolution to c_out outputs.  Inputs / outputs are NHWC FP32 device
+ * arrays of H x W pixels.  precision: LBM_BF16 (activations and gradients
+ * stored in BF16, every product accumulated in FP32; master weights and Adam
+ * state FP32) or LBM_FP32.  Parameters are one FP32 vector, layer by layer
+ * (encoder levels top-down, decoder levels bottom-up, head), each layer its
+ * weights [kh][kw][ci][co] then its biases; lbm_net_create draws He-normal
+ * weights from `seed` and zero biases.  Calls synchronise `stream`.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_net lbm_net_t;
+int lbm_net_create(int32_t base, int32_t levels, int32_t c_in, int32_t c_out, int32_t precision,
+                   int32_t max_batch, int32_t H, int32_t W, uint64_t seed, void *stream,
+                   lbm_net_t **out);
+int64_t lbm_net_num_params(const lbm_net_t *n);
+int lbm_net_set_params(lbm_net_t *n, const float *params, int64_t count);  /* host; resets Adam */
+int lbm_net_get_params(const lbm_net_t *n, float *params, int64_t count);  /* host */
+/* y = net(x) for `batch` samples (device arrays). */
+int lbm_net_forward(lbm_net_t *n, const float *x, int32_t batch, float *y);
+/* Mean squared error of net(x) against t and its gradient with respect to
+ * every parameter (host array of lbm_net_num_params floats, may be NULL). */
+int lbm_net_gradients(lbm_net_t *n, const float *x, const float *t, int32_t batch, float *grads,
+                      double *loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on that loss. */
+int lbm_net_train_step(lbm_net_t *n, const float *x, const float *t, int32_t batch, float lr,
+                       double *loss);
+void lbm_net_destroy(lbm_net_t *n);
+const char *lbm_net_last_error(const lbm_net_t *n);
+
 /* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
 void lbm_destroy(lbm_handle_t *h);
 

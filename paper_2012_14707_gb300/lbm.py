@@ -28,7 +28,10 @@ EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_re
            "lbm_run_to", "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info",
            "lbm_precompute", "lbm_residual_noalloc", "lbm_destroy", "lbm_last_error",
            "lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
-           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error")
+           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
+           "lbm_net_create", "lbm_net_num_params", "lbm_net_set_params", "lbm_net_get_params",
+           "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_destroy",
+           "lbm_net_last_error")
 
 
 class LbmError(RuntimeError):
@@ -122,6 +125,24 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_batch_last_error.restype = ctypes.c_char_p
     for name in ("lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
                  "lbm_batch_info"):
+        getattr(lib, name).restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.lbm_net_create.argtypes = [ctypes.c_int32] * 8 + [ctypes.c_uint64, ctypes.c_void_p,
+                                                          ctypes.POINTER(H)]
+    lib.lbm_net_num_params.argtypes = [H]
+    lib.lbm_net_num_params.restype = ctypes.c_int64
+    lib.lbm_net_set_params.argtypes = [H, fp, ctypes.c_int64]
+    lib.lbm_net_get_params.argtypes = [H, fp, ctypes.c_int64]
+    lib.lbm_net_forward.argtypes = [H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    lib.lbm_net_gradients.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, fp, dp]
+    lib.lbm_net_train_step.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_float, dp]
+    lib.lbm_net_destroy.argtypes = [H]
+    lib.lbm_net_destroy.restype = None
+    lib.lbm_net_last_error.argtypes = [H]
+    lib.lbm_net_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_net_create", "lbm_net_set_params", "lbm_net_get_params", "lbm_net_forward",
+                 "lbm_net_gradients", "lbm_net_train_step"):
         getattr(lib, name).restype = ctypes.c_int
     lib.lbm_last_error.argtypes = [H]
     lib.lbm_last_error.restype = ctypes.c_char_p
@@ -459,3 +480,71 @@ class Batch:
         _bcheck(load().lbm_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t),
                                       ctypes.byref(nt)), self.h)
         return dict(total_nodes=a.value, total_fluid=b.value, cta_threads=t.value, n_tiles=nt.value)
+
+
+# --------------------------------------------------------------------------
+# warm-start network
+# --------------------------------------------------------------------------
+
+def _ncheck(rc, n=None):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm_net_last_error(n).decode())
+
+
+class Net:
+    """The warm-start encoder-decoder (lbm_net_*).  Inputs and outputs are
+    device pointers (int) to NHWC FP32 arrays, e.g. torch tensors'
+    data_ptr()."""
+
+    def __init__(self, H, W, base=32, levels=4, c_in=3, c_out=3, precision="bf16", max_batch=8,
+                 seed=0, stream=None):
+        lib = load()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _ncheck(lib.lbm_net_create(base, levels, c_in, c_out, prec, max_batch, H, W, seed, stream,
+                                   ctypes.byref(h)))
+        self.h = h.value
+        self.H, self.W, self.c_in, self.c_out, self.max_batch = H, W, c_in, c_out, max_batch
+
+    @property
+    def n_params(self) -> int:
+        return int(load().lbm_net_num_params(self.h))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, np.float32)
+        _ncheck(load().lbm_net_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          p.size), self.h)
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _ncheck(load().lbm_net_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          p.size), self.h)
+
+    def forward(self, x_ptr: int, n: int, y_ptr: int):
+        _ncheck(load().lbm_net_forward(self.h, x_ptr, int(n), y_ptr), self.h)
+
+    def gradients(self, x_ptr: int, t_ptr: int, n: int):
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        _ncheck(load().lbm_net_gradients(self.h, x_ptr, t_ptr, int(n),
+                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         ctypes.byref(loss)), self.h)
+        return g, loss.value
+
+    def train_step(self, x_ptr: int, t_ptr: int, n: int, lr: float) -> float:
+        loss = ctypes.c_double()
+        _ncheck(load().lbm_net_train_step(self.h, x_ptr, t_ptr, int(n), float(lr),
+                                          ctypes.byref(loss)), self.h)
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -158,6 +158,17 @@ int lbm_run_to(lbm_handle_t *h, double tol, int64_t max_steps, int64_t *steps_do
 int lbm_get_f(lbm_handle_t *h, double *f);
 int lbm_set_f(lbm_handle_t *h, const double *f);
 
+/* Warm start: replace the state by populations built from density and
+ * velocity fields (nx*ny doubles each, the convention of lbm_fields; host
+ * pointers, or device pointers with on_device = 1): at every fluid node the
+ * equilibrium of Eq. LBEequi at u - a/2 (so that Eq. FluidMacr returns u)
+ * plus the first-order Chapman-Enskog non-equilibrium part
+ * -3 tau_s w_i rho (c_i c_i - I/3) : grad u, with grad u by central
+ * differences over fluid neighbours (one-sided next to walls).  The previous
+ * state is set equal to it (residual 0 until a step).  Synchronises. */
+int lbm_set_fields(lbm_handle_t *h, const double *rho, const double *ux, const double *uy,
+                   int on_device);
+
 /* Per-link free parameter l and combination parameter r as used, in the
  * order the links were given at creation (n_links doubles each, host). */
 int lbm_link_params(const lbm_handle_t *h, double *r, double *l);
@@ -241,6 +252,11 @@ int lbm_batch_reset(lbm_batch_t *b);
  * residual; *steps_total = steps taken by the batch.  Synchronises. */
 int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t check_every,
                      int64_t *steps_per_case, double *residual_per_case, int64_t *steps_total);
+/* Warm start of case c from density / velocity fields (host, nx*ny
+ * doubles each), as lbm_set_fields; call after lbm_batch_create or
+ * lbm_batch_reset and before lbm_batch_run_to. */
+int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const double *ux,
+                         const double *uy);
 /* Density and velocity of case c (host arrays of nx*ny doubles, may be NULL). */
 int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double *uy);
 int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fluid,

@@ -451,3 +451,28 @@ def batch_cases(n_cases: int = 512, seed: int = 0, nx_range=(64, 1024), ny_range
         c.meta["batch_kind"] = ("channel", "annulus", "cylinders")[kind]
         out.append(c)
     return out
+
+
+def signed_distance(case: Case, clip: float = 32.0) -> np.ndarray:
+    """Signed distance (lattice units, clipped to +-clip) of every node to
+    the nearest wall of a cylinder_array or channel case: positive in the
+    fluid, negative inside solids.  Flat walls sit half a spacing inside
+    the solid edge rows (gamma = 1/2 for the cylinder arrays)."""
+    ny, nx = case.solid.shape
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    if "q_bottom" in case.meta:
+        lo = 1.0 - case.meta["q_bottom"]
+        hi = ny - 2 + case.meta["q_top"]
+    else:
+        lo, hi = 0.5, ny - 1.5
+    d = np.minimum(yy - lo, hi - yy)
+    d = np.minimum(d, clip)
+    cxs = case.meta.get("centers_x", np.zeros(0))
+    cys = case.meta.get("centers_y", np.zeros(0))
+    rs = case.meta.get("radii", np.zeros(0))
+    for X, Y, R in zip(cxs, cys, rs):
+        x0, x1 = max(0, int(X - R - clip)), min(nx, int(X + R + clip) + 2)
+        y0, y1 = max(0, int(Y - R - clip)), min(ny, int(Y + R + clip) + 2)
+        sub = np.hypot(xx[y0:y1, x0:x1] - X, yy[y0:y1, x0:x1] - Y) - R
+        d[y0:y1, x0:x1] = np.minimum(d[y0:y1, x0:x1], sub)
+    return np.clip(d, -clip, clip)

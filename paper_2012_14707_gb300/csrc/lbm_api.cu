@@ -538,6 +538,37 @@ int lbm_set_f(lbm_handle_t *h, const double *f) {
   return LBM_OK;
 }
 
+int lbm_set_fields(lbm_handle_t *h, const double *rho, const double *ux, const double *uy,
+                   int on_device) {
+  if (!h || !rho || !ux || !uy) return h ? fail(h, LBM_EINVAL, "null field") : LBM_EINVAL;
+  const int64_t n = static_cast<int64_t>(h->nx) * h->ny;
+  double *d = nullptr;
+  const double *r = rho, *u = ux, *v = uy;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), 3 * n * sizeof(double), h->stream));
+    e = cudaMemcpyAsync(d, rho, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, ux, n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * n, uy, n * 8, cudaMemcpyHostToDevice, h->stream);
+    r = d;
+    u = d + n;
+    v = d + 2 * n;
+  }
+  if (e == cudaSuccess)
+    e = dispatch(h->precision, [&](auto tT, auto tC) {
+      LBM_TYPES(tT, tC);
+      return lbm::launch_set_fields<T>(r, u, v, h->flags, h->nx, h->ny, h->pitch, h->plane, h->px,
+                                       h->py, h->ax, h->ay, h->cp.tau_s, h->scale,
+                                       static_cast<T *>(h->f[0]), static_cast<T *>(h->f[1]),
+                                       h->stream);
+    });
+  if (d) cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
+  h->steps = 0;
+  return LBM_OK;
+}
+
 int lbm_link_params(const lbm_handle_t *h, double *r, double *l) {
   if (!h) return LBM_EINVAL;
   if (r) std::copy(h->link_r.begin(), h->link_r.end(), r);

@@ -163,7 +163,8 @@ struct lbm_batch {
   int n_cases = 0;
   std::vector<int32_t> nx, ny, pitch;
   std::vector<int64_t> f_off, node_off, n_fluid;
-  std::vector<double> ax, ay, scale;
+  std::vector<double> ax, ay, scale, tau_s;
+  std::vector<int32_t> px, py;
   void *f[2] = {nullptr, nullptr};
   uint8_t *flags = nullptr;
   int32_t *lbase = nullptr;
@@ -361,6 +362,9 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     b->ax.push_back(h.ax);
     b->ay.push_back(h.ay);
     b->scale.push_back(h.scale);
+    b->tau_s.push_back(h.cp.tau_s);
+    b->px.push_back(h.px);
+    b->py.push_back(h.py);
     b->total_nodes += static_cast<int64_t>(h.nx) * h.ny;
     b->total_fluid += h.n_fluid;
     std::memcpy(&flags[noff], h.flags.data(), h.flags.size());
@@ -546,6 +550,34 @@ int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double 
   if (e == cudaSuccess && rho) e = cudaMemcpy(rho, d, n * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && ux) e = cudaMemcpy(ux, d + n, n * 8, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && uy) e = cudaMemcpy(uy, d + 2 * n, n * 8, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return bfail(b, LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const double *ux,
+                         const double *uy) {
+  if (!b || !rho || !ux || !uy) return b ? bfail(b, LBM_EINVAL, "null field") : LBM_EINVAL;
+  if (c < 0 || c >= b->n_cases) return bfail(b, LBM_EINVAL, "case index out of range");
+  if (b->cur != 0) return bfail(b, LBM_EINVAL, "batch state is mid-graph; call lbm_batch_reset");
+  const int64_t n = static_cast<int64_t>(b->nx[c]) * b->ny[c];
+  double *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 3 * n * sizeof(double));
+  if (e != cudaSuccess) return bfail(b, LBM_ENOMEM, cudaGetErrorString(e));
+  e = cudaMemcpy(d, rho, n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + n, ux, n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + 2 * n, uy, n * 8, cudaMemcpyHostToDevice);
+  const int64_t plane = static_cast<int64_t>(b->pitch[c]) * b->ny[c];
+  if (e == cudaSuccess)
+    e = dispatch_b(b->precision, [&](auto tT, auto tC) {
+      using T = std::remove_pointer_t<decltype(tT)>;
+      return lbm::launch_set_fields<T>(d, d + n, d + 2 * n, b->flags + b->node_off[c], b->nx[c],
+                                       b->ny[c], b->pitch[c], plane, b->px[c], b->py[c], b->ax[c],
+                                       b->ay[c], b->tau_s[c], b->scale[c],
+                                       static_cast<T *>(b->f[0]) + b->f_off[c],
+                                       static_cast<T *>(b->f[1]) + b->f_off[c], b->stream);
+    });
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   cudaFree(d);
   if (e != cudaSuccess) return bfail(b, LBM_ECUDA, cudaGetErrorString(e));
   return LBM_OK;

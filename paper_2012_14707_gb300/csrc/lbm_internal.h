@@ -143,6 +143,12 @@ cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, i
                             double scale, double *out, cudaStream_t s);
 
 template <typename T>
+cudaError_t launch_set_fields(const double *rho, const double *ux, const double *uy,
+                              const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
+                              int64_t plane, int32_t px, int32_t py, double ax, double ay,
+                              double tau_s, double scale, T *f0, T *f1, cudaStream_t s);
+
+template <typename T>
 cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch,
                             int64_t plane, double scale, T *f, cudaStream_t s);
 

@@ -140,6 +140,78 @@ __global__ void fields_kernel(const T *__restrict__ f, const uint8_t *__restrict
   }
 }
 
+// Populations from macroscopic fields (a warm start): for every fluid node
+// f_i = f_i^eq(rho, u - a/2) - 3 tau_s w_i rho (c_i c_i - I/3) : grad u,
+// i.e. the equilibrium (Eq. LBEequi) at the velocity whose half-force
+// corrected moment (Eq. FluidMacr) is u, plus the first-order
+// Chapman-Enskog non-equilibrium part; grad u by central differences over
+// fluid neighbours (one-sided next to a wall, 0 if both neighbours are
+// solid).  Written as deviations into both lattices; solid nodes get 0.
+template <typename T>
+__global__ void set_fields_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
+                                  const double *__restrict__ uy, const uint8_t *__restrict__ flags,
+                                  int32_t nx, int32_t ny, int32_t pitch, int64_t plane, int32_t px,
+                                  int32_t py, double ax, double ay, double tau_s, double scale,
+                                  T *f0, T *f1) {
+  using C = typename Stor<T>::C;
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int y = static_cast<int>(p / nx), x = static_cast<int>(p - static_cast<int64_t>(y) * nx);
+    const int64_t node = static_cast<int64_t>(y) * pitch + x;
+    double dv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (flags[node] != kSolid) {
+      auto fluid_at = [&](int xx, int yy, int64_t *q) {
+        if (xx < 0 || xx >= nx) {
+          if (!px) return false;
+          xx = (xx + nx) % nx;
+        }
+        if (yy < 0 || yy >= ny) {
+          if (!py) return false;
+          yy = (yy + ny) % ny;
+        }
+        if (flags[static_cast<int64_t>(yy) * pitch + xx] == kSolid) return false;
+        *q = static_cast<int64_t>(yy) * nx + xx;
+        return true;
+      };
+      // d/dx and d/dy of (ux, uy)
+      double g[2][2];
+      for (int axis = 0; axis < 2; axis++) {
+        int64_t qp = 0, qm = 0;
+        const bool hp = fluid_at(x + (axis == 0), y + (axis == 1), &qp);
+        const bool hm = fluid_at(x - (axis == 0), y - (axis == 1), &qm);
+        for (int comp = 0; comp < 2; comp++) {
+          const double *u = comp == 0 ? ux : uy;
+          double d = 0.0;
+          if (hp && hm) d = 0.5 * (u[qp] - u[qm]);
+          else if (hp) d = u[qp] - u[p];
+          else if (hm) d = u[p] - u[qm];
+          g[axis][comp] = d;  // d u_comp / d x_axis
+        }
+      }
+      const double r = rho[p];
+      const double vx = ux[p] - 0.5 * ax, vy = uy[p] - 0.5 * ay;
+      const double vv = vx * vx + vy * vy;
+      const double div = g[0][0] + g[1][1];
+      for (int i = 0; i < 9; i++) {
+        const double cu = cx[i] * vx + cy[i] * vy;
+        const double feq = w[i] * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * vv);
+        const double qg = cx[i] * cx[i] * g[0][0] + cx[i] * cy[i] * (g[0][1] + g[1][0]) +
+                          cy[i] * cy[i] * g[1][1] - div / 3.0;
+        dv[i] = feq - 3.0 * tau_s * w[i] * r * qg - w[i];
+      }
+    }
+    for (int i = 0; i < 9; i++) {
+      const T v = Stor<T>::st(static_cast<C>(dv[i]), static_cast<C>(scale));
+      f0[i * plane + node] = v;
+      f1[i * plane + node] = v;
+    }
+  }
+}
+
 __constant__ double kWd[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                               1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
@@ -213,6 +285,17 @@ cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, i
 }
 
 template <typename T>
+cudaError_t launch_set_fields(const double *rho, const double *ux, const double *uy,
+                              const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
+                              int64_t plane, int32_t px, int32_t py, double ax, double ay,
+                              double tau_s, double scale, T *f0, T *f1, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(nx) * ny;
+  set_fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(rho, ux, uy, flags, nx, ny, pitch, plane, px,
+                                                        py, ax, ay, tau_s, scale, f0, f1);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
                             double scale, T *f, cudaStream_t s) {
   const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
@@ -232,7 +315,11 @@ cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pi
   template cudaError_t launch_export_f<T>(const T *, int32_t, int32_t, int32_t, int64_t, double,   \
                                           double *, cudaStream_t);                                 \
   template cudaError_t launch_import_f<T>(const double *, int32_t, int32_t, int32_t, int64_t,      \
-                                          double, T *, cudaStream_t);
+                                          double, T *, cudaStream_t);                              \
+  template cudaError_t launch_set_fields<T>(const double *, const double *, const double *,        \
+                                            const uint8_t *, int32_t, int32_t, int32_t, int64_t,   \
+                                            int32_t, int32_t, double, double, double, double, T *, \
+                                            T *, cudaStream_t);
 
 LBM_INSTANTIATE(double, double)
 LBM_INSTANTIATE(float, float)

@@ -25,9 +25,11 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16": LBM_BF16, "fp16": LBM_
 
 # Every entry point include/lbm.h declares.
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_residual",
+           "lbm_set_fields",
            "lbm_run_to", "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info",
            "lbm_precompute", "lbm_residual_noalloc", "lbm_destroy", "lbm_last_error",
            "lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
+           "lbm_batch_set_fields",
            "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
            "lbm_net_create", "lbm_net_num_params", "lbm_net_set_params", "lbm_net_get_params",
            "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_destroy",
@@ -102,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_get_f.argtypes = [H, dp]
     lib.lbm_set_f.argtypes = [H, dp]
     lib.lbm_link_params.argtypes = [H, dp, dp]
+    lib.lbm_set_fields.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.lbm_set_fields.restype = ctypes.c_int
     lib.lbm_get_info.argtypes = [H, ctypes.POINTER(Info)]
     lib.lbm_precompute.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(Params),
                                    ctypes.c_size_t, ip, dp, dp, dp, dp, dp, ctypes.POINTER(Info)]
@@ -117,6 +121,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_batch_run_to.argtypes = [H, ctypes.c_double, ctypes.c_int64, ctypes.c_int32, i64p, dp,
                                      i64p]
     lib.lbm_batch_fields.argtypes = [H, ctypes.c_int32, dp, dp, dp]
+    lib.lbm_batch_set_fields.argtypes = [H, ctypes.c_int32, dp, dp, dp]
+    lib.lbm_batch_set_fields.restype = ctypes.c_int
     lib.lbm_batch_info.argtypes = [H, i64p, i64p, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int32)]
     lib.lbm_batch_destroy.argtypes = [H]
@@ -237,6 +243,17 @@ def lbm_get_f(h, out: np.ndarray):
 def lbm_set_f(h, f: np.ndarray):
     f = np.ascontiguousarray(f, np.float64)
     _check(load().lbm_set_f(h, _dp(f)), h)
+
+
+def lbm_set_fields(h, rho, ux, uy, on_device: bool = False):
+    """Warm start from density / velocity fields (host float64 arrays of
+    nx*ny, or device pointers when on_device)."""
+    lib = load()
+    if on_device:
+        _check(lib.lbm_set_fields(h, rho, ux, uy, 1), h)
+        return
+    arrs = [np.ascontiguousarray(a, np.float64).reshape(-1) for a in (rho, ux, uy)]
+    _check(lib.lbm_set_fields(h, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data, 0), h)
 
 
 def lbm_link_params(h, n_links: int):
@@ -370,6 +387,9 @@ class Solver:
     def link_params(self):
         return lbm_link_params(self.h, self.case.n_links)
 
+    def set_fields(self, rho, ux, uy):
+        lbm_set_fields(self.h, rho, ux, uy)
+
     def info(self) -> Info:
         return lbm_get_info(self.h)
 
@@ -473,6 +493,11 @@ class Batch:
         _bcheck(load().lbm_batch_fields(self.h, int(k), _dp(rho), _dp(ux), _dp(uy)), self.h)
         s = (c.ny, c.nx)
         return rho.reshape(s), ux.reshape(s), uy.reshape(s)
+
+    def set_fields(self, k: int, rho, ux, uy):
+        arrs = [np.ascontiguousarray(a, np.float64).reshape(-1) for a in (rho, ux, uy)]
+        _bcheck(load().lbm_batch_set_fields(self.h, int(k), _dp(arrs[0]), _dp(arrs[1]),
+                                            _dp(arrs[2])), self.h)
 
     def info(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()

@@ -225,3 +225,69 @@ def test_fp64_bgk_matches_oracle(name):
     g.step(150)
     np.testing.assert_allclose(_fluid_f(c, g.get_f()), _fluid_f(c, o.get_f()), rtol=0, atol=1e-13)
     assert g.info().tau_q == pytest.approx(g.info().tau_s, rel=1e-12)
+
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+UNIT_ROUNDOFF = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}  # 8 and 11 significant bits
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("name", ["cylinders", "annulus", "channel_moving", "inclined"])
+def test_16bit_one_step_is_the_oracle_step_rounded_to_storage(name, precision):
+    """Both sides start from the same state, one that the 16-bit storage
+    holds exactly (a seeded state imported by the GPU and read back), and
+    take one step.  A streamed population is the oracle's value rounded once
+    to storage: |error| <= u |f_i - w_i| with u the unit round-off, plus a
+    floor for the FP32 arithmetic.  A link population also carries the
+    roundings of the post-collision values it is built from, and the rest
+    population those of the eight others (it closes the mass balance):
+    <= u (|f_i - w_i| + 10 s), s the node's largest deviation."""
+    c = CASES[name]()
+    kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    o, g = _pair(c, precision, start_seed=7, amp=1e-3, **kw)
+    o.set_f(g.get_f())
+    o.step(1)
+    g.step(1)
+    fl = c.solid == 0
+    a = g.get_f()[:, fl] - W9[:, None]
+    b = o.get_f()[:, fl] - W9[:, None]
+    u = UNIT_ROUNDOFF[precision]
+    s = np.abs(b).max(axis=0)
+    err = np.abs(a - b)
+    link = np.zeros((9, c.ny, c.nx), bool)
+    link[np.asarray(c.link_dir), np.asarray(c.link_y), np.asarray(c.link_x)] = True
+    link = link[:, fl]
+    link[0] = True
+    floor = 2.0 ** -20 * s
+    plain = ~link
+    assert (err[plain] <= u * np.abs(b[plain]) + np.broadcast_to(floor, b.shape)[plain]).all()
+    assert (err[link] <= u * (np.abs(b[link]) + 10 * np.broadcast_to(s, b.shape)[link])).all()
+    # and not a loose bound in practice: the typical error is a fraction of one rounding
+    assert np.median(err[plain] / (u * np.abs(b[plain]) + 1e-300)) <= 0.5
+
+
+# Velocity rel. L2 and mass drift against the oracle after 500 steps from rest
+# (bounds ~2x the values measured on a GB300).  BF16 keeps 8 significant bits
+# of each deviation: ~1e-3 to 1e-2 in velocity where u ~ 1e-3 to 1e-2, and the
+# slow 4 x 32 channel (u ~ 2e-4, deviations ~ 2e-5) loses most of its profile
+# -- BF16 storage does not meet a 1e-3 target there.  FP16 (deviations x 4096)
+# keeps 11 bits: 2e-4 to 2e-3.
+BOUNDS_16 = {
+    ("bf16", "annulus"): (3e-3, 3e-4), ("bf16", "cylinders"): (1.5e-2, 2e-6),
+    ("bf16", "channel_moving"): (3e-2, 1.2e-4), ("bf16", "poiseuille"): (0.25, 2e-8),
+    ("fp16", "annulus"): (4e-4, 3e-5), ("fp16", "cylinders"): (8e-4, 3e-7),
+    ("fp16", "channel_moving"): (4e-3, 1.3e-6), ("fp16", "poiseuille"): (2e-3, 1e-9),
+}
+
+
+@pytest.mark.parametrize("precision,name", list(BOUNDS_16))
+def test_16bit_velocity_and_mass_after_500_steps(precision, name):
+    c = CASES[name]()
+    kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    o, g = _pair(c, precision, **kw)
+    m0 = o.residual()[1]
+    o.step(500)
+    g.step(500)
+    vb, mb = BOUNDS_16[(precision, name)]
+    assert _vel_rel_l2(c, g.fields(), o.fields()) <= vb
+    assert abs(g.residual()[1] - o.residual()[1]) / m0 <= mb

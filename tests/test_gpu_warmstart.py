@@ -1,0 +1,70 @@
+"""Learned warm start (small scale): lbm_set_fields restarts a steady state
+in place, a network trained by the library's kernels cuts the steps to the
+residual, and a deliberately wrong start still converges to the same state
+(the solver is the fallback and the judge of the network)."""
+import numpy as np
+import pytest
+
+from paper_2012_14707_gb300 import build as lbm_build
+from paper_2012_14707_gb300 import cases, lbm, warmstart
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    lbm_build.build()
+    lbm.load()
+    torch.cuda.set_device(0)
+
+
+def test_set_fields_restart_from_a_steady_state():
+    """Restarting from converged fields (equilibrium plus first-order
+    non-equilibrium part) reaches tol 1e-6 in well under the steps from rest
+    and ends in the same state.  (The first-order populations miss the wall
+    nodes' own non-equilibrium structure, so the restart has a short
+    transient: at much tighter tolerances the saving shrinks.)"""
+    c = cases.cylinder_array(96, 64, 4, Kn=0.01, ax=1e-5, r_max=10.0)
+    s = lbm.Solver(c, precision="fp64", residual_every=100)
+    n_rest, r_rest = s.run_to(1e-6, 200000)
+    assert r_rest < 1e-6
+    s.run_to(1e-11, 200000)
+    rho, ux, uy = s.fields()
+    s2 = lbm.Solver(c, precision="fp64", residual_every=100)
+    s2.set_fields(rho, ux, uy)
+    got = s2.fields()
+    fl = c.solid == 0
+    # the fields round-trip through the populations
+    np.testing.assert_allclose(got[0][fl], rho[fl], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(got[1][fl], ux[fl], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(got[2][fl], uy[fl], rtol=0, atol=1e-14)
+    n_warm, r_warm = s2.run_to(1e-6, 200000)
+    assert r_warm < 1e-6
+    assert n_warm <= 0.7 * n_rest
+    s2.run_to(1e-11, 200000)
+    u2 = s2.fields()
+    assert np.abs(u2[1] - ux)[fl].max() <= 1e-7 * np.abs(ux).max()
+
+
+def test_network_warm_start_saves_steps_and_noise_falls_back():
+    size = 64
+    data = warmstart.make_dataset(48, 1, size, tol=1e-5, max_steps=20000, kn_range=(0.005, 0.1))
+    assert data.converged.mean() > 0.8
+    net = lbm.Net(size, size, base=8, levels=3, precision="bf16", max_batch=8, seed=0)
+    hist = warmstart.train(net, data, epochs=40, batch=8, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    held = warmstart.make_cases(12, 100000, size, kn_range=(0.005, 0.1))
+    ev = warmstart.evaluate(net, held, tol=1e-5, max_steps=20000, batch=8)
+    rest, nn_, noise = ev["rest"]["steps"], ev["network"]["steps"], ev["noise"]["steps"]
+    ok = (rest > 0) & (nn_ > 0)
+    assert ok.mean() > 0.8
+    # a small network on a small set must at least not cost steps
+    assert np.median(nn_[ok]) <= np.median(rest[ok])
+    # fallback: a wrong start converges too, to the same steady state
+    assert (noise > 0).mean() > 0.8
+    for k, c in enumerate(held):
+        if rest[k] > 0 and noise[k] > 0:
+            fl = c.solid == 0
+            a, b = ev["rest"]["fields"][k][1], ev["noise"]["fields"][k][1]
+            assert np.linalg.norm((a - b)[fl]) <= 2e-2 * np.linalg.norm(a[fl])

@@ -35,6 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FLUID_BYTES = {"fp32": 72, "fp64": 144, "bf16": 36, "fp16": 36}  # algorithmic bytes per fluid-node update
+ELEM_BYTES = {"fp32": 4, "fp64": 8, "bf16": 2, "fp16": 2}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -262,7 +263,8 @@ def run_ours(args):
         "config": {"workload": f"cylinders_{case.nx}x{case.ny}_phi0.7_Kn0.02",
                    "nx": case.nx, "ny": case.ny, "n_fluid": n_fluid, "n_links": case.n_links,
                    "precision": args.precision, "lattice_steps_per_step": per,
-                   "l2": "inputs larger than L2 (2 x 1.2 GB lattices)",
+                   "l2": "inputs larger than L2 (2 x %.2f GB lattices)" % (
+                       9 * ((case.nx + 31) // 32 * 32) * case.ny * ELEM_BYTES[args.precision] / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -305,7 +307,7 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch):
 
 
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
-KERNEL_REV = 4
+KERNEL_REV = 5
 
 
 def run_batch(args):

@@ -509,7 +509,7 @@ int lbm_get_f(lbm_handle_t *h, double *f) {
   LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), n * sizeof(double), h->stream));
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
-    return lbm::launch_export_f<T>(static_cast<const T *>(h->f[h->cur]), h->nx, h->ny, h->pitch,
+    return lbm::launch_export_f<T>(static_cast<const T *>(h->f[h->cur]), h->flags, h->nx, h->ny, h->pitch,
                                    h->plane, h->scale, d, h->stream);
   });
   if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);

@@ -147,17 +147,22 @@ __device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restri
   o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
   t[0] = Stor<T>::st(o[0], k.sc);
 
-  // Streaming: push f'_i to x + c_i unless that node is solid; bit (j-1)
-  // set <=> x - c_j solid, so push i needs bit opp(i) clear.
+  // Streaming: push every f'_i to x + c_i, solid or not.  A solid node
+  // never pushes and is never read, so a push into it lands in a slot no
+  // one else writes (non-periodic axes have solid edges: no push leaves
+  // the lattice).  Pushing unconditionally saves the per-direction
+  // predicates and writes whole 32-byte sectors along solid edges where
+  // predicated pushes would leave them partly written (a read-modify-write
+  // in DRAM).
   dst[node] = t[0];
-  if (!(fl & (1u << 2))) dst[1 * P + rowc + xe] = t[1];  // opp(1) = 3
-  if (!(fl & (1u << 3))) dst[2 * P + rown + x] = t[2];   // opp(2) = 4
-  if (!(fl & (1u << 0))) dst[3 * P + rowc + xw] = t[3];  // opp(3) = 1
-  if (!(fl & (1u << 1))) dst[4 * P + rows + x] = t[4];   // opp(4) = 2
-  if (!(fl & (1u << 6))) dst[5 * P + rown + xe] = t[5];  // opp(5) = 7
-  if (!(fl & (1u << 7))) dst[6 * P + rown + xw] = t[6];  // opp(6) = 8
-  if (!(fl & (1u << 4))) dst[7 * P + rows + xw] = t[7];  // opp(7) = 5
-  if (!(fl & (1u << 5))) dst[8 * P + rows + xe] = t[8];  // opp(8) = 6
+  dst[1 * P + rowc + xe] = t[1];
+  dst[2 * P + rown + x] = t[2];
+  dst[3 * P + rowc + xw] = t[3];
+  dst[4 * P + rows + x] = t[4];
+  dst[5 * P + rown + xe] = t[5];
+  dst[6 * P + rown + xw] = t[6];
+  dst[7 * P + rows + xw] = t[7];
+  dst[8 * P + rows + xe] = t[8];
 
   // Boundary links of this node, Eq. EqNewBDSC in the folded form of
   // LinkCoef.  Directions that no active lane of the warp needs are

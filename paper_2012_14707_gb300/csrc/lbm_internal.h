@@ -139,7 +139,7 @@ cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t 
                           double *rho, double *ux, double *uy, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+cudaError_t launch_export_f(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
                             double scale, double *out, cudaStream_t s);
 
 template <typename T>

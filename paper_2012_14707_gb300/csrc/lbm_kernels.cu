@@ -5,9 +5,10 @@
 // u = 0 is d = 0), one plane per direction: d[i][y][x] with a padded row
 // pitch.  The step kernel is a push scheme (Sec. 2: collide, then stream):
 // each fluid node reads its nine values once, collides in moment space, and
-// writes f'_i to x + c_i in the other lattice.  Unknown populations of a
-// boundary node (x_f - c_i solid) are never pushed by anyone; the node fills
-// them itself from values it holds in registers (Eq. EqNewBDSC is local:
+// writes f'_i to x + c_i in the other lattice (also into solid nodes, whose
+// slots no one reads).  Unknown populations of a boundary node (x_f - c_i
+// solid) are never pushed by anyone; the node fills them itself from values
+// it holds in registers (Eq. EqNewBDSC is local:
 // f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all belong to x_f).
 #include <cstdint>
 
@@ -21,8 +22,8 @@ using namespace dev;
 
 // One time step, one thread per node (x), one CTA row of kStepThreads nodes
 // per (blockIdx.x, y).  Each fluid node loads its nine deviations, collides
-// in moment space, pushes f'_i to x + c_i in the other lattice (unless that
-// node is solid) and fills its own unknown populations from the link table
+// in moment space, pushes every f'_i to x + c_i in the other lattice and
+// fills its own unknown populations from the link table
 // (Eq. EqNewBDSC is local: f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and
 // rho_f all belong to x_f).  Offsets are 32-bit (the lattice is limited to
 // 2^31 / 9 nodes per plane); row wraps are uniform per CTA.
@@ -216,15 +217,20 @@ __constant__ double kWd[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                               1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
 template <typename T>
-__global__ void export_kernel(const T *__restrict__ f, int32_t nx, int32_t ny, int32_t pitch,
-                              int64_t plane, double inv_scale, double *out) {
+__global__ void export_kernel(const T *__restrict__ f, const uint8_t *__restrict__ flags,
+                              int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+                              double inv_scale, double *out) {
   using C = typename Stor<T>::C;
   const int64_t n = static_cast<int64_t>(nx) * ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
-    out[p] = kWd[i] + static_cast<double>(
-                          Stor<T>::ld(f[i * plane + y * pitch + x], static_cast<C>(inv_scale)));
+    // solid nodes carry no state (their slots hold values parked by the
+    // pushes of their fluid neighbours): they read as the rest state w_i
+    const bool solid = flags[y * pitch + x] == kSolid;
+    out[p] = kWd[i] + (solid ? 0.0
+                             : static_cast<double>(Stor<T>::ld(f[i * plane + y * pitch + x],
+                                                               static_cast<C>(inv_scale))));
   }
 }
 
@@ -277,10 +283,10 @@ cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t 
 }
 
 template <typename T>
-cudaError_t launch_export_f(const T *f, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+cudaError_t launch_export_f(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
                             double scale, double *out, cudaStream_t s) {
   const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
-  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, nx, ny, pitch, plane, 1.0 / scale, out);
+  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, flags, nx, ny, pitch, plane, 1.0 / scale, out);
   return cudaGetLastError();
 }
 
@@ -312,7 +318,8 @@ cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pi
   template cudaError_t launch_fields<T>(const T *, const uint8_t *, int32_t, int32_t, int32_t,     \
                                         int64_t, double, double, double, double *, double *,       \
                                         double *, cudaStream_t);                                   \
-  template cudaError_t launch_export_f<T>(const T *, int32_t, int32_t, int32_t, int64_t, double,   \
+  template cudaError_t launch_export_f<T>(const T *, const uint8_t *, int32_t, int32_t, int32_t,    \
+                                          int64_t, double,                                         \
                                           double *, cudaStream_t);                                 \
   template cudaError_t launch_import_f<T>(const double *, int32_t, int32_t, int32_t, int64_t,      \
                                           double, T *, cudaStream_t);                              \

@@ -38,24 +38,33 @@ class Dataset:
     converged: np.ndarray  # bool per case
 
 
-def make_cases(n: int, seed0: int, size: int = 256, kn_range=(0.001, 0.1)) -> list:
+def make_cases(n: int, seed0: int, size: int = 256, kn_range=(0.001, 0.1),
+               u_ref: float = 0.01) -> list:
+    """Seeded random-cylinder arrays; Kn log-uniform over kn_range, the body
+    force set per case so that a H^2 / (8 nu) = u_ref (low Mach number at
+    every Kn, so every case has a steady state)."""
     rng = np.random.default_rng(seed0)
     out = []
     for k in range(n):
         Kn = float(math.exp(rng.uniform(math.log(kn_range[0]), math.log(kn_range[1]))))
         c = cases_mod.cylinder_array(size, size, seed0 * 100003 + k, porosity=0.7,
-                                     r_max=min(32.0, size / 8.0), Kn=Kn, ax=1e-5,
+                                     r_max=min(32.0, size / 8.0), Kn=Kn, ax=1.0,
                                      name=f"ws_{seed0}_{k}")
-        out.append(c)
+        nu = viscosity(c)
+        out.append(dataclasses.replace(c, ax=u_ref * 8.0 * nu / c.H ** 2))
     return out
 
 
-def velocity_scale(case) -> float:
-    """u_ref = a H^2 / (8 nu) with nu from tau_s (Eq. tKnrela, Eq. EqViscos)."""
+def viscosity(case) -> float:
+    """nu = (tau_s - 1/2) / 3 with tau_s from Kn and H (Eq. tKnrela, Eq. EqViscos)."""
     p = lbm.lbm_params_default()
     _, _, info = lbm.lbm_precompute(case.Kn, case.H, p, [1], [0.5])
-    nu = (info.tau_s - 0.5) / 3.0
-    return math.hypot(case.ax, case.ay) * case.H ** 2 / (8.0 * nu)
+    return (info.tau_s - 0.5) / 3.0
+
+
+def velocity_scale(case) -> float:
+    """u_ref = a H^2 / (8 nu), the centre-line speed of a channel of width H."""
+    return math.hypot(case.ax, case.ay) * case.H ** 2 / (8.0 * viscosity(case))
 
 
 def inputs(case) -> np.ndarray:
@@ -82,18 +91,27 @@ def decode(y, uref, solid):
 
 def make_dataset(n: int, seed0: int, size: int = 256, tol: float = 1e-6, max_steps: int = 30000,
                  check_every: int = 100, kn_range=(0.001, 0.1)) -> Dataset:
+    """Solve n seeded cases together; keep those that reached tol (a case
+    that ran out of steps or went unstable is no target)."""
     cl = make_cases(n, seed0, size, kn_range)
     b = lbm.Batch(cl, precision="fp32")
     steps, res, total = b.run_to(tol, max_steps, check_every)
-    xs, ys, urefs = [], [], []
+    keep, xs, ys, urefs = [], [], [], []
     for k, c in enumerate(cl):
+        if steps[k] <= 0:
+            continue
         rho, ux, uy = b.fields(k)
+        if not (np.isfinite(rho).all() and np.isfinite(ux).all() and np.isfinite(uy).all()):
+            continue
         u = velocity_scale(c)
+        keep.append(k)
         xs.append(inputs(c))
         ys.append(encode(rho, ux, uy, u, c.solid))
         urefs.append(u)
     b.close()
-    return Dataset(cl, np.stack(xs), np.stack(ys), np.array(urefs), steps, steps > 0)
+    keep = np.array(keep, np.int64)
+    return Dataset([cl[k] for k in keep], np.stack(xs), np.stack(ys), np.array(urefs), steps[keep],
+                   np.ones(len(keep), bool))
 
 
 def train(net, data: Dataset, epochs: int, batch: int, lr: float, seed: int = 0, log=None):
@@ -166,6 +184,15 @@ def evaluate(net, cl: list, tol: float = 1e-6, max_steps: int = 30000, check_eve
         fields = [b.fields(k) for k in range(len(cl))]
         b.close()
         result[mode] = dict(steps=steps, residual=res, total=total, wall=wall, fields=fields)
+    # the network's error against the converged state (from rest)
+    err = []
+    for k, c in enumerate(cl):
+        fl = c.solid == 0
+        _, ux, uy = result["rest"]["fields"][k]
+        den = np.sqrt((ux[fl] ** 2 + uy[fl] ** 2).sum())
+        num = np.sqrt(((preds[k][1] - ux)[fl] ** 2 + (preds[k][2] - uy)[fl] ** 2).sum())
+        err.append(num / den if den > 0 else np.inf)
+    result["network"]["prediction_error"] = np.array(err)
     return result
 
 
@@ -190,24 +217,27 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=30000)
     ap.add_argument("--base", type=int, default=32)
     ap.add_argument("--levels", type=int, default=4)
+    ap.add_argument("--kn-min", type=float, default=0.001)
+    ap.add_argument("--kn-max", type=float, default=0.1)
     args = ap.parse_args(argv)
+    kn = (args.kn_min, args.kn_max)
     build.build()
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    data = make_dataset(args.train, 1, args.size, args.tol, args.max_steps)
+    data = make_dataset(args.train, 1, args.size, args.tol, args.max_steps, kn_range=kn)
     t_data = time.perf_counter() - t0
     net = lbm.Net(args.size, args.size, base=args.base, levels=args.levels, precision="bf16",
                   max_batch=args.batch, seed=0)
     t0 = time.perf_counter()
     hist = train(net, data, args.epochs, args.batch, args.lr, log=print)
     t_train = time.perf_counter() - t0
-    held = make_cases(args.test, 100000, args.size)
+    held = make_cases(args.test, 100000, args.size, kn_range=kn)
     ev = evaluate(net, held, args.tol, args.max_steps, batch=args.batch)
     rest, nn_, noise = ev["rest"]["steps"], ev["network"]["steps"], ev["noise"]["steps"]
     both = (rest > 0) & (nn_ > 0)
     rep = {
         "train_cases": args.train, "test_cases": args.test, "size": args.size,
-        "train_converged": int(data.converged.sum()), "data_seconds": t_data,
+        "train_converged": len(data.cases), "data_seconds": t_data,
         "train_seconds": t_train, "epochs": args.epochs, "loss_first": hist[0], "loss_last": hist[-1],
         "tol": args.tol, "max_steps": args.max_steps,
         "converged": {"rest": int((rest > 0).sum()), "network": int((nn_ > 0).sum()),
@@ -215,6 +245,11 @@ def main(argv=None):
         "median_steps": {"rest": float(np.median(rest[both])) if both.any() else None,
                          "network": float(np.median(nn_[both])) if both.any() else None},
         "median_step_ratio": float(np.median(nn_[both] / rest[both])) if both.any() else None,
+        "step_ratio_quartiles": ([float(v) for v in np.percentile(nn_[both] / rest[both], [25, 75])]
+                                 if both.any() else None),
+        "prediction_error_median": (float(np.median(ev["network"]["prediction_error"][rest > 0]))
+                                    if (rest > 0).any() else None),
+        "params": net.n_params,
         "batch_wall_seconds": {m: ev[m]["wall"] for m in ev},
         "batch_total_steps": {m: int(ev[m]["total"]) for m in ev},
     }

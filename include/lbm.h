@@ -104,7 +104,8 @@ typedef struct {
   double tau_s, tau_q, E, E_max, L1, L2;
   int64_t n_clamped;      /* links whose l was set to 0 by the clamp */
   int64_t device_bytes;   /* device memory held by the handle */
-  int32_t precision, pitch; /* storage precision; row pitch in elements */
+  int32_t precision, pitch; /* storage precision; row pitch in elements of a dense lattice
+                               (0: the single-case solver stores fluid nodes only) */
 } lbm_info_t;
 
 /* Fill *p with the defaults listed above (no side effects). */
@@ -116,7 +117,9 @@ void lbm_params_default(lbm_params_t *p);
  * links whose node is solid or whose neighbour x_f - c_i is fluid, gamma
  * outside (0, 1], and fluid nodes with an unknown direction that no link
  * covers are LBM_EINVAL).  Kn is the Knudsen number of Eq. tKnrela.  The
- * state starts at rest, f_i = w_i (rho = 1, u = 0).  On success *out holds
+ * state starts at rest, f_i = w_i (rho = 1, u = 0).  The device copy keeps
+ * the fluid nodes only (row-major, with per-node neighbour indices), so its
+ * size follows the fluid fraction, not nx*ny.  On success *out holds
  * the handle; on failure *out is NULL and the returned code says why
  * (lbm_last_error(NULL) gives the message of the last failed creation on
  * this thread).
@@ -152,9 +155,11 @@ int lbm_residual(lbm_handle_t *h, double *residual, double *mass);
 int lbm_run_to(lbm_handle_t *h, double tol, int64_t max_steps, int64_t *steps_done,
                double *residual);
 
-/* All populations f_i (not deviations) as 9*nx*ny host doubles (get: the
- * current state; set: replaces the state and the previous-step state, so
- * the next residual is 0 until a step is taken).  Synchronise. */
+/* All populations f_i (not deviations) as 9*nx*ny host doubles, plane i at
+ * i*nx*ny (get: the current state, solid nodes as the rest state w_i; set:
+ * replaces the state and the previous-step state of every fluid node, so
+ * the next residual is 0 until a step is taken; solid entries are
+ * ignored).  Synchronise. */
 int lbm_get_f(lbm_handle_t *h, double *f);
 int lbm_set_f(lbm_handle_t *h, const double *f);
 

@@ -24,8 +24,12 @@ struct lbm_handle {
   lbm_params_t params{};
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
-  uint8_t *flags = nullptr;
-  int32_t *lbase = nullptr;
+  // compacted lattice (see lbm::CompactCase)
+  uint16_t *meta = nullptr;
+  int32_t *n_lb = nullptr, *s_lb = nullptr, *lbase = nullptr, *rowstart = nullptr;
+  int32_t *index = nullptr;  // y * nx + x -> compacted index or -1
+  lbm::RowTile *tiles = nullptr;
+  int64_t n_tiles = 0;
   void *links = nullptr;
   double *partials = nullptr;
   double *result = nullptr;
@@ -85,9 +89,11 @@ void release(lbm_handle_t *h) {
   if (!h) return;
   cudaStream_t s = h->stream;
   cudaStreamSynchronize(s);
-  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->flags), static_cast<void *>(h->lbase),
-                  h->links, static_cast<void *>(h->partials), static_cast<void *>(h->result),
-                  static_cast<void *>(h->d_err)})
+  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->meta), static_cast<void *>(h->n_lb),
+                  static_cast<void *>(h->s_lb), static_cast<void *>(h->lbase),
+                  static_cast<void *>(h->rowstart), static_cast<void *>(h->index),
+                  static_cast<void *>(h->tiles), h->links, static_cast<void *>(h->partials),
+                  static_cast<void *>(h->result), static_cast<void *>(h->d_err)})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
   if (h->h_result) cudaFreeHost(h->h_result);
@@ -97,18 +103,26 @@ void release(lbm_handle_t *h) {
 
 template <typename C>
 lbm::StepConst<C> step_const(const lbm_handle_t *h) {
-  return lbm::make_step_const<C>(h->cp, h->nx, h->ny, h->pitch, h->plane, h->px, h->py, h->ax, h->ay,
+  return lbm::make_step_const<C>(h->cp, h->nx, h->ny, 0, h->plane, h->px, h->py, h->ax, h->ay,
                                  h->params.diffuse_mode, h->scale);
+}
+
+lbm::NodeMap node_map(const lbm_handle_t *h) {
+  lbm::NodeMap m;
+  m.index = h->index;
+  m.nx = h->nx;
+  m.ny = h->ny;
+  return m;
 }
 
 cudaError_t do_step(lbm_handle_t *h) {
   const int src = h->cur, dst = 1 - h->cur;
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
-    return lbm::launch_step<T, C>(static_cast<const T *>(h->f[src]), static_cast<T *>(h->f[dst]),
-                                  h->flags, h->lbase,
-                                  static_cast<const lbm::LinkCoef<C> *>(h->links),
-                                  step_const<C>(h), h->stream);
+    return lbm::launch_step_compact<T, C>(
+        static_cast<const T *>(h->f[src]), static_cast<T *>(h->f[dst]), h->meta, h->n_lb, h->s_lb,
+        h->lbase, h->rowstart, h->tiles, h->n_tiles,
+        static_cast<const lbm::LinkCoef<C> *>(h->links), step_const<C>(h), h->stream);
   });
   if (e == cudaSuccess) {
     h->cur = dst;
@@ -275,6 +289,56 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
 }  // namespace lbm
 
 namespace lbm {
+
+void build_compact(const HostCase &hc, CompactCase *cc) {
+  const int32_t nx = hc.nx, ny = hc.ny, pitch = hc.pitch;
+  const int64_t nn = static_cast<int64_t>(nx) * ny;
+  // before[y * nx + x]: fluid nodes ahead of (x, y) in row-major order,
+  // i.e. the compacted index of (x, y) if fluid, else of the next fluid node
+  std::vector<int32_t> before(static_cast<size_t>(nn));
+  cc->index.assign(static_cast<size_t>(nn), -1);
+  cc->rowstart.assign(static_cast<size_t>(ny) + 1, 0);
+  int32_t n = 0;
+  for (int32_t y = 0; y < ny; y++) {
+    cc->rowstart[y] = n;
+    for (int32_t x = 0; x < nx; x++) {
+      const int64_t q = static_cast<int64_t>(y) * nx + x;
+      before[q] = n;
+      if (hc.flags[static_cast<size_t>(y) * pitch + x] != kSolid) cc->index[q] = n++;
+    }
+  }
+  cc->rowstart[ny] = n;
+  cc->n_fluid = n;
+  cc->plane = (std::max<int64_t>(n, 1) + 31) / 32 * 32;
+  const size_t P = static_cast<size_t>(cc->plane);
+  cc->meta.assign(P, 0);
+  cc->n_lb.assign(P, 0);
+  cc->s_lb.assign(P, 0);
+  cc->lbase.assign(P, 0);
+  cc->tiles.clear();
+  for (int32_t y = 0; y < ny; y++) {
+    // rows above and below; non-periodic y has solid edge rows, so the fluid
+    // rows 1 .. ny - 2 never leave the lattice
+    const int32_t yn = y + 1 < ny ? y + 1 : (hc.py ? 0 : y);
+    const int32_t ys = y > 0 ? y - 1 : (hc.py ? ny - 1 : y);
+    for (int32_t x = 0; x < nx; x++) {
+      const int32_t i = cc->index[static_cast<size_t>(y) * nx + x];
+      if (i < 0) continue;
+      const uint8_t fl = hc.flags[static_cast<size_t>(y) * pitch + x];
+      uint16_t m = fl;
+      if (hc.px && x == nx - 1) m |= static_cast<uint16_t>(kMetaWrapE);
+      if (hc.px && x == 0) m |= static_cast<uint16_t>(kMetaWrapW);
+      cc->meta[i] = m;
+      cc->n_lb[i] = before[static_cast<size_t>(yn) * nx + x];
+      cc->s_lb[i] = before[static_cast<size_t>(ys) * nx + x];
+      const int32_t lb = hc.lbase[static_cast<size_t>(y) * pitch + x];
+      cc->lbase[i] = lb < 0 ? 0 : lb;
+    }
+    for (int32_t c = cc->rowstart[y]; c < cc->rowstart[y + 1]; c += kStepThreads)
+      cc->tiles.push_back(RowTile{y, c, std::min<int32_t>(kStepThreads, cc->rowstart[y + 1] - c), 0});
+  }
+}
+
 // Error text for handle-less calls, read back by lbm_last_error(NULL).
 const char *set_thread_error(const std::string &msg) {
   g_create_error = msg;
@@ -328,19 +392,19 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     return LBM_ENOMEM;
   }
   const lbm_params_t &p = *params;
-  const int64_t plane = hc.plane;
   h->link_r.swap(hc.link_r);
   h->link_l.swap(hc.link_l);
-  std::vector<uint8_t> &flags = hc.flags;
-  std::vector<int32_t> &lbase = hc.lbase;
   const size_t n_links_sz = static_cast<size_t>(hc.n_links);
   h->precision = p.precision;
   h->scale = hc.scale;
   h->stream = static_cast<cudaStream_t>(p.stream);
+  lbm::CompactCase cc;
+  lbm::build_compact(hc, &cc);
   h->nx = hc.nx;
   h->ny = hc.ny;
-  h->pitch = hc.pitch;
-  h->plane = hc.plane;
+  h->pitch = 0;
+  h->plane = cc.plane;
+  h->n_tiles = static_cast<int64_t>(cc.tiles.size());
   h->px = hc.px;
   h->py = hc.py;
   h->ax = hc.ax;
@@ -352,7 +416,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   cudaGetDevice(&h->device);
 
   const size_t es = elem_size(p.precision);
-  const size_t fbytes = 9 * static_cast<size_t>(plane) * es;
+  const size_t fbytes = 9 * static_cast<size_t>(cc.plane) * es;
   const size_t ces = p.precision == LBM_FP64 ? 8 : 4;  // link coefficients: FP64 or FP32
   const size_t lbytes = std::max<size_t>(1, n_links_sz) * 4 * ces;
   const size_t pbytes = lbm::kResidualBlocks * lbm::kPartialStride * sizeof(double);
@@ -375,8 +439,16 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = alloc(&h->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&h->f[1], fbytes);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->flags), flags.size());
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), lbase.size() * 4);
+  const size_t P = static_cast<size_t>(cc.plane);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->meta), P * 2);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->n_lb), P * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->s_lb), P * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), P * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->rowstart), cc.rowstart.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->index), cc.index.size() * 4);
+  if (e == cudaSuccess)
+    e = alloc(reinterpret_cast<void **>(&h->tiles),
+              std::max<size_t>(1, cc.tiles.size()) * sizeof(lbm::RowTile));
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
@@ -387,10 +459,17 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, fbytes, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->flags, flags.data(), flags.size(), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->lbase, lbase.data(), lbase.size() * 4, cudaMemcpyHostToDevice, h->stream);
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess && bytes)
+      e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
+  };
+  up(h->meta, cc.meta.data(), P * 2);
+  up(h->n_lb, cc.n_lb.data(), P * 4);
+  up(h->s_lb, cc.s_lb.data(), P * 4);
+  up(h->lbase, cc.lbase.data(), P * 4);
+  up(h->rowstart, cc.rowstart.data(), cc.rowstart.size() * 4);
+  up(h->index, cc.index.data(), cc.index.size() * 4);
+  up(h->tiles, cc.tiles.data(), cc.tiles.size() * sizeof(lbm::RowTile));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->links, lhost.data(), lbytes, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -419,9 +498,10 @@ int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   const int c = h->cur, pv = 1 - h->cur;
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
-    return lbm::launch_residual<T>(static_cast<const T *>(h->f[c]), static_cast<const T *>(h->f[pv]),
-                                   h->flags, h->nx, h->ny, h->pitch, h->plane, h->ax, h->ay,
-                                   h->scale, h->partials, h->result, h->stream);
+    return lbm::launch_residual_compact<T>(static_cast<const T *>(h->f[c]),
+                                           static_cast<const T *>(h->f[pv]), h->n_fluid, h->plane,
+                                           h->ax, h->ay, h->scale, h->partials, h->result,
+                                           h->stream);
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
   LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -485,8 +565,8 @@ int lbm_fields(lbm_handle_t *h, double *rho, double *ux, double *uy, int on_devi
   }
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
-    return lbm::launch_fields<T>(static_cast<const T *>(h->f[h->cur]), h->flags, h->nx, h->ny,
-                                 h->pitch, h->plane, h->ax, h->ay, h->scale, r, u, v, h->stream);
+    return lbm::launch_fields<T>(static_cast<const T *>(h->f[h->cur]), node_map(h), h->plane, h->ax,
+                                 h->ay, h->scale, r, u, v, h->stream);
   });
   if (e == cudaSuccess && !on_device) {
     if (rho && e == cudaSuccess)
@@ -509,8 +589,8 @@ int lbm_get_f(lbm_handle_t *h, double *f) {
   LBM_CK(h, cudaMallocAsync(reinterpret_cast<void **>(&d), n * sizeof(double), h->stream));
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
-    return lbm::launch_export_f<T>(static_cast<const T *>(h->f[h->cur]), h->flags, h->nx, h->ny, h->pitch,
-                                   h->plane, h->scale, d, h->stream);
+    return lbm::launch_export_f<T>(static_cast<const T *>(h->f[h->cur]), node_map(h), h->plane,
+                                   h->scale, d, h->stream);
   });
   if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   cudaFreeAsync(d, h->stream);
@@ -528,8 +608,8 @@ int lbm_set_f(lbm_handle_t *h, const double *f) {
   for (int b = 0; b < 2 && e == cudaSuccess; b++)
     e = dispatch(h->precision, [&](auto tT, auto tC) {
       LBM_TYPES(tT, tC);
-      return lbm::launch_import_f<T>(d, h->nx, h->ny, h->pitch, h->plane, h->scale,
-                                     static_cast<T *>(h->f[b]), h->stream);
+      return lbm::launch_import_f<T>(d, node_map(h), h->plane, h->scale, static_cast<T *>(h->f[b]),
+                                     h->stream);
     });
   cudaFreeAsync(d, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -557,8 +637,8 @@ int lbm_set_fields(lbm_handle_t *h, const double *rho, const double *ux, const d
   if (e == cudaSuccess)
     e = dispatch(h->precision, [&](auto tT, auto tC) {
       LBM_TYPES(tT, tC);
-      return lbm::launch_set_fields<T>(r, u, v, h->flags, h->nx, h->ny, h->pitch, h->plane, h->px,
-                                       h->py, h->ax, h->ay, h->cp.tau_s, h->scale,
+      return lbm::launch_set_fields<T>(r, u, v, node_map(h), h->plane, h->px, h->py, h->ax, h->ay,
+                                       h->cp.tau_s, h->scale,
                                        static_cast<T *>(h->f[0]), static_cast<T *>(h->f[1]),
                                        h->stream);
     });

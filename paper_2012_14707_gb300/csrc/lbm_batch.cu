@@ -207,6 +207,15 @@ cudaError_t dispatch_b(int precision, F &&f) {
   }
 }
 
+lbm::NodeMap case_map(const lbm_batch_t *b, int c) {
+  lbm::NodeMap m;
+  m.flags = b->flags + b->node_off[c];
+  m.nx = b->nx[c];
+  m.ny = b->ny[c];
+  m.pitch = b->pitch[c];
+  return m;
+}
+
 std::vector<lbm::Tile> make_tiles(const lbm_batch_t *b, int threads) {
   std::vector<lbm::Tile> t;
   for (int c = 0; c < b->n_cases; c++) {
@@ -542,9 +551,9 @@ int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double 
   const int64_t plane = static_cast<int64_t>(b->pitch[c]) * b->ny[c];
   e = dispatch_b(b->precision, [&](auto tT, auto tC) {
     using T = std::remove_pointer_t<decltype(tT)>;
-    return lbm::launch_fields<T>(static_cast<const T *>(b->f[b->cur]) + b->f_off[c],
-                                 b->flags + b->node_off[c], b->nx[c], b->ny[c], b->pitch[c], plane,
-                                 b->ax[c], b->ay[c], b->scale[c], d, d + n, d + 2 * n, b->stream);
+    return lbm::launch_fields<T>(static_cast<const T *>(b->f[b->cur]) + b->f_off[c], case_map(b, c),
+                                 plane, b->ax[c], b->ay[c], b->scale[c], d, d + n, d + 2 * n,
+                                 b->stream);
   });
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess && rho) e = cudaMemcpy(rho, d, n * 8, cudaMemcpyDeviceToHost);
@@ -571,9 +580,8 @@ int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const dou
   if (e == cudaSuccess)
     e = dispatch_b(b->precision, [&](auto tT, auto tC) {
       using T = std::remove_pointer_t<decltype(tT)>;
-      return lbm::launch_set_fields<T>(d, d + n, d + 2 * n, b->flags + b->node_off[c], b->nx[c],
-                                       b->ny[c], b->pitch[c], plane, b->px[c], b->py[c], b->ax[c],
-                                       b->ay[c], b->tau_s[c], b->scale[c],
+      return lbm::launch_set_fields<T>(d, d + n, d + 2 * n, case_map(b, c), plane, b->px[c],
+                                       b->py[c], b->ax[c], b->ay[c], b->tau_s[c], b->scale[c],
                                        static_cast<T *>(b->f[0]) + b->f_off[c],
                                        static_cast<T *>(b->f[1]) + b->f_off[c], b->stream);
     });

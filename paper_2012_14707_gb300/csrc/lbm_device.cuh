@@ -49,33 +49,21 @@ __device__ __forceinline__ double recip<double>(double v) {
   return 1.0 / v;
 }
 
-// One time step for node (x, y), x < nx (see the file comment of
-// lbm_kernels.cu): load, collide, push, link epilogue.  xe / xw are the
-// (wrapped) columns x +- 1.
+// Post-collision state of one node: the nine values (arithmetic type and
+// rounded to storage) and the macroscopic quantities the links need.
 template <typename T, typename C>
-__device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restrict__ dst,
-                                          const uint8_t *__restrict__ flags,
-                                          const int32_t *__restrict__ lbase,
-                                          const LinkCoef<C> *__restrict__ links,
-                                          const StepConst<C> &k, const int x, const int y,
-                                          const int xe, const int xw) {
-  const uint32_t P = static_cast<uint32_t>(k.plane);
-  const uint32_t rowc = static_cast<uint32_t>(y) * k.pitch;
-  const uint32_t node = rowc + x;
-  const uint8_t fl = flags[node];
-  if (fl == kSolid) return;
-  const int yn = (y + 1 == k.ny) ? (k.periodic_y ? 0 : y + 1) : y + 1;
-  const int ys = (y == 0) ? (k.periodic_y ? k.ny - 1 : 0) : y - 1;
-  const uint32_t rown = static_cast<uint32_t>(yn) * k.pitch;
-  const uint32_t rows = static_cast<uint32_t>(ys) * k.pitch;
+struct Collided {
+  C o[9];
+  T t[9];
+  C drho, rho, ux, uy, uu;
+};
 
-  C d[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) d[i] = Stor<T>::ld(src[i * P + node], k.inv_sc);
-  // First link of this node (links sorted by node, then direction), loaded
-  // now so that its latency overlaps the collision.
-  const int lb = fl ? lbase[node] : 0;
-
+// Eq. FluidMacr, Eq. MomentPost and f' = M^-1 m' for the deviations d of one
+// node; f'_1..f'_8 rounded to storage, f'_0 closing the mass balance.
+template <typename T, typename C>
+__device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, Collided<T, C> &r) {
+  C(&o)[9] = r.o;
+  T(&t)[9] = r.t;
   // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
   const C s14 = (d[1] + d[2]) + (d[3] + d[4]);
   const C s58 = (d[5] + d[6]) + (d[7] + d[8]);
@@ -123,7 +111,6 @@ __device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restri
   const C diag = r9 + C(2) * e36 + p36;
   const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
   const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
-  C o[9];
   o[1] = axis + ax_x + xx4;
   o[2] = axis + ax_y - xx4;
   o[3] = axis - ax_x + xx4;
@@ -138,7 +125,6 @@ __device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restri
   // unchanged by the collision to within one rounding of f'_0.
   // Round f'_1..f'_8 to storage first (a no-op for FP32/FP64), so that the
   // closure below balances the values actually stored.
-  T t[9];
 #pragma unroll
   for (int i = 1; i < 9; i++) {
     t[i] = Stor<T>::st(o[i], k.sc);
@@ -147,23 +133,26 @@ __device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restri
   o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
   t[0] = Stor<T>::st(o[0], k.sc);
 
-  // Streaming: push every f'_i to x + c_i, solid or not.  A solid node
-  // never pushes and is never read, so a push into it lands in a slot no
-  // one else writes (non-periodic axes have solid edges: no push leaves
-  // the lattice).  Pushing unconditionally saves the per-direction
-  // predicates and writes whole 32-byte sectors along solid edges where
-  // predicated pushes would leave them partly written (a read-modify-write
-  // in DRAM).
-  dst[node] = t[0];
-  dst[1 * P + rowc + xe] = t[1];
-  dst[2 * P + rown + x] = t[2];
-  dst[3 * P + rowc + xw] = t[3];
-  dst[4 * P + rows + x] = t[4];
-  dst[5 * P + rown + xe] = t[5];
-  dst[6 * P + rown + xw] = t[6];
-  dst[7 * P + rows + xw] = t[7];
-  dst[8 * P + rows + xe] = t[8];
+  r.drho = drho;
+  r.rho = rho;
+  r.ux = ux;
+  r.uy = uy;
+  r.uu = uu;
+}
 
+// The unknown populations of a boundary node (bits of fl), Eq. EqNewBDSC in
+// the folded form of LinkCoef, from the node's own pre-collision deviations
+// d and post-collision state c; records links[lb], links[lb + 1], ... in
+// direction order.  Written to dst_node[j * P].  Directions that no active
+// lane of the warp needs are skipped warp-uniformly.
+template <typename T, typename C>
+__device__ __forceinline__ void link_epilogue(T *__restrict__ dst_node, const uint32_t P,
+                                              const uint8_t fl, const int lb,
+                                              const LinkCoef<C> *__restrict__ links,
+                                              const C (&d)[9], const Collided<T, C> &c_,
+                                              const StepConst<C> &k) {
+  const C(&o)[9] = c_.o;
+  const C drho = c_.drho, rho = c_.rho, ux = c_.ux, uy = c_.uy, uu = c_.uu;
   // Boundary links of this node, Eq. EqNewBDSC in the folded form of
   // LinkCoef.  Directions that no active lane of the warp needs are
   // skipped warp-uniformly (solid lanes and lanes past nx have left).
@@ -194,10 +183,87 @@ __device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restri
         const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
         const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
                     c2 * (drho + rho * pj);
-        dst[j * P + node] = Stor<T>::st(v, k.sc);
+        dst_node[j * P] = Stor<T>::st(v, k.sc);
       }
     }
   }
+}
+
+// One time step for node (x, y) of a dense lattice, x < nx (batched
+// solver): load, collide, push every f'_i to x + c_i (a solid neighbour
+// never pushes and is never read, so its slot absorbs the push; non-periodic
+// axes have solid edges, so no push leaves the lattice), link epilogue.
+// xe / xw are the (wrapped) columns x +- 1.
+template <typename T, typename C>
+__device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restrict__ dst,
+                                          const uint8_t *__restrict__ flags,
+                                          const int32_t *__restrict__ lbase,
+                                          const LinkCoef<C> *__restrict__ links,
+                                          const StepConst<C> &k, const int x, const int y,
+                                          const int xe, const int xw) {
+  const uint32_t P = static_cast<uint32_t>(k.plane);
+  const uint32_t rowc = static_cast<uint32_t>(y) * k.pitch;
+  const uint32_t node = rowc + x;
+  const uint8_t fl = flags[node];
+  if (fl == kSolid) return;
+  const int yn = (y + 1 == k.ny) ? (k.periodic_y ? 0 : y + 1) : y + 1;
+  const int ys = (y == 0) ? (k.periodic_y ? k.ny - 1 : 0) : y - 1;
+  const uint32_t rown = static_cast<uint32_t>(yn) * k.pitch;
+  const uint32_t rows = static_cast<uint32_t>(ys) * k.pitch;
+
+  C d[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) d[i] = Stor<T>::ld(src[i * P + node], k.inv_sc);
+  // First link of this node (links sorted by node, then direction), loaded
+  // now so that its latency overlaps the collision.
+  const int lb = fl ? lbase[node] : 0;
+  Collided<T, C> c;
+  collide<T, C>(d, k, c);
+  dst[node] = c.t[0];
+  dst[1 * P + rowc + xe] = c.t[1];
+  dst[2 * P + rown + x] = c.t[2];
+  dst[3 * P + rowc + xw] = c.t[3];
+  dst[4 * P + rows + x] = c.t[4];
+  dst[5 * P + rown + xe] = c.t[5];
+  dst[6 * P + rown + xw] = c.t[6];
+  dst[7 * P + rows + xw] = c.t[7];
+  dst[8 * P + rows + xe] = c.t[8];
+  link_epilogue<T, C>(dst + node, P, fl, lb, links, d, c, k);
+}
+
+// One time step for fluid node i (row y) of a compacted lattice
+// (single-case solver; see CompactCase): load, collide, push f'_q to every
+// fluid target x + c_q (compact_targets), link epilogue.
+template <typename T, typename C>
+__device__ __forceinline__ void step_node_compact(
+    const T *__restrict__ src, T *__restrict__ dst, const uint16_t *__restrict__ meta,
+    const int32_t *__restrict__ n_lb, const int32_t *__restrict__ s_lb,
+    const int32_t *__restrict__ lbase, const int32_t *__restrict__ rowstart,
+    const LinkCoef<C> *__restrict__ links, const StepConst<C> &k, const uint32_t i, const int y) {
+  const uint32_t P = static_cast<uint32_t>(k.plane);
+  const uint32_t m = meta[i];
+  const uint8_t fl = static_cast<uint8_t>(m & 0xFFu);
+  C d[9];
+#pragma unroll
+  for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[q * P + i], k.inv_sc);
+  const int lb = fl ? lbase[i] : 0;
+  const uint32_t nb = static_cast<uint32_t>(n_lb[i]), sb = static_cast<uint32_t>(s_lb[i]);
+  Collided<T, C> c;
+  collide<T, C>(d, k, c);
+  // Targets x + c_q.  bit (j - 1) of fl set <=> x - c_j solid, so x + c_q is
+  // fluid iff bit (opp(q) - 1) is clear; a solid target has no slot.
+  uint32_t tq[9];
+  compact_targets(m, i, nb, sb, y, k.ny, k.periodic_y, rowstart, tq);
+  dst[i] = c.t[0];
+  if (!(fl & (1u << 2))) dst[1 * P + tq[1]] = c.t[1];  // opp(1) = 3
+  if (!(fl & (1u << 3))) dst[2 * P + tq[2]] = c.t[2];  // opp(2) = 4
+  if (!(fl & (1u << 0))) dst[3 * P + tq[3]] = c.t[3];  // opp(3) = 1
+  if (!(fl & (1u << 1))) dst[4 * P + tq[4]] = c.t[4];  // opp(4) = 2
+  if (!(fl & (1u << 6))) dst[5 * P + tq[5]] = c.t[5];  // opp(5) = 7
+  if (!(fl & (1u << 7))) dst[6 * P + tq[6]] = c.t[6];  // opp(6) = 8
+  if (!(fl & (1u << 4))) dst[7 * P + tq[7]] = c.t[7];  // opp(7) = 5
+  if (!(fl & (1u << 5))) dst[8 * P + tq[8]] = c.t[8];  // opp(8) = 6
+  link_epilogue<T, C>(dst + i, P, fl, lb, links, d, c, k);
 }
 
 // Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).

@@ -67,6 +67,84 @@ struct HostCase {
   std::vector<double> link_r, link_l;  // per link in input order
 };
 
+// Where node (x, y) of a case lives in a lattice: a dense lattice (row
+// pitch; flag byte kSolid marks solid nodes) or a compacted one (index map
+// y * nx + x -> compacted index, -1 for solid nodes).  at() returns the
+// element offset within a population plane, or -1 for a solid node.
+struct NodeMap {
+  const uint8_t *flags = nullptr;  // dense
+  const int32_t *index = nullptr;  // compacted
+  int32_t nx = 0, ny = 0, pitch = 0;
+  __host__ __device__ int64_t at(int x, int y) const {
+    if (index) return index[static_cast<int64_t>(y) * nx + x];
+    const int64_t n = static_cast<int64_t>(y) * pitch + x;
+    return flags[n] == kSolid ? -1 : n;
+  }
+};
+
+// Bits above the flag byte in a compacted lattice's node word.
+constexpr uint32_t kMetaWrapE = 1u << 8;  // x = nx - 1 on a periodic x axis
+constexpr uint32_t kMetaWrapW = 1u << 9;  // x = 0 on a periodic x axis
+
+// Compacted indices of the push targets x + c_q (q = 1..8, tq[0] = i) of
+// fluid node i in row y, from its node word m, n_lb / s_lb and rowstart.
+// Neighbours in the own row are i +- 1; in the rows above and below n_lb or
+// s_lb, +1 past a fluid (x, y +- 1) (bits 3 and 1 of the flag byte clear),
+// -1 for x - 1; across the periodic seam of x the row's first or last fluid
+// node.  Only targets that are fluid (bit opp(q) - 1 of the flag byte
+// clear) are meaningful.  Shared by the step kernel and host-side checks.
+__host__ __device__ inline void compact_targets(uint32_t m, uint32_t i, uint32_t nb, uint32_t sb,
+                                                int y, int ny, int periodic_y,
+                                                const int32_t *rowstart, uint32_t (&tq)[9]) {
+  tq[0] = i;
+  tq[1] = i + 1;
+  tq[2] = nb;
+  tq[3] = i - 1;
+  tq[4] = sb;
+  tq[5] = nb + ((m & (1u << 3)) ? 0u : 1u);
+  tq[6] = nb - 1;
+  tq[7] = sb - 1;
+  tq[8] = sb + ((m & (1u << 1)) ? 0u : 1u);
+  if (m & (kMetaWrapE | kMetaWrapW)) {
+    // the seam exists only on a periodic x axis; rows y +- 1 exist (wrapped
+    // where y is periodic, else the fluid rows are 1 .. ny - 2)
+    const int yn = y + 1 < ny ? y + 1 : (periodic_y ? 0 : y);
+    const int ys = y > 0 ? y - 1 : (periodic_y ? ny - 1 : y);
+    if (m & kMetaWrapE) {
+      tq[1] = static_cast<uint32_t>(rowstart[y]);
+      tq[5] = static_cast<uint32_t>(rowstart[yn]);
+      tq[8] = static_cast<uint32_t>(rowstart[ys]);
+    }
+    if (m & kMetaWrapW) {
+      tq[3] = static_cast<uint32_t>(rowstart[y + 1] - 1);
+      tq[6] = static_cast<uint32_t>(rowstart[yn + 1] - 1);
+      tq[7] = static_cast<uint32_t>(rowstart[ys + 1] - 1);
+    }
+  }
+}
+
+// A run of at most kStepThreads consecutive fluid nodes of one row of a
+// compacted lattice: row y, compacted indices start .. start + count - 1.
+struct RowTile {
+  int32_t y, start, count, pad;
+};
+
+// Compacted lattice of one case (host copy): only fluid nodes, in
+// row-major order, each population plane padded to `plane` elements.
+//   meta     flag byte | kMetaWrapE / kMetaWrapW (periodic seam of x)
+//   n_lb     compacted index of the first fluid node at or after (x, y+1)
+//   s_lb     ... at or after (x, y-1) (rows wrapped where periodic)
+//   lbase    first link of the node (links sorted by node, then direction)
+//   rowstart compacted index of every row's first fluid node (ny + 1)
+//   index    y * nx + x -> compacted index or -1 (conversions only)
+struct CompactCase {
+  int64_t n_fluid = 0, plane = 0;
+  std::vector<uint16_t> meta;
+  std::vector<int32_t> n_lb, s_lb, lbase, rowstart, index;
+  std::vector<RowTile> tiles;
+};
+void build_compact(const HostCase &hc, CompactCase *cc);
+
 // Kernel constants of one case in arithmetic type C.
 template <typename C>
 StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32_t pitch,
@@ -128,29 +206,41 @@ template <typename T, typename C>
 cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
                         const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
 
+template <typename T, typename C>
+cudaError_t launch_step_compact(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
+                                const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
+                                const RowTile *tiles, int64_t n_tiles, const LinkCoef<C> *links,
+                                const StepConst<C> &k, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_residual_compact(const T *cur, const T *prev, int64_t n_fluid, int64_t plane,
+                                    double ax, double ay, double scale, double *partials,
+                                    double *result, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
                             int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
                             double scale, double *partials, double *result, cudaStream_t s);
 
+// Conversions between a lattice (dense or compacted, see NodeMap) and
+// caller arrays over the nx x ny nodes (row-major, y * nx + x).
 template <typename T>
-cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t ny,
-                          int32_t pitch, int64_t plane, double ax, double ay, double scale,
-                          double *rho, double *ux, double *uy, cudaStream_t s);
+cudaError_t launch_fields(const T *f, const NodeMap &map, int64_t plane, double ax, double ay,
+                          double scale, double *rho, double *ux, double *uy, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_export_f(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
-                            double scale, double *out, cudaStream_t s);
+cudaError_t launch_export_f(const T *f, const NodeMap &map, int64_t plane, double scale,
+                            double *out, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_set_fields(const double *rho, const double *ux, const double *uy,
-                              const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
-                              int64_t plane, int32_t px, int32_t py, double ax, double ay,
-                              double tau_s, double scale, T *f0, T *f1, cudaStream_t s);
+                              const NodeMap &map, int64_t plane, int32_t px, int32_t py,
+                              double ax, double ay, double tau_s, double scale, T *f0, T *f1,
+                              cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch,
-                            int64_t plane, double scale, T *f, cudaStream_t s);
+cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane, double scale,
+                            T *f, cudaStream_t s);
 
 // Fixed reduction geometry: deterministic partial order on every device.
 constexpr int kResidualBlocks = 1024;

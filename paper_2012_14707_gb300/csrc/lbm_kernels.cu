@@ -2,11 +2,15 @@
 // FP64 residual/mass reduction, and field/population conversion.
 //
 // Populations are stored as deviations d_i = f_i - w_i (rest state rho = 1,
-// u = 0 is d = 0), one plane per direction: d[i][y][x] with a padded row
-// pitch.  The step kernel is a push scheme (Sec. 2: collide, then stream):
+// u = 0 is d = 0), one plane per direction.  Two layouts: the single-case
+// solver keeps only the fluid nodes, in row-major order (compacted lattice:
+// every thread of the step kernel owns a fluid node, no sector holds solid
+// slots); the batched solver keeps each case dense, d[i][y][x] with a padded
+// row pitch.  The step kernel is a push scheme (Sec. 2: collide, then stream):
 // each fluid node reads its nine values once, collides in moment space, and
-// writes f'_i to x + c_i in the other lattice (also into solid nodes, whose
-// slots no one reads).  Unknown populations of a boundary node (x_f - c_i
+// writes f'_i to x + c_i in the other lattice (compacted: only to fluid
+// targets, solid nodes have no slots; dense: to every target, a solid
+// node's slot absorbing the push unread).  Unknown populations of a boundary node (x_f - c_i
 // solid) are never pushed by anyone; the node fills them itself from values
 // it holds in registers (Eq. EqNewBDSC is local:
 // f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all belong to x_f).
@@ -38,6 +42,73 @@ step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__res
   const int xw = (x == 0) ? (k.periodic_x ? k.nx - 1 : 0) : x - 1;
   for (int y = blockIdx.y; y < k.ny; y += gridDim.y)
     step_node<T, C>(src, dst, flags, lbase, links, k, x, y, xe, xw);
+}
+
+// One time step on a compacted lattice: CTA b runs the fluid nodes of row
+// tile b (one thread per node, every lane a fluid node).
+template <typename T, typename C>
+__global__ void __launch_bounds__(kStepThreads, StepOcc<T>::min_blocks)
+step_kernel_compact(const T *__restrict__ src, T *__restrict__ dst,
+                    const uint16_t *__restrict__ meta, const int32_t *__restrict__ n_lb,
+                    const int32_t *__restrict__ s_lb, const int32_t *__restrict__ lbase,
+                    const int32_t *__restrict__ rowstart, const RowTile *__restrict__ tiles,
+                    const LinkCoef<C> *__restrict__ links, const StepConst<C> k) {
+  const RowTile t = tiles[blockIdx.x];
+  if (static_cast<int>(threadIdx.x) >= t.count) return;
+  step_node_compact<T, C>(src, dst, meta, n_lb, s_lb, lbase, rowstart, links, k,
+                          static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
+}
+
+// Residual partials on a compacted lattice: thread g of the fixed grid
+// reduces nodes g, g + G, g + 2G, ... (G threads in all), then as below.
+template <typename T>
+__global__ void __launch_bounds__(kResidualThreads)
+residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
+                          int64_t n_fluid, int64_t plane, double ax, double ay,
+                          double inv_scale, double *__restrict__ partials) {
+  using C = typename Stor<T>::C;
+  const C inv = static_cast<C>(inv_scale);
+  double num = 0.0, den = 0.0, dm = 0.0, bad = 0.0;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t node = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; node < n_fluid;
+       node += G) {
+    C a[9], b[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      a[i] = Stor<T>::ld(cur[i * plane + node], inv);
+      b[i] = Stor<T>::ld(prev[i * plane + node], inv);
+    }
+    C n1, d1, m1;
+    residual_terms<C>(a, b, static_cast<C>(ax), static_cast<C>(ay), n1, d1, m1);
+    if (!(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
+      bad += 1.0;
+      continue;
+    }
+    num += static_cast<double>(n1);
+    den += static_cast<double>(d1);
+    double sm = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) sm += static_cast<double>(a[i]);
+    dm += sm;
+  }
+  __shared__ double sh[kResidualThreads / 32][kPartialStride];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  dm = warp_sum(dm);
+  bad = warp_sum(bad);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[w][0] = num;
+    sh[w][1] = den;
+    sh[w][2] = dm;
+    sh[w][3] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPartialStride) {
+    double t = 0.0;
+    for (int i = 0; i < kResidualThreads / 32; i++) t += sh[i][threadIdx.x];
+    partials[blockIdx.x * kPartialStride + threadIdx.x] = t;
+  }
 }
 
 // Pass 1: block b reduces rows b, b + gridDim.x, ... into
@@ -119,17 +190,16 @@ residual_final(const double *__restrict__ partials, double *__restrict__ out) {
 }
 
 template <typename T>
-__global__ void fields_kernel(const T *__restrict__ f, const uint8_t *__restrict__ flags,
-                              int32_t nx, int32_t ny, int32_t pitch, int64_t plane, double ax,
+__global__ void fields_kernel(const T *__restrict__ f, const NodeMap map, int64_t plane, double ax,
                               double ay, double inv_scale, double *rho, double *ux, double *uy) {
   using C = typename Stor<T>::C;
-  const int64_t n = static_cast<int64_t>(nx) * ny;
+  const int64_t n = static_cast<int64_t>(map.nx) * map.ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t y = p / nx, x = p - y * nx;
-    const int64_t node = y * pitch + x;
+    const int64_t y = p / map.nx, x = p - y * map.nx;
+    const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
     double r = 0.0, u = 0.0, v = 0.0;
-    if (flags[node] != kSolid) {
+    if (node >= 0) {
       double a[9];
       for (int i = 0; i < 9; i++)
         a[i] = static_cast<double>(Stor<T>::ld(f[i * plane + node], static_cast<C>(inv_scale)));
@@ -150,11 +220,11 @@ __global__ void fields_kernel(const T *__restrict__ f, const uint8_t *__restrict
 // solid).  Written as deviations into both lattices; solid nodes get 0.
 template <typename T>
 __global__ void set_fields_kernel(const double *__restrict__ rho, const double *__restrict__ ux,
-                                  const double *__restrict__ uy, const uint8_t *__restrict__ flags,
-                                  int32_t nx, int32_t ny, int32_t pitch, int64_t plane, int32_t px,
-                                  int32_t py, double ax, double ay, double tau_s, double scale,
-                                  T *f0, T *f1) {
+                                  const double *__restrict__ uy, const NodeMap map, int64_t plane,
+                                  int32_t px, int32_t py, double ax, double ay, double tau_s,
+                                  double scale, T *f0, T *f1) {
   using C = typename Stor<T>::C;
+  const int32_t nx = map.nx, ny = map.ny;
   const int64_t n = static_cast<int64_t>(nx) * ny;
   const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
   const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -162,9 +232,10 @@ __global__ void set_fields_kernel(const double *__restrict__ rho, const double *
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int y = static_cast<int>(p / nx), x = static_cast<int>(p - static_cast<int64_t>(y) * nx);
-    const int64_t node = static_cast<int64_t>(y) * pitch + x;
-    double dv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (flags[node] != kSolid) {
+    const int64_t node = map.at(x, y);
+    if (node < 0) continue;
+    double dv[9];
+    {
       auto fluid_at = [&](int xx, int yy, int64_t *q) {
         if (xx < 0 || xx >= nx) {
           if (!px) return false;
@@ -174,7 +245,7 @@ __global__ void set_fields_kernel(const double *__restrict__ rho, const double *
           if (!py) return false;
           yy = (yy + ny) % ny;
         }
-        if (flags[static_cast<int64_t>(yy) * pitch + xx] == kSolid) return false;
+        if (map.at(xx, yy) < 0) return false;
         *q = static_cast<int64_t>(yy) * nx + xx;
         return true;
       };
@@ -217,33 +288,32 @@ __constant__ double kWd[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                               1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
 template <typename T>
-__global__ void export_kernel(const T *__restrict__ f, const uint8_t *__restrict__ flags,
-                              int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
+__global__ void export_kernel(const T *__restrict__ f, const NodeMap map, int64_t plane,
                               double inv_scale, double *out) {
   using C = typename Stor<T>::C;
-  const int64_t n = static_cast<int64_t>(nx) * ny;
+  const int64_t n = static_cast<int64_t>(map.nx) * map.ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
-    // solid nodes carry no state (their slots hold values parked by the
-    // pushes of their fluid neighbours): they read as the rest state w_i
-    const bool solid = flags[y * pitch + x] == kSolid;
-    out[p] = kWd[i] + (solid ? 0.0
-                             : static_cast<double>(Stor<T>::ld(f[i * plane + y * pitch + x],
-                                                               static_cast<C>(inv_scale))));
+    const int64_t i = p / n, q = p - i * n, y = q / map.nx, x = q - y * map.nx;
+    // solid nodes carry no state (a dense lattice's solid slots hold values
+    // parked by the pushes of fluid neighbours): they read as the rest state
+    const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
+    out[p] = kWd[i] + (node < 0 ? 0.0
+                                : static_cast<double>(Stor<T>::ld(f[i * plane + node],
+                                                                  static_cast<C>(inv_scale))));
   }
 }
 
 template <typename T>
-__global__ void import_kernel(const double *__restrict__ in, int32_t nx, int32_t ny,
-                              int32_t pitch, int64_t plane, double scale, T *f) {
+__global__ void import_kernel(const double *__restrict__ in, const NodeMap map, int64_t plane,
+                              double scale, T *f) {
   using C = typename Stor<T>::C;
-  const int64_t n = static_cast<int64_t>(nx) * ny;
+  const int64_t n = static_cast<int64_t>(map.nx) * map.ny;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = p / n, q = p - i * n, y = q / nx, x = q - y * nx;
-    f[i * plane + y * pitch + x] =
-        Stor<T>::st(static_cast<C>(in[p] - kWd[i]), static_cast<C>(scale));
+    const int64_t i = p / n, q = p - i * n, y = q / map.nx, x = q - y * map.nx;
+    const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
+    if (node >= 0) f[i * plane + node] = Stor<T>::st(static_cast<C>(in[p] - kWd[i]), static_cast<C>(scale));
   }
 }
 
@@ -272,61 +342,84 @@ cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, i
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_fields(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
-                          int64_t plane, double ax, double ay, double scale, double *rho,
-                          double *ux, double *uy, cudaStream_t s) {
-  const int64_t n = static_cast<int64_t>(nx) * ny;
-  fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, flags, nx, ny, pitch, plane, ax, ay,
-                                                    1.0 / scale, rho, ux, uy);
+template <typename T, typename C>
+cudaError_t launch_step_compact(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
+                                const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
+                                const RowTile *tiles, int64_t n_tiles, const LinkCoef<C> *links,
+                                const StepConst<C> &k, cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  step_kernel_compact<T, C><<<static_cast<unsigned>(n_tiles), kStepThreads, 0, s>>>(
+      src, dst, meta, n_lb, s_lb, lbase, rowstart, tiles, links, k);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_export_f(const T *f, const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
-                            double scale, double *out, cudaStream_t s) {
-  const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
-  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, flags, nx, ny, pitch, plane, 1.0 / scale, out);
+cudaError_t launch_residual_compact(const T *cur, const T *prev, int64_t n_fluid, int64_t plane,
+                                    double ax, double ay, double scale, double *partials,
+                                    double *result, cudaStream_t s) {
+  residual_partials_compact<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(
+      cur, prev, n_fluid, plane, ax, ay, 1.0 / scale, partials);
+  residual_final<<<1, kResidualBlocks, 0, s>>>(partials, result);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fields(const T *f, const NodeMap &map, int64_t plane, double ax, double ay,
+                          double scale, double *rho, double *ux, double *uy, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(map.nx) * map.ny;
+  fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, map, plane, ax, ay, 1.0 / scale, rho, ux, uy);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_export_f(const T *f, const NodeMap &map, int64_t plane, double scale,
+                            double *out, cudaStream_t s) {
+  const int64_t n = 9 * static_cast<int64_t>(map.nx) * map.ny;
+  export_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(f, map, plane, 1.0 / scale, out);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_set_fields(const double *rho, const double *ux, const double *uy,
-                              const uint8_t *flags, int32_t nx, int32_t ny, int32_t pitch,
-                              int64_t plane, int32_t px, int32_t py, double ax, double ay,
-                              double tau_s, double scale, T *f0, T *f1, cudaStream_t s) {
-  const int64_t n = static_cast<int64_t>(nx) * ny;
-  set_fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(rho, ux, uy, flags, nx, ny, pitch, plane, px,
-                                                        py, ax, ay, tau_s, scale, f0, f1);
+                              const NodeMap &map, int64_t plane, int32_t px, int32_t py,
+                              double ax, double ay, double tau_s, double scale, T *f0, T *f1,
+                              cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(map.nx) * map.ny;
+  set_fields_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(rho, ux, uy, map, plane, px, py, ax, ay,
+                                                        tau_s, scale, f0, f1);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_import_f(const double *in, int32_t nx, int32_t ny, int32_t pitch, int64_t plane,
-                            double scale, T *f, cudaStream_t s) {
-  const int64_t n = 9 * static_cast<int64_t>(nx) * ny;
-  import_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(in, nx, ny, pitch, plane, scale, f);
+cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane, double scale,
+                            T *f, cudaStream_t s) {
+  const int64_t n = 9 * static_cast<int64_t>(map.nx) * map.ny;
+  import_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(in, map, plane, scale, f);
   return cudaGetLastError();
 }
 
 #define LBM_INSTANTIATE(T, C)                                                                      \
   template cudaError_t launch_step<T, C>(const T *, T *, const uint8_t *, const int32_t *,         \
                                          const LinkCoef<C> *, const StepConst<C> &, cudaStream_t); \
+  template cudaError_t launch_step_compact<T, C>(                                                  \
+      const T *, T *, const uint16_t *, const int32_t *, const int32_t *, const int32_t *,         \
+      const int32_t *, const RowTile *, int64_t, const LinkCoef<C> *, const StepConst<C> &,        \
+      cudaStream_t);                                                                               \
+  template cudaError_t launch_residual_compact<T>(const T *, const T *, int64_t, int64_t, double,  \
+                                                  double, double, double *, double *,              \
+                                                  cudaStream_t);                                   \
   template cudaError_t launch_residual<T>(const T *, const T *, const uint8_t *, int32_t, int32_t,  \
                                          int32_t, int64_t, double, double, double, double *,       \
                                          double *, cudaStream_t);                                  \
-  template cudaError_t launch_fields<T>(const T *, const uint8_t *, int32_t, int32_t, int32_t,     \
-                                        int64_t, double, double, double, double *, double *,       \
-                                        double *, cudaStream_t);                                   \
-  template cudaError_t launch_export_f<T>(const T *, const uint8_t *, int32_t, int32_t, int32_t,    \
-                                          int64_t, double,                                         \
-                                          double *, cudaStream_t);                                 \
-  template cudaError_t launch_import_f<T>(const double *, int32_t, int32_t, int32_t, int64_t,      \
-                                          double, T *, cudaStream_t);                              \
+  template cudaError_t launch_fields<T>(const T *, const NodeMap &, int64_t, double, double,       \
+                                        double, double *, double *, double *, cudaStream_t);       \
+  template cudaError_t launch_export_f<T>(const T *, const NodeMap &, int64_t, double, double *,   \
+                                          cudaStream_t);                                           \
+  template cudaError_t launch_import_f<T>(const double *, const NodeMap &, int64_t, double, T *,   \
+                                          cudaStream_t);                                           \
   template cudaError_t launch_set_fields<T>(const double *, const double *, const double *,        \
-                                            const uint8_t *, int32_t, int32_t, int32_t, int64_t,   \
-                                            int32_t, int32_t, double, double, double, double, T *, \
-                                            T *, cudaStream_t);
+                                            const NodeMap &, int64_t, int32_t, int32_t, double,    \
+                                            double, double, double, T *, T *, cudaStream_t);
 
 LBM_INSTANTIATE(double, double)
 LBM_INSTANTIATE(float, float)

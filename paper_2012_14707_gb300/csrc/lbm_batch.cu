@@ -1,9 +1,10 @@
 // Batched solver of liblbm.so (lbm_batch_*): many independent cases of
 // different sizes, geometries and parameters advanced together.
 //
-// All cases live in one device arena (two lattices of each case's nine
-// deviation planes, flags, link-table bases, link coefficients) and share
-// one tile list: a tile is one row segment of one case.  A time step is one
+// All cases live in one device arena (each case's compacted lattice: two
+// lattices of its nine deviation planes over its fluid nodes, node words,
+// neighbour indices, link bases and link coefficients) and share one tile
+// list: a tile is a run of fluid nodes of one row of one case.  A time step is one
 // launch over all tiles; a CTA looks up its case's constants in a
 // descriptor table and runs the same per-node update as the single-case
 // kernel (so a case in a batch follows exactly the arithmetic of the case
@@ -33,16 +34,21 @@ namespace {
 
 using namespace dev;
 
+// One case in the arenas: its compacted lattice (see CompactCase) at these
+// offsets; link bases already global (case link offset added).
 template <typename C>
 struct BatchCase {
-  StepConst<C> k;
+  StepConst<C> k;    // plane = the case's padded fluid-node count
   int64_t f_off;     // element offset of the case's plane 0 in a lattice arena
-  int64_t node_off;  // node offset of the case in the flags / link-base arenas
+  int64_t node_off;  // offset of the case in the meta / n_lb / s_lb / lbase arenas
+  int64_t row_off;   // offset of the case's rowstart
+  int64_t idx_off;   // offset of the case's node map (nx * ny)
   int64_t n_fluid;
 };
 
+// A row tile of one case: rows y, compacted indices start .. start + count - 1.
 struct Tile {
-  int32_t c, y, xb, pad;
+  int32_t c, y, start, count;
 };
 
 constexpr int kBatchResidualThreads = 256;
@@ -52,19 +58,18 @@ constexpr int kBatchResidualThreads = 256;
 template <typename T, typename C, int THREADS>
 __global__ void __launch_bounds__(THREADS, StepOcc<T>::min_blocks * kStepThreads / THREADS)
 batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
-                  const uint8_t *__restrict__ flags, const int32_t *__restrict__ lbase,
-                  const LinkCoef<C> *__restrict__ links, const BatchCase<C> *__restrict__ cases,
-                  const Tile *__restrict__ tiles, const int32_t *__restrict__ active) {
+                  const uint16_t *__restrict__ meta, const int32_t *__restrict__ n_lb,
+                  const int32_t *__restrict__ s_lb, const int32_t *__restrict__ lbase,
+                  const int32_t *__restrict__ rowstart, const LinkCoef<C> *__restrict__ links,
+                  const BatchCase<C> *__restrict__ cases, const Tile *__restrict__ tiles,
+                  const int32_t *__restrict__ active) {
   const Tile t = tiles[blockIdx.x];
-  if (!active[t.c]) return;
+  if (!active[t.c] || static_cast<int>(threadIdx.x) >= t.count) return;
   const BatchCase<C> &bc = cases[t.c];
-  const StepConst<C> &k = bc.k;  // read through the cache, not copied to registers
-  const int x = t.xb * THREADS + threadIdx.x;
-  if (x >= k.nx) return;
-  const int xe = (x + 1 == k.nx) ? (k.periodic_x ? 0 : x + 1) : x + 1;
-  const int xw = (x == 0) ? (k.periodic_x ? k.nx - 1 : 0) : x - 1;
-  step_node<T, C>(src + bc.f_off, dst + bc.f_off, flags + bc.node_off, lbase + bc.node_off, links,
-                  k, x, t.y, xe, xw);
+  const int64_t no = bc.node_off;
+  step_node_compact<T, C>(src + bc.f_off, dst + bc.f_off, meta + no, n_lb + no, s_lb + no,
+                          lbase + no, rowstart + bc.row_off, links, bc.k,
+                          static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
 }
 
 // One CTA per case: residual of the case (FP64 sums in a fixed order); a
@@ -74,7 +79,7 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
 template <typename T, typename C>
 __global__ void __launch_bounds__(kBatchResidualThreads)
 batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
-                      const uint8_t *__restrict__ flags, const BatchCase<C> *__restrict__ cases,
+                      const BatchCase<C> *__restrict__ cases,
                       int32_t *__restrict__ active, double tol, const int64_t *__restrict__ counter,
                       int64_t K, int64_t *__restrict__ steps_done, double *__restrict__ res_out,
                       int32_t *__restrict__ n_active) {
@@ -84,13 +89,9 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
   const StepConst<C> k = bc.k;
   const T *a_base = cur + bc.f_off;
   const T *b_base = prev + bc.f_off;
-  const uint8_t *fl = flags + bc.node_off;
   double num = 0.0, den = 0.0, bad = 0.0;
-  for (int y = 0; y < k.ny; y++) {
-    const int64_t row = static_cast<int64_t>(y) * k.pitch;
-    for (int x = threadIdx.x; x < k.nx; x += blockDim.x) {
-      const int64_t node = row + x;
-      if (fl[node] == kSolid) continue;
+  {
+    for (int64_t node = threadIdx.x; node < bc.n_fluid; node += blockDim.x) {
       C a[9], b[9];
 #pragma unroll
       for (int i = 0; i < 9; i++) {
@@ -140,11 +141,13 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
 __global__ void batch_advance(int64_t *counter, int64_t K) { *counter += K; }
 
 template <typename T, typename C, int THREADS>
-cudaError_t launch_batch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
+cudaError_t launch_batch_step(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
+                              const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
                               const void *links, const void *cases, const Tile *tiles,
                               int n_tiles, const int32_t *active, cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
   batch_step_kernel<T, C, THREADS><<<n_tiles, THREADS, 0, s>>>(
-      src, dst, flags, lbase, static_cast<const LinkCoef<C> *>(links),
+      src, dst, meta, n_lb, s_lb, lbase, rowstart, static_cast<const LinkCoef<C> *>(links),
       static_cast<const BatchCase<C> *>(cases), tiles, active);
   return cudaGetLastError();
 }
@@ -161,13 +164,15 @@ struct lbm_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int n_cases = 0;
-  std::vector<int32_t> nx, ny, pitch;
-  std::vector<int64_t> f_off, node_off, n_fluid;
+  std::vector<int32_t> nx, ny;
+  std::vector<int64_t> f_off, node_off, idx_off, plane, n_fluid;
+  std::vector<std::vector<int32_t>> rowstart_h;  // per case, for the tile lists
   std::vector<double> ax, ay, scale, tau_s;
   std::vector<int32_t> px, py;
   void *f[2] = {nullptr, nullptr};
-  uint8_t *flags = nullptr;
-  int32_t *lbase = nullptr;
+  uint16_t *meta = nullptr;
+  int32_t *n_lb = nullptr, *s_lb = nullptr, *lbase = nullptr, *rowstart = nullptr;
+  int32_t *index = nullptr;
   void *links = nullptr;
   void *cases = nullptr;
   lbm::Tile *tiles = nullptr;
@@ -209,19 +214,20 @@ cudaError_t dispatch_b(int precision, F &&f) {
 
 lbm::NodeMap case_map(const lbm_batch_t *b, int c) {
   lbm::NodeMap m;
-  m.flags = b->flags + b->node_off[c];
+  m.index = b->index + b->idx_off[c];
   m.nx = b->nx[c];
   m.ny = b->ny[c];
-  m.pitch = b->pitch[c];
   return m;
 }
 
+// Row tiles of `threads` fluid nodes (the CTA width) over every case.
 std::vector<lbm::Tile> make_tiles(const lbm_batch_t *b, int threads) {
   std::vector<lbm::Tile> t;
   for (int c = 0; c < b->n_cases; c++) {
-    const int nxb = (b->nx[c] + threads - 1) / threads;
+    const std::vector<int32_t> &rs = b->rowstart_h[c];
     for (int y = 0; y < b->ny[c]; y++)
-      for (int xb = 0; xb < nxb; xb++) t.push_back(lbm::Tile{c, y, xb, 0});
+      for (int32_t i = rs[y]; i < rs[y + 1]; i += threads)
+        t.push_back(lbm::Tile{c, y, i, std::min<int32_t>(threads, rs[y + 1] - i)});
   }
   return t;
 }
@@ -234,8 +240,8 @@ cudaError_t step_once(lbm_batch_t *b, int threads, const lbm::Tile *tiles, int n
     auto go = [&](auto kernel_threads) {
       constexpr int TH = decltype(kernel_threads)::value;
       return lbm::launch_batch_step<T, C, TH>(
-          static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->flags, b->lbase,
-          b->links, b->cases, tiles, n_tiles, b->active, b->stream);
+          static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->meta, b->n_lb, b->s_lb,
+          b->lbase, b->rowstart, b->links, b->cases, tiles, n_tiles, b->active, b->stream);
     };
     if (threads == 64) return go(std::integral_constant<int, 64>());
     if (threads == 128) return go(std::integral_constant<int, 128>());
@@ -252,8 +258,9 @@ void batch_release(lbm_batch_t *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->flags), static_cast<void *>(b->lbase),
-                  b->links, b->cases, static_cast<void *>(b->tiles), static_cast<void *>(b->active),
+  for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->meta), static_cast<void *>(b->n_lb),
+                  static_cast<void *>(b->s_lb), static_cast<void *>(b->lbase),
+                  static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->tiles), static_cast<void *>(b->active),
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active)})
     if (p) cudaFree(p);
@@ -320,7 +327,8 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     return LBM_EINVAL;
   }
   std::vector<lbm::HostCase> hc(static_cast<size_t>(n_cases));
-  int64_t nodes = 0, links = 0;
+  std::vector<lbm::CompactCase> cc(static_cast<size_t>(n_cases));
+  int64_t nodes = 0, links = 0, rows = 0, dense = 0;
   for (int c = 0; c < n_cases; c++) {
     lbm_params_t p = cases[c].params;
     p.precision = precision;
@@ -333,8 +341,11 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       g_batch_error = "case " + std::to_string(c) + ": " + msg;
       return rc;
     }
-    nodes += hc[c].plane;
+    lbm::build_compact(hc[c], &cc[c]);
+    nodes += cc[c].plane;
     links += hc[c].n_links;
+    rows += hc[c].ny + 1;
+    dense += static_cast<int64_t>(hc[c].nx) * hc[c].ny;
   }
   if (nodes * 9 >= (int64_t(1) << 40) || links >= (int64_t(1) << 31)) {
     g_batch_error = "batch too large";
@@ -355,18 +366,22 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   }
   const size_t es = elem_size_b(precision);
   const size_t ces = precision == LBM_FP64 ? 8 : 4;
-  std::vector<uint8_t> flags(static_cast<size_t>(nodes));
-  std::vector<int32_t> lbase(static_cast<size_t>(nodes));
+  std::vector<uint16_t> meta(static_cast<size_t>(nodes), 0);
+  std::vector<int32_t> n_lb(static_cast<size_t>(nodes), 0), s_lb(static_cast<size_t>(nodes), 0),
+      lbase(static_cast<size_t>(nodes), 0), rowstart(static_cast<size_t>(rows), 0),
+      index(static_cast<size_t>(dense), -1);
   std::vector<unsigned char> lhost(std::max<int64_t>(1, links) * 4 * ces, 0);
   std::vector<unsigned char> chost;
-  int64_t noff = 0, loff = 0;
+  int64_t noff = 0, loff = 0, roff = 0, ioff = 0;
   for (int c = 0; c < n_cases; c++) {
     const lbm::HostCase &h = hc[c];
+    lbm::CompactCase &k = cc[c];
     b->nx.push_back(h.nx);
     b->ny.push_back(h.ny);
-    b->pitch.push_back(h.pitch);
     b->f_off.push_back(9 * noff);
     b->node_off.push_back(noff);
+    b->idx_off.push_back(ioff);
+    b->plane.push_back(k.plane);
     b->n_fluid.push_back(h.n_fluid);
     b->ax.push_back(h.ax);
     b->ay.push_back(h.ay);
@@ -376,9 +391,13 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     b->py.push_back(h.py);
     b->total_nodes += static_cast<int64_t>(h.nx) * h.ny;
     b->total_fluid += h.n_fluid;
-    std::memcpy(&flags[noff], h.flags.data(), h.flags.size());
-    for (size_t q = 0; q < h.lbase.size(); q++)
-      lbase[noff + q] = h.lbase[q] < 0 ? -1 : static_cast<int32_t>(h.lbase[q] + loff);
+    std::copy(k.meta.begin(), k.meta.end(), meta.begin() + noff);
+    std::copy(k.n_lb.begin(), k.n_lb.end(), n_lb.begin() + noff);
+    std::copy(k.s_lb.begin(), k.s_lb.end(), s_lb.begin() + noff);
+    for (size_t q = 0; q < k.lbase.size(); q++)
+      lbase[noff + q] = static_cast<int32_t>(k.lbase[q] + loff);
+    std::copy(k.rowstart.begin(), k.rowstart.end(), rowstart.begin() + roff);
+    std::copy(k.index.begin(), k.index.end(), index.begin() + ioff);
     for (int64_t q = 0; q < h.n_links; q++) {
       const double *cf = &h.coef[4 * q];
       if (ces == 8) {
@@ -393,10 +412,12 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     auto put = [&](auto tag) {
       using C = decltype(tag);
       lbm::BatchCase<C> d;
-      d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, h.pitch, h.plane, h.px, h.py, h.ax, h.ay,
+      d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, 0, k.plane, h.px, h.py, h.ax, h.ay,
                                     h.params.diffuse_mode, h.scale);
       d.f_off = 9 * noff;
       d.node_off = noff;
+      d.row_off = roff;
+      d.idx_off = ioff;
       d.n_fluid = h.n_fluid;
       const unsigned char *p = reinterpret_cast<const unsigned char *>(&d);
       chost.insert(chost.end(), p, p + sizeof(d));
@@ -405,17 +426,25 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       put(double());
     else
       put(float());
-    noff += h.plane;
+    b->rowstart_h.push_back(k.rowstart);
+    noff += k.plane;
     loff += h.n_links;
+    roff += h.ny + 1;
+    ioff += static_cast<int64_t>(h.nx) * h.ny;
   }
   hc.clear();
+  cc.clear();
   b->arena_nodes = nodes;
   auto alloc = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
   const size_t fbytes = 9 * static_cast<size_t>(nodes) * es;
   if (e == cudaSuccess) e = alloc(&b->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&b->f[1], fbytes);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->flags), flags.size());
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->meta), meta.size() * 2);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->n_lb), n_lb.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->s_lb), s_lb.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->lbase), lbase.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->rowstart), rowstart.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->index), index.size() * 4);
   if (e == cudaSuccess) e = alloc(&b->links, lhost.size());
   if (e == cudaSuccess) e = alloc(&b->cases, chost.size());
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->active), n_cases * 4);
@@ -424,8 +453,15 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->counter), 8);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->n_active), 4);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&b->h_n_active), 4);
-  if (e == cudaSuccess) e = cudaMemcpy(b->flags, flags.data(), flags.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->lbase, lbase.data(), lbase.size() * 4, cudaMemcpyHostToDevice);
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(b->meta, meta.data(), meta.size() * 2);
+  up(b->n_lb, n_lb.data(), n_lb.size() * 4);
+  up(b->s_lb, s_lb.data(), s_lb.size() * 4);
+  up(b->lbase, lbase.data(), lbase.size() * 4);
+  up(b->rowstart, rowstart.data(), rowstart.size() * 4);
+  up(b->index, index.data(), index.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(b->links, lhost.data(), lhost.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->cases, chost.data(), chost.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
@@ -500,7 +536,7 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
         using T = std::remove_pointer_t<decltype(tT)>;
         using C = std::remove_pointer_t<decltype(tC)>;
         lbm::batch_residual_kernel<T, C><<<b->n_cases, lbm::kBatchResidualThreads, 0, b->stream>>>(
-            static_cast<const T *>(b->f[0]), static_cast<const T *>(b->f[1]), b->flags,
+            static_cast<const T *>(b->f[0]), static_cast<const T *>(b->f[1]),
             static_cast<const lbm::BatchCase<C> *>(b->cases), b->active, tol, b->counter,
             check_every, b->steps_done, b->res, b->n_active);
         return cudaGetLastError();
@@ -548,7 +584,7 @@ int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double 
   double *d = nullptr;
   cudaError_t e = cudaMalloc(&d, 3 * n * sizeof(double));
   if (e != cudaSuccess) return bfail(b, LBM_ENOMEM, cudaGetErrorString(e));
-  const int64_t plane = static_cast<int64_t>(b->pitch[c]) * b->ny[c];
+  const int64_t plane = b->plane[c];
   e = dispatch_b(b->precision, [&](auto tT, auto tC) {
     using T = std::remove_pointer_t<decltype(tT)>;
     return lbm::launch_fields<T>(static_cast<const T *>(b->f[b->cur]) + b->f_off[c], case_map(b, c),
@@ -576,7 +612,7 @@ int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const dou
   e = cudaMemcpy(d, rho, n * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d + n, ux, n * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d + 2 * n, uy, n * 8, cudaMemcpyHostToDevice);
-  const int64_t plane = static_cast<int64_t>(b->pitch[c]) * b->ny[c];
+  const int64_t plane = b->plane[c];
   if (e == cudaSuccess)
     e = dispatch_b(b->precision, [&](auto tT, auto tC) {
       using T = std::remove_pointer_t<decltype(tT)>;

@@ -189,50 +189,8 @@ __device__ __forceinline__ void link_epilogue(T *__restrict__ dst_node, const ui
   }
 }
 
-// One time step for node (x, y) of a dense lattice, x < nx (batched
-// solver): load, collide, push every f'_i to x + c_i (a solid neighbour
-// never pushes and is never read, so its slot absorbs the push; non-periodic
-// axes have solid edges, so no push leaves the lattice), link epilogue.
-// xe / xw are the (wrapped) columns x +- 1.
-template <typename T, typename C>
-__device__ __forceinline__ void step_node(const T *__restrict__ src, T *__restrict__ dst,
-                                          const uint8_t *__restrict__ flags,
-                                          const int32_t *__restrict__ lbase,
-                                          const LinkCoef<C> *__restrict__ links,
-                                          const StepConst<C> &k, const int x, const int y,
-                                          const int xe, const int xw) {
-  const uint32_t P = static_cast<uint32_t>(k.plane);
-  const uint32_t rowc = static_cast<uint32_t>(y) * k.pitch;
-  const uint32_t node = rowc + x;
-  const uint8_t fl = flags[node];
-  if (fl == kSolid) return;
-  const int yn = (y + 1 == k.ny) ? (k.periodic_y ? 0 : y + 1) : y + 1;
-  const int ys = (y == 0) ? (k.periodic_y ? k.ny - 1 : 0) : y - 1;
-  const uint32_t rown = static_cast<uint32_t>(yn) * k.pitch;
-  const uint32_t rows = static_cast<uint32_t>(ys) * k.pitch;
-
-  C d[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) d[i] = Stor<T>::ld(src[i * P + node], k.inv_sc);
-  // First link of this node (links sorted by node, then direction), loaded
-  // now so that its latency overlaps the collision.
-  const int lb = fl ? lbase[node] : 0;
-  Collided<T, C> c;
-  collide<T, C>(d, k, c);
-  dst[node] = c.t[0];
-  dst[1 * P + rowc + xe] = c.t[1];
-  dst[2 * P + rown + x] = c.t[2];
-  dst[3 * P + rowc + xw] = c.t[3];
-  dst[4 * P + rows + x] = c.t[4];
-  dst[5 * P + rown + xe] = c.t[5];
-  dst[6 * P + rown + xw] = c.t[6];
-  dst[7 * P + rows + xw] = c.t[7];
-  dst[8 * P + rows + xe] = c.t[8];
-  link_epilogue<T, C>(dst + node, P, fl, lb, links, d, c, k);
-}
-
-// One time step for fluid node i (row y) of a compacted lattice
-// (single-case solver; see CompactCase): load, collide, push f'_q to every
+// One time step for fluid node i (row y) of a compacted lattice (see
+// CompactCase): load, collide, push f'_q to every
 // fluid target x + c_q (compact_targets), link epilogue.
 template <typename T, typename C>
 __device__ __forceinline__ void step_node_compact(

@@ -24,10 +24,10 @@ struct StepConst {
   C h_e, h_eps, h_q, h_s, h_j;  // 1 - s/2: weights of the forcing moments (Eq. MomentPost)
   C sc, inv_sc;                 // storage scale of the 16-bit types (1 otherwise)
   C ax, ay;                     // body acceleration
-  int32_t nx, ny, pitch;        // lattice size and row pitch (elements)
+  int32_t nx, ny, pitch;        // lattice size; row pitch (unused by the compacted lattice)
   int32_t periodic_x, periodic_y;
   int32_t diffuse_mode;         // reading of the Maxwell part, see LinkCoef
-  int64_t plane;                // elements per population plane = ny * pitch
+  int64_t plane;                // elements per population plane (padded fluid-node count)
 };
 
 // Coefficients of one link in the kernels' folded form of Eq. EqNewBDSC,
@@ -67,18 +67,14 @@ struct HostCase {
   std::vector<double> link_r, link_l;  // per link in input order
 };
 
-// Where node (x, y) of a case lives in a lattice: a dense lattice (row
-// pitch; flag byte kSolid marks solid nodes) or a compacted one (index map
-// y * nx + x -> compacted index, -1 for solid nodes).  at() returns the
+// Where node (x, y) of a case lives in its compacted lattice: the index
+// map y * nx + x -> compacted index, -1 for solid nodes.  at() returns the
 // element offset within a population plane, or -1 for a solid node.
 struct NodeMap {
-  const uint8_t *flags = nullptr;  // dense
-  const int32_t *index = nullptr;  // compacted
-  int32_t nx = 0, ny = 0, pitch = 0;
+  const int32_t *index = nullptr;
+  int32_t nx = 0, ny = 0;
   __host__ __device__ int64_t at(int x, int y) const {
-    if (index) return index[static_cast<int64_t>(y) * nx + x];
-    const int64_t n = static_cast<int64_t>(y) * pitch + x;
-    return flags[n] == kSolid ? -1 : n;
+    return index[static_cast<int64_t>(y) * nx + x];
   }
 };
 
@@ -189,8 +185,9 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                const double *uby, double *r_out, double *l_out,
                                double *coef8_out /* n x 8 */, int64_t *n_clamped);
 
-// Step kernel geometry: one thread per node, kStepThreads nodes of a row
-// per CTA, registers bounded for kStepMinBlocks resident CTAs per SM.
+// Step kernel geometry: one thread per fluid node, up to kStepThreads
+// nodes of a row per CTA, registers bounded for StepOcc<T>::min_blocks
+// resident CTAs per SM.
 constexpr int kStepThreads = 256;
 template <typename T>
 struct StepOcc {
@@ -203,10 +200,6 @@ struct StepOcc<double> {
 
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
 template <typename T, typename C>
-cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
-                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
-
-template <typename T, typename C>
 cudaError_t launch_step_compact(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
                                 const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
                                 const RowTile *tiles, int64_t n_tiles, const LinkCoef<C> *links,
@@ -217,12 +210,7 @@ cudaError_t launch_residual_compact(const T *cur, const T *prev, int64_t n_fluid
                                     double ax, double ay, double scale, double *partials,
                                     double *result, cudaStream_t s);
 
-template <typename T>
-cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
-                            int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
-                            double scale, double *partials, double *result, cudaStream_t s);
-
-// Conversions between a lattice (dense or compacted, see NodeMap) and
+// Conversions between a compacted lattice (see NodeMap) and
 // caller arrays over the nx x ny nodes (row-major, y * nx + x).
 template <typename T>
 cudaError_t launch_fields(const T *f, const NodeMap &map, int64_t plane, double ax, double ay,

@@ -2,15 +2,14 @@
 // FP64 residual/mass reduction, and field/population conversion.
 //
 // Populations are stored as deviations d_i = f_i - w_i (rest state rho = 1,
-// u = 0 is d = 0), one plane per direction.  Two layouts: the single-case
-// solver keeps only the fluid nodes, in row-major order (compacted lattice:
-// every thread of the step kernel owns a fluid node, no sector holds solid
-// slots); the batched solver keeps each case dense, d[i][y][x] with a padded
-// row pitch.  The step kernel is a push scheme (Sec. 2: collide, then stream):
-// each fluid node reads its nine values once, collides in moment space, and
-// writes f'_i to x + c_i in the other lattice (compacted: only to fluid
-// targets, solid nodes have no slots; dense: to every target, a solid
-// node's slot absorbing the push unread).  Unknown populations of a boundary node (x_f - c_i
+// u = 0 is d = 0), one plane per direction, over the fluid nodes only, in
+// row-major order (compacted lattice: every thread of the step kernel owns
+// a fluid node, no sector holds solid slots; the batched solver keeps every
+// case the same way in one arena).  The step kernel is a push scheme
+// (Sec. 2: collide, then stream): each fluid node reads its nine values
+// once, collides in moment space, and writes f'_i to x + c_i in the other
+// lattice (fluid targets only: solid nodes have no slots).  Unknown
+// populations of a boundary node (x_f - c_i
 // solid) are never pushed by anyone; the node fills them itself from values
 // it holds in registers (Eq. EqNewBDSC is local:
 // f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all belong to x_f).
@@ -23,26 +22,6 @@ namespace lbm {
 namespace {
 
 using namespace dev;
-
-// One time step, one thread per node (x), one CTA row of kStepThreads nodes
-// per (blockIdx.x, y).  Each fluid node loads its nine deviations, collides
-// in moment space, pushes every f'_i to x + c_i in the other lattice and
-// fills its own unknown populations from the link table
-// (Eq. EqNewBDSC is local: f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and
-// rho_f all belong to x_f).  Offsets are 32-bit (the lattice is limited to
-// 2^31 / 9 nodes per plane); row wraps are uniform per CTA.
-template <typename T, typename C>
-__global__ void __launch_bounds__(kStepThreads, StepOcc<T>::min_blocks)
-step_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint8_t *__restrict__ flags,
-            const int32_t *__restrict__ lbase, const LinkCoef<C> *__restrict__ links,
-            const StepConst<C> k) {
-  const int x = blockIdx.x * kStepThreads + threadIdx.x;
-  if (x >= k.nx) return;
-  const int xe = (x + 1 == k.nx) ? (k.periodic_x ? 0 : x + 1) : x + 1;
-  const int xw = (x == 0) ? (k.periodic_x ? k.nx - 1 : 0) : x - 1;
-  for (int y = blockIdx.y; y < k.ny; y += gridDim.y)
-    step_node<T, C>(src, dst, flags, lbase, links, k, x, y, xe, xw);
-}
 
 // One time step on a compacted lattice: CTA b runs the fluid nodes of row
 // tile b (one thread per node, every lane a fluid node).
@@ -59,8 +38,12 @@ step_kernel_compact(const T *__restrict__ src, T *__restrict__ dst,
                           static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
 }
 
-// Residual partials on a compacted lattice: thread g of the fixed grid
-// reduces nodes g, g + G, g + 2G, ... (G threads in all), then as below.
+// Residual pass 1: thread g of the fixed grid reduces nodes g, g + G,
+// g + 2G, ... (G threads in all) into num, den, mass deviation, non-finite
+// count: per-node terms in the storage's arithmetic type, sums in FP64
+// (warp shuffles, then shared memory), block b's four sums to
+// partials[b * 4 + {0..3}].  The node-to-thread map is fixed, so the result
+// is bitwise reproducible.
 template <typename T>
 __global__ void __launch_bounds__(kResidualThreads)
 residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
@@ -90,66 +73,6 @@ residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
 #pragma unroll
     for (int i = 0; i < 9; i++) sm += static_cast<double>(a[i]);
     dm += sm;
-  }
-  __shared__ double sh[kResidualThreads / 32][kPartialStride];
-  num = warp_sum(num);
-  den = warp_sum(den);
-  dm = warp_sum(dm);
-  bad = warp_sum(bad);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    sh[w][0] = num;
-    sh[w][1] = den;
-    sh[w][2] = dm;
-    sh[w][3] = bad;
-  }
-  __syncthreads();
-  if (threadIdx.x < kPartialStride) {
-    double t = 0.0;
-    for (int i = 0; i < kResidualThreads / 32; i++) t += sh[i][threadIdx.x];
-    partials[blockIdx.x * kPartialStride + threadIdx.x] = t;
-  }
-}
-
-// Pass 1: block b reduces rows b, b + gridDim.x, ... into
-// partials[b * 4 + {0..3}] (num, den, mass deviation, non-finite count):
-// per-node terms in the storage's arithmetic type, sums in FP64 (warp
-// shuffles, then shared memory).  The row-to-block map is fixed, so the
-// result is bitwise reproducible.
-template <typename T>
-__global__ void __launch_bounds__(kResidualThreads)
-residual_partials(const T *__restrict__ cur, const T *__restrict__ prev,
-                  const uint8_t *__restrict__ flags, int32_t nx, int32_t ny, int32_t pitch,
-                  int64_t plane, double ax, double ay, double inv_scale,
-                  double *__restrict__ partials) {
-  using C = typename Stor<T>::C;
-  const C inv = static_cast<C>(inv_scale);
-  double num = 0.0, den = 0.0, dm = 0.0, bad = 0.0;
-  for (int y = blockIdx.x; y < ny; y += gridDim.x) {
-    const int64_t row = static_cast<int64_t>(y) * pitch;
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-      const int64_t node = row + x;
-      if (flags[node] == kSolid) continue;
-      C a[9], b[9];
-#pragma unroll
-      for (int i = 0; i < 9; i++) {
-        a[i] = Stor<T>::ld(cur[i * plane + node], inv);
-        b[i] = Stor<T>::ld(prev[i * plane + node], inv);
-      }
-      C n1, d1, m1;
-      residual_terms<C>(a, b, static_cast<C>(ax), static_cast<C>(ay), n1, d1, m1);
-      if (!(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
-        bad += 1.0;
-        continue;
-      }
-      num += static_cast<double>(n1);
-      den += static_cast<double>(d1);
-      // mass: the exact sum of the stored deviations, in FP64
-      double s = 0.0;
-#pragma unroll
-      for (int i = 0; i < 9; i++) s += static_cast<double>(a[i]);
-      dm += s;
-    }
   }
   __shared__ double sh[kResidualThreads / 32][kPartialStride];
   num = warp_sum(num);
@@ -325,24 +248,6 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <typename T, typename C>
-cudaError_t launch_step(const T *src, T *dst, const uint8_t *flags, const int32_t *lbase,
-                        const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
-  dim3 grid((k.nx + kStepThreads - 1) / kStepThreads, k.ny < 65535 ? k.ny : 65535);
-  step_kernel<T, C><<<grid, kStepThreads, 0, s>>>(src, dst, flags, lbase, links, k);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_residual(const T *cur, const T *prev, const uint8_t *flags, int32_t nx,
-                            int32_t ny, int32_t pitch, int64_t plane, double ax, double ay,
-                            double scale, double *partials, double *result, cudaStream_t s) {
-  residual_partials<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(
-      cur, prev, flags, nx, ny, pitch, plane, ax, ay, 1.0 / scale, partials);
-  residual_final<<<1, kResidualBlocks, 0, s>>>(partials, result);
-  return cudaGetLastError();
-}
-
-template <typename T, typename C>
 cudaError_t launch_step_compact(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
                                 const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
                                 const RowTile *tiles, int64_t n_tiles, const LinkCoef<C> *links,
@@ -399,8 +304,6 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
 }
 
 #define LBM_INSTANTIATE(T, C)                                                                      \
-  template cudaError_t launch_step<T, C>(const T *, T *, const uint8_t *, const int32_t *,         \
-                                         const LinkCoef<C> *, const StepConst<C> &, cudaStream_t); \
   template cudaError_t launch_step_compact<T, C>(                                                  \
       const T *, T *, const uint16_t *, const int32_t *, const int32_t *, const int32_t *,         \
       const int32_t *, const RowTile *, int64_t, const LinkCoef<C> *, const StepConst<C> &,        \
@@ -408,9 +311,6 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
   template cudaError_t launch_residual_compact<T>(const T *, const T *, int64_t, int64_t, double,  \
                                                   double, double, double *, double *,              \
                                                   cudaStream_t);                                   \
-  template cudaError_t launch_residual<T>(const T *, const T *, const uint8_t *, int32_t, int32_t,  \
-                                         int32_t, int64_t, double, double, double, double *,       \
-                                         double *, cudaStream_t);                                  \
   template cudaError_t launch_fields<T>(const T *, const NodeMap &, int64_t, double, double,       \
                                         double, double *, double *, double *, cudaStream_t);       \
   template cudaError_t launch_export_f<T>(const T *, const NodeMap &, int64_t, double, double *,   \

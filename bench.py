@@ -330,6 +330,9 @@ def run_batch(args):
     b = lbm.Batch(cl, precision=args.precision)
     t_create = time.perf_counter() - t0
     info = b.info()
+    # warm-up: graph capture and a few hundred steps, then back to rest
+    b.run_to(args.batch_tol, max(args.warmup, 1) * args.lbm_steps, check_every=args.lbm_steps)
+    b.reset()
     sampler = ClockSampler(local)
     sampler.start()
     torch.cuda.synchronize()
@@ -337,13 +340,45 @@ def run_batch(args):
     steps, res, total = b.run_to(args.batch_tol, args.batch_max_steps, check_every=args.lbm_steps)
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
+    b.close()
     nf = np.array([c.n_fluid for c in cl], np.float64)
-    run = np.where(steps > 0, steps, total).astype(np.float64)
+    run = np.where(steps != 0, np.abs(steps), total).astype(np.float64)
     updates = float((nf * run).sum())
     conv = steps > 0
+    # time to steady state of the same cases one at a time through the
+    # single-case solver, against the batch, on a subset of the cases
+    comp = None
+    if args.batch_single > 0:
+        sub = cl[:args.batch_single]
+        bs = lbm.Batch(sub, precision=args.precision)
+        bs.run_to(args.batch_tol, args.lbm_steps, check_every=args.lbm_steps)
+        bs.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s_b, _, _ = bs.run_to(args.batch_tol, args.batch_max_steps, check_every=args.lbm_steps)
+        t_batch = time.perf_counter() - t0
+        bs.close()
+        t0 = time.perf_counter()
+        s_single = []
+        for c in sub:
+            sv = lbm.Solver(c, precision=args.precision, residual_every=args.lbm_steps)
+            try:
+                n, r = sv.run_to(args.batch_tol, args.batch_max_steps)
+                s_single.append(n if r < args.batch_tol else 0)
+            except lbm.LbmError:
+                s_single.append(-1)
+            sv.close()
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - t0
+        same = int(sum(1 for a, c in zip(s_b, s_single) if a == c))
+        comp = {"cases": len(sub), "single_case_seconds": t_single, "batched_seconds": t_batch,
+                "speedup": t_single / t_batch, "same_steps_to_steady": same,
+                "note": "each case alone through lbm_create/lbm_run_to (create included) vs "
+                        "all of them in one batch (create excluded), same tol and check interval"}
     line = {
         "metric": "MLUPS (batched)", "value": updates / wall / 1e6, "unit": "MLUPS",
-        "n_gpus": world, "steps": int(total), "warmup": 0, "ms_per_step": wall / max(total, 1) * 1e3,
+        "n_gpus": world, "steps": int(total), "warmup": max(args.warmup, 1) * args.lbm_steps,
+        "ms_per_step": wall / max(total, 1) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "fp16": "f16"}[args.precision],
         "data": "synthetic",
@@ -355,6 +390,7 @@ def run_batch(args):
                   "steps_to_steady_median": float(np.median(steps[conv])) if conv.any() else None,
                   "steps_to_steady_p90": float(np.percentile(steps[conv], 90)) if conv.any() else None,
                   "create_seconds": t_create, "wall_seconds": wall},
+        "time_to_steady_vs_single": comp,
         "clocks": clocks,
     }
     if rank == 0:
@@ -376,6 +412,8 @@ def main():
     ap.add_argument("--workload", choices=("throughput", "batch"), default="throughput")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-max-steps", type=int, default=20000)
+    ap.add_argument("--batch-single", type=int, default=32,
+                    help="cases also solved one at a time for the time-to-steady comparison")
     ap.add_argument("--batch-tol", type=float, default=1e-6,
                     help="residual to reach; the one-step FP32 residual floors near 1e-8")
     ap.add_argument("--nx", type=int, default=0, help="profiling only: smaller lattice width")

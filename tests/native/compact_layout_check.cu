@@ -1,0 +1,136 @@
+// Host-side check of the compacted lattice (no GPU needed): the library's
+// own build_host_case + build_compact, then compact_targets (the index
+// function the step kernel uses) against the dense neighbourhood for every
+// fluid node and direction, and the row tiles against the fluid nodes.
+// Geometries: walled and periodic channels, a periodic box, 1-wide
+// lattices, random cylinders on every combination of periodic axes, and
+// any lattices given as files (int32 nx, ny, periodic_x, periodic_y, then
+// nx*ny solid bytes).
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+#include <string>
+#include <vector>
+#include "lbm_internal.h"
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t> solid) {
+  std::vector<int32_t> lx, ly, ld;
+  std::vector<double> q, ub;
+  auto wrapok = [&](int x, int y, int &xx, int &yy) {
+    xx = x; yy = y;
+    if (xx < 0 || xx >= nx) { if (!px) return false; xx = (xx + nx) % nx; }
+    if (yy < 0 || yy >= ny) { if (!py) return false; yy = (yy + ny) % ny; }
+    return true;
+  };
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      if (solid[y * nx + x]) continue;
+      for (int i = 1; i < 9; i++) {
+        int xx, yy;
+        if (!wrapok(x - CX[i], y - CY[i], xx, yy) || solid[yy * nx + xx]) {
+          lx.push_back(x); ly.push_back(y); ld.push_back(i); q.push_back(0.5); ub.push_back(0.0);
+        }
+      }
+    }
+  lbm_domain_t dom{};
+  dom.nx = nx; dom.ny = ny; dom.periodic_x = px; dom.periodic_y = py; dom.H = 10.0; dom.ax = 1e-6; dom.ay = 0;
+  lbm_params_t p;
+  lbm_params_default(&p);
+  lbm::HostCase hc;
+  std::string err;
+  int rc = lbm::build_host_case(&dom, solid.data(), lx.size(), lx.data(), ly.data(), ld.data(), q.data(),
+                                ub.data(), ub.data(), 0.05, &p, &hc, &err);
+  if (rc) { printf("%s: build_host_case failed: %s\n", name, err.c_str()); return 1; }
+  lbm::CompactCase cc;
+  lbm::build_compact(hc, &cc);
+  long bad = 0, checked = 0;
+  std::vector<int> covered(cc.n_fluid, 0);
+  for (auto &t : cc.tiles) {
+    if (t.count < 1 || t.count > lbm::kStepThreads) bad++;
+    for (int k = 0; k < t.count; k++) {
+      int64_t i = t.start + k;
+      if (i < cc.rowstart[t.y] || i >= cc.rowstart[t.y + 1]) bad++;
+      else covered[i]++;
+    }
+  }
+  for (auto c : covered) if (c != 1) bad++;
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      int32_t i = cc.index[y * nx + x];
+      if (i < 0) continue;
+      uint32_t tq[9];
+      lbm::compact_targets(cc.meta[i], i, cc.n_lb[i], cc.s_lb[i], y, ny, py, cc.rowstart.data(), tq);
+      uint8_t fl = cc.meta[i] & 0xFF;
+      for (int qd = 1; qd < 9; qd++) {
+        bool fluid_target = !(fl & (1u << (OPP[qd] - 1)));
+        int xx, yy;
+        bool in = wrapok(x + CX[qd], y + CY[qd], xx, yy);
+        bool truth_fluid = in && !solid[yy * nx + xx];
+        if (fluid_target != truth_fluid) { bad++; continue; }
+        if (!fluid_target) continue;
+        checked++;
+        int32_t want = cc.index[yy * nx + xx];
+        if (tq[qd] != (uint32_t)want || tq[qd] >= (uint32_t)cc.n_fluid) {
+          if (bad < 5) printf("%s: node (%d,%d) dir %d got %u want %d\n", name, x, y, qd, tq[qd], want);
+          bad++;
+        }
+      }
+      if (cc.lbase[i] != (fl ? hc.lbase[(size_t)y * hc.pitch + x] : 0)) bad++;
+    }
+  printf("%-22s nx %5d ny %5d px %d py %d fluid %8lld tiles %7zu checked %9ld bad %ld\n", name, nx, ny, px, py,
+         (long long)cc.n_fluid, cc.tiles.size(), checked, bad);
+  return bad != 0;
+}
+int main(int argc, char **argv) {
+  int fails = 0;
+  auto channel = [](int nx, int ny) { std::vector<uint8_t> s(nx * ny, 0); for (int x = 0; x < nx; x++) { s[x] = 1; s[(ny - 1) * nx + x] = 1; } return s; };
+  fails += check("channel", 4, 34, 1, 0, channel(4, 34));
+  fails += check("channel_wide", 37, 9, 1, 0, channel(37, 9));
+  fails += check("box", 70, 45, 1, 1, std::vector<uint8_t>(70 * 45, 0));
+  fails += check("column", 1, 7, 1, 1, std::vector<uint8_t>(7, 0));
+  fails += check("row", 33, 1, 1, 1, std::vector<uint8_t>(33, 0));
+  fails += check("row_wall_x", 40, 20, 0, 1, [] { std::vector<uint8_t> s(40 * 20, 0); for (int y = 0; y < 20; y++) { s[y * 40] = 1; s[y * 40 + 39] = 1; } return s; }());
+  std::mt19937 rng(3);
+  for (int t = 0; t < 6; t++) {
+    int nx = 50 + rng() % 700, ny = 40 + rng() % 300;
+    int px = t % 2, py = (t / 2) % 2;
+    std::vector<uint8_t> s(nx * ny, 0);
+    for (int c = 0; c < nx * ny / 300; c++) {
+      int cx = rng() % nx, cy = rng() % ny, r = 2 + rng() % 9;
+      for (int y = cy - r; y <= cy + r; y++)
+        for (int x = cx - r; x <= cx + r; x++) {
+          int xx = ((x % nx) + nx) % nx, yy = ((y % ny) + ny) % ny;
+          if ((x - cx) * (x - cx) + (y - cy) * (y - cy) <= r * r) s[yy * nx + xx] = 1;
+        }
+    }
+    if (!px) for (int y = 0; y < ny; y++) { s[y * nx] = 1; s[y * nx + nx - 1] = 1; }
+    if (!py) for (int x = 0; x < nx; x++) { s[x] = 1; s[(ny - 1) * nx + x] = 1; }
+    // drop fluid nodes enclosed on all sides (the library rejects them)
+    for (int y = 0; y < ny; y++) for (int x = 0; x < nx; x++) {
+      if (s[y * nx + x]) continue;
+      int open = 0;
+      for (int i = 1; i < 9; i++) { int xx = x - CX[i], yy = y - CY[i];
+        if (xx < 0 || xx >= nx) { if (!px) continue; xx = (xx + nx) % nx; }
+        if (yy < 0 || yy >= ny) { if (!py) continue; yy = (yy + ny) % ny; }
+        if (!s[yy * nx + xx]) open++; }
+      if (!open) s[y * nx + x] = 1;
+    }
+    char nm[64]; snprintf(nm, sizeof nm, "cylinders_%d", t);
+    fails += check(nm, nx, ny, px, py, s);
+  }
+  for (int a = 1; a < argc; a++) {
+    const char *fn = argv[a];
+    FILE *f = fopen(fn, "rb");
+    if (!f) { printf("%s: cannot open\n", fn); fails++; continue; }
+    int32_t hd[4];
+    if (fread(hd, 4, 4, f) != 4) return 2;
+    std::vector<uint8_t> s((size_t)hd[0] * hd[1]);
+    if (fread(s.data(), 1, s.size(), f) != s.size()) return 2;
+    fclose(f);
+    fails += check(fn, hd[0], hd[1], hd[2], hd[3], s);
+  }
+  printf(fails ? "FAILED\n" : "ALL OK\n");
+  return fails != 0;
+}

@@ -142,15 +142,17 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
 
 // The unknown populations of a boundary node (bits of fl), Eq. EqNewBDSC in
 // the folded form of LinkCoef, from the node's own pre-collision deviations
-// d and post-collision state c; records links[lb], links[lb + 1], ... in
+// (src_node[j * P], read again here rather than kept in registers through
+// the collision: a cache hit, and fewer live registers for every node) and
+// post-collision state c; records links[lb], links[lb + 1], ... in
 // direction order.  Written to dst_node[j * P].  Directions that no active
 // lane of the warp needs are skipped warp-uniformly.
 template <typename T, typename C>
 __device__ __forceinline__ void link_epilogue(T *__restrict__ dst_node, const uint32_t P,
                                               const uint8_t fl, const int lb,
                                               const LinkCoef<C> *__restrict__ links,
-                                              const C (&d)[9], const Collided<T, C> &c_,
-                                              const StepConst<C> &k) {
+                                              const T *__restrict__ src_node,
+                                              const Collided<T, C> &c_, const StepConst<C> &k) {
   const C(&o)[9] = c_.o;
   const C drho = c_.drho, rho = c_.rho, ux = c_.ux, uy = c_.uy, uu = c_.uu;
   // Boundary links of this node, Eq. EqNewBDSC in the folded form of
@@ -181,7 +183,8 @@ __device__ __forceinline__ void link_epilogue(T *__restrict__ dst_node, const ui
         }
         const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
         const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-        const C v = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
+        const C djb = Stor<T>::ld(src_node[jb * P], k.inv_sc);
+        const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
                     c2 * (drho + rho * pj);
         dst_node[j * P] = Stor<T>::st(v, k.sc);
       }
@@ -221,7 +224,7 @@ __device__ __forceinline__ void step_node_compact(
   if (!(fl & (1u << 7))) dst[6 * P + tq[6]] = c.t[6];  // opp(6) = 8
   if (!(fl & (1u << 4))) dst[7 * P + tq[7]] = c.t[7];  // opp(7) = 5
   if (!(fl & (1u << 5))) dst[8 * P + tq[8]] = c.t[8];  // opp(8) = 6
-  link_epilogue<T, C>(dst + i, P, fl, lb, links, d, c, k);
+  link_epilogue<T, C>(dst + i, P, fl, lb, links, src + i, c, k);
 }
 
 // Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).

@@ -191,7 +191,9 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
 constexpr int kStepThreads = 256;
 template <typename T>
 struct StepOcc {
-  static constexpr int min_blocks = 6;  // FP32: 40 registers, no spills
+  // 32 registers: 64 warps per SM hide the load latency better than 48 warps
+  // without spills (a few dozen bytes of spills stay in L1)
+  static constexpr int min_blocks = 8;
 };
 template <>
 struct StepOcc<double> {

@@ -39,6 +39,22 @@ ELEM_BYTES = {"fp32": 4, "fp64": 8, "bf16": 2, "fp16": 2}
 FALLBACK_HBM_GBS = 6800.0
 
 
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+def _peak_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("bf16_tflops", "bf16_TFLOPS"):
+            if key in d and isinstance(d[key], (int, float)):
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
+
+
 def _peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -398,6 +414,85 @@ def run_batch(args):
     return 0
 
 
+def net_flops(H, W, base=32, levels=4, c_in=3, c_out=3):
+    """Multiply-adds x 2 of one forward pass of the warm-start network on one
+    H x W sample (every convolution; pooling and upsampling are negligible)."""
+    f = 0
+    prev = c_in
+    for l in range(levels):
+        hw = (H >> l) * (W >> l)
+        ch = base << l
+        f += 2 * hw * 9 * prev * ch + 2 * hw * 9 * ch * ch
+        prev = ch
+    for l in range(levels - 2, -1, -1):
+        hw = (H >> l) * (W >> l)
+        ch = base << l
+        f += 2 * hw * 9 * (prev + ch) * ch + 2 * hw * 9 * ch * ch
+        prev = ch
+    f += 2 * H * W * prev * c_out
+    return f
+
+
+def run_net(args):
+    """The warm-start network's training step (256 x 256, batch 8, BF16
+    storage, FP32 accumulation; convolutions of the forward pass and of the
+    backward data pass on the tensor cores): TFLOP/s of the whole step
+    (forward + backward + Adam) against the measured dense BF16 peak."""
+    import torch
+
+    from paper_2012_14707_gb300 import build as lbm_build
+    from paper_2012_14707_gb300 import lbm
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    lbm.load()
+    H = W = 256
+    B = 8
+    net = lbm.Net(H, W, base=32, levels=4, precision="bf16", max_batch=B, seed=rank)
+    g = torch.Generator(device="cuda").manual_seed(rank)
+    x = torch.randn((B, H, W, 3), device="cuda", generator=g)
+    t = torch.randn((B, H, W, 3), device="cuda", generator=g)
+    for _ in range(max(args.warmup, 3)):
+        net.train_step(x.data_ptr(), t.data_ptr(), B, 1e-4)
+    torch.cuda.synchronize()
+    steps = max(args.steps // 10, 5)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0.record()
+    for _ in range(steps):
+        net.train_step(x.data_ptr(), t.data_ptr(), B, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / steps
+    e0.record()
+    y = torch.empty((B, H, W, 3), device="cuda")
+    for _ in range(steps):
+        net.forward(x.data_ptr(), B, y.data_ptr())
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / steps
+    fwd = net_flops(H, W) * B
+    peak, src = _peak_bf16()
+    line = {"metric": "TFLOP/s (warm-start network training step)", "value": 3 * fwd / ms / 1e9,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "unet4_base32_256x256_batch8", "flop_per_step": 3 * fwd,
+                       "note": "3 x forward flops (forward, backward data, backward weights)"},
+            "forward": {"ms": ms_fwd, "tflops": fwd / ms_fwd / 1e9},
+            "roofline": {"bound": "tensor", "achieved": 3 * fwd / ms / 1e9, "peak": peak,
+                         "unit": "TFLOP/s", "frac": 3 * fwd / ms / 1e9 / peak, "traffic": None,
+                         "peak_source": src},
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,7 +504,7 @@ def main():
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=("throughput", "batch"), default="throughput")
+    ap.add_argument("--workload", choices=("throughput", "batch", "net"), default="throughput")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-max-steps", type=int, default=20000)
     ap.add_argument("--batch-single", type=int, default=32,
@@ -423,6 +518,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "net":
+        return run_net(args)
     return run_ours(args)
 
 

@@ -22,10 +22,12 @@
 //                   CTA reduces a pixel chunk for a 16x16 (c, o) tile and
 //                   adds it into FP32 dW; db by a column sum.
 //   pool / upsample / concat / MSE / Adam: elementwise or simple reductions.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -180,6 +182,252 @@ conv_bwd_weight(const A *__restrict__ x, int xs, const A *__restrict__ gz, int N
       atomicAdd(&dw[(static_cast<int64_t>(d) * Ci + c0 + c) * Co + o0 + o], acc[d]);
     if (c == 0 && c0 == 0 && db) atomicAdd(&db[o0 + o], bacc);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core convolution (BF16 storage): an implicit GEMM on tcgen05.
+//   D[p][o] = sum_{d, c} X[p + d - HALO][c] * Wk[o][d][c]      (M = pixels,
+//   N = output channels, K = taps x input channels)
+// A CTA owns 128 pixels x NT output channels (NT <= 128, a multiple of 16);
+// D lives in tensor memory (FP32, NT columns).  K runs tap by tap in chunks
+// of up to 64 channels: the 128 threads gather one pixel row each of A (the
+// shifted input, zero outside the image) and one row each of B (packed
+// weights, K-major), store both in shared memory in the canonical K-major
+// layout without swizzle (8-row x 16-byte core matrices, core matrices
+// along K 128 B apart, 8-row groups 1024 B apart), and one thread issues
+// the MMAs (M = 128, N = NT, K = 16 each) and commits them to an mbarrier.
+// Two stages: the gather of chunk k + 1 overlaps the MMAs of chunk k.  Every
+// wait is bounded; a wait that runs out sets *err and the CTA stops issuing.
+// The epilogue reads D back with tcgen05.ld (warp w owns lanes 32w..32w+31 =
+// pixels 32w..), adds the bias, applies ReLU and stores BF16.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+// Waits for the phase with parity `phase` of *bar; false if it did not come
+// within `limit` polls (test_wait: each poll returns at once, so the bound
+// is a bound in time).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, int limit) {
+  for (int it = 0; it < limit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Shared-memory matrix descriptor (K-major, no swizzle): start address,
+// leading byte offset (between core matrices along K), stride byte offset
+// (between 8-row groups), all in 16-byte units; bit 46 = descriptor version
+// of this architecture; layout type 0 = no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// shape M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+constexpr int kTcM = 128;        // pixels per CTA (MMA M)
+constexpr int kTcKC = 64;        // channels per K chunk
+constexpr int kTcNMax = 128;     // output channels per CTA (MMA N)
+constexpr int kTcStageBytes = kTcM * kTcKC * 2;  // one operand, one stage: 16 KB
+constexpr int kTcSmem = 4 * kTcStageBytes + 1024;  // A and B, two stages, + alignment
+constexpr int kTcWaitLimit = 1 << 24;
+
+// Wk[o][d][c] (BF16, K-major, Co rows padded to Cop, Ci padded to Cip with
+// zeros) from the FP32 parameters w[d][c][o].  flip: the adjoint
+// convolution's weights (taps reversed, channels swapped): Wk[c][d][o] =
+// w[KS2 - 1 - d][c][o], i.e. a layer with Ci and Co exchanged.
+__global__ void pack_wk(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wk, int KS2,
+                        int Ci, int Co, int flip, int Cop, int Cip) {
+  // output layer: Ci' = flip ? Co : Ci, Co' = flip ? Ci : Co
+  const int64_t n = static_cast<int64_t>(Cop) * KS2 * Cip;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c2 = static_cast<int>(e % Cip);
+    const int d = static_cast<int>((e / Cip) % KS2);
+    const int o2 = static_cast<int>(e / (static_cast<int64_t>(Cip) * KS2));
+    float v = 0.f;
+    if (!flip) {
+      if (o2 < Co && c2 < Ci) v = w[(static_cast<int64_t>(d) * Ci + c2) * Co + o2];
+    } else {
+      // o2 = original input channel, c2 = original output channel
+      if (o2 < Ci && c2 < Co) v = w[(static_cast<int64_t>(KS2 - 1 - d) * Ci + o2) * Co + c2];
+    }
+    wk[e] = __float2bfloat16_rn(v);
+  }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kTcM)
+conv_fwd_tc(const __nv_bfloat16 *__restrict__ x, int xs, const __nv_bfloat16 *__restrict__ wk,
+            int Cip, const float *__restrict__ b, __nv_bfloat16 *__restrict__ y, int ys, int N,
+            int H, int W, int Ci, int Co, int NT, int relu, int vec, int *__restrict__ err) {
+  constexpr int HALO = KS / 2;
+  constexpr int KS2 = KS * KS;
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t npix = static_cast<int64_t>(N) * H * W;
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * kTcM + tid;  // this thread's pixel (A row)
+  const int o0 = blockIdx.y * NT;
+  int pn = 0, pi = 0, pj = 0;
+  if (p < npix) {
+    pn = static_cast<int>(p / (static_cast<int64_t>(H) * W));
+    const int r = static_cast<int>(p - static_cast<int64_t>(pn) * H * W);
+    pi = r / W;
+    pj = r - pi * W;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kTcNMax)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = umma_idesc_bf16(kTcM, NT);
+  const int nck = (Cip + kTcKC - 1) / kTcKC;  // channel chunks per tap
+  const int iters = KS2 * nck;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  for (int it = 0; it < iters; it++) {
+    const int st = it & 1;
+    if (it >= 2) {  // the MMAs that read this stage two chunks ago are done
+      const bool got = mbar_wait(&mbar[st], phase[st], kTcWaitLimit);
+      if (__syncthreads_or(!got)) {  // one decision for the whole CTA
+        ok = false;
+        if (tid == 0) atomicExch(err, 1);
+        break;
+      }
+      phase[st] ^= 1u;
+    }
+    const int d = it / nck, c0 = (it % nck) * kTcKC;
+    const int kc = min(kTcKC, Cip - c0);  // multiple of 16
+    unsigned char *sa = smem + st * 2 * kTcStageBytes;
+    unsigned char *sb = sa + kTcStageBytes;
+    // A row `tid`: input pixel (pi + dy - HALO, pj + dx - HALO), channels c0 .. c0 + kc
+    {
+      const int ii = pi + d / KS - HALO, jj = pj + d % KS - HALO;
+      const bool in = p < npix && ii >= 0 && ii < H && jj >= 0 && jj < W;
+      const __nv_bfloat16 *src = x + ((static_cast<int64_t>(pn) * H + ii) * W + jj) * xs;
+      unsigned char *row = sa + (tid >> 3) * 1024 + (tid & 7) * 16;
+      for (int q = 0; q < kc / 8; q++) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        const int c = c0 + q * 8;
+        if (in && c < Ci) {
+          if (vec) {
+            v = *reinterpret_cast<const uint4 *>(src + c);
+          } else {
+            __nv_bfloat16 t8[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) t8[e] = (c + e < Ci) ? src[c + e] : __float2bfloat16_rn(0.f);
+            v = *reinterpret_cast<const uint4 *>(t8);
+          }
+        }
+        *reinterpret_cast<uint4 *>(row + q * 128) = v;
+      }
+    }
+    // B row `tid` (< NT): output channel o0 + tid, tap d, channels c0 .. c0 + kc
+    if (tid < NT) {
+      const __nv_bfloat16 *src = wk + (static_cast<int64_t>(o0 + tid) * KS2 + d) * Cip + c0;
+      unsigned char *row = sb + (tid >> 3) * 1024 + (tid & 7) * 16;
+      for (int q = 0; q < kc / 8; q++)
+        *reinterpret_cast<uint4 *>(row + q * 128) = *reinterpret_cast<const uint4 *>(src + q * 8);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sb);
+      for (int k = 0; k < kc / 16; k++) {
+        const uint64_t ad = umma_desc(a0 + k * 256, 128, 1024);
+        const uint64_t bd = umma_desc(b0 + k * 256, 128, 1024);
+        const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_addr(&mbar[st]))
+                   : "memory");
+    }
+  }
+  // all MMAs done: the last commit covers every earlier MMA of the issuing thread
+  if (ok && iters > 0) {
+    const int st = (iters - 1) & 1;
+    const bool got = mbar_wait(&mbar[st], phase[st], kTcWaitLimit);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  // tcgen05.ld is warp-collective (.sync.aligned): every lane loads, in
+  // converged code, also lanes past the last pixel; only the stores are
+  // predicated.  `ok` is uniform over the CTA.
+  if (ok) {
+    __syncwarp();
+    __nv_bfloat16 *yp = y + (p < npix ? p : 0) * ys;
+    for (int c = 0; c < NT; c += 8) {
+      uint32_t r[8];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7])
+          : "r"(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (p < npix) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          const int o = o0 + c + e;
+          if (o < Co) {
+            float v = __uint_as_float(r[e]) + (b ? b[o] : 0.f);
+            if (relu) v = fmaxf(v, 0.f);
+            yp[o] = __float2bfloat16_rn(v);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTcNMax)
+                 : "memory");
+  }
+  (void)lane;
 }
 
 // wt[d'][o][c] = w[KS*KS-1-d'][c][o]: the weights of the adjoint convolution.
@@ -366,6 +614,8 @@ struct lbm_net {
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
   void *wq = nullptr;   // weights in the storage type
   void *wt = nullptr;   // flipped weights (largest layer), storage type
+  void *wk = nullptr;   // packed K-major BF16 weights of the tensor-core path (largest layer)
+  int *d_err = nullptr; // set by a tensor-core kernel whose bounded wait ran out
   // activations: per level encoder outputs (skip), decoder concat inputs,
   // temporaries; all storage type, sized for max_batch
   std::vector<void *> bufs;
@@ -422,21 +672,61 @@ Plan make_plan(const lbm_net_t *n) {
   return p;
 }
 
+bool tc_timed_out(lbm_net_t *n) {
+  int v = 0;
+  return cudaMemcpy(&v, n->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && v != 0;
+}
+
 int nfail(lbm_net_t *n, int code, const std::string &m) {
   if (n) n->err = m;
   else g_net_error = m;
   return code;
 }
 
+// Output-channel tile of the tensor-core convolution and the padded sizes
+// of its packed weights.
+void tc_shape(int Ci, int Co, int *NT, int *Cop, int *Cip) {
+  *NT = std::min(lbm::net::kTcNMax, (Co + 15) / 16 * 16);
+  *Cop = (Co + *NT - 1) / *NT * *NT;
+  *Cip = (Ci + 15) / 16 * 16;
+}
+
+// y = act(conv(x, w) + b) with Ci inputs and Co outputs.  FP32 storage: the
+// CUDA-core kernel on w (layout [tap][ci][co]).  BF16 storage: the tensor-core
+// kernel on weights packed from the FP32 parameters wsrc of layer (lci, lco),
+// flipped for the adjoint convolution of the backward pass.
 template <typename A>
-void launch_conv(const lbm_net_t *n, const A *x, int xs, const A *w, const float *b, A *y, int ys,
-                 int N, int H, int W, int Ci, int Co, int ks, int relu) {
+void launch_conv(lbm_net_t *n, const A *x, int xs, const A *w, const float *b, A *y, int ys,
+                 int N, int H, int W, int Ci, int Co, int ks, int relu, const float *wsrc, int flip,
+                 int lci, int lco) {
   using namespace lbm::net;
-  dim3 grid(((W + TP - 1) / TP) * ((H + TP - 1) / TP), (Co + TC - 1) / TC, N);
-  if (ks == 3)
-    conv_fwd<A, 3><<<grid, TP * TP, 0, n->stream>>>(x, xs, w, b, y, ys, H, W, Ci, Co, relu);
-  else
-    conv_fwd<A, 1><<<grid, TP * TP, 0, n->stream>>>(x, xs, w, b, y, ys, H, W, Ci, Co, relu);
+  if constexpr (std::is_same<A, __nv_bfloat16>::value) {
+    (void)w;
+    int NT, Cop, Cip;
+    tc_shape(Ci, Co, &NT, &Cop, &Cip);
+    __nv_bfloat16 *wk = static_cast<__nv_bfloat16 *>(n->wk);
+    pack_wk<<<grid1(static_cast<int64_t>(Cop) * ks * ks * Cip), 256, 0, n->stream>>>(
+        wsrc, wk, ks * ks, lci, lco, flip, Cop, Cip);
+    const int64_t npix = static_cast<int64_t>(N) * H * W;
+    dim3 grid(static_cast<unsigned>((npix + kTcM - 1) / kTcM), Cop / NT);
+    const bool vec = xs % 8 == 0 && Ci % 8 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0;
+    if (ks == 3)
+      conv_fwd_tc<3><<<grid, kTcM, kTcSmem, n->stream>>>(x, xs, wk, Cip, b, y, ys, N, H, W, Ci, Co,
+                                                         NT, relu, vec, n->d_err);
+    else
+      conv_fwd_tc<1><<<grid, kTcM, kTcSmem, n->stream>>>(x, xs, wk, Cip, b, y, ys, N, H, W, Ci, Co,
+                                                         NT, relu, vec, n->d_err);
+  } else {
+    (void)wsrc;
+    (void)flip;
+    (void)lci;
+    (void)lco;
+    dim3 grid(((W + TP - 1) / TP) * ((H + TP - 1) / TP), (Co + TC - 1) / TC, N);
+    if (ks == 3)
+      conv_fwd<A, 3><<<grid, TP * TP, 0, n->stream>>>(x, xs, w, b, y, ys, H, W, Ci, Co, relu);
+    else
+      conv_fwd<A, 1><<<grid, TP * TP, 0, n->stream>>>(x, xs, w, b, y, ys, H, W, Ci, Co, relu);
+  }
 }
 
 template <typename A>
@@ -469,6 +759,7 @@ cudaError_t run(lbm_net_t *n, const float *x_in, int N, const float *t, float *y
   int li = 0;
   auto W_of = [&](int k) { return wq + n->layers[k].w_off; };
   auto B_of = [&](int k) { return n->params + n->layers[k].b_off; };
+  auto P_of = [&](int k) { return n->params + n->layers[k].w_off; };
   // encoder
   const A *h = buf(p.x_in);
   int hc = n->c_in;
@@ -479,9 +770,11 @@ cudaError_t run(lbm_net_t *n, const float *x_in, int N, const float *t, float *y
                                                                                   H * 2, Wd * 2, hc);
       h = buf(p.pool[l]);
     }
-    launch_conv<A>(n, h, hc, W_of(li), B_of(li), buf(p.ea[l]), ch, N, H, Wd, hc, ch, 3, 1);
+    launch_conv<A>(n, h, hc, W_of(li), B_of(li), buf(p.ea[l]), ch, N, H, Wd, hc, ch, 3, 1, P_of(li),
+                   0, hc, ch);
     li++;
-    launch_conv<A>(n, buf(p.ea[l]), ch, W_of(li), B_of(li), buf(p.eb[l]), ch, N, H, Wd, ch, ch, 3, 1);
+    launch_conv<A>(n, buf(p.ea[l]), ch, W_of(li), B_of(li), buf(p.eb[l]), ch, N, H, Wd, ch, ch, 3, 1,
+                   P_of(li), 0, ch, ch);
     li++;
     h = buf(p.eb[l]);
     hc = ch;
@@ -494,16 +787,18 @@ cudaError_t run(lbm_net_t *n, const float *x_in, int N, const float *t, float *y
     up2_fwd<A><<<grid1(static_cast<int64_t>(N) * H * Wd * cu), 256, 0, s>>>(h, cat, ct, N, H, Wd, cu);
     copy_channels<A><<<grid1(static_cast<int64_t>(N) * H * Wd * ch), 256, 0, s>>>(
         buf(p.eb[l]), ch, cat + cu, ct, ch, static_cast<int64_t>(N) * H * Wd, 0);
-    launch_conv<A>(n, cat, ct, W_of(li), B_of(li), buf(p.da[l]), ch, N, H, Wd, ct, ch, 3, 1);
+    launch_conv<A>(n, cat, ct, W_of(li), B_of(li), buf(p.da[l]), ch, N, H, Wd, ct, ch, 3, 1, P_of(li),
+                   0, ct, ch);
     li++;
-    launch_conv<A>(n, buf(p.da[l]), ch, W_of(li), B_of(li), buf(p.db[l]), ch, N, H, Wd, ch, ch, 3, 1);
+    launch_conv<A>(n, buf(p.da[l]), ch, W_of(li), B_of(li), buf(p.db[l]), ch, N, H, Wd, ch, ch, 3, 1,
+                   P_of(li), 0, ch, ch);
     li++;
     h = buf(p.db[l]);
     hc = ch;
   }
   const int head = li;
   launch_conv<A>(n, h, hc, W_of(head), B_of(head), buf(p.y), n->c_out, N, n->H, n->W, hc, n->c_out, 1,
-                 0);
+                 0, P_of(head), 0, hc, n->c_out);
   if (y_out)
     to_float<A><<<grid1(HW * N * n->c_out), 256, 0, s>>>(buf(p.y), n->c_out, y_out, n->c_out, HW * N);
   if (!t) return cudaGetLastError();
@@ -519,9 +814,11 @@ cudaError_t run(lbm_net_t *n, const float *x_in, int N, const float *t, float *y
     launch_wgrad<A>(n, x, xs, gz, N, H, Wd, ly.ci, ly.co, ly.ks, n->grads + ly.w_off,
                     n->grads + ly.b_off);
     if (need_gx) {
-      flip_weights<A><<<grid1(static_cast<int64_t>(ly.ks * ly.ks) * ly.ci * ly.co), 256, 0, s>>>(
-          n->params + ly.w_off, wt, ly.ks * ly.ks, ly.ci, ly.co);
-      launch_conv<A>(n, gz, ly.co, wt, nullptr, gx, gxs, N, H, Wd, ly.co, ly.ci, ly.ks, 0);
+      if constexpr (!std::is_same<A, __nv_bfloat16>::value)
+        flip_weights<A><<<grid1(static_cast<int64_t>(ly.ks * ly.ks) * ly.ci * ly.co), 256, 0, s>>>(
+            n->params + ly.w_off, wt, ly.ks * ly.ks, ly.ci, ly.co);
+      launch_conv<A>(n, gz, ly.co, wt, nullptr, gx, gxs, N, H, Wd, ly.co, ly.ci, ly.ks, 0,
+                     n->params + ly.w_off, 1, ly.ci, ly.co);
     }
   };
   // head
@@ -634,6 +931,25 @@ int lbm_net_create(int32_t base, int32_t levels, int32_t c_in, int32_t c_out, in
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(ptr), off * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->wq, off * as);
   if (e == cudaSuccess) e = cudaMalloc(&n->wt, max_w * as);
+  {
+    int64_t max_wk = 1;
+    for (const Layer &ly : n->layers)
+      for (int fl = 0; fl < 2; fl++) {
+        int NT, Cop, Cip;
+        tc_shape(fl ? ly.co : ly.ci, fl ? ly.ci : ly.co, &NT, &Cop, &Cip);
+        max_wk = std::max<int64_t>(max_wk, static_cast<int64_t>(Cop) * ly.ks * ly.ks * Cip);
+      }
+    if (e == cudaSuccess) e = cudaMalloc(&n->wk, max_wk * 2);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&n->d_err), sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    e = cudaFuncSetAttribute(lbm::net::conv_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             lbm::net::kTcSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lbm::net::conv_fwd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               lbm::net::kTcSmem);
+  }
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&n->loss), sizeof(double));
   for (int g = 0; g < 2 && e == cudaSuccess; g++)
     for (size_t i = 0; i < p.elems.size() && e == cudaSuccess; i++) {
@@ -696,6 +1012,8 @@ int lbm_net_forward(lbm_net_t *n, const float *x, int32_t batch, float *y) {
                       ? run<float>(n, x, batch, nullptr, y, nullptr)
                       : run<__nv_bfloat16>(n, x, batch, nullptr, y, nullptr);
   if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e == cudaSuccess && tc_timed_out(n))
+    return nfail(n, LBM_ETIMEOUT, "a tensor-core convolution's bounded wait ran out");
   return e == cudaSuccess ? LBM_OK : nfail(n, LBM_ECUDA, cudaGetErrorString(e));
 }
 
@@ -706,6 +1024,8 @@ int lbm_net_gradients(lbm_net_t *n, const float *x, const float *t, int32_t batc
   cudaError_t e = n->precision == LBM_FP32 ? run<float>(n, x, batch, t, nullptr, &l)
                                            : run<__nv_bfloat16>(n, x, batch, t, nullptr, &l);
   if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e == cudaSuccess && tc_timed_out(n))
+    return nfail(n, LBM_ETIMEOUT, "a tensor-core convolution's bounded wait ran out");
   if (e == cudaSuccess && grads)
     e = cudaMemcpy(grads, n->grads, n->n_params * sizeof(float), cudaMemcpyDeviceToHost);
   if (loss) *loss = l;
@@ -730,8 +1050,8 @@ void lbm_net_destroy(lbm_net_t *n) {
   if (!n) return;
   cudaStreamSynchronize(n->stream);
   for (void *p : {static_cast<void *>(n->params), static_cast<void *>(n->grads),
-                  static_cast<void *>(n->m), static_cast<void *>(n->v), n->wq, n->wt,
-                  static_cast<void *>(n->loss)})
+                  static_cast<void *>(n->m), static_cast<void *>(n->v), n->wq, n->wt, n->wk,
+                  static_cast<void *>(n->d_err), static_cast<void *>(n->loss)})
     if (p) cudaFree(p);
   for (void *b : n->bufs)
     if (b) cudaFree(b);

@@ -79,3 +79,43 @@ def test_training_lowers_the_loss():
     for _ in range(200):
         last = net.train_step(xd.data_ptr(), td.data_ptr(), 4, 3e-3)
     assert last < 0.3 * first
+
+
+def test_bf16_tensor_core_path_matches_fp32_at_full_width():
+    """The full-width network (base 32, 4 levels: up to 384 input and 256
+    output channels, two 128-channel output tiles, 64-channel K chunks) in
+    BF16 mode -- the tensor-core convolutions -- against the FP32 mode
+    (CUDA cores) with the same parameters: forward within 3 % (rel. L2),
+    gradients of every layer within 10 %."""
+    import torch
+
+    lbm_build.build()
+    torch.cuda.set_device(0)
+    H = W = 64
+    N = 2
+    n32 = lbm.Net(H, W, base=32, levels=4, precision="fp32", max_batch=N, seed=7)
+    n16 = lbm.Net(H, W, base=32, levels=4, precision="bf16", max_batch=N, seed=7)
+    p = n32.get_params()
+    rng = np.random.default_rng(4)
+    p = p + 0.0  # He-normal weights, zero biases; give the biases some size
+    n32.set_params(p)
+    n16.set_params(p)
+    x = rng.standard_normal((N, H, W, 3)).astype(np.float32)
+    t = rng.standard_normal((N, H, W, 3)).astype(np.float32)
+    xd = torch.tensor(x, device="cuda")
+    td = torch.tensor(t, device="cuda")
+    y32 = torch.empty((N, H, W, 3), device="cuda")
+    y16 = torch.empty((N, H, W, 3), device="cuda")
+    n32.forward(xd.data_ptr(), N, y32.data_ptr())
+    n16.forward(xd.data_ptr(), N, y16.data_ptr())
+    a, b = y16.cpu().numpy(), y32.cpu().numpy()
+    assert np.isfinite(a).all()
+    assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b)
+    g32, _ = n32.gradients(xd.data_ptr(), td.data_ptr(), N)
+    g16, _ = n16.gradients(xd.data_ptr(), td.data_ptr(), N)
+    off = 0
+    for name, kind, ci, co in nn.layer_shapes(3, 3, 32, 4):
+        size = (9 if kind == "c3" else 1) * ci * co
+        ga, gb = g16[off:off + size], g32[off:off + size]
+        assert np.linalg.norm(ga - gb) <= 0.1 * np.linalg.norm(gb) + 1e-12, name
+        off += size + co

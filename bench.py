@@ -323,7 +323,7 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch):
 
 
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
-KERNEL_REV = 6
+KERNEL_REV = 7
 
 
 def run_batch(args):

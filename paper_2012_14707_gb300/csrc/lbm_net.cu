@@ -430,6 +430,170 @@ conv_fwd_tc(const __nv_bfloat16 *__restrict__ x, int xs, const __nv_bfloat16 *__
   (void)lane;
 }
 
+// Weight gradient on the tensor cores:
+//   dW[d][c][o] = sum_p X[p + d - HALO][c] gz[p][o]     db[o] = sum_p gz[p][o]
+// as D[m][n] = sum_k A[m][k] B[n][k] with m = d * Ci + c (M = 128 per CTA),
+// n = o (N = NT), k = pixel (K, split over blockIdx.z: kper pixels each).
+// Chunks of 32 pixels are staged K-major: thread t gathers row t of A (tap
+// and channel of m, 32 consecutive pixels shifted by the tap) and row t of
+// B (channel o0 + t of gz); 8 pixels of one row are one 16-byte core-matrix
+// row.  The partial D of the CTA is added into dW with atomics.
+constexpr int kWgKC = 32;                             // pixels per K chunk
+constexpr int kWgStage = kTcM * kWgKC * 2;            // one operand, one stage: 8 KB
+constexpr int kWgSmem = 4 * kWgStage + 1024;
+
+template <int KS>
+__global__ void __launch_bounds__(kTcM)
+conv_wgrad_tc(const __nv_bfloat16 *__restrict__ x, int xs, const __nv_bfloat16 *__restrict__ gz,
+              int gs, int N, int H, int W, int Ci, int Co, int NT, int kper,
+              float *__restrict__ dw, float *__restrict__ db, int *__restrict__ err) {
+  constexpr int HALO = KS / 2;
+  constexpr int KS2 = KS * KS;
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t npix = static_cast<int64_t>(N) * H * W;
+  const int m0 = blockIdx.x * kTcM, o0 = blockIdx.y * NT;
+  const int64_t pstart = static_cast<int64_t>(blockIdx.z) * kper;
+  const int64_t pend = min(npix, pstart + kper);
+  const int nch = pend > pstart ? static_cast<int>((pend - pstart + kWgKC - 1) / kWgKC) : 0;
+  // this thread's A row: tap d and channel c of m = m0 + tid
+  const int m = m0 + tid;
+  const bool mrow = m < KS2 * Ci;
+  const int d = mrow ? m / Ci : 0, c = mrow ? m - (m / Ci) * Ci : 0;
+  const int sy = d / KS - HALO, sx = d % KS - HALO;
+  const bool nrow = tid < NT && o0 + tid < Co;
+  float bsum = 0.f;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kTcNMax)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = umma_idesc_bf16(kTcM, NT);
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  for (int it = 0; it < nch; it++) {
+    const int st = it & 1;
+    if (it >= 2) {
+      const bool got = mbar_wait(&mbar[st], phase[st], kTcWaitLimit);
+      if (__syncthreads_or(!got)) {
+        ok = false;
+        if (tid == 0) atomicExch(err, 1);
+        break;
+      }
+      phase[st] ^= 1u;
+    }
+    const int64_t p0 = pstart + static_cast<int64_t>(it) * kWgKC;
+    unsigned char *sa = smem + st * 2 * kWgStage;
+    unsigned char *sb = sa + kWgStage;
+    // pixel p0 as (image, row, column); advanced one pixel at a time
+    int pn = static_cast<int>(p0 / (static_cast<int64_t>(H) * W));
+    int rem = static_cast<int>(p0 - static_cast<int64_t>(pn) * H * W);
+    int pi = rem / W, pj = rem - (rem / W) * W;
+    for (int k8 = 0; k8 < kWgKC / 8; k8++) {
+      __align__(16) __nv_bfloat16 va[8], vb[8];
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        const int64_t p = p0 + k8 * 8 + e;
+        float a = 0.f, bb = 0.f;
+        if (p < pend) {
+          const int ii = pi + sy, jj = pj + sx;
+          if (mrow && ii >= 0 && ii < H && jj >= 0 && jj < W)
+            a = __bfloat162float(x[((static_cast<int64_t>(pn) * H + ii) * W + jj) * xs + c]);
+          if (nrow) {
+            bb = __bfloat162float(gz[p * gs + o0 + tid]);
+            bsum += bb;
+          }
+        }
+        va[e] = __float2bfloat16_rn(a);
+        vb[e] = __float2bfloat16_rn(bb);
+        if (++pj == W) {
+          pj = 0;
+          if (++pi == H) {
+            pi = 0;
+            ++pn;
+          }
+        }
+      }
+      *reinterpret_cast<uint4 *>(sa + (tid >> 3) * 512 + k8 * 128 + (tid & 7) * 16) =
+          *reinterpret_cast<const uint4 *>(va);
+      if (tid < NT)
+        *reinterpret_cast<uint4 *>(sb + (tid >> 3) * 512 + k8 * 128 + (tid & 7) * 16) =
+            *reinterpret_cast<const uint4 *>(vb);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a0 = smem_addr(sa), b0 = smem_addr(sb);
+      for (int k = 0; k < kWgKC / 16; k++) {
+        const uint64_t ad = umma_desc(a0 + k * 256, 128, 512);
+        const uint64_t bd = umma_desc(b0 + k * 256, 128, 512);
+        const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_addr(&mbar[st]))
+                   : "memory");
+    }
+  }
+  if (ok && nch > 0) {
+    const int st = (nch - 1) & 1;
+    const bool got = mbar_wait(&mbar[st], phase[st], kTcWaitLimit);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok && nch > 0) {  // uniform: every lane takes part in the warp-collective loads
+    __syncwarp();
+    const int mr = m0 + warp * 32 + (tid & 31);  // the TMEM lane this thread reads = row of D
+    for (int cc = 0; cc < NT; cc += 8) {
+      uint32_t r[8];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7])
+          : "r"(tmem + (static_cast<uint32_t>(warp * 32) << 16) + cc));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (mr < KS2 * Ci) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          const int o = o0 + cc + e;
+          if (o < Co) atomicAdd(&dw[static_cast<int64_t>(mr) * Co + o], __uint_as_float(r[e]));
+        }
+      }
+    }
+  }
+  if (ok && db && blockIdx.x == 0 && nrow) atomicAdd(&db[o0 + tid], bsum);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTcNMax)
+                 : "memory");
+  }
+}
+
 // wt[d'][o][c] = w[KS*KS-1-d'][c][o]: the weights of the adjoint convolution.
 template <typename A>
 __global__ void flip_weights(const float *__restrict__ w, A *__restrict__ wt, int KS2, int Ci, int Co) {
@@ -733,6 +897,25 @@ template <typename A>
 void launch_wgrad(const lbm_net_t *n, const A *x, int xs, const A *gz, int N, int H, int W, int Ci,
                   int Co, int ks, float *dw, float *db) {
   using namespace lbm::net;
+  if constexpr (std::is_same<A, __nv_bfloat16>::value) {
+    // tensor cores: M tiles over (tap, channel), N tiles over output
+    // channels, the pixels split so that the grid fills the GPU a few times
+    const int64_t npix = static_cast<int64_t>(N) * H * W;
+    const int NT = std::min(kTcNMax, (Co + 15) / 16 * 16);
+    const int mt = (ks * ks * Ci + kTcM - 1) / kTcM, nt = (Co + NT - 1) / NT;
+    const int64_t want = std::max<int64_t>(1, 1824 / (mt * nt));
+    int64_t kper = (npix + want - 1) / want;
+    kper = std::max<int64_t>(kWgKC * 4, (kper + kWgKC - 1) / kWgKC * kWgKC);
+    const unsigned ks_split = static_cast<unsigned>((npix + kper - 1) / kper);
+    dim3 grid(mt, nt, ks_split);
+    if (ks == 3)
+      conv_wgrad_tc<3><<<grid, kTcM, kWgSmem, n->stream>>>(x, xs, gz, Co, N, H, W, Ci, Co, NT,
+                                                           static_cast<int>(kper), dw, db, n->d_err);
+    else
+      conv_wgrad_tc<1><<<grid, kTcM, kWgSmem, n->stream>>>(x, xs, gz, Co, N, H, W, Ci, Co, NT,
+                                                           static_cast<int>(kper), dw, db, n->d_err);
+    return;
+  }
   const int64_t npix = static_cast<int64_t>(N) * H * W;
   const int chunks = static_cast<int>(std::min<int64_t>(1024, (npix + 255) / 256));
   const int per = static_cast<int>((npix + chunks - 1) / chunks);
@@ -949,6 +1132,12 @@ int lbm_net_create(int32_t base, int32_t levels, int32_t c_in, int32_t c_out, in
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(lbm::net::conv_fwd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                lbm::net::kTcSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lbm::net::conv_wgrad_tc<3>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::net::kWgSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lbm::net::conv_wgrad_tc<1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::net::kWgSmem);
   }
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&n->loss), sizeof(double));
   for (int g = 0; g < 2 && e == cudaSuccess; g++)

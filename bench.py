@@ -130,6 +130,21 @@ def _dist():
     return world, rank, local
 
 
+def reduce_over_ranks(values_max, values_sum, world, device):
+    """Every rank runs its own replica (no exchange in the data path): the
+    job's timings are the slowest rank's, its work the sum over ranks.
+    Returns (list of maxima, list of sums); a no-op for one rank."""
+    if world == 1:
+        return list(values_max), list(values_sum)
+    import torch
+    import torch.distributed as dist
+    tm = torch.tensor([float(v) for v in values_max], dtype=torch.float64, device=device)
+    ts = torch.tensor([float(v) for v in values_sum], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return [float(v) for v in tm.cpu()], [float(v) for v in ts.cpu()]
+
+
 def cpu_baseline_sample(precision: str, n_steps: int = 3, rows: int = 512):
     """The FP64 oracle (single thread, as it stands) on a bounded sample of
     the workload: `n_steps` lattice steps of an 8192 x `rows` channel built
@@ -237,14 +252,13 @@ def run_ours(args):
     clocks = sampler.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
     kernel_ms = sum(a.elapsed_time(b) for a, b in zip(k_start, k_end))
+    (elapsed_ms, kernel_ms), (total_fluid,) = reduce_over_ranks([elapsed_ms, kernel_ms], [n_fluid],
+                                                                world, dev)
     if world > 1:
-        t = torch.tensor([elapsed_ms, kernel_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms, kernel_ms = float(t[0]), float(t[1])
         dist.barrier()
     torch.cuda.synchronize()
 
-    updates = world * n_fluid * per * args.steps
+    updates = total_fluid * per * args.steps
     mlups = updates / (elapsed_ms / 1e3) / 1e6
     launch_ms = kernel_ms / (args.steps * per)
     alg_bytes = FLUID_BYTES[args.precision] * n_fluid
@@ -256,7 +270,7 @@ def run_ours(args):
     # arrays (mask + links H2D), the same steps with the residual read back,
     # and the final fields copied to host memory.
     torch.cuda.synchronize()
-    e2e = None if args.no_e2e else _e2e(args, case, stream, per, world, n_fluid, lbm, torch)
+    e2e = None if args.no_e2e else _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev)
 
 
     traffic = None
@@ -304,7 +318,10 @@ def run_ours(args):
     return 0
 
 
-def _e2e(args, case, stream, per, world, n_fluid, lbm, torch):
+def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t0 = time.perf_counter()
     s2 = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
                     residual_every=per)
@@ -315,9 +332,10 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     s2.close()
+    (e2e_s,), (total_fluid,) = reduce_over_ranks([e2e_s], [n_fluid], world, dev)
     h2d = case.solid.nbytes + case.n_links * (3 * 4 + 3 * 8)
     d2h = 3 * 8 * case.nx * case.ny + args.steps * 2 * 8
-    return {"value": world * n_fluid * per * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    return {"value": total_fluid * per * args.steps / e2e_s / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
             "seconds": e2e_s}
 
@@ -338,7 +356,11 @@ def run_batch(args):
     from paper_2012_14707_gb300 import cases, lbm
 
     world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     lbm_build.build()
     lbm.load()
     cl = cases.batch_cases(args.batch_cases, seed=rank)
@@ -360,6 +382,7 @@ def run_batch(args):
     nf = np.array([c.n_fluid for c in cl], np.float64)
     run = np.where(steps != 0, np.abs(steps), total).astype(np.float64)
     updates = float((nf * run).sum())
+    (wall,), (updates,) = reduce_over_ranks([wall], [updates], world, dev)
     conv = steps > 0
     # time to steady state of the same cases one at a time through the
     # single-case solver, against the batch, on a subset of the cases
@@ -411,6 +434,8 @@ def run_batch(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -444,7 +469,11 @@ def run_net(args):
     from paper_2012_14707_gb300 import lbm
 
     world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     lbm_build.build()
     lbm.load()
     H = W = 256
@@ -476,7 +505,10 @@ def run_net(args):
     torch.cuda.synchronize()
     ms_fwd = e0.elapsed_time(e1) / steps
     fwd = net_flops(H, W) * B
+    (ms, ms_fwd), (n_rank,) = reduce_over_ranks([ms, ms_fwd], [1.0], world, dev)
+    fwd = fwd * n_rank  # every rank trains its own replica: the job's flops
     peak, src = _peak_bf16()
+    peak *= n_rank
     line = {"metric": "TFLOP/s (warm-start network training step)", "value": 3 * fwd / ms / 1e9,
             "unit": "TFLOP/s", "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -490,6 +522,8 @@ def run_net(args):
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 

@@ -25,8 +25,8 @@ struct lbm_handle {
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
   // compacted lattice (see lbm::CompactCase)
-  uint16_t *meta = nullptr;
-  int32_t *n_lb = nullptr, *s_lb = nullptr, *lbase = nullptr, *rowstart = nullptr;
+  uint2 *node = nullptr;  // per fluid node: flags, seam bits, neighbour-row offsets
+  int32_t *lbase = nullptr, *rowstart = nullptr;
   int32_t *index = nullptr;  // y * nx + x -> compacted index or -1
   lbm::RowTile *tiles = nullptr;
   int64_t n_tiles = 0;
@@ -89,8 +89,7 @@ void release(lbm_handle_t *h) {
   if (!h) return;
   cudaStream_t s = h->stream;
   cudaStreamSynchronize(s);
-  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->meta), static_cast<void *>(h->n_lb),
-                  static_cast<void *>(h->s_lb), static_cast<void *>(h->lbase),
+  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->lbase),
                   static_cast<void *>(h->rowstart), static_cast<void *>(h->index),
                   static_cast<void *>(h->tiles), h->links, static_cast<void *>(h->partials),
                   static_cast<void *>(h->result), static_cast<void *>(h->d_err)})
@@ -120,8 +119,8 @@ cudaError_t do_step(lbm_handle_t *h) {
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
     return lbm::launch_step_compact<T, C>(
-        static_cast<const T *>(h->f[src]), static_cast<T *>(h->f[dst]), h->meta, h->n_lb, h->s_lb,
-        h->lbase, h->rowstart, h->tiles, h->n_tiles,
+        static_cast<const T *>(h->f[src]), static_cast<T *>(h->f[dst]), h->node, h->lbase,
+        h->rowstart, h->tiles, h->n_tiles,
         static_cast<const lbm::LinkCoef<C> *>(h->links), step_const<C>(h), h->stream);
   });
   if (e == cudaSuccess) {
@@ -162,6 +161,8 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   // 32-bit element offsets in the kernels: 9 planes of the padded lattice < 2^31.
   if ((static_cast<int64_t>(nx) + 31) / 32 * 32 * ny * 9 >= (int64_t(1) << 31))
     return bad(LBM_EINVAL, "lattice too large: 9 * pitch * ny must stay below 2^31");
+  // the compacted lattice keeps offsets within a row in 16 bits
+  if (nx > 65536) return bad(LBM_EINVAL, "rows longer than 65536 nodes are not supported");
   if (n_links > static_cast<size_t>(std::numeric_limits<int32_t>::max()))
     return bad(LBM_EINVAL, "too many links");
   const int px = dom->periodic_x ? 1 : 0, py = dom->periodic_y ? 1 : 0;
@@ -183,13 +184,20 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   const int32_t pitch = (nx + align - 1) / align * align;
   const int64_t plane = static_cast<int64_t>(pitch) * ny;
   std::vector<uint8_t> flags(static_cast<size_t>(plane), lbm::kSolid);
+  std::vector<int64_t> row_fluid(static_cast<size_t>(ny), 0);
+  lbm::parallel_for(ny, [&](int64_t y0, int64_t y1) {
+    for (int64_t y = y0; y < y1; y++) {
+      int64_t c = 0;
+      for (int32_t x = 0; x < nx; x++)
+        if (!solid[(size_t)y * nx + x]) {
+          flags[(size_t)y * pitch + x] = 0;
+          c++;
+        }
+      row_fluid[y] = c;
+    }
+  }, 64);
   int64_t n_fluid = 0;
-  for (int32_t y = 0; y < ny; y++)
-    for (int32_t x = 0; x < nx; x++)
-      if (!solid[(size_t)y * nx + x]) {
-        flags[(size_t)y * pitch + x] = 0;
-        n_fluid++;
-      }
+  for (int64_t c : row_fluid) n_fluid += c;
   auto wrapped = [&](int32_t x, int32_t y, int dx, int dy, int32_t *xo, int32_t *yo) {
     int32_t a = x + dx, b = y + dy;
     if (a < 0 || a >= nx) {
@@ -229,22 +237,37 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
     }
     fl |= static_cast<uint8_t>(1u << (i - 1));
   }
-  // Every unknown direction of every fluid node needs its link.
-  for (int32_t y = 0; y < ny; y++)
-    for (int32_t x = 0; x < nx; x++) {
-      if (solid[(size_t)y * nx + x]) continue;
-      const uint8_t fl = flags[(size_t)y * pitch + x];
-      if (fl == lbm::kSolid) return bad(LBM_EINVAL, "fluid node enclosed on all eight sides");
-      for (int i = 1; i < 9; i++) {
-        int32_t xr, yr;
-        const bool unknown = !wrapped(x, y, -kCx[i], -kCy[i], &xr, &yr) || solid[(size_t)yr * nx + xr];
-        if (unknown != static_cast<bool>(fl & (1u << (i - 1)))) {
-          char buf[200];
-          std::snprintf(buf, sizeof buf, "node (%d, %d) direction %d: no link for an unknown population",
-                        x, y, i);
-          return bad(LBM_EINVAL, buf);
+  // Every unknown direction of every fluid node needs its link (rows in
+  // parallel; the first offending node in row-major order is reported).
+  std::vector<int64_t> row_bad(static_cast<size_t>(ny), -1);  // x * 16 + kind (0: enclosed) or dir
+  lbm::parallel_for(ny, [&](int64_t y0, int64_t y1) {
+    for (int64_t y = y0; y < y1; y++)
+      for (int32_t x = 0; x < nx && row_bad[y] < 0; x++) {
+        if (solid[(size_t)y * nx + x]) continue;
+        const uint8_t fl = flags[(size_t)y * pitch + x];
+        if (fl == lbm::kSolid) {
+          row_bad[y] = static_cast<int64_t>(x) * 16;
+          break;
+        }
+        for (int i = 1; i < 9; i++) {
+          int32_t xr, yr;
+          const bool unknown = !wrapped(x, static_cast<int32_t>(y), -kCx[i], -kCy[i], &xr, &yr) ||
+                               solid[(size_t)yr * nx + xr];
+          if (unknown != static_cast<bool>(fl & (1u << (i - 1)))) {
+            row_bad[y] = static_cast<int64_t>(x) * 16 + i;
+            break;
+          }
         }
       }
+  }, 64);
+  for (int32_t y = 0; y < ny; y++)
+    if (row_bad[y] >= 0) {
+      const int32_t x = static_cast<int32_t>(row_bad[y] / 16), i = static_cast<int32_t>(row_bad[y] % 16);
+      if (i == 0) return bad(LBM_EINVAL, "fluid node enclosed on all eight sides");
+      char buf[200];
+      std::snprintf(buf, sizeof buf, "node (%d, %d) direction %d: no link for an unknown population",
+                    x, y, i);
+      return bad(LBM_EINVAL, buf);
     }
 
   // Per-link parameters (input order), then the node-sorted table.
@@ -254,20 +277,48 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   msg = lbm::compute_link_coefs(cp, p, n_links, link_dir, link_q, link_ubx, link_uby,
                                 hc->link_r.data(), hc->link_l.data(), coef.data(), &cp.n_clamped);
   if (!msg.empty()) return bad(LBM_EINVAL, msg);
-  std::vector<int64_t> order(n_links);
-  std::iota(order.begin(), order.end(), 0);
-  auto key = [&](int64_t k) {
-    return (static_cast<int64_t>(link_y[k]) * pitch + link_x[k]) * 16 + link_dir[k];
-  };
-  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+  // Node-sorted table without a sort: the links of a node are its unknown
+  // directions in order, so a link's slot is the node's first link (a
+  // prefix sum of the per-node link counts in row-major order) plus the
+  // number of the node's unknown directions below its own.
+  std::vector<int64_t> row_links(static_cast<size_t>(ny) + 1, 0);
+  lbm::parallel_for(ny, [&](int64_t y0, int64_t y1) {
+    for (int64_t y = y0; y < y1; y++) {
+      int64_t c = 0;
+      for (int32_t x = 0; x < nx; x++) {
+        const uint8_t fl = flags[(size_t)y * pitch + x];
+        if (fl != lbm::kSolid) c += __builtin_popcount(fl);
+      }
+      row_links[y + 1] = c;
+    }
+  }, 64);
+  for (int32_t y = 0; y < ny; y++) row_links[y + 1] += row_links[y];
   hc->lbase.assign(static_cast<size_t>(plane), -1);
-  for (int64_t s = static_cast<int64_t>(n_links) - 1; s >= 0; s--) {
-    const int64_t k = order[s];
-    hc->lbase[(size_t)link_y[k] * pitch + link_x[k]] = static_cast<int32_t>(s);
-  }
+  lbm::parallel_for(ny, [&](int64_t y0, int64_t y1) {
+    for (int64_t y = y0; y < y1; y++) {
+      int64_t c = row_links[y];
+      for (int32_t x = 0; x < nx; x++) {
+        const uint8_t fl = flags[(size_t)y * pitch + x];
+        if (fl != lbm::kSolid && fl) {
+          hc->lbase[(size_t)y * pitch + x] = static_cast<int32_t>(c);
+          c += __builtin_popcount(fl);
+        }
+      }
+    }
+  }, 64);
+  std::vector<int64_t> order(n_links);
+  lbm::parallel_for(static_cast<int64_t>(n_links), [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; k++) {
+      const size_t node = (size_t)link_y[k] * pitch + link_x[k];
+      const uint32_t below = flags[node] & ((1u << (link_dir[k] - 1)) - 1u);
+      order[hc->lbase[node] + __builtin_popcount(below)] = k;
+    }
+  });
   hc->coef.resize(4 * n_links);
-  for (size_t q = 0; q < n_links; q++)
-    for (int j = 0; j < 4; j++) hc->coef[4 * q + j] = coef[8 * order[q] + j];
+  lbm::parallel_for(static_cast<int64_t>(n_links), [&](int64_t q0, int64_t q1) {
+    for (int64_t q = q0; q < q1; q++)
+      for (int j = 0; j < 4; j++) hc->coef[4 * q + j] = coef[8 * order[q] + j];
+  });
   hc->flags.swap(flags);
   hc->nx = nx;
   hc->ny = ny;
@@ -293,50 +344,64 @@ namespace lbm {
 void build_compact(const HostCase &hc, CompactCase *cc) {
   const int32_t nx = hc.nx, ny = hc.ny, pitch = hc.pitch;
   const int64_t nn = static_cast<int64_t>(nx) * ny;
-  // before[y * nx + x]: fluid nodes ahead of (x, y) in row-major order,
-  // i.e. the compacted index of (x, y) if fluid, else of the next fluid node
-  std::vector<int32_t> before(static_cast<size_t>(nn));
-  cc->index.assign(static_cast<size_t>(nn), -1);
+  auto fluid = [&](int32_t x, int32_t y) {
+    return hc.flags[static_cast<size_t>(y) * pitch + x] != kSolid;
+  };
   cc->rowstart.assign(static_cast<size_t>(ny) + 1, 0);
-  int32_t n = 0;
-  for (int32_t y = 0; y < ny; y++) {
-    cc->rowstart[y] = n;
-    for (int32_t x = 0; x < nx; x++) {
-      const int64_t q = static_cast<int64_t>(y) * nx + x;
-      before[q] = n;
-      if (hc.flags[static_cast<size_t>(y) * pitch + x] != kSolid) cc->index[q] = n++;
+  parallel_for(ny, [&](int64_t y0, int64_t y1) {
+    for (int64_t y = y0; y < y1; y++) {
+      int32_t c = 0;
+      for (int32_t x = 0; x < nx; x++) c += fluid(x, static_cast<int32_t>(y));
+      cc->rowstart[y + 1] = c;
     }
-  }
-  cc->rowstart[ny] = n;
+  }, 64);
+  for (int32_t y = 0; y < ny; y++) cc->rowstart[y + 1] += cc->rowstart[y];
+  const int32_t n = cc->rowstart[ny];
   cc->n_fluid = n;
   cc->plane = (std::max<int64_t>(n, 1) + 31) / 32 * 32;
   const size_t P = static_cast<size_t>(cc->plane);
-  cc->meta.assign(P, 0);
-  cc->n_lb.assign(P, 0);
-  cc->s_lb.assign(P, 0);
+  cc->index.resize(static_cast<size_t>(nn));
   cc->lbase.assign(P, 0);
-  cc->tiles.clear();
-  for (int32_t y = 0; y < ny; y++) {
-    // rows above and below; non-periodic y has solid edge rows, so the fluid
-    // rows 1 .. ny - 2 never leave the lattice
-    const int32_t yn = y + 1 < ny ? y + 1 : (hc.py ? 0 : y);
-    const int32_t ys = y > 0 ? y - 1 : (hc.py ? ny - 1 : y);
-    for (int32_t x = 0; x < nx; x++) {
-      const int32_t i = cc->index[static_cast<size_t>(y) * nx + x];
-      if (i < 0) continue;
-      const uint8_t fl = hc.flags[static_cast<size_t>(y) * pitch + x];
-      uint16_t m = fl;
-      if (hc.px && x == nx - 1) m |= static_cast<uint16_t>(kMetaWrapE);
-      if (hc.px && x == 0) m |= static_cast<uint16_t>(kMetaWrapW);
-      cc->meta[i] = m;
-      cc->n_lb[i] = before[static_cast<size_t>(yn) * nx + x];
-      cc->s_lb[i] = before[static_cast<size_t>(ys) * nx + x];
-      const int32_t lb = hc.lbase[static_cast<size_t>(y) * pitch + x];
-      cc->lbase[i] = lb < 0 ? 0 : lb;
+  cc->node.assign(P, uint2{0u, 0u});
+  parallel_for(ny, [&](int64_t y0, int64_t y1) {
+    // ahead_n[x] / ahead_s[x]: fluid nodes of the row above / below before
+    // column x, so that (x, y +- 1), or the next fluid node after it, has
+    // the compacted index rowstart[y +- 1] + ahead
+    std::vector<int32_t> ahead_n(nx), ahead_s(nx);
+    for (int64_t yy = y0; yy < y1; yy++) {
+      const int32_t y = static_cast<int32_t>(yy);
+      const int32_t yn = row_above(y, ny, hc.py);
+      const int32_t ys = row_below(y, ny, hc.py);
+      int32_t cn = 0, cs = 0;
+      for (int32_t x = 0; x < nx; x++) {
+        ahead_n[x] = cn;
+        ahead_s[x] = cs;
+        cn += fluid(x, yn);
+        cs += fluid(x, ys);
+      }
+      int32_t i = cc->rowstart[y];
+      for (int32_t x = 0; x < nx; x++) {
+        if (!fluid(x, y)) {
+          cc->index[static_cast<size_t>(y) * nx + x] = -1;
+          continue;
+        }
+        cc->index[static_cast<size_t>(y) * nx + x] = i;
+        uint32_t m = hc.flags[static_cast<size_t>(y) * pitch + x];
+        if (hc.px && x == nx - 1) m |= kMetaWrapE;
+        if (hc.px && x == 0) m |= kMetaWrapW;
+        // offsets within the neighbour rows: at most x < nx <= 65536
+        cc->node[i].x = m | (static_cast<uint32_t>(ahead_n[x]) << 16);
+        cc->node[i].y = static_cast<uint32_t>(ahead_s[x]);
+        const int32_t lb = hc.lbase[static_cast<size_t>(y) * pitch + x];
+        cc->lbase[i] = lb < 0 ? 0 : lb;
+        i++;
+      }
     }
+  }, 64);
+  cc->tiles.clear();
+  for (int32_t y = 0; y < ny; y++)
     for (int32_t c = cc->rowstart[y]; c < cc->rowstart[y + 1]; c += kStepThreads)
       cc->tiles.push_back(RowTile{y, c, std::min<int32_t>(kStepThreads, cc->rowstart[y + 1] - c), 0});
-  }
 }
 
 // Error text for handle-less calls, read back by lbm_last_error(NULL).
@@ -440,9 +505,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (e == cudaSuccess) e = alloc(&h->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&h->f[1], fbytes);
   const size_t P = static_cast<size_t>(cc.plane);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->meta), P * 2);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->n_lb), P * 4);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->s_lb), P * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->node), P * sizeof(uint2));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), P * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->rowstart), cc.rowstart.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->index), cc.index.size() * 4);
@@ -463,9 +526,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     if (e == cudaSuccess && bytes)
       e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
   };
-  up(h->meta, cc.meta.data(), P * 2);
-  up(h->n_lb, cc.n_lb.data(), P * 4);
-  up(h->s_lb, cc.s_lb.data(), P * 4);
+  up(h->node, cc.node.data(), P * sizeof(uint2));
   up(h->lbase, cc.lbase.data(), P * 4);
   up(h->rowstart, cc.rowstart.data(), cc.rowstart.size() * 4);
   up(h->index, cc.index.data(), cc.index.size() * 4);

@@ -40,7 +40,7 @@ template <typename C>
 struct BatchCase {
   StepConst<C> k;    // plane = the case's padded fluid-node count
   int64_t f_off;     // element offset of the case's plane 0 in a lattice arena
-  int64_t node_off;  // offset of the case in the meta / n_lb / s_lb / lbase arenas
+  int64_t node_off;  // offset of the case in the node-word / link-base arenas
   int64_t row_off;   // offset of the case's rowstart
   int64_t idx_off;   // offset of the case's node map (nx * ny)
   int64_t n_fluid;
@@ -58,8 +58,7 @@ constexpr int kBatchResidualThreads = 256;
 template <typename T, typename C, int THREADS>
 __global__ void __launch_bounds__(THREADS, StepOcc<T>::min_blocks * kStepThreads / THREADS)
 batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
-                  const uint16_t *__restrict__ meta, const int32_t *__restrict__ n_lb,
-                  const int32_t *__restrict__ s_lb, const int32_t *__restrict__ lbase,
+                  const uint2 *__restrict__ node, const int32_t *__restrict__ lbase,
                   const int32_t *__restrict__ rowstart, const LinkCoef<C> *__restrict__ links,
                   const BatchCase<C> *__restrict__ cases, const Tile *__restrict__ tiles,
                   const int32_t *__restrict__ active) {
@@ -67,8 +66,8 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
   if (!active[t.c] || static_cast<int>(threadIdx.x) >= t.count) return;
   const BatchCase<C> &bc = cases[t.c];
   const int64_t no = bc.node_off;
-  step_node_compact<T, C>(src + bc.f_off, dst + bc.f_off, meta + no, n_lb + no, s_lb + no,
-                          lbase + no, rowstart + bc.row_off, links, bc.k,
+  step_node_compact<T, C>(src + bc.f_off, dst + bc.f_off, node + no, lbase + no,
+                          rowstart + bc.row_off, links, bc.k,
                           static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
 }
 
@@ -141,13 +140,13 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
 __global__ void batch_advance(int64_t *counter, int64_t K) { *counter += K; }
 
 template <typename T, typename C, int THREADS>
-cudaError_t launch_batch_step(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
-                              const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
+cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int32_t *lbase,
+                              const int32_t *rowstart,
                               const void *links, const void *cases, const Tile *tiles,
                               int n_tiles, const int32_t *active, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
   batch_step_kernel<T, C, THREADS><<<n_tiles, THREADS, 0, s>>>(
-      src, dst, meta, n_lb, s_lb, lbase, rowstart, static_cast<const LinkCoef<C> *>(links),
+      src, dst, node, lbase, rowstart, static_cast<const LinkCoef<C> *>(links),
       static_cast<const BatchCase<C> *>(cases), tiles, active);
   return cudaGetLastError();
 }
@@ -170,8 +169,8 @@ struct lbm_batch {
   std::vector<double> ax, ay, scale, tau_s;
   std::vector<int32_t> px, py;
   void *f[2] = {nullptr, nullptr};
-  uint16_t *meta = nullptr;
-  int32_t *n_lb = nullptr, *s_lb = nullptr, *lbase = nullptr, *rowstart = nullptr;
+  uint2 *node = nullptr;
+  int32_t *lbase = nullptr, *rowstart = nullptr;
   int32_t *index = nullptr;
   void *links = nullptr;
   void *cases = nullptr;
@@ -240,8 +239,8 @@ cudaError_t step_once(lbm_batch_t *b, int threads, const lbm::Tile *tiles, int n
     auto go = [&](auto kernel_threads) {
       constexpr int TH = decltype(kernel_threads)::value;
       return lbm::launch_batch_step<T, C, TH>(
-          static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->meta, b->n_lb, b->s_lb,
-          b->lbase, b->rowstart, b->links, b->cases, tiles, n_tiles, b->active, b->stream);
+          static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->node, b->lbase,
+          b->rowstart, b->links, b->cases, tiles, n_tiles, b->active, b->stream);
     };
     if (threads == 64) return go(std::integral_constant<int, 64>());
     if (threads == 128) return go(std::integral_constant<int, 128>());
@@ -258,8 +257,7 @@ void batch_release(lbm_batch_t *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->meta), static_cast<void *>(b->n_lb),
-                  static_cast<void *>(b->s_lb), static_cast<void *>(b->lbase),
+  for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->node), static_cast<void *>(b->lbase),
                   static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->tiles), static_cast<void *>(b->active),
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active)})
@@ -366,9 +364,8 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   }
   const size_t es = elem_size_b(precision);
   const size_t ces = precision == LBM_FP64 ? 8 : 4;
-  std::vector<uint16_t> meta(static_cast<size_t>(nodes), 0);
-  std::vector<int32_t> n_lb(static_cast<size_t>(nodes), 0), s_lb(static_cast<size_t>(nodes), 0),
-      lbase(static_cast<size_t>(nodes), 0), rowstart(static_cast<size_t>(rows), 0),
+  std::vector<uint2> node(static_cast<size_t>(nodes), uint2{0u, 0u});
+  std::vector<int32_t> lbase(static_cast<size_t>(nodes), 0), rowstart(static_cast<size_t>(rows), 0),
       index(static_cast<size_t>(dense), -1);
   std::vector<unsigned char> lhost(std::max<int64_t>(1, links) * 4 * ces, 0);
   std::vector<unsigned char> chost;
@@ -391,9 +388,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     b->py.push_back(h.py);
     b->total_nodes += static_cast<int64_t>(h.nx) * h.ny;
     b->total_fluid += h.n_fluid;
-    std::copy(k.meta.begin(), k.meta.end(), meta.begin() + noff);
-    std::copy(k.n_lb.begin(), k.n_lb.end(), n_lb.begin() + noff);
-    std::copy(k.s_lb.begin(), k.s_lb.end(), s_lb.begin() + noff);
+    std::copy(k.node.begin(), k.node.end(), node.begin() + noff);
     for (size_t q = 0; q < k.lbase.size(); q++)
       lbase[noff + q] = static_cast<int32_t>(k.lbase[q] + loff);
     std::copy(k.rowstart.begin(), k.rowstart.end(), rowstart.begin() + roff);
@@ -439,9 +434,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   const size_t fbytes = 9 * static_cast<size_t>(nodes) * es;
   if (e == cudaSuccess) e = alloc(&b->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&b->f[1], fbytes);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->meta), meta.size() * 2);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->n_lb), n_lb.size() * 4);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->s_lb), s_lb.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->node), node.size() * sizeof(uint2));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->lbase), lbase.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->rowstart), rowstart.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->index), index.size() * 4);
@@ -456,9 +449,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   auto up = [&](void *dst, const void *src, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
   };
-  up(b->meta, meta.data(), meta.size() * 2);
-  up(b->n_lb, n_lb.data(), n_lb.size() * 4);
-  up(b->s_lb, s_lb.data(), s_lb.size() * 4);
+  up(b->node, node.data(), node.size() * sizeof(uint2));
   up(b->lbase, lbase.data(), lbase.size() * 4);
   up(b->rowstart, rowstart.data(), rowstart.size() * 4);
   up(b->index, index.data(), index.size() * 4);

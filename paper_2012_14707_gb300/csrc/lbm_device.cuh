@@ -197,18 +197,19 @@ __device__ __forceinline__ void link_epilogue(T *__restrict__ dst_node, const ui
 // fluid target x + c_q (compact_targets), link epilogue.
 template <typename T, typename C>
 __device__ __forceinline__ void step_node_compact(
-    const T *__restrict__ src, T *__restrict__ dst, const uint16_t *__restrict__ meta,
-    const int32_t *__restrict__ n_lb, const int32_t *__restrict__ s_lb,
+    const T *__restrict__ src, T *__restrict__ dst, const uint2 *__restrict__ node,
     const int32_t *__restrict__ lbase, const int32_t *__restrict__ rowstart,
     const LinkCoef<C> *__restrict__ links, const StepConst<C> &k, const uint32_t i, const int y) {
   const uint32_t P = static_cast<uint32_t>(k.plane);
-  const uint32_t m = meta[i];
+  const uint2 nw = node[i];  // one 8-byte load: flags, seam bits, neighbour-row offsets
+  const uint32_t m = nw.x & 0xFFFFu;
   const uint8_t fl = static_cast<uint8_t>(m & 0xFFu);
   C d[9];
 #pragma unroll
   for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[q * P + i], k.inv_sc);
   const int lb = fl ? lbase[i] : 0;
-  const uint32_t nb = static_cast<uint32_t>(n_lb[i]), sb = static_cast<uint32_t>(s_lb[i]);
+  const uint32_t nb = static_cast<uint32_t>(rowstart[row_above(y, k.ny, k.periodic_y)]) + (nw.x >> 16);
+  const uint32_t sb = static_cast<uint32_t>(rowstart[row_below(y, k.ny, k.periodic_y)]) + (nw.y & 0xFFFFu);
   Collided<T, C> c;
   collide<T, C>(d, k, c);
   // Targets x + c_q.  bit (j - 1) of fl set <=> x - c_j solid, so x + c_q is

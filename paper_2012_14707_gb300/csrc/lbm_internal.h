@@ -1,8 +1,10 @@
 // Internal declarations shared by the host side and the kernels of liblbm.so.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -82,6 +84,16 @@ struct NodeMap {
 constexpr uint32_t kMetaWrapE = 1u << 8;  // x = nx - 1 on a periodic x axis
 constexpr uint32_t kMetaWrapW = 1u << 9;  // x = 0 on a periodic x axis
 
+// Rows of the compacted lattice above and below row y (wrapped where y is
+// periodic; a non-periodic axis has solid edge rows, so fluid rows never
+// need the wrap).
+__host__ __device__ inline int row_above(int y, int ny, int periodic_y) {
+  return y + 1 < ny ? y + 1 : (periodic_y ? 0 : y);
+}
+__host__ __device__ inline int row_below(int y, int ny, int periodic_y) {
+  return y > 0 ? y - 1 : (periodic_y ? ny - 1 : y);
+}
+
 // Compacted indices of the push targets x + c_q (q = 1..8, tq[0] = i) of
 // fluid node i in row y, from its node word m, n_lb / s_lb and rowstart.
 // Neighbours in the own row are i +- 1; in the rows above and below n_lb or
@@ -102,10 +114,9 @@ __host__ __device__ inline void compact_targets(uint32_t m, uint32_t i, uint32_t
   tq[7] = sb - 1;
   tq[8] = sb + ((m & (1u << 1)) ? 0u : 1u);
   if (m & (kMetaWrapE | kMetaWrapW)) {
-    // the seam exists only on a periodic x axis; rows y +- 1 exist (wrapped
-    // where y is periodic, else the fluid rows are 1 .. ny - 2)
-    const int yn = y + 1 < ny ? y + 1 : (periodic_y ? 0 : y);
-    const int ys = y > 0 ? y - 1 : (periodic_y ? ny - 1 : y);
+    // the seam exists only on a periodic x axis
+    const int yn = row_above(y, ny, periodic_y);
+    const int ys = row_below(y, ny, periodic_y);
     if (m & kMetaWrapE) {
       tq[1] = static_cast<uint32_t>(rowstart[y]);
       tq[5] = static_cast<uint32_t>(rowstart[yn]);
@@ -127,16 +138,20 @@ struct RowTile {
 
 // Compacted lattice of one case (host copy): only fluid nodes, in
 // row-major order, each population plane padded to `plane` elements.
-//   meta     flag byte | kMetaWrapE / kMetaWrapW (periodic seam of x)
-//   n_lb     compacted index of the first fluid node at or after (x, y+1)
-//   s_lb     ... at or after (x, y-1) (rows wrapped where periodic)
+//   node     one 8-byte word per node, what the step kernel reads:
+//            .x = flag byte | kMetaWrapE / kMetaWrapW (periodic seam of x)
+//                 | (n_lb - rowstart[y+1]) << 16,
+//            .y = s_lb - rowstart[y-1],
+//            n_lb / s_lb = compacted index of the first fluid node at or
+//            after (x, y+1) / (x, y-1) (rows wrapped where periodic); the
+//            offsets within the neighbour rows are < nx <= 65536
 //   lbase    first link of the node (links sorted by node, then direction)
 //   rowstart compacted index of every row's first fluid node (ny + 1)
 //   index    y * nx + x -> compacted index or -1 (conversions only)
 struct CompactCase {
   int64_t n_fluid = 0, plane = 0;
-  std::vector<uint16_t> meta;
-  std::vector<int32_t> n_lb, s_lb, lbase, rowstart, index;
+  std::vector<int32_t> lbase, rowstart, index;
+  std::vector<uint2> node;
   std::vector<RowTile> tiles;
 };
 void build_compact(const HostCase &hc, CompactCase *cc);
@@ -171,6 +186,26 @@ StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32
   return k;
 }
 
+// Host-side preparation runs over rows or links in parallel: f(begin, end)
+// on contiguous ranges of [0, n), one per hardware thread.  Every index is
+// handled independently, so the result does not depend on the split.
+template <typename F>
+void parallel_for(int64_t n, F &&f, int64_t min_per_thread = 1 << 14) {
+  const int64_t hw = std::max<int64_t>(1, static_cast<int64_t>(std::thread::hardware_concurrency()));
+  const int64_t T = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n / min_per_thread));
+  if (T <= 1) {
+    f(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(static_cast<size_t>(T));
+  for (int64_t t = 0; t < T; t++) {
+    const int64_t b = n * t / T, e = n * (t + 1) / T;
+    th.emplace_back([&f, b, e] { f(b, e); });
+  }
+  for (auto &t : th) t.join();
+}
+
 // Validation and layout of one case (lbm_api.cu).
 int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
                     const int32_t *link_x, const int32_t *link_y, const int32_t *link_dir,
@@ -202,10 +237,9 @@ struct StepOcc<double> {
 
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
 template <typename T, typename C>
-cudaError_t launch_step_compact(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
-                                const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
-                                const RowTile *tiles, int64_t n_tiles, const LinkCoef<C> *links,
-                                const StepConst<C> &k, cudaStream_t s);
+cudaError_t launch_step_compact(const T *src, T *dst, const uint2 *node, const int32_t *lbase,
+                                const int32_t *rowstart, const RowTile *tiles, int64_t n_tiles,
+                                const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_residual_compact(const T *cur, const T *prev, int64_t n_fluid, int64_t plane,

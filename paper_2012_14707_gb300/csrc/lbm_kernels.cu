@@ -28,13 +28,12 @@ using namespace dev;
 template <typename T, typename C>
 __global__ void __launch_bounds__(kStepThreads, StepOcc<T>::min_blocks)
 step_kernel_compact(const T *__restrict__ src, T *__restrict__ dst,
-                    const uint16_t *__restrict__ meta, const int32_t *__restrict__ n_lb,
-                    const int32_t *__restrict__ s_lb, const int32_t *__restrict__ lbase,
+                    const uint2 *__restrict__ node, const int32_t *__restrict__ lbase,
                     const int32_t *__restrict__ rowstart, const RowTile *__restrict__ tiles,
                     const LinkCoef<C> *__restrict__ links, const StepConst<C> k) {
   const RowTile t = tiles[blockIdx.x];
   if (static_cast<int>(threadIdx.x) >= t.count) return;
-  step_node_compact<T, C>(src, dst, meta, n_lb, s_lb, lbase, rowstart, links, k,
+  step_node_compact<T, C>(src, dst, node, lbase, rowstart, links, k,
                           static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
 }
 
@@ -248,13 +247,12 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <typename T, typename C>
-cudaError_t launch_step_compact(const T *src, T *dst, const uint16_t *meta, const int32_t *n_lb,
-                                const int32_t *s_lb, const int32_t *lbase, const int32_t *rowstart,
-                                const RowTile *tiles, int64_t n_tiles, const LinkCoef<C> *links,
-                                const StepConst<C> &k, cudaStream_t s) {
+cudaError_t launch_step_compact(const T *src, T *dst, const uint2 *node, const int32_t *lbase,
+                                const int32_t *rowstart, const RowTile *tiles, int64_t n_tiles,
+                                const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
   step_kernel_compact<T, C><<<static_cast<unsigned>(n_tiles), kStepThreads, 0, s>>>(
-      src, dst, meta, n_lb, s_lb, lbase, rowstart, tiles, links, k);
+      src, dst, node, lbase, rowstart, tiles, links, k);
   return cudaGetLastError();
 }
 
@@ -305,9 +303,8 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
 
 #define LBM_INSTANTIATE(T, C)                                                                      \
   template cudaError_t launch_step_compact<T, C>(                                                  \
-      const T *, T *, const uint16_t *, const int32_t *, const int32_t *, const int32_t *,         \
-      const int32_t *, const RowTile *, int64_t, const LinkCoef<C> *, const StepConst<C> &,        \
-      cudaStream_t);                                                                               \
+      const T *, T *, const uint2 *, const int32_t *, const int32_t *, const RowTile *, int64_t,   \
+      const LinkCoef<C> *, const StepConst<C> &, cudaStream_t);                                    \
   template cudaError_t launch_residual_compact<T>(const T *, const T *, int64_t, int64_t, double,  \
                                                   double, double, double *, double *,              \
                                                   cudaStream_t);                                   \

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <limits>
+#include <mutex>
 #include <string>
 
 #include "lbm_internal.h"
@@ -78,8 +79,8 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                int64_t *n_clamped) {
   const double s6 = std::sqrt(6.0 / kPi);
   const double ts = cp.tau_s, a = 2.0 * ts - 1.0, L1 = cp.L1;
-  int64_t clamped = 0;
-  for (size_t k = 0; k < n; k++) {
+  // one link: "" or an error text; sets *cl when the clamp applied
+  auto one = [&](size_t k, int *cl) -> std::string {
     const double g = q[k];
     const int i = dir[k];
     double l;
@@ -89,7 +90,7 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
         l = (s6 * g * g + g * a * (L1 + s6)) / (s6 * a) + cp.E;
         if (l < p.l_clamp) {
           l = 0.0;
-          clamped++;
+          *cl = 1;
         }
         break;
       }
@@ -133,7 +134,31 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
     c[2] = k3;
     c[3] = alpha;
     c[4] = c[5] = c[6] = c[7] = 0.0;
-  }
+    return "";
+  };
+  // links in parallel; the lowest-numbered failing link's message wins
+  std::mutex mu;
+  int64_t clamped = 0, first_bad = -1;
+  std::string first_msg;
+  parallel_for(static_cast<int64_t>(n), [&](int64_t k0, int64_t k1) {
+    int64_t cl_sum = 0;
+    for (int64_t k = k0; k < k1; k++) {
+      int cl = 0;
+      std::string m = one(static_cast<size_t>(k), &cl);
+      cl_sum += cl;
+      if (!m.empty()) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (first_bad < 0 || k < first_bad) {
+          first_bad = k;
+          first_msg = m;
+        }
+        break;
+      }
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    clamped += cl_sum;
+  });
+  if (first_bad >= 0) return first_msg;
   *n_clamped = clamped;
   return "";
 }

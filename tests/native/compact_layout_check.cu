@@ -60,9 +60,16 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
     for (int x = 0; x < nx; x++) {
       int32_t i = cc.index[y * nx + x];
       if (i < 0) continue;
+      // decode the 8-byte node word as the kernel does
+      const uint2 nw = cc.node[i];
+      const int32_t nb = cc.rowstart[lbm::row_above(y, ny, py)] + (int32_t)(nw.x >> 16);
+      const int32_t sb = cc.rowstart[lbm::row_below(y, ny, py)] + (int32_t)(nw.y & 0xFFFFu);
       uint32_t tq[9];
-      lbm::compact_targets(cc.meta[i], i, cc.n_lb[i], cc.s_lb[i], y, ny, py, cc.rowstart.data(), tq);
-      uint8_t fl = cc.meta[i] & 0xFF;
+      lbm::compact_targets(nw.x & 0xFFFFu, i, nb, sb, y, ny, py, cc.rowstart.data(), tq);
+      uint8_t fl = nw.x & 0xFF;
+      if (fl != hc.flags[(size_t)y * hc.pitch + x]) bad++;
+      const bool we = px && x == nx - 1, ww = px && x == 0;
+      if (((nw.x & lbm::kMetaWrapE) != 0) != we || ((nw.x & lbm::kMetaWrapW) != 0) != ww) bad++;
       for (int qd = 1; qd < 9; qd++) {
         bool fluid_target = !(fl & (1u << (OPP[qd] - 1)));
         int xx, yy;

@@ -166,7 +166,10 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    rows = 512
+    # a band of the same recipe, as tall as keeps the whole run within about
+    # three minutes of one host core (~4 M fluid-node updates per second)
+    rows = int(min(512, max(16, 180 * 4e6 / (0.7 * 8192 * max(1, args.steps + args.warmup)))))
+    rows -= rows % 16
     import oracle
     from oracle import params as P
     from paper_2012_14707_gb300 import cases
@@ -185,8 +188,9 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "cylinders_8192x4096_phi0.7_Kn0.02 (oracle on an 8192x512 band)",
-                   "model": "D2Q9 MRT + curved slip boundary (FP64 CPU oracle)",
+        "config": {"workload": "cylinders_8192x4096_phi0.7_Kn0.02", "nx": 8192, "ny": 4096,
+                   "precision": "fp64 (oracle)", "lattice_steps_per_step": 1,
+                   "sample_rows": rows,
                    "l2": "inputs larger than L2 not applicable (CPU)"},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": sample},

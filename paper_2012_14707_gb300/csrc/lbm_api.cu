@@ -34,8 +34,6 @@ struct lbm_handle {
   double *partials = nullptr;
   double *result = nullptr;
   double *h_result = nullptr;  // pinned, 4 doubles
-  int *d_err = nullptr;        // device: set by a kernel whose bounded wait ran out
-  int *h_err = nullptr;        // pinned copy of *err
   int64_t n_fluid = 0, n_links = 0, steps = 0, dev_bytes = 0;
   std::vector<double> link_r, link_l;
   std::string err;
@@ -92,11 +90,10 @@ void release(lbm_handle_t *h) {
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->lbase),
                   static_cast<void *>(h->rowstart), static_cast<void *>(h->index),
                   static_cast<void *>(h->tiles), h->links, static_cast<void *>(h->partials),
-                  static_cast<void *>(h->result), static_cast<void *>(h->d_err)})
+                  static_cast<void *>(h->result)})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
   if (h->h_result) cudaFreeHost(h->h_result);
-  if (h->h_err) cudaFreeHost(h->h_err);
   delete h;
 }
 
@@ -515,10 +512,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->d_err), sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_result), 4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_err), sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, fbytes, h->stream);
@@ -567,11 +561,7 @@ int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
   LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
-  LBM_CK(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LBM_CK(h, cudaStreamSynchronize(h->stream));
-  if (*h->h_err)
-    return fail(h, LBM_ETIMEOUT,
-                "a step kernel's bounded wait for its bulk copies ran out; the state is invalid");
   const double num = h->h_result[0], den = h->h_result[1];
   double res;
   if (std::isnan(num) || std::isnan(den))

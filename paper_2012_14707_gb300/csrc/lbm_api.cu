@@ -24,12 +24,13 @@ struct lbm_handle {
   lbm_params_t params{};
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
-  // compacted lattice (see lbm::CompactCase)
-  uint2 *node = nullptr;  // per fluid node: flags, seam bits, neighbour-row offsets
-  int32_t *lbase = nullptr, *rowstart = nullptr;
+  // compacted lattice in the pull layout (see lbm::CompactCase, lbm::pull_slots);
+  // f[b] holds 9 planes of `plane` elements, then the link tail
+  uint2 *node = nullptr;  // per fluid node: flags, seam bits, row and link offsets
+  int2 *grp = nullptr;    // per group of lbm::kGroup nodes: first row, first link
+  uint32_t *jbslot = nullptr;  // per link: slot of f_jb(x, t) (lbm::link_jb_slots)
+  int32_t *rowstart = nullptr;
   int32_t *index = nullptr;  // y * nx + x -> compacted index or -1
-  lbm::RowTile *tiles = nullptr;
-  int64_t n_tiles = 0;
   void *links = nullptr;
   double *partials = nullptr;
   double *result = nullptr;
@@ -87,10 +88,10 @@ void release(lbm_handle_t *h) {
   if (!h) return;
   cudaStream_t s = h->stream;
   cudaStreamSynchronize(s);
-  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->lbase),
-                  static_cast<void *>(h->rowstart), static_cast<void *>(h->index),
-                  static_cast<void *>(h->tiles), h->links, static_cast<void *>(h->partials),
-                  static_cast<void *>(h->result)})
+  for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->grp),
+                  static_cast<void *>(h->jbslot),
+                  static_cast<void *>(h->rowstart), static_cast<void *>(h->index), h->links,
+                  static_cast<void *>(h->partials), static_cast<void *>(h->result)})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
   if (h->h_result) cudaFreeHost(h->h_result);
@@ -103,11 +104,24 @@ lbm::StepConst<C> step_const(const lbm_handle_t *h) {
                                  h->params.diffuse_mode, h->scale);
 }
 
+lbm::PullGeom pull_geom(const lbm_handle_t *h) {
+  lbm::PullGeom g;
+  g.node = h->node;
+  g.grp = h->grp;
+  g.rowstart = h->rowstart;
+  g.jbslot = h->jbslot;
+  g.ny = h->ny;
+  g.periodic_y = h->py;
+  g.plane = static_cast<uint32_t>(h->plane);
+  return g;
+}
+
 lbm::NodeMap node_map(const lbm_handle_t *h) {
   lbm::NodeMap m;
   m.index = h->index;
   m.nx = h->nx;
   m.ny = h->ny;
+  m.pull = pull_geom(h);
   return m;
 }
 
@@ -115,10 +129,10 @@ cudaError_t do_step(lbm_handle_t *h) {
   const int src = h->cur, dst = 1 - h->cur;
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
-    return lbm::launch_step_compact<T, C>(
-        static_cast<const T *>(h->f[src]), static_cast<T *>(h->f[dst]), h->node, h->lbase,
-        h->rowstart, h->tiles, h->n_tiles,
-        static_cast<const lbm::LinkCoef<C> *>(h->links), step_const<C>(h), h->stream);
+    return lbm::launch_step_pull<T, C>(static_cast<const T *>(h->f[src]),
+                                       static_cast<T *>(h->f[dst]), pull_geom(h), h->n_fluid,
+                                       static_cast<const lbm::LinkCoef<C> *>(h->links),
+                                       step_const<C>(h), h->stream);
   });
   if (e == cudaSuccess) {
     h->cur = dst;
@@ -338,7 +352,7 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
 
 namespace lbm {
 
-void build_compact(const HostCase &hc, CompactCase *cc) {
+std::string build_compact(const HostCase &hc, CompactCase *cc) {
   const int32_t nx = hc.nx, ny = hc.ny, pitch = hc.pitch;
   const int64_t nn = static_cast<int64_t>(nx) * ny;
   auto fluid = [&](int32_t x, int32_t y) {
@@ -395,10 +409,68 @@ void build_compact(const HostCase &hc, CompactCase *cc) {
       }
     }
   }, 64);
+  // Group records and the node words' row and link offsets.  Links are
+  // sorted by node, so a group's links follow its first node with links.
+  const int64_t n_groups = (static_cast<int64_t>(n) + kGroup - 1) / kGroup;
+  cc->grp.assign(static_cast<size_t>(n_groups), int2{0, 0});
+  std::vector<char> group_bad(static_cast<size_t>(n_groups), 0);
+  parallel_for(n_groups, [&](int64_t g0, int64_t g1) {
+    for (int64_t g = g0; g < g1; g++) {
+      const int32_t i0 = static_cast<int32_t>(g * kGroup);
+      const int32_t i1 = std::min<int32_t>(n, i0 + kGroup);
+      int32_t y = static_cast<int32_t>(
+          std::upper_bound(cc->rowstart.begin(), cc->rowstart.end(), i0) - cc->rowstart.begin() - 1);
+      const int32_t y0 = y;
+      int32_t l0 = -1;
+      for (int32_t i = i0; i < i1; i++)
+        if (cc->node[i].x & 0xFFu) {
+          l0 = cc->lbase[i];
+          break;
+        }
+      cc->grp[g] = int2{y0, l0 < 0 ? 0 : l0};
+      for (int32_t i = i0; i < i1; i++) {
+        while (cc->rowstart[y + 1] <= i) y++;
+        const uint32_t dy = static_cast<uint32_t>(y - y0);
+        const int32_t loff = (cc->node[i].x & 0xFFu) ? cc->lbase[i] - l0 : 0;
+        if (dy >= static_cast<uint32_t>(kMaxGroupRows) || loff < 0 || loff > 255) {
+          group_bad[g] = 1;
+          continue;
+        }
+        cc->node[i].x |= (dy & 63u) << 10;
+        cc->node[i].y |= (static_cast<uint32_t>(loff) << 16) | ((dy >> 6) << 24);
+      }
+    }
+  }, 1024);
+  for (char b : group_bad)
+    if (b)
+      return "more than 16383 solid rows between two fluid nodes " + std::to_string(kGroup) +
+             " places apart in row-major order";
   cc->tiles.clear();
   for (int32_t y = 0; y < ny; y++)
     for (int32_t c = cc->rowstart[y]; c < cc->rowstart[y + 1]; c += kStepThreads)
       cc->tiles.push_back(RowTile{y, c, std::min<int32_t>(kStepThreads, cc->rowstart[y + 1] - c), 0});
+  return std::string();
+}
+
+std::vector<uint32_t> link_jb_slots(const CompactCase &cc, int ny, int periodic_y,
+                                    int64_t n_links) {
+  std::vector<uint32_t> out(static_cast<size_t>(n_links), 0u);
+  const uint32_t P = static_cast<uint32_t>(cc.plane);
+  static const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  parallel_for(cc.n_fluid, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; i++) {
+      const uint2 nw = cc.node[static_cast<size_t>(i)];
+      const uint32_t fl = nw.x & 0xFFu;
+      if (!fl) continue;
+      uint32_t s[9];
+      pull_slots(nw, cc.grp[static_cast<size_t>(i / kGroup)], static_cast<uint32_t>(i), P, ny,
+                 periodic_y, cc.rowstart.data(), s);
+      int64_t l = cc.lbase[static_cast<size_t>(i)];
+      for (int j = 1; j < 9; j++)
+        if (fl & (1u << (j - 1))) out[static_cast<size_t>(l++)] = s[opp[j]];
+    }
+  });
+  return out;
 }
 
 // Error text for handle-less calls, read back by lbm_last_error(NULL).
@@ -461,12 +533,22 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   h->scale = hc.scale;
   h->stream = static_cast<cudaStream_t>(p.stream);
   lbm::CompactCase cc;
-  lbm::build_compact(hc, &cc);
+  const std::string cerr = lbm::build_compact(hc, &cc);
+  // pull slots are 32-bit: nine planes and the link tail below 2^32
+  if (cerr.empty() && 9 * cc.plane + hc.n_links >= (int64_t(1) << 32)) {
+    delete h;
+    g_create_error = "lattice too large: 9 x fluid nodes + links must stay below 2^32";
+    return LBM_EINVAL;
+  }
+  if (!cerr.empty()) {
+    delete h;
+    g_create_error = cerr;
+    return LBM_EINVAL;
+  }
   h->nx = hc.nx;
   h->ny = hc.ny;
   h->pitch = 0;
   h->plane = cc.plane;
-  h->n_tiles = static_cast<int64_t>(cc.tiles.size());
   h->px = hc.px;
   h->py = hc.py;
   h->ax = hc.ax;
@@ -478,7 +560,8 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   cudaGetDevice(&h->device);
 
   const size_t es = elem_size(p.precision);
-  const size_t fbytes = 9 * static_cast<size_t>(cc.plane) * es;
+  // nine planes, then the link tail (rounded up to whole 128-byte lines)
+  const size_t fbytes = (9 * static_cast<size_t>(cc.plane) + (n_links_sz + 63) / 64 * 64) * es;
   const size_t ces = p.precision == LBM_FP64 ? 8 : 4;  // link coefficients: FP64 or FP32
   const size_t lbytes = std::max<size_t>(1, n_links_sz) * 4 * ces;
   const size_t pbytes = lbm::kResidualBlocks * lbm::kPartialStride * sizeof(double);
@@ -503,12 +586,13 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (e == cudaSuccess) e = alloc(&h->f[1], fbytes);
   const size_t P = static_cast<size_t>(cc.plane);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->node), P * sizeof(uint2));
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), P * 4);
+  if (e == cudaSuccess)
+    e = alloc(reinterpret_cast<void **>(&h->grp), std::max<size_t>(1, cc.grp.size()) * sizeof(int2));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->rowstart), cc.rowstart.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->index), cc.index.size() * 4);
+  const std::vector<uint32_t> jbs = lbm::link_jb_slots(cc, hc.ny, hc.py, hc.n_links);
   if (e == cudaSuccess)
-    e = alloc(reinterpret_cast<void **>(&h->tiles),
-              std::max<size_t>(1, cc.tiles.size()) * sizeof(lbm::RowTile));
+    e = alloc(reinterpret_cast<void **>(&h->jbslot), std::max<size_t>(1, jbs.size()) * 4);
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
@@ -521,10 +605,10 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
       e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
   };
   up(h->node, cc.node.data(), P * sizeof(uint2));
-  up(h->lbase, cc.lbase.data(), P * 4);
+  up(h->grp, cc.grp.data(), cc.grp.size() * sizeof(int2));
+  up(h->jbslot, jbs.data(), jbs.size() * 4);
   up(h->rowstart, cc.rowstart.data(), cc.rowstart.size() * 4);
   up(h->index, cc.index.data(), cc.index.size() * 4);
-  up(h->tiles, cc.tiles.data(), cc.tiles.size() * sizeof(lbm::RowTile));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->links, lhost.data(), lbytes, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -554,9 +638,9 @@ int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
     LBM_TYPES(tT, tC);
     return lbm::launch_residual_compact<T>(static_cast<const T *>(h->f[c]),
-                                           static_cast<const T *>(h->f[pv]), h->n_fluid, h->plane,
-                                           h->ax, h->ay, h->scale, h->partials, h->result,
-                                           h->stream);
+                                           static_cast<const T *>(h->f[pv]), node_map(h),
+                                           h->n_fluid, h->plane, h->ax, h->ay, h->scale,
+                                           h->partials, h->result, h->stream);
   });
   if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
   LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,

@@ -202,7 +202,7 @@ __device__ __forceinline__ void step_node_compact(
     const LinkCoef<C> *__restrict__ links, const StepConst<C> &k, const uint32_t i, const int y) {
   const uint32_t P = static_cast<uint32_t>(k.plane);
   const uint2 nw = node[i];  // one 8-byte load: flags, seam bits, neighbour-row offsets
-  const uint32_t m = nw.x & 0xFFFFu;
+  const uint32_t m = nw.x & kNodeMeta;
   const uint8_t fl = static_cast<uint8_t>(m & 0xFFu);
   C d[9];
 #pragma unroll
@@ -226,6 +226,105 @@ __device__ __forceinline__ void step_node_compact(
   if (!(fl & (1u << 4))) dst[7 * P + tq[7]] = c.t[7];  // opp(7) = 5
   if (!(fl & (1u << 5))) dst[8 * P + tq[8]] = c.t[8];  // opp(8) = 6
   link_epilogue<T, C>(dst + i, P, fl, lb, links, src + i, c, k);
+}
+
+// Loads that the compiler must issue where they stand (not merged with an
+// earlier load of the same address and kept in registers meanwhile).
+__device__ __forceinline__ uint2 reload_u2(const uint2 *p) {
+  uint2 v;
+  asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int2 reload_i2(const int2 *p) {
+  int2 v;
+  asm volatile("ld.global.nc.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
+// The unknown populations of boundary node i for the next step (bits of
+// its flag byte), Eq. EqNewBDSC in the folded form of LinkCoef, written to
+// the link tail of dst (pull layout, see pull_slots): link k of the table
+// has tail element 9 P + k.  Inputs: the node's post-collision state c and
+// its pre-collision f_jb(x, t), gathered again from src at the slot the
+// link's jbslot entry names (a cache hit; fewer live registers than
+// keeping nine values through the collision).  Directions that no active
+// lane of the warp needs are skipped warp-uniformly.
+template <typename T, typename C>
+__device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T *__restrict__ dst,
+                                                   const PullGeom &g, const uint32_t i,
+                                                   const LinkCoef<C> *__restrict__ links,
+                                                   const Collided<T, C> &c_,
+                                                   const StepConst<C> &k) {
+  // the node word and group record again (cache hits), not kept live
+  // through the collision
+  const uint2 nw = reload_u2(g.node + i);
+  const uint8_t fl = static_cast<uint8_t>(nw.x & 0xFFu);
+  const unsigned wmask = __reduce_or_sync(__activemask(), static_cast<unsigned>(fl));
+  if (!wmask) return;
+  const int2 gr = reload_i2(g.grp + i / kGroup);
+  const C(&o)[9] = c_.o;
+  const C drho = c_.drho, rho = c_.rho, ux = c_.ux, uy = c_.uy, uu = c_.uu;
+  const uint32_t tail = 9u * g.plane;
+  const uint32_t li = static_cast<uint32_t>(gr.y) + node_loff(nw);  // the node's first link
+#pragma unroll
+  for (int j = 1; j < 9; j++) {
+    if (!(wmask & (1u << (j - 1)))) continue;
+    if (fl & (1u << (j - 1))) {
+      constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+      constexpr int cx_tab[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+      constexpr int cy_tab[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+      constexpr double w_tab[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                   1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+      const int jb = opp_tab[j];
+      // link j is the node's k-th, k = links in lower directions
+      const uint32_t lj = li + __popc(fl & ((1u << (j - 1)) - 1u));
+      const LinkCoef<C> c = links[lj];
+      const C r = c.k1 + c.k2 + c.k3;
+      C c0, c2;
+      if (k.diffuse_mode == 0) {
+        c0 = c.alpha;
+        c2 = (C(1) - r) * C(w_tab[j]);
+      } else {
+        c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
+        c2 = C(0);
+      }
+      const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
+      const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+      const C djb = Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
+      const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
+                  c2 * (drho + rho * pj);
+      dst[tail + lj] = Stor<T>::st(v, k.sc);
+    }
+  }
+}
+
+// One time step for fluid node i of a single-case lattice in the pull
+// layout (pull_slots): gather f(x, t) (streaming, Sec. 2), collide
+// (collide), store f'(x, t) in the node's own slots of dst, then the link
+// epilogue.  The arithmetic is the push kernel's, value for value.
+template <typename T, typename C>
+__device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__restrict__ dst,
+                                               const PullGeom &g,
+                                               const LinkCoef<C> *__restrict__ links,
+                                               const StepConst<C> &k, const uint32_t i) {
+  const uint32_t P = g.plane;
+  const uint2 nw = g.node[i];
+  const int2 gr = g.grp[i / kGroup];
+  C d[9];
+  {
+    uint32_t s[9];
+    pull_slots(nw, gr, i, P, g.ny, g.periodic_y, g.rowstart, s);
+#pragma unroll
+    for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[s[q]], k.inv_sc);
+    // the link records are read after the collision: start fetching them now
+    if (nw.x & 0xFFu)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(links + gr.y + node_loff(nw)));
+  }
+  Collided<T, C> c;
+  collide<T, C>(d, k, c);
+#pragma unroll
+  for (int q = 0; q < 9; q++) dst[q * P + i] = c.t[q];
+  link_epilogue_pull<T, C>(src, dst, g, i, links, c, k);
 }
 
 // Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).

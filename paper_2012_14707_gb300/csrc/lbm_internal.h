@@ -69,20 +69,21 @@ struct HostCase {
   std::vector<double> link_r, link_l;  // per link in input order
 };
 
-// Where node (x, y) of a case lives in its compacted lattice: the index
-// map y * nx + x -> compacted index, -1 for solid nodes.  at() returns the
-// element offset within a population plane, or -1 for a solid node.
-struct NodeMap {
-  const int32_t *index = nullptr;
-  int32_t nx = 0, ny = 0;
-  __host__ __device__ int64_t at(int x, int y) const {
-    return index[static_cast<int64_t>(y) * nx + x];
-  }
-};
-
-// Bits above the flag byte in a compacted lattice's node word.
+// Bits above the flag byte in a compacted lattice's node word (.x; the
+// full layout is described at CompactCase).
 constexpr uint32_t kMetaWrapE = 1u << 8;  // x = nx - 1 on a periodic x axis
 constexpr uint32_t kMetaWrapW = 1u << 9;  // x = 0 on a periodic x axis
+constexpr uint32_t kNodeMeta = 0x3FFu;    // flag byte and the two seam bits
+constexpr int kGroup = 32;                // nodes per group record (CompactCase::grp)
+constexpr int kMaxGroupRows = 1 << 14;    // rows a group may span (14-bit row offset)
+
+// Row offset of a node from its group's first row, and the offset of its
+// first link from the group's first link (node word bits .x 10..15 with
+// .y 24..31, and .y 16..23).
+__host__ __device__ inline int node_dy(uint2 nw) {
+  return static_cast<int>(((nw.x >> 10) & 63u) | ((nw.y >> 24) << 6));
+}
+__host__ __device__ inline uint32_t node_loff(uint2 nw) { return (nw.y >> 16) & 255u; }
 
 // Rows of the compacted lattice above and below row y (wrapped where y is
 // periodic; a non-periodic axis has solid edge rows, so fluid rows never
@@ -130,6 +131,93 @@ __host__ __device__ inline void compact_targets(uint32_t m, uint32_t i, uint32_t
   }
 }
 
+// The same target for one direction q (tq[q] of compact_targets; the host
+// checks compare the two).  With q a constant the switch folds away.
+__host__ __device__ inline uint32_t push_target(int q, uint32_t m, uint32_t i, uint32_t nb,
+                                                uint32_t sb, int y, int ny, int periodic_y,
+                                                const int32_t *rowstart) {
+  const bool we = (m & kMetaWrapE) != 0, ww = (m & kMetaWrapW) != 0;
+  switch (q) {
+    case 1: return we ? static_cast<uint32_t>(rowstart[y]) : i + 1;
+    case 2: return nb;
+    case 3: return ww ? static_cast<uint32_t>(rowstart[y + 1] - 1) : i - 1;
+    case 4: return sb;
+    case 5:
+      return we ? static_cast<uint32_t>(rowstart[row_above(y, ny, periodic_y)])
+                : nb + ((m & (1u << 3)) ? 0u : 1u);
+    case 6: return ww ? static_cast<uint32_t>(rowstart[row_above(y, ny, periodic_y) + 1] - 1) : nb - 1;
+    case 7: return ww ? static_cast<uint32_t>(rowstart[row_below(y, ny, periodic_y) + 1] - 1) : sb - 1;
+    case 8:
+      return we ? static_cast<uint32_t>(rowstart[row_below(y, ny, periodic_y)])
+                : sb + ((m & (1u << 1)) ? 0u : 1u);
+    default: return i;
+  }
+}
+
+// Where the single-case lattice keeps node i's populations (pull layout).
+// A step stores f'_q(x, t) in x's own slot q * P + i, so that its stores
+// are aligned and coalesced, and the next step gathers
+// f_q(x, t + 1) = f'_q(x - c_q, t) from the slot of x - c_q, which is the
+// push target of direction opp(q) (compact_targets).  Where x - c_q is
+// solid (a boundary link), f_q(x, t + 1) is Eq. EqNewBDSC, which x itself
+// evaluates during step t (every input is x's own) and keeps in the
+// lattice's link tail: element 9 P + (index of the link), links sorted by
+// node, then direction.  Every slot holds one population of one node, so
+// the gather below is also the scatter that writes a state.
+struct PullGeom {
+  const uint2 *node = nullptr;      // node words (CompactCase::node)
+  const int2 *grp = nullptr;        // group records (CompactCase::grp)
+  const int32_t *rowstart = nullptr;
+  const uint32_t *jbslot = nullptr; // per link (x, j): pull slot of f_jb(x) (link_jb_slots)
+  int32_t ny = 0, periodic_y = 0;
+  uint32_t plane = 0;               // P
+};
+
+// s[q] = element of the pre-collision f_q of fluid node i, q = 0..8.
+__host__ __device__ inline void pull_slots(uint2 nw, int2 grp, uint32_t i, uint32_t P, int ny,
+                                           int periodic_y, const int32_t *rowstart,
+                                           uint32_t (&s)[9]) {
+  const uint32_t m = nw.x & kNodeMeta;
+  const int y = grp.x + node_dy(nw);
+  const uint32_t nb = static_cast<uint32_t>(rowstart[row_above(y, ny, periodic_y)]) + (nw.x >> 16);
+  const uint32_t sb = static_cast<uint32_t>(rowstart[row_below(y, ny, periodic_y)]) + (nw.y & 0xFFFFu);
+  uint32_t tq[9];
+  compact_targets(m, i, nb, sb, y, ny, periodic_y, rowstart, tq);
+  uint32_t li = 9u * P + static_cast<uint32_t>(grp.y) + node_loff(nw);
+  // bit q - 1 of the flag byte set <=> x - c_q solid; opp = {0, 3, 4, 1, 2, 7, 8, 5, 6}
+  s[0] = i;
+  s[1] = (m & 0x01u) ? li++ : 1u * P + tq[3];
+  s[2] = (m & 0x02u) ? li++ : 2u * P + tq[4];
+  s[3] = (m & 0x04u) ? li++ : 3u * P + tq[1];
+  s[4] = (m & 0x08u) ? li++ : 4u * P + tq[2];
+  s[5] = (m & 0x10u) ? li++ : 5u * P + tq[7];
+  s[6] = (m & 0x20u) ? li++ : 6u * P + tq[8];
+  s[7] = (m & 0x40u) ? li++ : 7u * P + tq[5];
+  s[8] = (m & 0x80u) ? li : 8u * P + tq[6];
+}
+
+// Where node (x, y) of a case lives in its compacted lattice: the index
+// map y * nx + x -> compacted index, -1 for solid nodes.  at() returns the
+// compacted index, or -1 for a solid node; slots() the elements of its nine
+// populations: q * plane + i in the push layout of the batched solver's
+// arena (pull.node null), pull_slots in the pull layout of a single case.
+struct NodeMap {
+  const int32_t *index = nullptr;
+  int32_t nx = 0, ny = 0;
+  PullGeom pull{};
+  __host__ __device__ int64_t at(int x, int y) const {
+    return index[static_cast<int64_t>(y) * nx + x];
+  }
+  __host__ __device__ void slots(uint32_t i, uint32_t plane, uint32_t (&s)[9]) const {
+    if (pull.node) {
+      pull_slots(pull.node[i], pull.grp[i / kGroup], i, plane, pull.ny, pull.periodic_y,
+                 pull.rowstart, s);
+    } else {
+      for (int q = 0; q < 9; q++) s[q] = static_cast<uint32_t>(q) * plane + i;
+    }
+  }
+};
+
 // A run of at most kStepThreads consecutive fluid nodes of one row of a
 // compacted lattice: row y, compacted indices start .. start + count - 1.
 struct RowTile {
@@ -138,23 +226,41 @@ struct RowTile {
 
 // Compacted lattice of one case (host copy): only fluid nodes, in
 // row-major order, each population plane padded to `plane` elements.
-//   node     one 8-byte word per node, what the step kernel reads:
-//            .x = flag byte | kMetaWrapE / kMetaWrapW (periodic seam of x)
-//                 | (n_lb - rowstart[y+1]) << 16,
-//            .y = s_lb - rowstart[y-1],
+//   node     one 8-byte word per node, what the step kernels read:
+//            .x bits 0..7   flag byte (bit q - 1: x - c_q solid)
+//               bits 8, 9   kMetaWrapE / kMetaWrapW (periodic seam of x)
+//               bits 10..15 row offset dy from the group's row, low 6 bits
+//               bits 16..31 n_lb - rowstart[y+1]
+//            .y bits 0..15  s_lb - rowstart[y-1]
+//               bits 16..23 first link of the node - first link of its group
+//               bits 24..31 dy, high 8 bits
 //            n_lb / s_lb = compacted index of the first fluid node at or
 //            after (x, y+1) / (x, y-1) (rows wrapped where periodic); the
 //            offsets within the neighbour rows are < nx <= 65536
+//   grp      one record per group of kGroup consecutive nodes (node i is in
+//            group i / kGroup): .x = row of the group's first node,
+//            .y = first link of the group's first node with links; a group
+//            spans fewer than kMaxGroupRows rows, and holds at most
+//            kGroup * 8 links, so the offsets fit the node word
 //   lbase    first link of the node (links sorted by node, then direction)
 //   rowstart compacted index of every row's first fluid node (ny + 1)
 //   index    y * nx + x -> compacted index or -1 (conversions only)
+//   tiles    row tiles of the batched solver's push kernel
 struct CompactCase {
   int64_t n_fluid = 0, plane = 0;
   std::vector<int32_t> lbase, rowstart, index;
   std::vector<uint2> node;
+  std::vector<int2> grp;
   std::vector<RowTile> tiles;
 };
-void build_compact(const HostCase &hc, CompactCase *cc);
+// Returns "" or the reason the case does not fit the node word.
+std::string build_compact(const HostCase &hc, CompactCase *cc);
+// For every link (node x, direction j) of a compacted case, in link-table
+// order: the pull slot of f_jb(x, t) (jb = opp(j)), the pre-collision value
+// Eq. EqNewBDSC takes from x.  The step kernel's link epilogue reads it
+// there instead of recomputing the neighbour's index.
+std::vector<uint32_t> link_jb_slots(const CompactCase &cc, int ny, int periodic_y,
+                                    int64_t n_links);
 
 // Kernel constants of one case in arithmetic type C.
 template <typename C>
@@ -220,9 +326,9 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                const double *uby, double *r_out, double *l_out,
                                double *coef8_out /* n x 8 */, int64_t *n_clamped);
 
-// Step kernel geometry: one thread per fluid node, up to kStepThreads
-// nodes of a row per CTA, registers bounded for StepOcc<T>::min_blocks
-// resident CTAs per SM.
+// Batched step kernel geometry: one thread per fluid node, up to
+// kStepThreads nodes of a row per CTA, registers bounded for
+// StepOcc<T>::min_blocks resident CTAs per SM.
 constexpr int kStepThreads = 256;
 template <typename T>
 struct StepOcc {
@@ -235,16 +341,26 @@ struct StepOcc<double> {
   static constexpr int min_blocks = 2;
 };
 
+// Single-case (pull) step kernel geometry: CTA b runs fluid nodes
+// b * kPullThreads .. b * kPullThreads + kPullThreads - 1, whatever their
+// rows; small CTAs leave fewer warp slots idle behind a CTA's slowest warp.
+constexpr int kPullThreads = 128;
+template <typename T>
+struct PullOcc {
+  static constexpr int min_blocks = StepOcc<T>::min_blocks * kStepThreads / kPullThreads;
+};
+
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
 template <typename T, typename C>
-cudaError_t launch_step_compact(const T *src, T *dst, const uint2 *node, const int32_t *lbase,
-                                const int32_t *rowstart, const RowTile *tiles, int64_t n_tiles,
-                                const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
+cudaError_t launch_step_pull(const T *src, T *dst, const PullGeom &g, int64_t n_fluid,
+                             const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);
 
+// Residual and mass of the states in cur and prev (the lattices of two
+// consecutive steps), nodes in the layout of map.
 template <typename T>
-cudaError_t launch_residual_compact(const T *cur, const T *prev, int64_t n_fluid, int64_t plane,
-                                    double ax, double ay, double scale, double *partials,
-                                    double *result, cudaStream_t s);
+cudaError_t launch_residual_compact(const T *cur, const T *prev, const NodeMap &map,
+                                    int64_t n_fluid, int64_t plane, double ax, double ay,
+                                    double scale, double *partials, double *result, cudaStream_t s);
 
 // Conversions between a compacted lattice (see NodeMap) and
 // caller arrays over the nx x ny nodes (row-major, y * nx + x).

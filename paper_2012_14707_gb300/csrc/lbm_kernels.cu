@@ -4,15 +4,17 @@
 // Populations are stored as deviations d_i = f_i - w_i (rest state rho = 1,
 // u = 0 is d = 0), one plane per direction, over the fluid nodes only, in
 // row-major order (compacted lattice: every thread of the step kernel owns
-// a fluid node, no sector holds solid slots; the batched solver keeps every
-// case the same way in one arena).  The step kernel is a push scheme
-// (Sec. 2: collide, then stream): each fluid node reads its nine values
-// once, collides in moment space, and writes f'_i to x + c_i in the other
-// lattice (fluid targets only: solid nodes have no slots).  Unknown
-// populations of a boundary node (x_f - c_i
-// solid) are never pushed by anyone; the node fills them itself from values
-// it holds in registers (Eq. EqNewBDSC is local:
-// f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all belong to x_f).
+// a fluid node, no sector holds solid slots).  A single case's step kernel
+// is a pull scheme (pull_slots): each fluid node gathers f(x, t) from the
+// post-collision values its neighbours stored in the previous step,
+// collides in moment space (Sec. 2), and stores f'(x, t) in its own slots
+// of the other lattice: every store is aligned and coalesced.  Unknown
+// populations of a boundary node (x_f - c_i solid) come from Eq. EqNewBDSC,
+// which is local (f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all
+// belong to x_f): the node evaluates them in the same step and keeps them
+// in the lattice's link tail, where its next gather finds them.  The
+// batched solver's arena keeps the push layout (lbm_batch.cu); both
+// compute the same values.
 #include <cstdint>
 
 #include "lbm_device.cuh"
@@ -23,18 +25,16 @@ namespace {
 
 using namespace dev;
 
-// One time step on a compacted lattice: CTA b runs the fluid nodes of row
-// tile b (one thread per node, every lane a fluid node).
+// One time step of a single case (pull layout): thread t of CTA b runs
+// fluid node b * kPullThreads + t.
 template <typename T, typename C>
-__global__ void __launch_bounds__(kStepThreads, StepOcc<T>::min_blocks)
-step_kernel_compact(const T *__restrict__ src, T *__restrict__ dst,
-                    const uint2 *__restrict__ node, const int32_t *__restrict__ lbase,
-                    const int32_t *__restrict__ rowstart, const RowTile *__restrict__ tiles,
-                    const LinkCoef<C> *__restrict__ links, const StepConst<C> k) {
-  const RowTile t = tiles[blockIdx.x];
-  if (static_cast<int>(threadIdx.x) >= t.count) return;
-  step_node_compact<T, C>(src, dst, node, lbase, rowstart, links, k,
-                          static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
+__global__ void __launch_bounds__(kPullThreads, PullOcc<T>::min_blocks)
+step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom g,
+                 const uint32_t n_fluid, const LinkCoef<C> *__restrict__ links,
+                 const StepConst<C> k) {
+  const uint32_t i = blockIdx.x * kPullThreads + threadIdx.x;
+  if (i >= n_fluid) return;
+  step_node_pull<T, C>(src, dst, g, links, k, i);
 }
 
 // Residual pass 1: thread g of the fixed grid reduces nodes g, g + G,
@@ -46,7 +46,7 @@ step_kernel_compact(const T *__restrict__ src, T *__restrict__ dst,
 template <typename T>
 __global__ void __launch_bounds__(kResidualThreads)
 residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
-                          int64_t n_fluid, int64_t plane, double ax, double ay,
+                          const NodeMap map, int64_t n_fluid, int64_t plane, double ax, double ay,
                           double inv_scale, double *__restrict__ partials) {
   using C = typename Stor<T>::C;
   const C inv = static_cast<C>(inv_scale);
@@ -54,11 +54,13 @@ residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
   const int64_t G = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t node = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; node < n_fluid;
        node += G) {
+    uint32_t s[9];
+    map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
     C a[9], b[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-      a[i] = Stor<T>::ld(cur[i * plane + node], inv);
-      b[i] = Stor<T>::ld(prev[i * plane + node], inv);
+      a[i] = Stor<T>::ld(cur[s[i]], inv);
+      b[i] = Stor<T>::ld(prev[s[i]], inv);
     }
     C n1, d1, m1;
     residual_terms<C>(a, b, static_cast<C>(ax), static_cast<C>(ay), n1, d1, m1);
@@ -122,9 +124,11 @@ __global__ void fields_kernel(const T *__restrict__ f, const NodeMap map, int64_
     const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
     double r = 0.0, u = 0.0, v = 0.0;
     if (node >= 0) {
+      uint32_t s[9];
+      map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
       double a[9];
       for (int i = 0; i < 9; i++)
-        a[i] = static_cast<double>(Stor<T>::ld(f[i * plane + node], static_cast<C>(inv_scale)));
+        a[i] = static_cast<double>(Stor<T>::ld(f[s[i]], static_cast<C>(inv_scale)));
       node_velocity(a, ax, ay, r, u, v);
     }
     if (rho) rho[p] = r;
@@ -198,10 +202,12 @@ __global__ void set_fields_kernel(const double *__restrict__ rho, const double *
         dv[i] = feq - 3.0 * tau_s * w[i] * r * qg - w[i];
       }
     }
+    uint32_t s[9];
+    map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
     for (int i = 0; i < 9; i++) {
       const T v = Stor<T>::st(static_cast<C>(dv[i]), static_cast<C>(scale));
-      f0[i * plane + node] = v;
-      f1[i * plane + node] = v;
+      f0[s[i]] = v;
+      f1[s[i]] = v;
     }
   }
 }
@@ -220,9 +226,13 @@ __global__ void export_kernel(const T *__restrict__ f, const NodeMap map, int64_
     // solid nodes carry no state (a dense lattice's solid slots hold values
     // parked by the pushes of fluid neighbours): they read as the rest state
     const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
-    out[p] = kWd[i] + (node < 0 ? 0.0
-                                : static_cast<double>(Stor<T>::ld(f[i * plane + node],
-                                                                  static_cast<C>(inv_scale))));
+    double d = 0.0;
+    if (node >= 0) {
+      uint32_t s[9];
+      map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
+      d = static_cast<double>(Stor<T>::ld(f[s[i]], static_cast<C>(inv_scale)));
+    }
+    out[p] = kWd[i] + d;
   }
 }
 
@@ -235,7 +245,11 @@ __global__ void import_kernel(const double *__restrict__ in, const NodeMap map, 
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = p / n, q = p - i * n, y = q / map.nx, x = q - y * map.nx;
     const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
-    if (node >= 0) f[i * plane + node] = Stor<T>::st(static_cast<C>(in[p] - kWd[i]), static_cast<C>(scale));
+    if (node >= 0) {
+      uint32_t s[9];
+      map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
+      f[s[i]] = Stor<T>::st(static_cast<C>(in[p] - kWd[i]), static_cast<C>(scale));
+    }
   }
 }
 
@@ -247,21 +261,21 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <typename T, typename C>
-cudaError_t launch_step_compact(const T *src, T *dst, const uint2 *node, const int32_t *lbase,
-                                const int32_t *rowstart, const RowTile *tiles, int64_t n_tiles,
-                                const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
-  if (n_tiles <= 0) return cudaSuccess;
-  step_kernel_compact<T, C><<<static_cast<unsigned>(n_tiles), kStepThreads, 0, s>>>(
-      src, dst, node, lbase, rowstart, tiles, links, k);
+cudaError_t launch_step_pull(const T *src, T *dst, const PullGeom &g, int64_t n_fluid,
+                             const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
+  if (n_fluid <= 0) return cudaSuccess;
+  const int64_t blocks = (n_fluid + kPullThreads - 1) / kPullThreads;
+  step_kernel_pull<T, C><<<static_cast<unsigned>(blocks), kPullThreads, 0, s>>>(
+      src, dst, g, static_cast<uint32_t>(n_fluid), links, k);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_residual_compact(const T *cur, const T *prev, int64_t n_fluid, int64_t plane,
-                                    double ax, double ay, double scale, double *partials,
-                                    double *result, cudaStream_t s) {
+cudaError_t launch_residual_compact(const T *cur, const T *prev, const NodeMap &map,
+                                    int64_t n_fluid, int64_t plane, double ax, double ay,
+                                    double scale, double *partials, double *result, cudaStream_t s) {
   residual_partials_compact<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(
-      cur, prev, n_fluid, plane, ax, ay, 1.0 / scale, partials);
+      cur, prev, map, n_fluid, plane, ax, ay, 1.0 / scale, partials);
   residual_final<<<1, kResidualBlocks, 0, s>>>(partials, result);
   return cudaGetLastError();
 }
@@ -302,12 +316,12 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
 }
 
 #define LBM_INSTANTIATE(T, C)                                                                      \
-  template cudaError_t launch_step_compact<T, C>(                                                  \
-      const T *, T *, const uint2 *, const int32_t *, const int32_t *, const RowTile *, int64_t,   \
-      const LinkCoef<C> *, const StepConst<C> &, cudaStream_t);                                    \
-  template cudaError_t launch_residual_compact<T>(const T *, const T *, int64_t, int64_t, double,  \
-                                                  double, double, double *, double *,              \
-                                                  cudaStream_t);                                   \
+  template cudaError_t launch_step_pull<T, C>(const T *, T *, const PullGeom &, int64_t,          \
+                                              const LinkCoef<C> *, const StepConst<C> &,           \
+                                              cudaStream_t);                                       \
+  template cudaError_t launch_residual_compact<T>(const T *, const T *, const NodeMap &, int64_t,  \
+                                                  int64_t, double, double, double, double *,       \
+                                                  double *, cudaStream_t);                         \
   template cudaError_t launch_fields<T>(const T *, const NodeMap &, int64_t, double, double,       \
                                         double, double *, double *, double *, cudaStream_t);       \
   template cudaError_t launch_export_f<T>(const T *, const NodeMap &, int64_t, double, double *,   \

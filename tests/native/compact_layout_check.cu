@@ -1,7 +1,10 @@
 // Host-side check of the compacted lattice (no GPU needed): the library's
-// own build_host_case + build_compact, then compact_targets (the index
-// function the step kernel uses) against the dense neighbourhood for every
-// fluid node and direction, and the row tiles against the fluid nodes.
+// own build_host_case + build_compact, then compact_targets and push_target
+// (the batched push kernel's index functions) against the dense
+// neighbourhood for every fluid node and direction, the row tiles against
+// the fluid nodes, and pull_slots (where the single-case kernels gather
+// and scatter) against the same neighbourhood and the link table: every
+// slot in range and held by exactly one (node, direction).
 // Geometries: walled and periodic channels, a periodic box, 1-wide
 // lattices, random cylinders on every combination of periodic axes, and
 // any lattices given as files (int32 nx, ny, periodic_x, periodic_y, then
@@ -44,8 +47,15 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
                                 ub.data(), ub.data(), 0.05, &p, &hc, &err);
   if (rc) { printf("%s: build_host_case failed: %s\n", name, err.c_str()); return 1; }
   lbm::CompactCase cc;
-  lbm::build_compact(hc, &cc);
+  const std::string cerr = lbm::build_compact(hc, &cc);
+  if (!cerr.empty()) { printf("%s: build_compact failed: %s\n", name, cerr.c_str()); return 1; }
   long bad = 0, checked = 0;
+  const uint32_t P = (uint32_t)cc.plane;
+  const std::vector<uint32_t> jbs = lbm::link_jb_slots(cc, ny, py, hc.n_links);
+  if ((int64_t)jbs.size() != hc.n_links) bad++;
+  const uint64_t n_slots = 9ull * P + (uint64_t)hc.n_links;
+  std::vector<uint8_t> slot_use(n_slots, 0);
+  if (cc.grp.size() != (size_t)((cc.n_fluid + lbm::kGroup - 1) / lbm::kGroup)) bad++;
   std::vector<int> covered(cc.n_fluid, 0);
   for (auto &t : cc.tiles) {
     if (t.count < 1 || t.count > lbm::kStepThreads) bad++;
@@ -65,8 +75,49 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
       const int32_t nb = cc.rowstart[lbm::row_above(y, ny, py)] + (int32_t)(nw.x >> 16);
       const int32_t sb = cc.rowstart[lbm::row_below(y, ny, py)] + (int32_t)(nw.y & 0xFFFFu);
       uint32_t tq[9];
-      lbm::compact_targets(nw.x & 0xFFFFu, i, nb, sb, y, ny, py, cc.rowstart.data(), tq);
+      lbm::compact_targets(nw.x & lbm::kNodeMeta, i, nb, sb, y, ny, py, cc.rowstart.data(), tq);
       uint8_t fl = nw.x & 0xFF;
+      // row and first link from the group record and the node word's offsets
+      const int2 gr = cc.grp[i / lbm::kGroup];
+      if (gr.x + lbm::node_dy(nw) != y) bad++;
+      if (fl && gr.y + (int32_t)lbm::node_loff(nw) != hc.lbase[(size_t)y * hc.pitch + x]) bad++;
+      uint32_t ps[9];
+      lbm::pull_slots(nw, gr, i, P, ny, py, cc.rowstart.data(), ps);
+      if (ps[0] != (uint32_t)i) bad++;
+      int rank = 0;
+      for (int qd = 0; qd < 9; qd++) {
+        if (ps[qd] >= n_slots) { bad++; continue; }
+        if (slot_use[ps[qd]]++) bad++;  // two (node, direction) pairs share a slot
+        if (qd == 0) continue;
+        int xs, ys;
+        const bool src_in = wrapok(x - CX[qd], y - CY[qd], xs, ys);
+        const bool src_fluid = src_in && !solid[ys * nx + xs];
+        if (src_fluid) {
+          if (fl & (1u << (qd - 1))) bad++;
+          if (ps[qd] != (uint32_t)qd * P + (uint32_t)cc.index[ys * nx + xs]) {
+            if (bad < 5) printf("%s: node (%d,%d) gather %d got %u\n", name, x, y, qd, ps[qd]);
+            bad++;
+          }
+        } else {
+          if (!(fl & (1u << (qd - 1)))) bad++;
+          // the link of (x, y, qd) in the table, in direction order within the node
+          const int64_t link = hc.lbase[(size_t)y * hc.pitch + x] + rank;
+          if (ps[qd] != 9u * P + (uint32_t)link) bad++;
+          // the link's f_jb slot: x + c_qd if fluid, else the tail slot of link (x, opp(qd))
+          int xo, yo;
+          const bool opp_in = wrapok(x + CX[qd], y + CY[qd], xo, yo);
+          uint32_t want_jb;
+          if (opp_in && !solid[yo * nx + xo]) {
+            want_jb = (uint32_t)OPP[qd] * P + (uint32_t)cc.index[yo * nx + xo];
+          } else {
+            const int ob = OPP[qd];
+            want_jb = 9u * P + (uint32_t)(hc.lbase[(size_t)y * hc.pitch + x] +
+                                          __builtin_popcount(fl & ((1u << (ob - 1)) - 1u)));
+          }
+          if (jbs[link] != want_jb) bad++;
+          rank++;
+        }
+      }
       if (fl != hc.flags[(size_t)y * hc.pitch + x]) bad++;
       const bool we = px && x == nx - 1, ww = px && x == 0;
       if (((nw.x & lbm::kMetaWrapE) != 0) != we || ((nw.x & lbm::kMetaWrapW) != 0) != ww) bad++;
@@ -79,6 +130,9 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
         if (!fluid_target) continue;
         checked++;
         int32_t want = cc.index[yy * nx + xx];
+        const uint32_t t1 = lbm::push_target(qd, nw.x & lbm::kNodeMeta, i, nb, sb, y, ny, py,
+                                             cc.rowstart.data());
+        if (t1 != tq[qd]) bad++;
         if (tq[qd] != (uint32_t)want || tq[qd] >= (uint32_t)cc.n_fluid) {
           if (bad < 5) printf("%s: node (%d,%d) dir %d got %u want %d\n", name, x, y, qd, tq[qd], want);
           bad++;
@@ -86,6 +140,9 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
       }
       if (cc.lbase[i] != (fl ? hc.lbase[(size_t)y * hc.pitch + x] : 0)) bad++;
     }
+  // every link's tail slot is used (by its own node and direction)
+  for (uint64_t t = 9ull * P; t < n_slots; t++)
+    if (slot_use[t] != 1) bad++;
   printf("%-22s nx %5d ny %5d px %d py %d fluid %8lld tiles %7zu checked %9ld bad %ld\n", name, nx, ny, px, py,
          (long long)cc.n_fluid, cc.tiles.size(), checked, bad);
   return bad != 0;

@@ -141,3 +141,19 @@ def test_batch_create_reports_the_bad_case(lib):
         lbm.Batch([good, bad])
     assert ei.value.code == lbm.LBM_EINVAL
     assert "case 1" in str(ei.value)
+
+
+def test_create_refuses_groups_spanning_too_many_rows(lib):
+    """A node word holds its row as a 14-bit offset from the first row of its
+    group of 32 consecutive fluid nodes: two fluid pockets more than 16383
+    solid rows apart inside one group are refused on the host."""
+    nx, gap = 4, 16384
+    solid = np.ones((gap + 6, nx), np.uint8)
+    solid[2:4, :] = 0            # 8 fluid nodes
+    solid[gap + 3:gap + 5, :] = 0  # 8 more, same group, gap + 1 rows further up
+    lx, ly, li, _, _ = cases._wall_candidates(solid, True, False)
+    c = cases._make_case("pockets", solid, True, False, lx, ly, li, np.full(lx.size, 0.5),
+                         np.zeros(lx.size), np.zeros(lx.size), Kn=0.05, H=2.0)
+    with pytest.raises(lbm.LbmError) as ei:
+        _create(c)
+    assert ei.value.code == lbm.LBM_EINVAL and "16383" in str(ei.value)

@@ -29,6 +29,7 @@ struct lbm_handle {
   uint2 *node = nullptr;  // per fluid node: flags, seam bits, row and link offsets
   int2 *grp = nullptr;    // per group of lbm::kGroup nodes: first row, first link
   uint32_t *jbslot = nullptr;  // per link: slot of f_jb(x, t) (lbm::link_jb_slots)
+  uint32_t pf_dist = 0;        // L2 prefetch distance of the step kernel, in CTAs
   int32_t *rowstart = nullptr;
   int32_t *index = nullptr;  // y * nx + x -> compacted index or -1
   void *links = nullptr;
@@ -100,8 +101,8 @@ void release(lbm_handle_t *h) {
 
 template <typename C>
 lbm::StepConst<C> step_const(const lbm_handle_t *h) {
-  return lbm::make_step_const<C>(h->cp, h->nx, h->ny, 0, h->plane, h->px, h->py, h->ax, h->ay,
-                                 h->params.diffuse_mode, h->scale);
+  return lbm::make_step_const<C>(h->cp, h->nx, h->ny, 0, h->plane, h->n_fluid, h->px, h->py,
+                                 h->ax, h->ay, h->params.diffuse_mode, h->scale);
 }
 
 lbm::PullGeom pull_geom(const lbm_handle_t *h) {
@@ -113,6 +114,8 @@ lbm::PullGeom pull_geom(const lbm_handle_t *h) {
   g.ny = h->ny;
   g.periodic_y = h->py;
   g.plane = static_cast<uint32_t>(h->plane);
+  g.n_fluid = static_cast<uint32_t>(h->n_fluid);
+  g.pf_dist = h->pf_dist;
   return g;
 }
 
@@ -173,7 +176,7 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   if ((static_cast<int64_t>(nx) + 31) / 32 * 32 * ny * 9 >= (int64_t(1) << 31))
     return bad(LBM_EINVAL, "lattice too large: 9 * pitch * ny must stay below 2^31");
   // the compacted lattice keeps offsets within a row in 16 bits
-  if (nx > 65536) return bad(LBM_EINVAL, "rows longer than 65536 nodes are not supported");
+  if (nx > 65535) return bad(LBM_EINVAL, "rows longer than 65535 nodes are not supported");
   if (n_links > static_cast<size_t>(std::numeric_limits<int32_t>::max()))
     return bad(LBM_EINVAL, "too many links");
   const int px = dom->periodic_x ? 1 : 0, py = dom->periodic_y ? 1 : 0;
@@ -400,9 +403,12 @@ std::string build_compact(const HostCase &hc, CompactCase *cc) {
         uint32_t m = hc.flags[static_cast<size_t>(y) * pitch + x];
         if (hc.px && x == nx - 1) m |= kMetaWrapE;
         if (hc.px && x == 0) m |= kMetaWrapW;
-        // offsets within the neighbour rows: at most x < nx <= 65536
-        cc->node[i].x = m | (static_cast<uint32_t>(ahead_n[x]) << 16);
-        cc->node[i].y = static_cast<uint32_t>(ahead_s[x]);
+        // n_lb - i and i - s_lb (see neighbour_rows): at most nx <= 65535
+        const int64_t nl = cc->rowstart[yn] + ahead_n[x], sl = cc->rowstart[ys] + ahead_s[x];
+        const int64_t dn = nl - i + ((hc.py && y == ny - 1) ? n : 0);
+        const int64_t ds = i - sl + ((hc.py && y == 0) ? n : 0);
+        cc->node[i].x = m | (static_cast<uint32_t>(dn) << 16);
+        cc->node[i].y = static_cast<uint32_t>(ds);
         const int32_t lb = hc.lbase[static_cast<size_t>(y) * pitch + x];
         cc->lbase[i] = lb < 0 ? 0 : lb;
         i++;
@@ -463,8 +469,8 @@ std::vector<uint32_t> link_jb_slots(const CompactCase &cc, int ny, int periodic_
       const uint32_t fl = nw.x & 0xFFu;
       if (!fl) continue;
       uint32_t s[9];
-      pull_slots(nw, cc.grp[static_cast<size_t>(i / kGroup)], static_cast<uint32_t>(i), P, ny,
-                 periodic_y, cc.rowstart.data(), s);
+      pull_slots(nw, cc.grp[static_cast<size_t>(i / kGroup)], static_cast<uint32_t>(i), P,
+                 static_cast<uint32_t>(cc.n_fluid), ny, periodic_y, cc.rowstart.data(), s);
       int64_t l = cc.lbase[static_cast<size_t>(i)];
       for (int j = 1; j < 9; j++)
         if (fl & (1u << (j - 1))) out[static_cast<size_t>(l++)] = s[opp[j]];
@@ -558,6 +564,15 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   h->n_fluid = hc.n_fluid;
   h->n_links = hc.n_links;
   cudaGetDevice(&h->device);
+  // half the step kernel's resident CTAs (see lbm::step_kernel_pull)
+  int resident = 0;
+  switch (p.precision) {
+    case LBM_FP64: resident = lbm::pull_resident_ctas<double, double>(); break;
+    case LBM_FP32: resident = lbm::pull_resident_ctas<float, float>(); break;
+    case LBM_BF16: resident = lbm::pull_resident_ctas<__nv_bfloat16, float>(); break;
+    default: resident = lbm::pull_resident_ctas<__half, float>(); break;
+  }
+  h->pf_dist = static_cast<uint32_t>(resident / 2);
 
   const size_t es = elem_size(p.precision);
   // nine planes, then the link tail (rounded up to whole 128-byte lines)

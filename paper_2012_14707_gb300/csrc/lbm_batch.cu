@@ -409,8 +409,8 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     auto put = [&](auto tag) {
       using C = decltype(tag);
       lbm::BatchCase<C> d;
-      d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, 0, k.plane, h.px, h.py, h.ax, h.ay,
-                                    h.params.diffuse_mode, h.scale);
+      d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, 0, k.plane, h.n_fluid, h.px, h.py, h.ax,
+                                    h.ay, h.params.diffuse_mode, h.scale);
       d.f_off = 9 * noff;
       d.node_off = noff;
       d.row_off = roff;

@@ -208,8 +208,8 @@ __device__ __forceinline__ void step_node_compact(
 #pragma unroll
   for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[q * P + i], k.inv_sc);
   const int lb = fl ? lbase[i] : 0;
-  const uint32_t nb = static_cast<uint32_t>(rowstart[row_above(y, k.ny, k.periodic_y)]) + (nw.x >> 16);
-  const uint32_t sb = static_cast<uint32_t>(rowstart[row_below(y, k.ny, k.periodic_y)]) + (nw.y & 0xFFFFu);
+  uint32_t nb, sb;
+  neighbour_rows(nw, i, static_cast<uint32_t>(k.n_fluid), y, k.ny, k.periodic_y, nb, sb);
   Collided<T, C> c;
   collide<T, C>(d, k, c);
   // Targets x + c_q.  bit (j - 1) of fl set <=> x - c_j solid, so x + c_q is
@@ -228,44 +228,28 @@ __device__ __forceinline__ void step_node_compact(
   link_epilogue<T, C>(dst + i, P, fl, lb, links, src + i, c, k);
 }
 
-// Loads that the compiler must issue where they stand (not merged with an
-// earlier load of the same address and kept in registers meanwhile).
-__device__ __forceinline__ uint2 reload_u2(const uint2 *p) {
-  uint2 v;
-  asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ int2 reload_i2(const int2 *p) {
-  int2 v;
-  asm volatile("ld.global.nc.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-  return v;
-}
-
-// The unknown populations of boundary node i for the next step (bits of
-// its flag byte), Eq. EqNewBDSC in the folded form of LinkCoef, written to
-// the link tail of dst (pull layout, see pull_slots): link k of the table
-// has tail element 9 P + k.  Inputs: the node's post-collision state c and
+// The unknown populations of a boundary node for the next step (bits of
+// fl, its flag byte; li is its first link), Eq. EqNewBDSC in the folded
+// form of LinkCoef, written to the link tail of dst (pull layout, see
+// pull_slots): link k of the table has tail element 9 P + k.  The link
+// records and jbslot entries were prefetched before the collision.
+// Inputs: the node's post-collision state c and
 // its pre-collision f_jb(x, t), gathered again from src at the slot the
 // link's jbslot entry names (a cache hit; fewer live registers than
 // keeping nine values through the collision).  Directions that no active
 // lane of the warp needs are skipped warp-uniformly.
 template <typename T, typename C>
 __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T *__restrict__ dst,
-                                                   const PullGeom &g, const uint32_t i,
+                                                   const PullGeom &g, const uint32_t fl,
+                                                   const uint32_t li,
                                                    const LinkCoef<C> *__restrict__ links,
                                                    const Collided<T, C> &c_,
                                                    const StepConst<C> &k) {
-  // the node word and group record again (cache hits), not kept live
-  // through the collision
-  const uint2 nw = reload_u2(g.node + i);
-  const uint8_t fl = static_cast<uint8_t>(nw.x & 0xFFu);
-  const unsigned wmask = __reduce_or_sync(__activemask(), static_cast<unsigned>(fl));
+  const unsigned wmask = __reduce_or_sync(__activemask(), fl);
   if (!wmask) return;
-  const int2 gr = reload_i2(g.grp + i / kGroup);
   const C(&o)[9] = c_.o;
   const C drho = c_.drho, rho = c_.rho, ux = c_.ux, uy = c_.uy, uu = c_.uu;
   const uint32_t tail = 9u * g.plane;
-  const uint32_t li = static_cast<uint32_t>(gr.y) + node_loff(nw);  // the node's first link
 #pragma unroll
   for (int j = 1; j < 9; j++) {
     if (!(wmask & (1u << (j - 1)))) continue;
@@ -313,18 +297,22 @@ __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__r
   C d[9];
   {
     uint32_t s[9];
-    pull_slots(nw, gr, i, P, g.ny, g.periodic_y, g.rowstart, s);
+    pull_slots(nw, gr, i, P, g.n_fluid, g.ny, g.periodic_y, g.rowstart, s);
 #pragma unroll
     for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[s[q]], k.inv_sc);
     // the link records are read after the collision: start fetching them now
-    if (nw.x & 0xFFu)
+    if (nw.x & 0xFFu) {
       asm volatile("prefetch.global.L1 [%0];" ::"l"(links + gr.y + node_loff(nw)));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.jbslot + gr.y + node_loff(nw)));
+    }
   }
   Collided<T, C> c;
   collide<T, C>(d, k, c);
 #pragma unroll
   for (int q = 0; q < 9; q++) dst[q * P + i] = c.t[q];
-  link_epilogue_pull<T, C>(src, dst, g, i, links, c, k);
+  // flag byte and first link (li) of the node
+  link_epilogue_pull<T, C>(src, dst, g, nw.x & 0xFFu,
+                           static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k);
 }
 
 // Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).

@@ -29,6 +29,7 @@ struct StepConst {
   int32_t nx, ny, pitch;        // lattice size; row pitch (unused by the compacted lattice)
   int32_t periodic_x, periodic_y;
   int32_t diffuse_mode;         // reading of the Maxwell part, see LinkCoef
+  int32_t n_fluid;              // fluid nodes (compacted lattice)
   int64_t plane;                // elements per population plane (padded fluid-node count)
 };
 
@@ -93,6 +94,17 @@ __host__ __device__ inline int row_above(int y, int ny, int periodic_y) {
 }
 __host__ __device__ inline int row_below(int y, int ny, int periodic_y) {
   return y > 0 ? y - 1 : (periodic_y ? ny - 1 : y);
+}
+
+// n_lb and s_lb of fluid node i in row y (see CompactCase) from its node
+// word, which holds n_lb - i and i - s_lb, each plus the fluid count n
+// where the row above (below) is reached across a periodic y axis: both
+// are then in [0, nx], and no row table is read.
+__host__ __device__ inline void neighbour_rows(uint2 nw, uint32_t i, uint32_t n, int y, int ny,
+                                               int periodic_y, uint32_t &nb, uint32_t &sb) {
+  const uint32_t dn = nw.x >> 16, ds = nw.y & 0xFFFFu;
+  nb = i + dn - ((periodic_y && y == ny - 1) ? n : 0u);
+  sb = i - ds + ((periodic_y && y == 0) ? n : 0u);
 }
 
 // Compacted indices of the push targets x + c_q (q = 1..8, tq[0] = i) of
@@ -171,16 +183,18 @@ struct PullGeom {
   const uint32_t *jbslot = nullptr; // per link (x, j): pull slot of f_jb(x) (link_jb_slots)
   int32_t ny = 0, periodic_y = 0;
   uint32_t plane = 0;               // P
+  uint32_t n_fluid = 0;
+  uint32_t pf_dist = 0;             // step kernel: CTAs ahead whose data it prefetches to L2
 };
 
 // s[q] = element of the pre-collision f_q of fluid node i, q = 0..8.
-__host__ __device__ inline void pull_slots(uint2 nw, int2 grp, uint32_t i, uint32_t P, int ny,
-                                           int periodic_y, const int32_t *rowstart,
-                                           uint32_t (&s)[9]) {
+__host__ __device__ inline void pull_slots(uint2 nw, int2 grp, uint32_t i, uint32_t P,
+                                           uint32_t n_fluid, int ny, int periodic_y,
+                                           const int32_t *rowstart, uint32_t (&s)[9]) {
   const uint32_t m = nw.x & kNodeMeta;
   const int y = grp.x + node_dy(nw);
-  const uint32_t nb = static_cast<uint32_t>(rowstart[row_above(y, ny, periodic_y)]) + (nw.x >> 16);
-  const uint32_t sb = static_cast<uint32_t>(rowstart[row_below(y, ny, periodic_y)]) + (nw.y & 0xFFFFu);
+  uint32_t nb, sb;
+  neighbour_rows(nw, i, n_fluid, y, ny, periodic_y, nb, sb);
   uint32_t tq[9];
   compact_targets(m, i, nb, sb, y, ny, periodic_y, rowstart, tq);
   uint32_t li = 9u * P + static_cast<uint32_t>(grp.y) + node_loff(nw);
@@ -210,8 +224,8 @@ struct NodeMap {
   }
   __host__ __device__ void slots(uint32_t i, uint32_t plane, uint32_t (&s)[9]) const {
     if (pull.node) {
-      pull_slots(pull.node[i], pull.grp[i / kGroup], i, plane, pull.ny, pull.periodic_y,
-                 pull.rowstart, s);
+      pull_slots(pull.node[i], pull.grp[i / kGroup], i, plane, pull.n_fluid, pull.ny,
+                 pull.periodic_y, pull.rowstart, s);
     } else {
       for (int q = 0; q < 9; q++) s[q] = static_cast<uint32_t>(q) * plane + i;
     }
@@ -230,13 +244,13 @@ struct RowTile {
 //            .x bits 0..7   flag byte (bit q - 1: x - c_q solid)
 //               bits 8, 9   kMetaWrapE / kMetaWrapW (periodic seam of x)
 //               bits 10..15 row offset dy from the group's row, low 6 bits
-//               bits 16..31 n_lb - rowstart[y+1]
-//            .y bits 0..15  s_lb - rowstart[y-1]
+//               bits 16..31 n_lb - i (+ n_fluid across a periodic y axis)
+//            .y bits 0..15  i - s_lb (+ n_fluid across a periodic y axis)
 //               bits 16..23 first link of the node - first link of its group
 //               bits 24..31 dy, high 8 bits
 //            n_lb / s_lb = compacted index of the first fluid node at or
-//            after (x, y+1) / (x, y-1) (rows wrapped where periodic); the
-//            offsets within the neighbour rows are < nx <= 65536
+//            after (x, y+1) / (x, y-1) (rows wrapped where periodic); both
+//            differences are at most nx <= 65535 (neighbour_rows)
 //   grp      one record per group of kGroup consecutive nodes (node i is in
 //            group i / kGroup): .x = row of the group's first node,
 //            .y = first link of the group's first node with links; a group
@@ -265,8 +279,8 @@ std::vector<uint32_t> link_jb_slots(const CompactCase &cc, int ny, int periodic_
 // Kernel constants of one case in arithmetic type C.
 template <typename C>
 StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32_t pitch,
-                             int64_t plane, int32_t px, int32_t py, double ax, double ay,
-                             int32_t diffuse_mode, double scale) {
+                             int64_t plane, int64_t n_fluid, int32_t px, int32_t py, double ax,
+                             double ay, int32_t diffuse_mode, double scale) {
   StepConst<C> k;
   k.s_e = static_cast<C>(1.0 / cp.tau_e);
   k.s_eps = static_cast<C>(1.0 / cp.tau_eps);
@@ -289,6 +303,7 @@ StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32
   k.periodic_y = py;
   k.diffuse_mode = diffuse_mode;
   k.plane = plane;
+  k.n_fluid = static_cast<int32_t>(n_fluid);
   return k;
 }
 
@@ -351,6 +366,9 @@ struct PullOcc {
 };
 
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
+// CTAs of step_kernel_pull<T, C> resident at once on the current device.
+template <typename T, typename C>
+int pull_resident_ctas();
 template <typename T, typename C>
 cudaError_t launch_step_pull(const T *src, T *dst, const PullGeom &g, int64_t n_fluid,
                              const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s);

@@ -27,11 +27,42 @@ using namespace dev;
 
 // One time step of a single case (pull layout): thread t of CTA b runs
 // fluid node b * kPullThreads + t.
+//
+// Each node waits out two dependent memory latencies (its node word, then
+// the gathers it addresses), which 64 warps per SM do not hide.  So every
+// CTA first asks L2 for the data of the CTA g.pf_dist blocks ahead (half
+// the CTAs resident at once: it starts about half a CTA lifetime from now
+// on some SM): its node words, group record and own slots in the nine
+// planes.  A prefetch holds no register and never waits; the later loads
+// then find their lines in L2 (the gathers from the rows above and below
+// mostly hit lines that the neighbouring rows' CTAs brought in).
 template <typename T, typename C>
 __global__ void __launch_bounds__(kPullThreads, PullOcc<T>::min_blocks)
 step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom g,
                  const uint32_t n_fluid, const LinkCoef<C> *__restrict__ links,
                  const StepConst<C> k) {
+  {
+    constexpr uint32_t kNodeLines = kPullThreads * sizeof(uint2) / 128;
+    constexpr uint32_t kPlaneLines = kPullThreads * sizeof(T) / 128;
+    constexpr uint32_t kPerLine = 128 / sizeof(T);
+    const uint32_t base = (blockIdx.x + g.pf_dist) * kPullThreads;
+    const uint32_t t = threadIdx.x;
+    // whole warps: the others skip the block without diverging
+    constexpr uint32_t kPfThreads = (kNodeLines + 9 * kPlaneLines + 1 + 31) / 32 * 32;
+    static_assert(kPfThreads <= kPullThreads, "one prefetch per thread");
+    if (t < kPfThreads && g.pf_dist && base < n_fluid) {
+      if (t < kNodeLines) {
+        if (base + t * 16 < n_fluid)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(g.node + base + t * 16));
+      } else if (t < kNodeLines + 9 * kPlaneLines) {
+        const uint32_t q = (t - kNodeLines) / kPlaneLines, l = (t - kNodeLines) % kPlaneLines;
+        if (base + l * kPerLine < n_fluid)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + q * g.plane + base + l * kPerLine));
+      } else if (t == kNodeLines + 9 * kPlaneLines) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(g.grp + base / kGroup));
+      }
+    }
+  }
   const uint32_t i = blockIdx.x * kPullThreads + threadIdx.x;
   if (i >= n_fluid) return;
   step_node_pull<T, C>(src, dst, g, links, k, i);
@@ -261,6 +292,17 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <typename T, typename C>
+int pull_resident_ctas() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_pull<T, C>, kPullThreads, 0) !=
+          cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
+template <typename T, typename C>
 cudaError_t launch_step_pull(const T *src, T *dst, const PullGeom &g, int64_t n_fluid,
                              const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
   if (n_fluid <= 0) return cudaSuccess;
@@ -316,6 +358,7 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
 }
 
 #define LBM_INSTANTIATE(T, C)                                                                      \
+  template int pull_resident_ctas<T, C>();                                                         \
   template cudaError_t launch_step_pull<T, C>(const T *, T *, const PullGeom &, int64_t,          \
                                               const LinkCoef<C> *, const StepConst<C> &,           \
                                               cudaStream_t);                                       \

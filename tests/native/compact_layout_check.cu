@@ -72,8 +72,19 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
       if (i < 0) continue;
       // decode the 8-byte node word as the kernel does
       const uint2 nw = cc.node[i];
-      const int32_t nb = cc.rowstart[lbm::row_above(y, ny, py)] + (int32_t)(nw.x >> 16);
-      const int32_t sb = cc.rowstart[lbm::row_below(y, ny, py)] + (int32_t)(nw.y & 0xFFFFu);
+      uint32_t nb, sb;
+      lbm::neighbour_rows(nw, (uint32_t)i, (uint32_t)cc.n_fluid, y, ny, py, nb, sb);
+      // n_lb / s_lb by definition: first fluid node at or after (x, y +- 1)
+      {
+        const int yn = lbm::row_above(y, ny, py), ys = lbm::row_below(y, ny, py);
+        int32_t wn = cc.rowstart[yn + 1], ws = cc.rowstart[ys + 1];
+        for (int xx = nx - 1; xx >= x; xx--) {
+          if (cc.index[yn * nx + xx] >= 0) wn = cc.index[yn * nx + xx];
+          if (cc.index[ys * nx + xx] >= 0) ws = cc.index[ys * nx + xx];
+        }
+        if (nb != (uint32_t)wn || sb != (uint32_t)ws) bad++;
+        if ((nw.x >> 16) > (uint32_t)nx || (nw.y & 0xFFFFu) > (uint32_t)nx) bad++;
+      }
       uint32_t tq[9];
       lbm::compact_targets(nw.x & lbm::kNodeMeta, i, nb, sb, y, ny, py, cc.rowstart.data(), tq);
       uint8_t fl = nw.x & 0xFF;
@@ -82,7 +93,7 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
       if (gr.x + lbm::node_dy(nw) != y) bad++;
       if (fl && gr.y + (int32_t)lbm::node_loff(nw) != hc.lbase[(size_t)y * hc.pitch + x]) bad++;
       uint32_t ps[9];
-      lbm::pull_slots(nw, gr, i, P, ny, py, cc.rowstart.data(), ps);
+      lbm::pull_slots(nw, gr, i, P, (uint32_t)cc.n_fluid, ny, py, cc.rowstart.data(), ps);
       if (ps[0] != (uint32_t)i) bad++;
       int rank = 0;
       for (int qd = 0; qd < 9; qd++) {

@@ -120,7 +120,7 @@ void lbm_params_default(lbm_params_t *p);
  * state starts at rest, f_i = w_i (rho = 1, u = 0).  The device copy keeps
  * the fluid nodes only (row-major, with per-node neighbour offsets), so its
  * size follows the fluid fraction, not nx*ny.  Limits of that layout, each
- * LBM_EINVAL: rows of at most 65536 nodes (nx <= 65536); 9 x fluid nodes +
+ * LBM_EINVAL: rows of at most 65535 nodes (nx <= 65535); 9 x fluid nodes +
  * links below 2^32; no 32 consecutive fluid nodes (row-major order) spread
  * over more than 16384 rows.  On success *out holds
  * the handle; on failure *out is NULL and the returned code says why

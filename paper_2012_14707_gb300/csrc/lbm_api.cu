@@ -175,7 +175,7 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   // 32-bit element offsets in the kernels: 9 planes of the padded lattice < 2^31.
   if ((static_cast<int64_t>(nx) + 31) / 32 * 32 * ny * 9 >= (int64_t(1) << 31))
     return bad(LBM_EINVAL, "lattice too large: 9 * pitch * ny must stay below 2^31");
-  // the compacted lattice keeps offsets within a row in 16 bits
+  // the node word keeps n_lb - i and i - s_lb (at most nx) in 16 bits
   if (nx > 65535) return bad(LBM_EINVAL, "rows longer than 65535 nodes are not supported");
   if (n_links > static_cast<size_t>(std::numeric_limits<int32_t>::max()))
     return bad(LBM_EINVAL, "too many links");

@@ -40,9 +40,14 @@ struct Stor<__nv_bfloat16> {
 
 template <typename C>
 __device__ __forceinline__ C recip(C v);
+// FP32: the hardware approximation (within one unit in the last place; rho
+// is near 1, and u enters f_eq far below the resolution of the stored
+// deviations at that level).
 template <>
 __device__ __forceinline__ float recip<float>(float v) {
-  return __frcp_rn(v);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
 }
 template <>
 __device__ __forceinline__ double recip<double>(double v) {
@@ -65,19 +70,19 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   C(&o)[9] = r.o;
   T(&t)[9] = r.t;
   // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
-  const C s14 = (d[1] + d[2]) + (d[3] + d[4]);
-  const C s58 = (d[5] + d[6]) + (d[7] + d[8]);
-  const C drho = d[0] + s14 + s58;
-  const C e = C(-4) * d[0] - s14 + C(2) * s58;
-  const C eps = C(4) * d[0] - C(2) * s14 + s58;
-  const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
+  const C a13 = d[1] + d[3], a24 = d[2] + d[4];
   const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
-  const C jx = d[1] - d[3] + d5m6 + d8m7;
-  const C qx = C(2) * (d[3] - d[1]) + d5m6 + d8m7;
-  const C jy = d[2] - d[4] + d5p6 - d7p8;
-  const C qy = C(2) * (d[4] - d[2]) + d5p6 - d7p8;
-  const C pxx = d[1] - d[2] + d[3] - d[4];
-  const C pxy = d[5] - d[6] + d[7] - d[8];
+  const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
+  const C s14 = a13 + a24, s58 = d5p6 + d7p8;
+  const C drho = (d[0] + s14) + s58;
+  const C e = C(2) * s58 + (C(-4) * d[0] - s14);
+  const C eps = C(-2) * s14 + (C(4) * d[0] + s58);
+  const C u13 = d[1] - d[3], t58 = d5m6 + d8m7;
+  const C v24 = d[2] - d[4], w58 = d5p6 - d7p8;
+  const C jx = u13 + t58, qx = C(-2) * u13 + t58;
+  const C jy = v24 + w58, qy = C(-2) * v24 + w58;
+  const C pxx = a13 - a24;
+  const C pxy = d5m6 - d8m7;
 
   // Eq. FluidMacr.
   const C rho = C(1) + drho;
@@ -88,49 +93,54 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   const C uu = ux * ux + uy * uy;
   const C rux = rho * ux, ruy = rho * uy;
 
-  // Eq. MomentPost: m' = m - S (m - m_eq) + (I - S/2) M Fbar, with M f_eq
-  // and M Fbar in closed form; the factors (1 - s/2) come precomputed.
+  // Eq. MomentPost, m' = m - S (m - m_eq) + (I - S/2) M Fbar, applied as
+  // the change f' - f = M^-1 (m' - m): the collision moves f by little, and
+  // adding that small change to the stored d_i rounds f'_i once (building
+  // f' from the full moments costs several roundings of |f| instead; in
+  // FP32 that bias adds up over thousands of steps).  M f_eq and M Fbar in
+  // closed form; each row of m' - m is already scaled by its entry of
+  // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) (the
+  // constants k.e2 .. k.y3 fold s and 1 - s/2 with that scale).  Mass does
+  // not change; momentum changes by rho a exactly, for any s_j, since
+  // rho u = j + rho a / 2.
   const C ua6 = C(6) * (rux * k.ax + ruy * k.ay);
-  const C e_p = e - k.s_e * (e + C(2) * drho - C(3) * rho * uu) + k.h_e * ua6;
-  const C eps_p = eps - k.s_eps * (eps - drho + C(3) * rho * uu) - k.h_eps * ua6;
-  const C jx_p = jx - k.s_j * (jx - rux) + k.h_j * rax;
-  const C jy_p = jy - k.s_j * (jy - ruy) + k.h_j * ray;
-  const C qx_p = qx - k.s_q * (qx + rux) - k.h_q * rax;
-  const C qy_p = qy - k.s_q * (qy + ruy) - k.h_q * ray;
-  const C pxx_p = pxx - k.s_s * (pxx - rho * (ux * ux - uy * uy)) +
-                  k.h_s * C(2) * (rux * k.ax - ruy * k.ay);
-  const C pxy_p = pxy - k.s_s * (pxy - rho * ux * uy) + k.h_s * (rux * k.ay + ruy * k.ax);
+  const C w3 = C(3) * rho * uu;
+  const C e36 = k.e3 * ua6 - k.e2 * (e + C(2) * drho - w3);
+  const C p36 = -k.p2 * (eps - drho + w3) - k.p3 * ua6;
+  const C jx6 = rax * C(1.0 / 6.0), jy6 = ray * C(1.0 / 6.0);
+  const C qx12 = -k.q2 * (qx + rux) - k.q3 * rax;
+  const C qy12 = -k.q2 * (qy + ruy) - k.q3 * ray;
+  const C xx4 = k.x3 * (rux * k.ax - ruy * k.ay) - k.x2 * (pxx - rho * (ux * ux - uy * uy));
+  const C xy4 = k.y3 * (rux * k.ay + ruy * k.ax) - k.x2 * (pxy - rho * ux * uy);
 
-  // f' = M^-1 m' with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
-  const C r9 = drho * C(1.0 / 9.0);
-  const C e36 = e_p * C(1.0 / 36.0), p36 = eps_p * C(1.0 / 36.0);
-  const C jx6 = jx_p * C(1.0 / 6.0), jy6 = jy_p * C(1.0 / 6.0);
-  const C qx12 = qx_p * C(1.0 / 12.0), qy12 = qy_p * C(1.0 / 12.0);
-  const C xx4 = pxx_p * C(0.25), xy4 = pxy_p * C(0.25);
-  const C axis = r9 - e36 - C(2) * p36;
-  const C diag = r9 + C(2) * e36 + p36;
+  // f' - f = M^-1 (m' - m).
+  const C axis = -e36 - C(2) * p36;
+  const C diag = C(2) * e36 + p36;
   const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
   const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
-  o[1] = axis + ax_x + xx4;
-  o[2] = axis + ax_y - xx4;
-  o[3] = axis - ax_x + xx4;
-  o[4] = axis - ax_y - xx4;
-  o[5] = diag + dg_x + dg_y + xy4;
-  o[6] = diag - dg_x + dg_y - xy4;
-  o[7] = diag - dg_x - dg_y + xy4;
-  o[8] = diag + dg_x - dg_y - xy4;
-  // The rest population closes the mass balance: M^-1 m' conserves sum f
-  // exactly only in exact arithmetic, so f'_0 = drho - sum_{i>0} f'_i
-  // (equal to r9 - 4 e36 + 4 p36 up to rounding) keeps the stored mass
-  // unchanged by the collision to within one rounding of f'_0.
-  // Round f'_1..f'_8 to storage first (a no-op for FP32/FP64), so that the
-  // closure below balances the values actually stored.
+  o[1] = d[1] + (axis + ax_x + xx4);
+  o[2] = d[2] + (axis + ax_y - xx4);
+  o[3] = d[3] + (axis - ax_x + xx4);
+  o[4] = d[4] + (axis - ax_y - xx4);
+  o[5] = d[5] + (diag + dg_x + dg_y + xy4);
+  o[6] = d[6] + (diag - dg_x + dg_y - xy4);
+  o[7] = d[7] + (diag - dg_x - dg_y + xy4);
+  o[8] = d[8] + (diag + dg_x - dg_y - xy4);
+  // The rest population closes the mass balance (M^-1 m' conserves sum f
+  // only in exact arithmetic).  Round f'_1..f'_8 to storage first (a no-op
+  // for FP32/FP64), then take their changes f'_i - f_i as stored: each is
+  // the difference of two nearby values of the storage grid, exact (or
+  // off by a unit of the small change), and so is their small sum.  So
+  // f'_0 = f_0 - sum_{i>0} (f'_i - f_i) changes the stored mass by the one
+  // rounding of f'_0 -- not by roundings of the sums of the full |f|.
+  C dd[9];
 #pragma unroll
   for (int i = 1; i < 9; i++) {
     t[i] = Stor<T>::st(o[i], k.sc);
     o[i] = Stor<T>::ld(t[i], k.inv_sc);
+    dd[i] = o[i] - d[i];
   }
-  o[0] = drho - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+  o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
   t[0] = Stor<T>::st(o[0], k.sc);
 
   r.drho = drho;

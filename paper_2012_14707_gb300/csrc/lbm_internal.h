@@ -22,8 +22,12 @@ constexpr uint8_t kSolid = 0xFF;
 // Relaxation rates and forcing of one case, as the kernels consume them.
 template <typename C>
 struct StepConst {
-  C s_e, s_eps, s_q, s_s, s_j;  // 1/tau of the non-conserved moments and of j
-  C h_e, h_eps, h_q, h_s, h_j;  // 1 - s/2: weights of the forcing moments (Eq. MomentPost)
+  // Relaxation rates s = 1/tau of e, eps, q and the stress (p_xx, p_xy),
+  // as the collide function consumes them: s and the forcing weight 1 - s/2
+  // (Eq. MomentPost), each times the moment's entry of
+  // diag(1/36, 1/36, 1/12, 1/4) in M^-1 (x3 = 2 (1 - s_s/2) / 4).  The
+  // momentum rows need no rate (collide).
+  C e2, e3, p2, p3, q2, q3, x2, x3, y3;
   C sc, inv_sc;                 // storage scale of the 16-bit types (1 otherwise)
   C ax, ay;                     // body acceleration
   int32_t nx, ny, pitch;        // lattice size; row pitch (unused by the compacted lattice)
@@ -282,16 +286,19 @@ StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32
                              int64_t plane, int64_t n_fluid, int32_t px, int32_t py, double ax,
                              double ay, int32_t diffuse_mode, double scale) {
   StepConst<C> k;
-  k.s_e = static_cast<C>(1.0 / cp.tau_e);
-  k.s_eps = static_cast<C>(1.0 / cp.tau_eps);
-  k.s_q = static_cast<C>(1.0 / cp.tau_q);
-  k.s_s = static_cast<C>(1.0 / cp.tau_s);
-  k.s_j = static_cast<C>(1.0 / cp.tau_j);
-  k.h_e = static_cast<C>(1.0 - 0.5 / cp.tau_e);
-  k.h_eps = static_cast<C>(1.0 - 0.5 / cp.tau_eps);
-  k.h_q = static_cast<C>(1.0 - 0.5 / cp.tau_q);
-  k.h_s = static_cast<C>(1.0 - 0.5 / cp.tau_s);
-  k.h_j = static_cast<C>(1.0 - 0.5 / cp.tau_j);
+  {
+    const double se = 1.0 / cp.tau_e, sp = 1.0 / cp.tau_eps, sq = 1.0 / cp.tau_q,
+                 ss = 1.0 / cp.tau_s;
+    k.e2 = static_cast<C>(se / 36.0);
+    k.e3 = static_cast<C>((1.0 - 0.5 * se) / 36.0);
+    k.p2 = static_cast<C>(sp / 36.0);
+    k.p3 = static_cast<C>((1.0 - 0.5 * sp) / 36.0);
+    k.q2 = static_cast<C>(sq / 12.0);
+    k.q3 = static_cast<C>((1.0 - 0.5 * sq) / 12.0);
+    k.x2 = static_cast<C>(ss / 4.0);
+    k.x3 = static_cast<C>((1.0 - 0.5 * ss) / 2.0);
+    k.y3 = static_cast<C>((1.0 - 0.5 * ss) / 4.0);
+  }
   k.sc = static_cast<C>(scale);
   k.inv_sc = static_cast<C>(1.0 / scale);
   k.ax = static_cast<C>(ax);

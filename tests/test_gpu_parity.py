@@ -114,19 +114,21 @@ def test_fp64_scheme_variants_match_oracle(l_mode, extra):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp32_velocity_and_mass_match_oracle(name):
-    """From rest, 2000 steps.  Velocity rel. L2 <= 1e-5 everywhere.  Mass
-    drift against the oracle trajectory: <= 1e-10 with stationary walls.
-    Moving walls (u_b ~ 0.03 and 0.01 here) exchange mass with the fluid
-    every step in tiny net amounts (~1e-8 per link and step) computed from
-    wall populations of size ~1e-3; their FP32 rounding is the same every
-    step once the flow is steady, so it adds up linearly (1.4e-8 relative
-    after 2000 steps on the 9-row channel): held to 3e-8.  The periodic
-    boxes accelerate without bound (u ~ 0.04): held to 1e-8."""
+    """From rest, 2000 steps.  Velocity rel. L2 <= 1e-5 everywhere (measured
+    5e-8 to 6e-7: the collision adds its small change to the stored
+    deviations).  Mass drift against the oracle trajectory: <= 1e-10 with
+    stationary walls.  Moving walls (u_b ~ 0.03 and 0.01 here) exchange
+    mass with the fluid every step in tiny net amounts (~1e-8 per link and
+    step) computed from wall populations of size ~1e-3; their FP32 rounding
+    is the same every step once the flow is steady, so it adds up linearly
+    (up to 9e-9 relative after 2000 steps): held to 3e-8.  The periodic
+    boxes accelerate without bound (u ~ 0.04; measured up to 3.6e-10): held
+    to 1e-9."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
     o, g = _pair(c, "fp32", **kw)
     m0 = o.residual()[1]
-    mass_tol = {"box": 1e-8, "column": 1e-8, "row": 1e-8, "annulus": 3e-8,
+    mass_tol = {"box": 1e-9, "column": 1e-9, "row": 1e-9, "annulus": 3e-8,
                 "channel_moving": 3e-8}.get(name, 1e-10)
     for n in (500, 1500):
         o.step(n)

@@ -157,3 +157,23 @@ def test_create_refuses_groups_spanning_too_many_rows(lib):
     with pytest.raises(lbm.LbmError) as ei:
         _create(c)
     assert ei.value.code == lbm.LBM_EINVAL and "16383" in str(ei.value)
+
+
+def test_create_refuses_rows_longer_than_65535(lib):
+    """The node word holds n_lb - i and i - s_lb, each at most nx, in 16 bits."""
+    for nx, ok in ((65536, False), (65535, True)):
+        solid = np.ones((3, nx), np.uint8)
+        solid[1, :] = 0
+        lx, ly, li, _, _ = cases._wall_candidates(solid, True, False)
+        c = cases._make_case("long_row", solid, True, False, lx, ly, li, np.full(lx.size, 0.5),
+                             np.zeros(lx.size), np.zeros(lx.size), Kn=0.05, H=1.0)
+        if ok:
+            # host validation passes; only the device part may fail without a GPU
+            try:
+                lbm.lbm_destroy(_create(c))
+            except lbm.LbmError as e:
+                assert e.code != lbm.LBM_EINVAL, str(e)
+        else:
+            with pytest.raises(lbm.LbmError) as ei:
+                _create(c)
+            assert ei.value.code == lbm.LBM_EINVAL and "65535" in str(ei.value)

@@ -451,10 +451,6 @@ std::string build_compact(const HostCase &hc, CompactCase *cc) {
     if (b)
       return "more than 16383 solid rows between two fluid nodes " + std::to_string(kGroup) +
              " places apart in row-major order";
-  cc->tiles.clear();
-  for (int32_t y = 0; y < ny; y++)
-    for (int32_t c = cc->rowstart[y]; c < cc->rowstart[y + 1]; c += kStepThreads)
-      cc->tiles.push_back(RowTile{y, c, std::min<int32_t>(kStepThreads, cc->rowstart[y + 1] - c), 0});
   return std::string();
 }
 

@@ -1,16 +1,18 @@
 // Batched solver of liblbm.so (lbm_batch_*): many independent cases of
 // different sizes, geometries and parameters advanced together.
 //
-// All cases live in one device arena (each case's compacted lattice: two
-// lattices of its nine deviation planes over its fluid nodes, node words,
-// neighbour indices, link bases and link coefficients) and share one tile
-// list: a tile is a run of fluid nodes of one row of one case.  A time step is one
-// launch over all tiles; a CTA looks up its case's constants in a
-// descriptor table and runs the same per-node update as the single-case
-// kernel (so a case in a batch follows exactly the arithmetic of the case
-// run alone).  Every K steps a batched reduction (one CTA per case, fixed
+// All cases live in one device arena (each case's compacted lattice in the
+// pull layout of pull_slots: two lattices of its nine deviation planes over
+// its fluid nodes plus its link tail, node words, group records, row
+// starts, link coefficients and f_jb slots).  In the node arena every
+// case starts on a multiple of kChunk nodes, so a CTA of the step launch
+// (at most kChunk threads) runs nodes of one case only, found in a
+// per-chunk case index: a time step is one launch over the whole node
+// arena; a CTA looks up its case's constants in a descriptor table and runs
+// the single-case kernel's per-node update (step_node_pull), so a case in a
+// batch follows exactly the arithmetic of the case run alone.  Every K steps a batched reduction (one CTA per case, fixed
 // order) computes each case's residual and retires converged cases on the
-// device; retired cases' tiles return immediately.  K steps plus the
+// device; retired cases' CTAs return immediately.  K steps plus the
 // reduction are captured once in a CUDA graph that the host replays, reading
 // back only the number of active cases.  The CTA width is picked by timing
 // the candidates on the batch itself (autotuner), cached per size class and
@@ -35,40 +37,74 @@ namespace {
 using namespace dev;
 
 // One case in the arenas: its compacted lattice (see CompactCase) at these
-// offsets; link bases already global (case link offset added).
+// offsets.  Indices inside a case (pull slots, links) are the case's own.
 template <typename C>
 struct BatchCase {
   StepConst<C> k;    // plane = the case's padded fluid-node count
-  int64_t f_off;     // element offset of the case's plane 0 in a lattice arena
-  int64_t node_off;  // offset of the case in the node-word / link-base arenas
+  int64_t f_off;     // element offset of the case's lattice (9 planes + link tail)
+  int64_t node_off;  // offset of the case in the node-word arena (a multiple of kChunk)
+  int64_t grp_off;   // offset of the case's group records
   int64_t row_off;   // offset of the case's rowstart
   int64_t idx_off;   // offset of the case's node map (nx * ny)
+  int64_t link_off;  // offset of the case's links (coefficients, f_jb slots)
   int64_t n_fluid;
 };
 
-// A row tile of one case: rows y, compacted indices start .. start + count - 1.
-struct Tile {
-  int32_t c, y, start, count;
-};
+// The pull geometry of case bc inside the arenas.
+template <typename C>
+__host__ __device__ inline PullGeom case_geom(const BatchCase<C> &bc, const uint2 *node,
+                                              const int2 *grp, const int32_t *rowstart,
+                                              const uint32_t *jbslot) {
+  PullGeom g;
+  g.node = node + bc.node_off;
+  g.grp = grp + bc.grp_off;
+  g.rowstart = rowstart + bc.row_off;
+  g.jbslot = jbslot ? jbslot + bc.link_off : nullptr;
+  g.ny = bc.k.ny;
+  g.periodic_y = bc.k.periodic_y;
+  g.plane = static_cast<uint32_t>(bc.k.plane);
+  g.n_fluid = static_cast<uint32_t>(bc.n_fluid);
+  g.pf_dist = 0;
+  return g;
+}
+
 
 constexpr int kBatchResidualThreads = 256;
+constexpr int kChunk = 256;  // node-arena alignment of every case (>= any CTA width)
 
 // Registers bounded like the single-case kernel (the same resident threads
-// per SM).
+// per SM).  CTA b runs node-arena entries b * THREADS .. b * THREADS +
+// THREADS - 1, all of case ccase[b * THREADS / kChunk] (the index is
+// CTA-uniform, so the case's constants stay out of the per-thread
+// registers).  Like the single-case kernel, each CTA first asks L2 for the
+// node words and case index of the CTA pf_dist blocks ahead.
 template <typename T, typename C, int THREADS>
 __global__ void __launch_bounds__(THREADS, StepOcc<T>::min_blocks * kStepThreads / THREADS)
 batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
-                  const uint2 *__restrict__ node, const int32_t *__restrict__ lbase,
-                  const int32_t *__restrict__ rowstart, const LinkCoef<C> *__restrict__ links,
-                  const BatchCase<C> *__restrict__ cases, const Tile *__restrict__ tiles,
-                  const int32_t *__restrict__ active) {
-  const Tile t = tiles[blockIdx.x];
-  if (!active[t.c] || static_cast<int>(threadIdx.x) >= t.count) return;
-  const BatchCase<C> &bc = cases[t.c];
-  const int64_t no = bc.node_off;
-  step_node_compact<T, C>(src + bc.f_off, dst + bc.f_off, node + no, lbase + no,
-                          rowstart + bc.row_off, links, bc.k,
-                          static_cast<uint32_t>(t.start) + threadIdx.x, t.y);
+                  const uint2 *__restrict__ node, const int2 *__restrict__ grp,
+                  const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,
+                  const uint32_t *__restrict__ jbslot, const LinkCoef<C> *__restrict__ links,
+                  const BatchCase<C> *__restrict__ cases, const int32_t *__restrict__ active,
+                  const uint32_t n_blocks, const uint32_t pf_dist) {
+  static_assert(kChunk % THREADS == 0, "a CTA stays inside one chunk");
+  {
+    constexpr uint32_t kNodeLines = THREADS * sizeof(uint2) / 128;
+    const uint32_t b2 = blockIdx.x + pf_dist;
+    const uint32_t t = threadIdx.x;
+    if (pf_dist && t < 32 && b2 < n_blocks) {
+      if (t < kNodeLines)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(node + b2 * THREADS + t * 16));
+      else if (t == kNodeLines)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ccase + b2 * THREADS / kChunk));
+    }
+  }
+  const int c = ccase[blockIdx.x * THREADS / kChunk];
+  if (!active[c]) return;
+  const BatchCase<C> &bc = cases[c];
+  const uint32_t i = blockIdx.x * THREADS + threadIdx.x - static_cast<uint32_t>(bc.node_off);
+  if (i >= static_cast<uint32_t>(bc.n_fluid)) return;
+  const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot);
+  step_node_pull<T, C>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i);
 }
 
 // One CTA per case: residual of the case (FP64 sums in a fixed order); a
@@ -78,6 +114,8 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
 template <typename T, typename C>
 __global__ void __launch_bounds__(kBatchResidualThreads)
 batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
+                      const uint2 *__restrict__ node, const int2 *__restrict__ grp,
+                      const int32_t *__restrict__ rowstart,
                       const BatchCase<C> *__restrict__ cases,
                       int32_t *__restrict__ active, double tol, const int64_t *__restrict__ counter,
                       int64_t K, int64_t *__restrict__ steps_done, double *__restrict__ res_out,
@@ -88,14 +126,18 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
   const StepConst<C> k = bc.k;
   const T *a_base = cur + bc.f_off;
   const T *b_base = prev + bc.f_off;
+  NodeMap map;
+  map.pull = case_geom(bc, node, grp, rowstart, static_cast<const uint32_t *>(nullptr));
   double num = 0.0, den = 0.0, bad = 0.0;
   {
-    for (int64_t node = threadIdx.x; node < bc.n_fluid; node += blockDim.x) {
+    for (int64_t i = threadIdx.x; i < bc.n_fluid; i += blockDim.x) {
+      uint32_t s[9];
+      map.slots(static_cast<uint32_t>(i), static_cast<uint32_t>(k.plane), s);
       C a[9], b[9];
 #pragma unroll
-      for (int i = 0; i < 9; i++) {
-        a[i] = Stor<T>::ld(a_base[i * k.plane + node], k.inv_sc);
-        b[i] = Stor<T>::ld(b_base[i * k.plane + node], k.inv_sc);
+      for (int q = 0; q < 9; q++) {
+        a[q] = Stor<T>::ld(a_base[s[q]], k.inv_sc);
+        b[q] = Stor<T>::ld(b_base[s[q]], k.inv_sc);
       }
       C n1, d1, m1;
       residual_terms<C>(a, b, k.ax, k.ay, n1, d1, m1);
@@ -140,20 +182,39 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
 __global__ void batch_advance(int64_t *counter, int64_t K) { *counter += K; }
 
 template <typename T, typename C, int THREADS>
-cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int32_t *lbase,
-                              const int32_t *rowstart,
-                              const void *links, const void *cases, const Tile *tiles,
-                              int n_tiles, const int32_t *active, cudaStream_t s) {
-  if (n_tiles <= 0) return cudaSuccess;
-  batch_step_kernel<T, C, THREADS><<<n_tiles, THREADS, 0, s>>>(
-      src, dst, node, lbase, rowstart, static_cast<const LinkCoef<C> *>(links),
-      static_cast<const BatchCase<C> *>(cases), tiles, active);
+cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int2 *grp,
+                              const int32_t *ccase, const int32_t *rowstart,
+                              const uint32_t *jbslot, const void *links, const void *cases,
+                              const int32_t *active, int64_t arena_nodes, uint32_t pf_dist,
+                              cudaStream_t s) {
+  if (arena_nodes <= 0) return cudaSuccess;
+  const int64_t blocks = arena_nodes / THREADS;  // arena_nodes: a multiple of kChunk
+  batch_step_kernel<T, C, THREADS><<<static_cast<unsigned>(blocks), THREADS, 0, s>>>(
+      src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<C> *>(links),
+      static_cast<const BatchCase<C> *>(cases), active, static_cast<uint32_t>(blocks), pf_dist);
   return cudaGetLastError();
 }
 
-// Autotuner cache: CTA width per (precision, size class = floor(log2 nodes)).
+// CTAs of batch_step_kernel<T, C, THREADS> resident at once on the current device.
+template <typename T, typename C, int THREADS>
+int batch_resident_ctas() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<T, C, THREADS>,
+                                                    THREADS, 0) != cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
+// Autotuner cache: CTA width and prefetch distance per (precision, size
+// class = floor(log2 nodes)).
+struct TuneChoice {
+  int threads;
+  uint32_t pf_dist;
+};
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tune_cache;
+std::map<std::pair<int, int>, TuneChoice> g_tune_cache;
 
 }  // namespace
 }  // namespace lbm
@@ -164,19 +225,21 @@ struct lbm_batch {
   bool own_stream = false;
   int n_cases = 0;
   std::vector<int32_t> nx, ny;
-  std::vector<int64_t> f_off, node_off, idx_off, plane, n_fluid;
-  std::vector<std::vector<int32_t>> rowstart_h;  // per case, for the tile lists
+  std::vector<int64_t> f_off, node_off, grp_off, row_off, idx_off, plane, n_fluid;
   std::vector<double> ax, ay, scale, tau_s;
   std::vector<int32_t> px, py;
   void *f[2] = {nullptr, nullptr};
   uint2 *node = nullptr;
-  int32_t *lbase = nullptr, *rowstart = nullptr;
+  int2 *grp = nullptr;
+  int32_t *ccase = nullptr;  // per kChunk node-arena entries: their case
+  int64_t arena_nodes = 0;   // node-arena entries (cases padded to kChunk)
+  int32_t *rowstart = nullptr;
+  uint32_t *jbslot = nullptr;
   int32_t *index = nullptr;
   void *links = nullptr;
   void *cases = nullptr;
-  lbm::Tile *tiles = nullptr;
-  int n_tiles = 0;
   int threads = 0;
+  uint32_t pf_dist = 0;  // L2 prefetch distance of the step kernel (CTAs), for `threads`
   int32_t *active = nullptr;
   int64_t *steps_done = nullptr;
   double *res = nullptr;
@@ -189,7 +252,7 @@ struct lbm_batch {
   int cur = 0;
   int64_t steps = 0;
   int64_t total_nodes = 0, total_fluid = 0;
-  int64_t arena_nodes = 0;  // padded nodes of all cases (one plane each)
+  int64_t arena_elems = 0;  // elements of one lattice arena (all cases' planes and link tails)
   std::string err;
 };
 
@@ -216,22 +279,17 @@ lbm::NodeMap case_map(const lbm_batch_t *b, int c) {
   m.index = b->index + b->idx_off[c];
   m.nx = b->nx[c];
   m.ny = b->ny[c];
+  m.pull.node = b->node + b->node_off[c];
+  m.pull.grp = b->grp + b->grp_off[c];
+  m.pull.rowstart = b->rowstart + b->row_off[c];
+  m.pull.ny = b->ny[c];
+  m.pull.periodic_y = b->py[c];
+  m.pull.plane = static_cast<uint32_t>(b->plane[c]);
+  m.pull.n_fluid = static_cast<uint32_t>(b->n_fluid[c]);
   return m;
 }
 
-// Row tiles of `threads` fluid nodes (the CTA width) over every case.
-std::vector<lbm::Tile> make_tiles(const lbm_batch_t *b, int threads) {
-  std::vector<lbm::Tile> t;
-  for (int c = 0; c < b->n_cases; c++) {
-    const std::vector<int32_t> &rs = b->rowstart_h[c];
-    for (int y = 0; y < b->ny[c]; y++)
-      for (int32_t i = rs[y]; i < rs[y + 1]; i += threads)
-        t.push_back(lbm::Tile{c, y, i, std::min<int32_t>(threads, rs[y + 1] - i)});
-  }
-  return t;
-}
-
-cudaError_t step_once(lbm_batch_t *b, int threads, const lbm::Tile *tiles, int n_tiles, int src) {
+cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src) {
   const int dst = 1 - src;
   return dispatch_b(b->precision, [&](auto tT, auto tC) {
     using T = std::remove_pointer_t<decltype(tT)>;
@@ -239,8 +297,9 @@ cudaError_t step_once(lbm_batch_t *b, int threads, const lbm::Tile *tiles, int n
     auto go = [&](auto kernel_threads) {
       constexpr int TH = decltype(kernel_threads)::value;
       return lbm::launch_batch_step<T, C, TH>(
-          static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->node, b->lbase,
-          b->rowstart, b->links, b->cases, tiles, n_tiles, b->active, b->stream);
+          static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->node, b->grp,
+          b->ccase, b->rowstart, b->jbslot, b->links, b->cases, b->active, b->arena_nodes,
+          pf_dist, b->stream);
     };
     if (threads == 64) return go(std::integral_constant<int, 64>());
     if (threads == 128) return go(std::integral_constant<int, 128>());
@@ -257,8 +316,8 @@ void batch_release(lbm_batch_t *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->node), static_cast<void *>(b->lbase),
-                  static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->tiles), static_cast<void *>(b->active),
+  for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->node), static_cast<void *>(b->grp),
+                  static_cast<void *>(b->jbslot), static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->ccase), static_cast<void *>(b->active),
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active)})
     if (p) cudaFree(p);
@@ -267,10 +326,25 @@ void batch_release(lbm_batch_t *b) {
   delete b;
 }
 
-// Autotuner: times each candidate CTA width for a few steps of the batch
-// itself (from rest; the caller resets the state afterwards) and keeps the
-// fastest, cached per (precision, size class).
-int autotune(lbm_batch_t *b) {
+// CTAs of the step kernel resident at once for this precision and width.
+int resident_ctas(int precision, int threads) {
+  int r = 0;
+  dispatch_b(precision, [&](auto tT, auto tC) {
+    using T = std::remove_pointer_t<decltype(tT)>;
+    using C = std::remove_pointer_t<decltype(tC)>;
+    if (threads == 64) r = lbm::batch_resident_ctas<T, C, 64>();
+    else if (threads == 128) r = lbm::batch_resident_ctas<T, C, 128>();
+    else r = lbm::batch_resident_ctas<T, C, 256>();
+    return cudaSuccess;
+  });
+  return r;
+}
+
+// Autotuner: times each candidate (CTA width; L2 prefetch off or half the
+// resident CTAs ahead) for a few steps of the batch itself (from rest; the
+// caller resets the state afterwards) and keeps the fastest, cached per
+// (precision, size class).
+lbm::TuneChoice autotune(lbm_batch_t *b) {
   const int size_class = static_cast<int>(std::log2(static_cast<double>(b->total_nodes) + 1.0));
   {
     std::lock_guard<std::mutex> lock(lbm::g_tune_mu);
@@ -279,26 +353,24 @@ int autotune(lbm_batch_t *b) {
   }
   const int cand[3] = {64, 128, 256};
   float best_ms = std::numeric_limits<float>::infinity();
-  int best = 256;
+  lbm::TuneChoice best{128, 0};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   for (int th : cand) {
-    std::vector<lbm::Tile> t = make_tiles(b, th);
-    lbm::Tile *dt = nullptr;
-    if (cudaMalloc(&dt, t.size() * sizeof(lbm::Tile)) != cudaSuccess) continue;
-    cudaMemcpy(dt, t.data(), t.size() * sizeof(lbm::Tile), cudaMemcpyHostToDevice);
-    for (int w = 0; w < 2; w++) step_once(b, th, dt, static_cast<int>(t.size()), w & 1);
-    cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < 6; r++) step_once(b, th, dt, static_cast<int>(t.size()), r & 1);
-    cudaEventRecord(e1, b->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaFree(dt);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = th;
+    const uint32_t half = static_cast<uint32_t>(resident_ctas(b->precision, th) / 2);
+    for (uint32_t pf : {0u, half}) {
+      for (int w = 0; w < 2; w++) step_once(b, th, pf, w & 1);
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 6; r++) step_once(b, th, pf, r & 1);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = lbm::TuneChoice{th, pf};
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -326,7 +398,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   }
   std::vector<lbm::HostCase> hc(static_cast<size_t>(n_cases));
   std::vector<lbm::CompactCase> cc(static_cast<size_t>(n_cases));
-  int64_t nodes = 0, links = 0, rows = 0, dense = 0;
+  int64_t nodes = 0, elems = 0, groups = 0, links = 0, rows = 0, dense = 0;
   for (int c = 0; c < n_cases; c++) {
     lbm_params_t p = cases[c].params;
     p.precision = precision;
@@ -339,15 +411,19 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       g_batch_error = "case " + std::to_string(c) + ": " + msg;
       return rc;
     }
-    // the arena's push layout reads no group offsets, so a case whose node
-    // words cannot hold them (more than 16383 solid rows in a row) is fine here
-    (void)lbm::build_compact(hc[c], &cc[c]);
-    nodes += cc[c].plane;
+    const std::string cerr = lbm::build_compact(hc[c], &cc[c]);
+    if (!cerr.empty()) {
+      g_batch_error = "case " + std::to_string(c) + ": " + cerr;
+      return LBM_EINVAL;
+    }
+    nodes += (std::max<int64_t>(cc[c].n_fluid, 1) + lbm::kChunk - 1) / lbm::kChunk * lbm::kChunk;
+    elems += 9 * cc[c].plane + (hc[c].n_links + 31) / 32 * 32;
+    groups += static_cast<int64_t>(cc[c].grp.size());
     links += hc[c].n_links;
     rows += hc[c].ny + 1;
     dense += static_cast<int64_t>(hc[c].nx) * hc[c].ny;
   }
-  if (nodes * 9 >= (int64_t(1) << 40) || links >= (int64_t(1) << 31)) {
+  if (elems >= (int64_t(1) << 40) || links >= (int64_t(1) << 31)) {
     g_batch_error = "batch too large";
     return LBM_EINVAL;
   }
@@ -367,18 +443,22 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   const size_t es = elem_size_b(precision);
   const size_t ces = precision == LBM_FP64 ? 8 : 4;
   std::vector<uint2> node(static_cast<size_t>(nodes), uint2{0u, 0u});
-  std::vector<int32_t> lbase(static_cast<size_t>(nodes), 0), rowstart(static_cast<size_t>(rows), 0),
-      index(static_cast<size_t>(dense), -1);
+  std::vector<int2> grp(static_cast<size_t>(std::max<int64_t>(1, groups)), int2{0, 0});
+  std::vector<int32_t> ccase(static_cast<size_t>(std::max<int64_t>(1, nodes / lbm::kChunk)), 0);
+  std::vector<uint32_t> jbs(static_cast<size_t>(std::max<int64_t>(1, links)), 0u);
+  std::vector<int32_t> rowstart(static_cast<size_t>(rows), 0), index(static_cast<size_t>(dense), -1);
   std::vector<unsigned char> lhost(std::max<int64_t>(1, links) * 4 * ces, 0);
   std::vector<unsigned char> chost;
-  int64_t noff = 0, loff = 0, roff = 0, ioff = 0;
+  int64_t noff = 0, foff = 0, goff = 0, loff = 0, roff = 0, ioff = 0;
   for (int c = 0; c < n_cases; c++) {
     const lbm::HostCase &h = hc[c];
     lbm::CompactCase &k = cc[c];
     b->nx.push_back(h.nx);
     b->ny.push_back(h.ny);
-    b->f_off.push_back(9 * noff);
+    b->f_off.push_back(foff);
     b->node_off.push_back(noff);
+    b->grp_off.push_back(goff);
+    b->row_off.push_back(roff);
     b->idx_off.push_back(ioff);
     b->plane.push_back(k.plane);
     b->n_fluid.push_back(h.n_fluid);
@@ -391,8 +471,13 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     b->total_nodes += static_cast<int64_t>(h.nx) * h.ny;
     b->total_fluid += h.n_fluid;
     std::copy(k.node.begin(), k.node.end(), node.begin() + noff);
-    for (size_t q = 0; q < k.lbase.size(); q++)
-      lbase[noff + q] = static_cast<int32_t>(k.lbase[q] + loff);
+    std::copy(k.grp.begin(), k.grp.end(), grp.begin() + goff);
+    // (at least one chunk: the case's node words, `plane` of them, fit)
+    const int64_t padded =
+        (std::max<int64_t>(k.n_fluid, 1) + lbm::kChunk - 1) / lbm::kChunk * lbm::kChunk;
+    std::fill(ccase.begin() + noff / lbm::kChunk, ccase.begin() + (noff + padded) / lbm::kChunk, c);
+    const std::vector<uint32_t> kj = lbm::link_jb_slots(k, h.ny, h.py, h.n_links);
+    std::copy(kj.begin(), kj.end(), jbs.begin() + loff);
     std::copy(k.rowstart.begin(), k.rowstart.end(), rowstart.begin() + roff);
     std::copy(k.index.begin(), k.index.end(), index.begin() + ioff);
     for (int64_t q = 0; q < h.n_links; q++) {
@@ -411,10 +496,12 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       lbm::BatchCase<C> d;
       d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, 0, k.plane, h.n_fluid, h.px, h.py, h.ax,
                                     h.ay, h.params.diffuse_mode, h.scale);
-      d.f_off = 9 * noff;
+      d.f_off = foff;
       d.node_off = noff;
+      d.grp_off = goff;
       d.row_off = roff;
       d.idx_off = ioff;
+      d.link_off = loff;
       d.n_fluid = h.n_fluid;
       const unsigned char *p = reinterpret_cast<const unsigned char *>(&d);
       chost.insert(chost.end(), p, p + sizeof(d));
@@ -423,21 +510,24 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       put(double());
     else
       put(float());
-    b->rowstart_h.push_back(k.rowstart);
-    noff += k.plane;
+    noff += padded;
+    foff += 9 * k.plane + (h.n_links + 31) / 32 * 32;
+    goff += static_cast<int64_t>(k.grp.size());
     loff += h.n_links;
     roff += h.ny + 1;
     ioff += static_cast<int64_t>(h.nx) * h.ny;
   }
   hc.clear();
   cc.clear();
-  b->arena_nodes = nodes;
+  b->arena_elems = elems;
   auto alloc = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
-  const size_t fbytes = 9 * static_cast<size_t>(nodes) * es;
+  const size_t fbytes = static_cast<size_t>(elems) * es;
   if (e == cudaSuccess) e = alloc(&b->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&b->f[1], fbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->node), node.size() * sizeof(uint2));
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->lbase), lbase.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->grp), grp.size() * sizeof(int2));
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->ccase), ccase.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->jbslot), jbs.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->rowstart), rowstart.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->index), index.size() * 4);
   if (e == cudaSuccess) e = alloc(&b->links, lhost.size());
@@ -452,7 +542,10 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
   };
   up(b->node, node.data(), node.size() * sizeof(uint2));
-  up(b->lbase, lbase.data(), lbase.size() * 4);
+  up(b->grp, grp.data(), grp.size() * sizeof(int2));
+  up(b->ccase, ccase.data(), ccase.size() * 4);
+  b->arena_nodes = nodes;
+  up(b->jbslot, jbs.data(), jbs.size() * 4);
   up(b->rowstart, rowstart.data(), rowstart.size() * 4);
   up(b->index, index.data(), index.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(b->links, lhost.data(), lhost.size(), cudaMemcpyHostToDevice);
@@ -464,15 +557,12 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     if (e == cudaSuccess) e = cudaMemset(b->f[0], 0, fbytes);
     if (e == cudaSuccess) e = cudaMemset(b->f[1], 0, fbytes);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) b->threads = autotune(b);
+    if (e == cudaSuccess) {
+      const lbm::TuneChoice t = autotune(b);
+      b->threads = t.threads;
+      b->pf_dist = t.pf_dist;
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) {
-    std::vector<lbm::Tile> t = make_tiles(b, b->threads);
-    b->n_tiles = static_cast<int>(t.size());
-    e = alloc(reinterpret_cast<void **>(&b->tiles), t.size() * sizeof(lbm::Tile));
-    if (e == cudaSuccess)
-      e = cudaMemcpy(b->tiles, t.data(), t.size() * sizeof(lbm::Tile), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = lbm_batch_reset(b) == LBM_OK ? cudaSuccess : cudaErrorUnknown;
   if (e != cudaSuccess) {
@@ -487,7 +577,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
 
 int lbm_batch_reset(lbm_batch_t *b) {
   if (!b) return LBM_EINVAL;
-  const size_t fbytes = 9 * static_cast<size_t>(b->arena_nodes) * elem_size_b(b->precision);
+  const size_t fbytes = static_cast<size_t>(b->arena_elems) * elem_size_b(b->precision);
   std::vector<int32_t> ones(b->n_cases, 1);
   std::vector<int64_t> zeros(b->n_cases, 0);
   const int32_t n = b->n_cases;
@@ -523,14 +613,15 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     for (int s = 0; s < check_every && e == cudaSuccess; s++)
-      e = step_once(b, b->threads, b->tiles, b->n_tiles, s & 1);
+      e = step_once(b, b->threads, b->pf_dist, s & 1);
     if (e == cudaSuccess)
       e = dispatch_b(b->precision, [&](auto tT, auto tC) {
         using T = std::remove_pointer_t<decltype(tT)>;
         using C = std::remove_pointer_t<decltype(tC)>;
         lbm::batch_residual_kernel<T, C><<<b->n_cases, lbm::kBatchResidualThreads, 0, b->stream>>>(
-            static_cast<const T *>(b->f[0]), static_cast<const T *>(b->f[1]),
-            static_cast<const lbm::BatchCase<C> *>(b->cases), b->active, tol, b->counter,
+            static_cast<const T *>(b->f[0]), static_cast<const T *>(b->f[1]), b->node, b->grp,
+            b->rowstart, static_cast<const lbm::BatchCase<C> *>(b->cases), b->active, tol,
+            b->counter,
             check_every, b->steps_done, b->res, b->n_active);
         return cudaGetLastError();
       });
@@ -626,7 +717,7 @@ int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fl
   if (total_nodes) *total_nodes = b->total_nodes;
   if (total_fluid) *total_fluid = b->total_fluid;
   if (cta_threads) *cta_threads = b->threads;
-  if (n_tiles) *n_tiles = b->n_tiles;
+  if (n_tiles) *n_tiles = static_cast<int32_t>(b->arena_nodes / b->threads);
   return LBM_OK;
 }
 

@@ -150,94 +150,6 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   r.uu = uu;
 }
 
-// The unknown populations of a boundary node (bits of fl), Eq. EqNewBDSC in
-// the folded form of LinkCoef, from the node's own pre-collision deviations
-// (src_node[j * P], read again here rather than kept in registers through
-// the collision: a cache hit, and fewer live registers for every node) and
-// post-collision state c; records links[lb], links[lb + 1], ... in
-// direction order.  Written to dst_node[j * P].  Directions that no active
-// lane of the warp needs are skipped warp-uniformly.
-template <typename T, typename C>
-__device__ __forceinline__ void link_epilogue(T *__restrict__ dst_node, const uint32_t P,
-                                              const uint8_t fl, const int lb,
-                                              const LinkCoef<C> *__restrict__ links,
-                                              const T *__restrict__ src_node,
-                                              const Collided<T, C> &c_, const StepConst<C> &k) {
-  const C(&o)[9] = c_.o;
-  const C drho = c_.drho, rho = c_.rho, ux = c_.ux, uy = c_.uy, uu = c_.uu;
-  // Boundary links of this node, Eq. EqNewBDSC in the folded form of
-  // LinkCoef.  Directions that no active lane of the warp needs are
-  // skipped warp-uniformly (solid lanes and lanes past nx have left).
-  const unsigned wmask = __reduce_or_sync(__activemask(), static_cast<unsigned>(fl));
-  if (wmask) {
-    int li = lb;
-#pragma unroll
-    for (int j = 1; j < 9; j++) {
-      if (!(wmask & (1u << (j - 1)))) continue;
-      if (fl & (1u << (j - 1))) {
-        constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-        constexpr int cx_tab[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-        constexpr int cy_tab[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-        constexpr double w_tab[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                                     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-        const int jb = opp_tab[j];
-        const LinkCoef<C> c = links[li++];
-        const C r = c.k1 + c.k2 + c.k3;
-        C c0, c2;
-        if (k.diffuse_mode == 0) {
-          c0 = c.alpha;
-          c2 = (C(1) - r) * C(w_tab[j]);
-        } else {
-          c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
-          c2 = C(0);
-        }
-        const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
-        const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-        const C djb = Stor<T>::ld(src_node[jb * P], k.inv_sc);
-        const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
-                    c2 * (drho + rho * pj);
-        dst_node[j * P] = Stor<T>::st(v, k.sc);
-      }
-    }
-  }
-}
-
-// One time step for fluid node i (row y) of a compacted lattice (see
-// CompactCase): load, collide, push f'_q to every
-// fluid target x + c_q (compact_targets), link epilogue.
-template <typename T, typename C>
-__device__ __forceinline__ void step_node_compact(
-    const T *__restrict__ src, T *__restrict__ dst, const uint2 *__restrict__ node,
-    const int32_t *__restrict__ lbase, const int32_t *__restrict__ rowstart,
-    const LinkCoef<C> *__restrict__ links, const StepConst<C> &k, const uint32_t i, const int y) {
-  const uint32_t P = static_cast<uint32_t>(k.plane);
-  const uint2 nw = node[i];  // one 8-byte load: flags, seam bits, neighbour-row offsets
-  const uint32_t m = nw.x & kNodeMeta;
-  const uint8_t fl = static_cast<uint8_t>(m & 0xFFu);
-  C d[9];
-#pragma unroll
-  for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[q * P + i], k.inv_sc);
-  const int lb = fl ? lbase[i] : 0;
-  uint32_t nb, sb;
-  neighbour_rows(nw, i, static_cast<uint32_t>(k.n_fluid), y, k.ny, k.periodic_y, nb, sb);
-  Collided<T, C> c;
-  collide<T, C>(d, k, c);
-  // Targets x + c_q.  bit (j - 1) of fl set <=> x - c_j solid, so x + c_q is
-  // fluid iff bit (opp(q) - 1) is clear; a solid target has no slot.
-  uint32_t tq[9];
-  compact_targets(m, i, nb, sb, y, k.ny, k.periodic_y, rowstart, tq);
-  dst[i] = c.t[0];
-  if (!(fl & (1u << 2))) dst[1 * P + tq[1]] = c.t[1];  // opp(1) = 3
-  if (!(fl & (1u << 3))) dst[2 * P + tq[2]] = c.t[2];  // opp(2) = 4
-  if (!(fl & (1u << 0))) dst[3 * P + tq[3]] = c.t[3];  // opp(3) = 1
-  if (!(fl & (1u << 1))) dst[4 * P + tq[4]] = c.t[4];  // opp(4) = 2
-  if (!(fl & (1u << 6))) dst[5 * P + tq[5]] = c.t[5];  // opp(5) = 7
-  if (!(fl & (1u << 7))) dst[6 * P + tq[6]] = c.t[6];  // opp(6) = 8
-  if (!(fl & (1u << 4))) dst[7 * P + tq[7]] = c.t[7];  // opp(7) = 5
-  if (!(fl & (1u << 5))) dst[8 * P + tq[8]] = c.t[8];  // opp(8) = 6
-  link_epilogue<T, C>(dst + i, P, fl, lb, links, src + i, c, k);
-}
-
 // The unknown populations of a boundary node for the next step (bits of
 // fl, its flag byte; li is its first link), Eq. EqNewBDSC in the folded
 // form of LinkCoef, written to the link tail of dst (pull layout, see
@@ -292,10 +204,10 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
   }
 }
 
-// One time step for fluid node i of a single-case lattice in the pull
-// layout (pull_slots): gather f(x, t) (streaming, Sec. 2), collide
-// (collide), store f'(x, t) in the node's own slots of dst, then the link
-// epilogue.  The arithmetic is the push kernel's, value for value.
+// One time step for fluid node i of a lattice in the pull layout
+// (pull_slots): gather f(x, t) (streaming, Sec. 2), collide (collide),
+// store f'(x, t) in the node's own slots of dst, then the link epilogue.
+// Used by the single-case and the batched step kernels alike.
 template <typename T, typename C>
 __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                const PullGeom &g,

@@ -236,11 +236,6 @@ struct NodeMap {
   }
 };
 
-// A run of at most kStepThreads consecutive fluid nodes of one row of a
-// compacted lattice: row y, compacted indices start .. start + count - 1.
-struct RowTile {
-  int32_t y, start, count, pad;
-};
 
 // Compacted lattice of one case (host copy): only fluid nodes, in
 // row-major order, each population plane padded to `plane` elements.
@@ -263,13 +258,11 @@ struct RowTile {
 //   lbase    first link of the node (links sorted by node, then direction)
 //   rowstart compacted index of every row's first fluid node (ny + 1)
 //   index    y * nx + x -> compacted index or -1 (conversions only)
-//   tiles    row tiles of the batched solver's push kernel
 struct CompactCase {
   int64_t n_fluid = 0, plane = 0;
   std::vector<int32_t> lbase, rowstart, index;
   std::vector<uint2> node;
   std::vector<int2> grp;
-  std::vector<RowTile> tiles;
 };
 // Returns "" or the reason the case does not fit the node word.
 std::string build_compact(const HostCase &hc, CompactCase *cc);

@@ -1,10 +1,10 @@
 // Host-side check of the compacted lattice (no GPU needed): the library's
-// own build_host_case + build_compact, then compact_targets and push_target
-// (the batched push kernel's index functions) against the dense
-// neighbourhood for every fluid node and direction, the row tiles against
-// the fluid nodes, and pull_slots (where the single-case kernels gather
-// and scatter) against the same neighbourhood and the link table: every
-// slot in range and held by exactly one (node, direction).
+// own build_host_case + build_compact, then the node word's neighbour rows,
+// compact_targets and push_target against the dense neighbourhood for
+// every fluid node and direction, and pull_slots (where the step kernels
+// gather and the conversions scatter) against the same neighbourhood and
+// the link table: every slot in range and held by exactly one (node,
+// direction); the f_jb slot of every link.
 // Geometries: walled and periodic channels, a periodic box, 1-wide
 // lattices, random cylinders on every combination of periodic axes, and
 // any lattices given as files (int32 nx, ny, periodic_x, periodic_y, then
@@ -56,16 +56,6 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
   const uint64_t n_slots = 9ull * P + (uint64_t)hc.n_links;
   std::vector<uint8_t> slot_use(n_slots, 0);
   if (cc.grp.size() != (size_t)((cc.n_fluid + lbm::kGroup - 1) / lbm::kGroup)) bad++;
-  std::vector<int> covered(cc.n_fluid, 0);
-  for (auto &t : cc.tiles) {
-    if (t.count < 1 || t.count > lbm::kStepThreads) bad++;
-    for (int k = 0; k < t.count; k++) {
-      int64_t i = t.start + k;
-      if (i < cc.rowstart[t.y] || i >= cc.rowstart[t.y + 1]) bad++;
-      else covered[i]++;
-    }
-  }
-  for (auto c : covered) if (c != 1) bad++;
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       int32_t i = cc.index[y * nx + x];
@@ -154,8 +144,8 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
   // every link's tail slot is used (by its own node and direction)
   for (uint64_t t = 9ull * P; t < n_slots; t++)
     if (slot_use[t] != 1) bad++;
-  printf("%-22s nx %5d ny %5d px %d py %d fluid %8lld tiles %7zu checked %9ld bad %ld\n", name, nx, ny, px, py,
-         (long long)cc.n_fluid, cc.tiles.size(), checked, bad);
+  printf("%-22s nx %5d ny %5d px %d py %d fluid %8lld links %8lld checked %9ld bad %ld\n", name, nx, ny,
+         px, py, (long long)cc.n_fluid, (long long)hc.n_links, checked, bad);
   return bad != 0;
 }
 int main(int argc, char **argv) {

@@ -1,9 +1,11 @@
 """The compacted lattice's index arithmetic, checked on the host (no GPU):
 tests/native/compact_layout_check.cu links the library, builds each case's
-compacted layout with the library's own code, and compares the push targets
-the step kernel computes (compact_targets) with the dense neighbourhood, for
-every fluid node and direction; the row tiles must cover every fluid node
-once.  A wrong target would be a silent out-of-bounds write on the GPU."""
+compacted layout with the library's own code, and compares the neighbour
+indices the step kernels compute (compact_targets, push_target) and the
+pull slots they gather from (pull_slots, the per-link f_jb slots) with the
+dense neighbourhood and the link table, for every fluid node and
+direction.  A wrong index would be a silent out-of-bounds access on the
+GPU."""
 import os
 import shutil
 import subprocess

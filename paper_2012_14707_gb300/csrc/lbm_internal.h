@@ -401,7 +401,7 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
                             T *f, cudaStream_t s);
 
 // Fixed reduction geometry: deterministic partial order on every device.
-constexpr int kResidualBlocks = 1024;
+constexpr int kResidualBlocks = 4096;
 constexpr int kResidualThreads = 256;
 constexpr int kPartialStride = 4;  // num, den, mass deviation, non-finite count
 

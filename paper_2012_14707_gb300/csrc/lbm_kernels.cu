@@ -68,6 +68,36 @@ step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom 
   step_node_pull<T, C>(src, dst, g, links, k, i);
 }
 
+// Error-free sum of two FP32 values: s + e == a + b exactly (Knuth's
+// TwoSum; no multiplication, so nothing is contracted into an FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Mass deviation of one node, sum_i d_i, to FP64 accuracy.  FP64 storage:
+// the plain FP64 sum.  FP32 arithmetic: cascaded TwoSum in FP32 (the sum
+// as if computed in twice the working precision, Ogita, Rump and Oishi's
+// Sum2), then one conversion -- the FP64 units of this GPU are few, and nine
+// conversions and eight FP64 additions per node would bound the pass.
+__device__ __forceinline__ double node_mass(const double (&a)[9]) {
+  double sm = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; i++) sm += a[i];
+  return sm;
+}
+__device__ __forceinline__ double node_mass(const float (&a)[9]) {
+  float s = a[0], e = 0.0f;
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    float t;
+    two_sum(s, a[i], s, t);
+    e += t;
+  }
+  return static_cast<double>(s) + static_cast<double>(e);
+}
+
 // Residual pass 1: thread g of the fixed grid reduces nodes g, g + G,
 // g + 2G, ... (G threads in all) into num, den, mass deviation, non-finite
 // count: per-node terms in the storage's arithmetic type, sums in FP64
@@ -101,10 +131,7 @@ residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
     }
     num += static_cast<double>(n1);
     den += static_cast<double>(d1);
-    double sm = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; i++) sm += static_cast<double>(a[i]);
-    dm += sm;
+    dm += node_mass(a);
   }
   __shared__ double sh[kResidualThreads / 32][kPartialStride];
   num = warp_sum(num);
@@ -126,20 +153,27 @@ residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
   }
 }
 
-// Pass 2: one block sums the partials in a fixed order.
-__global__ void __launch_bounds__(kResidualBlocks)
+// Pass 2: one block of kFinalThreads sums the partials in a fixed order
+// (thread t first adds blocks t, t + kFinalThreads, ...).
+constexpr int kFinalThreads = 1024;
+static_assert(kResidualBlocks % kFinalThreads == 0, "whole rounds of partials");
+__global__ void __launch_bounds__(kFinalThreads)
 residual_final(const double *__restrict__ partials, double *__restrict__ out) {
-  __shared__ double sh[kResidualBlocks / 32][kPartialStride];
+  __shared__ double sh[kFinalThreads / 32][kPartialStride];
   double v[kPartialStride];
-  for (int c = 0; c < kPartialStride; c++)
-    v[c] = warp_sum(partials[threadIdx.x * kPartialStride + c]);
+  for (int c = 0; c < kPartialStride; c++) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < kResidualBlocks; b += kFinalThreads)
+      t += partials[b * kPartialStride + c];
+    v[c] = warp_sum(t);
+  }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0)
     for (int c = 0; c < kPartialStride; c++) sh[w][c] = v[c];
   __syncthreads();
   if (threadIdx.x < kPartialStride) {
     double s = 0.0;
-    for (int i = 0; i < kResidualBlocks / 32; i++) s += sh[i][threadIdx.x];
+    for (int i = 0; i < kFinalThreads / 32; i++) s += sh[i][threadIdx.x];
     out[threadIdx.x] = s;
   }
 }
@@ -318,7 +352,7 @@ cudaError_t launch_residual_compact(const T *cur, const T *prev, const NodeMap &
                                     double scale, double *partials, double *result, cudaStream_t s) {
   residual_partials_compact<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(
       cur, prev, map, n_fluid, plane, ax, ay, 1.0 / scale, partials);
-  residual_final<<<1, kResidualBlocks, 0, s>>>(partials, result);
+  residual_final<<<1, kFinalThreads, 0, s>>>(partials, result);
   return cudaGetLastError();
 }
 

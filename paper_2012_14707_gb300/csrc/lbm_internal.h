@@ -111,13 +111,14 @@ __host__ __device__ inline void neighbour_rows(uint2 nw, uint32_t i, uint32_t n,
   sb = i - ds + ((periodic_y && y == 0) ? n : 0u);
 }
 
-// Compacted indices of the push targets x + c_q (q = 1..8, tq[0] = i) of
-// fluid node i in row y, from its node word m, n_lb / s_lb and rowstart.
+// Compacted indices of the neighbours x + c_q (q = 1..8, tq[0] = i) of
+// fluid node i in row y, from its node word m, n_lb / s_lb and rowstart
+// (pull_slots gathers direction q from the neighbour x - c_q = x + c_opp(q)).
 // Neighbours in the own row are i +- 1; in the rows above and below n_lb or
 // s_lb, +1 past a fluid (x, y +- 1) (bits 3 and 1 of the flag byte clear),
 // -1 for x - 1; across the periodic seam of x the row's first or last fluid
 // node.  Only targets that are fluid (bit opp(q) - 1 of the flag byte
-// clear) are meaningful.  Shared by the step kernel and host-side checks.
+// clear) are meaningful.  Shared by the kernels and host-side checks.
 __host__ __device__ inline void compact_targets(uint32_t m, uint32_t i, uint32_t nb, uint32_t sb,
                                                 int y, int ny, int periodic_y,
                                                 const int32_t *rowstart, uint32_t (&tq)[9]) {
@@ -147,30 +148,7 @@ __host__ __device__ inline void compact_targets(uint32_t m, uint32_t i, uint32_t
   }
 }
 
-// The same target for one direction q (tq[q] of compact_targets; the host
-// checks compare the two).  With q a constant the switch folds away.
-__host__ __device__ inline uint32_t push_target(int q, uint32_t m, uint32_t i, uint32_t nb,
-                                                uint32_t sb, int y, int ny, int periodic_y,
-                                                const int32_t *rowstart) {
-  const bool we = (m & kMetaWrapE) != 0, ww = (m & kMetaWrapW) != 0;
-  switch (q) {
-    case 1: return we ? static_cast<uint32_t>(rowstart[y]) : i + 1;
-    case 2: return nb;
-    case 3: return ww ? static_cast<uint32_t>(rowstart[y + 1] - 1) : i - 1;
-    case 4: return sb;
-    case 5:
-      return we ? static_cast<uint32_t>(rowstart[row_above(y, ny, periodic_y)])
-                : nb + ((m & (1u << 3)) ? 0u : 1u);
-    case 6: return ww ? static_cast<uint32_t>(rowstart[row_above(y, ny, periodic_y) + 1] - 1) : nb - 1;
-    case 7: return ww ? static_cast<uint32_t>(rowstart[row_below(y, ny, periodic_y) + 1] - 1) : sb - 1;
-    case 8:
-      return we ? static_cast<uint32_t>(rowstart[row_below(y, ny, periodic_y)])
-                : sb + ((m & (1u << 1)) ? 0u : 1u);
-    default: return i;
-  }
-}
-
-// Where the single-case lattice keeps node i's populations (pull layout).
+// Where a lattice keeps node i's populations (pull layout).
 // A step stores f'_q(x, t) in x's own slot q * P + i, so that its stores
 // are aligned and coalesced, and the next step gathers
 // f_q(x, t + 1) = f'_q(x - c_q, t) from the slot of x - c_q, which is the

@@ -13,8 +13,8 @@
 // which is local (f_ib(x_f, t), f'_i(x_f, t), f'_ib(x_f, t) and rho_f all
 // belong to x_f): the node evaluates them in the same step and keeps them
 // in the lattice's link tail, where its next gather finds them.  The
-// batched solver's arena keeps the push layout (lbm_batch.cu); both
-// compute the same values.
+// batched solver (lbm_batch.cu) runs the same per-node update on each case
+// of its arena.
 #include <cstdint>
 
 #include "lbm_device.cuh"
@@ -288,8 +288,8 @@ __global__ void export_kernel(const T *__restrict__ f, const NodeMap map, int64_
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < 9 * n;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = p / n, q = p - i * n, y = q / map.nx, x = q - y * map.nx;
-    // solid nodes carry no state (a dense lattice's solid slots hold values
-    // parked by the pushes of fluid neighbours): they read as the rest state
+    // solid nodes carry no state (the compacted lattice has no slots for
+    // them): they read as the rest state
     const int64_t node = map.at(static_cast<int>(x), static_cast<int>(y));
     double d = 0.0;
     if (node >= 0) {

@@ -1,6 +1,6 @@
 // Host-side check of the compacted lattice (no GPU needed): the library's
-// own build_host_case + build_compact, then the node word's neighbour rows,
-// compact_targets and push_target against the dense neighbourhood for
+// own build_host_case + build_compact, then the node word's neighbour rows
+// and compact_targets against the dense neighbourhood for
 // every fluid node and direction, and pull_slots (where the step kernels
 // gather and the conversions scatter) against the same neighbourhood and
 // the link table: every slot in range and held by exactly one (node,
@@ -131,9 +131,6 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
         if (!fluid_target) continue;
         checked++;
         int32_t want = cc.index[yy * nx + xx];
-        const uint32_t t1 = lbm::push_target(qd, nw.x & lbm::kNodeMeta, i, nb, sb, y, ny, py,
-                                             cc.rowstart.data());
-        if (t1 != tq[qd]) bad++;
         if (tq[qd] != (uint32_t)want || tq[qd] >= (uint32_t)cc.n_fluid) {
           if (bad < 5) printf("%s: node (%d,%d) dir %d got %u want %d\n", name, x, y, qd, tq[qd], want);
           bad++;

@@ -1,7 +1,7 @@
 """The compacted lattice's index arithmetic, checked on the host (no GPU):
 tests/native/compact_layout_check.cu links the library, builds each case's
 compacted layout with the library's own code, and compares the neighbour
-indices the step kernels compute (compact_targets, push_target) and the
+indices the step kernels compute (compact_targets) and the
 pull slots they gather from (pull_slots, the per-link f_jb slots) with the
 dense neighbourhood and the link table, for every fluid node and
 direction.  A wrong index would be a silent out-of-bounds access on the

@@ -246,9 +246,11 @@ typedef struct {
 } lbm_case_t;
 
 /* Copy and validate n_cases cases (errors name the case), lay them out on
- * the device, pick the CTA width by timing (cached per size class), start
- * every case at rest.  stream: cudaStream_t or NULL (the batch then makes
- * its own, since graph capture needs a non-legacy stream). */
+ * the device (each case in the layout lbm_create uses, with its limits),
+ * pick the step kernel's CTA width and L2 prefetch by timing (cached per
+ * size class), start every case at rest.  stream: cudaStream_t or NULL
+ * (the batch then makes its own, since graph capture needs a non-legacy
+ * stream). */
 int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision, void *stream,
                      lbm_batch_t **out);
 /* Back to rest, every case active, step counts zero. */
@@ -267,6 +269,8 @@ int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const dou
                          const double *uy);
 /* Density and velocity of case c (host arrays of nx*ny doubles, may be NULL). */
 int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double *uy);
+/* Sizes of the batch (outputs may be NULL): lattice nodes and fluid nodes
+ * of all cases, the step kernel's CTA width and its CTAs per step. */
 int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fluid,
                    int32_t *cta_threads, int32_t *n_tiles);
 void lbm_batch_destroy(lbm_batch_t *b);

@@ -342,6 +342,16 @@ template <typename T>
 struct PullOcc {
   static constexpr int min_blocks = StepOcc<T>::min_blocks * kStepThreads / kPullThreads;
 };
+// 16-bit storage: the conversions need more registers; 40 (12 CTAs/SM, no
+// spills) beat 32 (16 CTAs, spills) and 48 or 64 (fewer warps).
+template <>
+struct PullOcc<__half> {
+  static constexpr int min_blocks = 12;
+};
+template <>
+struct PullOcc<__nv_bfloat16> {
+  static constexpr int min_blocks = 12;
+};
 
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.
 // CTAs of step_kernel_pull<T, C> resident at once on the current device.

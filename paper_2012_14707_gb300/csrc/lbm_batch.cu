@@ -79,7 +79,7 @@ constexpr int kChunk = 256;  // node-arena alignment of every case (>= any CTA w
 // registers).  Like the single-case kernel, each CTA first asks L2 for the
 // node words and case index of the CTA pf_dist blocks ahead.
 template <typename T, typename C, int THREADS>
-__global__ void __launch_bounds__(THREADS, StepOcc<T>::min_blocks * kStepThreads / THREADS)
+__global__ void __launch_bounds__(THREADS, PullOcc<T>::min_blocks * kPullThreads / THREADS)
 batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
                   const uint2 *__restrict__ node, const int2 *__restrict__ grp,
                   const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,

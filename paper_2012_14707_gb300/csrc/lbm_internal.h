@@ -319,28 +319,20 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                const double *uby, double *r_out, double *l_out,
                                double *coef8_out /* n x 8 */, int64_t *n_clamped);
 
-// Batched step kernel geometry: one thread per fluid node, up to
-// kStepThreads nodes of a row per CTA, registers bounded for
-// StepOcc<T>::min_blocks resident CTAs per SM.
-constexpr int kStepThreads = 256;
-template <typename T>
-struct StepOcc {
-  // 32 registers: 64 warps per SM hide the load latency better than 48 warps
-  // without spills (a few dozen bytes of spills stay in L1)
-  static constexpr int min_blocks = 8;
-};
-template <>
-struct StepOcc<double> {
-  static constexpr int min_blocks = 2;
-};
-
-// Single-case (pull) step kernel geometry: CTA b runs fluid nodes
-// b * kPullThreads .. b * kPullThreads + kPullThreads - 1, whatever their
-// rows; small CTAs leave fewer warp slots idle behind a CTA's slowest warp.
+// Step kernel geometry (single case and batch): one thread per fluid
+// node; the single-case kernel runs kPullThreads consecutive fluid nodes per
+// CTA.  PullOcc<T>::min_blocks CTAs of kPullThreads threads per SM bound
+// the registers (the batch scales it to its CTA width).
 constexpr int kPullThreads = 128;
 template <typename T>
 struct PullOcc {
-  static constexpr int min_blocks = StepOcc<T>::min_blocks * kStepThreads / kPullThreads;
+  // FP32: 32 registers, 64 warps per SM -- more warps hide the load latency
+  // better than 40 registers without spills (one spilled register stays in L1)
+  static constexpr int min_blocks = 16;
+};
+template <>
+struct PullOcc<double> {
+  static constexpr int min_blocks = 4;
 };
 // 16-bit storage: the conversions need more registers; 40 (12 CTAs/SM, no
 // spills) beat 32 (16 CTAs, spills) and 48 or 64 (fewer warps).

@@ -45,7 +45,8 @@ typedef enum {
   LBM_ECUDA = 2,     /* a CUDA runtime call failed */
   LBM_EUNSTABLE = 3, /* a non-finite density or velocity was found */
   LBM_ETIMEOUT = 4,  /* a device-side wait hit its iteration limit */
-  LBM_ENOMEM = 5     /* device or host allocation failed */
+  LBM_ENOMEM = 5,    /* device or host allocation failed */
+  LBM_EIO = 6        /* a checkpoint file could not be written or read */
 } lbm_status;
 
 typedef enum {
@@ -308,6 +309,26 @@ int lbm_net_train_step(lbm_net_t *n, const float *x, const float *t, int32_t bat
                        double *loss);
 void lbm_net_destroy(lbm_net_t *n);
 const char *lbm_net_last_error(const lbm_net_t *n);
+
+/*
+ * Checkpoint and resume (the paper has no counterpart: a long solve can be
+ * stopped and continued bit for bit).  lbm_save writes the solver state --
+ * both lattices in their storage precision (the current one and the one of
+ * the step before, which the residual compares against) and the step
+ * count -- to the file `path` (created or truncated).  lbm_load reads such
+ * a file into a handle created for the same case (same domain, solid mask,
+ * links, Kn, parameters and precision: a fingerprint of these is stored in
+ * the file and checked) and sets its step count; the following steps and
+ * residuals are then those of the saved solver.  Both synchronise the
+ * handle's stream.  The file holds a 64-byte header (magic "LBMSTAT1",
+ * version, precision, nx, ny, fluid nodes, links, elements per lattice,
+ * steps, fingerprint; native byte order) and then the two lattices.
+ * Errors: LBM_EINVAL (null path, a file of another case, precision or
+ * version), LBM_EIO (the file cannot be opened, written or read in full),
+ * LBM_ECUDA, LBM_ENOMEM.
+ */
+int lbm_save(lbm_handle_t *h, const char *path);
+int lbm_load(lbm_handle_t *h, const char *path);
 
 /* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
 void lbm_destroy(lbm_handle_t *h);

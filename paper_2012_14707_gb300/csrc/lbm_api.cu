@@ -37,6 +37,8 @@ struct lbm_handle {
   double *result = nullptr;
   double *h_result = nullptr;  // pinned, 4 doubles
   int64_t n_fluid = 0, n_links = 0, steps = 0, dev_bytes = 0;
+  size_t fbytes = 0;          // bytes of one lattice (nine planes + link tail)
+  uint64_t fingerprint = 0;   // of the case's inputs (checkpoint files)
   std::vector<double> link_r, link_l;
   std::string err;
 };
@@ -63,6 +65,44 @@ int cuda_fail(lbm_handle_t *h, cudaError_t e, const char *what) {
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
+
+// FNV-1a over 8-byte words (the tail byte by byte): a fingerprint of a
+// case's inputs for checkpoint files, not a cryptographic hash.
+struct Fnv64 {
+  uint64_t h = 1469598103934665603ull;
+  void bytes(const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+      uint64_t w;
+      std::memcpy(&w, c + i, 8);
+      h = (h ^ w) * 1099511628211ull;
+    }
+    for (; i < n; i++) h = (h ^ c[i]) * 1099511628211ull;
+  }
+  template <typename V>
+  void value(const V &v) {
+    bytes(&v, sizeof(v));
+  }
+  // Large arrays: 1 MiB chunks hashed on all host threads, then the chunk
+  // hashes in order (the result does not depend on the thread count).
+  void big(const void *p, size_t n) {
+    constexpr size_t kChunkBytes = size_t(1) << 20;
+    const size_t nc = (n + kChunkBytes - 1) / kChunkBytes;
+    std::vector<uint64_t> part(nc);
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    lbm::parallel_for(static_cast<int64_t>(nc), [&](int64_t k0, int64_t k1) {
+      for (int64_t k = k0; k < k1; k++) {
+        Fnv64 f;
+        const size_t off = static_cast<size_t>(k) * kChunkBytes;
+        f.bytes(c + off, std::min(kChunkBytes, n - off));
+        part[static_cast<size_t>(k)] = f.h;
+      }
+    }, 4);
+    value(n);
+    bytes(part.data(), part.size() * sizeof(uint64_t));
+  }
+};
 
 size_t elem_size(int precision) {
   return precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
@@ -528,6 +568,35 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     return LBM_ENOMEM;
   }
   const lbm_params_t &p = *params;
+  {
+    Fnv64 f;
+    f.value(dom->nx);
+    f.value(dom->ny);
+    f.value(dom->periodic_x);
+    f.value(dom->periodic_y);
+    f.value(dom->H);
+    f.value(dom->ax);
+    f.value(dom->ay);
+    f.value(Kn);
+    f.big(solid, static_cast<size_t>(dom->nx) * static_cast<size_t>(dom->ny));
+    f.value(n_links);
+    f.big(link_x, n_links * sizeof(int32_t));
+    f.big(link_y, n_links * sizeof(int32_t));
+    f.big(link_dir, n_links * sizeof(int32_t));
+    f.big(link_q, n_links * sizeof(double));
+    f.big(link_ubx, n_links * sizeof(double));
+    f.big(link_uby, n_links * sizeof(double));
+    f.value(p.precision);
+    // the per-link coefficients carry every parameter that shapes the scheme
+    f.big(hc.coef.data(), hc.coef.size() * sizeof(double));
+    f.value(hc.cp.tau_s);
+    f.value(hc.cp.tau_q);
+    f.value(hc.cp.tau_e);
+    f.value(hc.cp.tau_eps);
+    f.value(hc.scale);
+    f.value(p.diffuse_mode);
+    h->fingerprint = f.h;
+  }
   h->link_r.swap(hc.link_r);
   h->link_l.swap(hc.link_l);
   const size_t n_links_sz = static_cast<size_t>(hc.n_links);
@@ -593,6 +662,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     return e;
   };
   cudaError_t e = cudaSuccess;
+  h->fbytes = fbytes;
   if (e == cudaSuccess) e = alloc(&h->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&h->f[1], fbytes);
   const size_t P = static_cast<size_t>(cc.plane);
@@ -858,6 +928,97 @@ int lbm_precompute(double Kn, double H, const lbm_params_t *params, size_t n, co
     info->n_clamped = cp.n_clamped;
     info->precision = params->precision;
   }
+  return LBM_OK;
+}
+
+namespace {
+struct CheckpointHeader {
+  char magic[8];
+  int32_t version, precision, nx, ny;
+  int64_t n_fluid, n_links, elems, steps;
+  uint64_t fingerprint;
+};
+static_assert(sizeof(CheckpointHeader) == 64, "64-byte header");
+constexpr char kCheckpointMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+
+CheckpointHeader checkpoint_header(const lbm_handle_t *h) {
+  CheckpointHeader hd{};
+  std::memcpy(hd.magic, kCheckpointMagic, 8);
+  hd.version = 1;
+  hd.precision = h->precision;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.n_fluid = h->n_fluid;
+  hd.n_links = h->n_links;
+  hd.elems = static_cast<int64_t>(h->fbytes / elem_size(h->precision));
+  hd.steps = h->steps;
+  hd.fingerprint = h->fingerprint;
+  return hd;
+}
+}  // namespace
+
+int lbm_save(lbm_handle_t *h, const char *path) {
+  if (!h) return LBM_EINVAL;
+  if (!path) return fail(h, LBM_EINVAL, "null path");
+  std::vector<unsigned char> buf;
+  try {
+    buf.resize(2 * h->fbytes);
+  } catch (...) {
+    return fail(h, LBM_ENOMEM, "host buffer for the checkpoint");
+  }
+  LBM_CK(h, cudaMemcpyAsync(buf.data(), h->f[h->cur], h->fbytes, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CK(h, cudaMemcpyAsync(buf.data() + h->fbytes, h->f[1 - h->cur], h->fbytes,
+                            cudaMemcpyDeviceToHost, h->stream));
+  LBM_CK(h, cudaStreamSynchronize(h->stream));
+  const CheckpointHeader hd = checkpoint_header(h);
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return fail(h, LBM_EIO, std::string("cannot open ") + path + " for writing");
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                  std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(h, LBM_EIO, std::string("cannot write ") + path);
+  return LBM_OK;
+}
+
+int lbm_load(lbm_handle_t *h, const char *path) {
+  if (!h) return LBM_EINVAL;
+  if (!path) return fail(h, LBM_EINVAL, "null path");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(h, LBM_EIO, std::string("cannot open ") + path);
+  CheckpointHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1) {
+    std::fclose(f);
+    return fail(h, LBM_EIO, std::string("cannot read the header of ") + path);
+  }
+  const CheckpointHeader want = checkpoint_header(h);
+  std::string why;
+  if (std::memcmp(hd.magic, kCheckpointMagic, 8) != 0) why = "not a checkpoint file";
+  else if (hd.version != 1) why = "unknown checkpoint version";
+  else if (hd.precision != want.precision) why = "checkpoint of another precision";
+  else if (hd.nx != want.nx || hd.ny != want.ny || hd.n_fluid != want.n_fluid ||
+           hd.n_links != want.n_links || hd.elems != want.elems ||
+           hd.fingerprint != want.fingerprint)
+    why = "checkpoint of another case";
+  else if (hd.steps < 0) why = "negative step count";
+  if (!why.empty()) {
+    std::fclose(f);
+    return fail(h, LBM_EINVAL, why + ": " + path);
+  }
+  std::vector<unsigned char> buf;
+  try {
+    buf.resize(2 * h->fbytes);
+  } catch (...) {
+    std::fclose(f);
+    return fail(h, LBM_ENOMEM, "host buffer for the checkpoint");
+  }
+  const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return fail(h, LBM_EIO, std::string("checkpoint file too short: ") + path);
+  LBM_CK(h, cudaMemcpyAsync(h->f[h->cur], buf.data(), h->fbytes, cudaMemcpyHostToDevice, h->stream));
+  LBM_CK(h, cudaMemcpyAsync(h->f[1 - h->cur], buf.data() + h->fbytes, h->fbytes,
+                            cudaMemcpyHostToDevice, h->stream));
+  LBM_CK(h, cudaStreamSynchronize(h->stream));
+  h->steps = hd.steps;
   return LBM_OK;
 }
 

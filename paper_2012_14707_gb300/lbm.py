@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOMEM = range(6)
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOMEM, LBM_EIO = range(7)
 LBM_FP64, LBM_FP32, LBM_BF16, LBM_FP16 = 0, 1, 2, 3
 L_MODES = {"paper": 0, "zero": 1, "gamma": 2, "2gamma": 3, "gamma2": 4, "gamma2+gamma": 5,
            "fixed": 6}
@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "bf16": LBM_BF16, "fp16": LBM_
 EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_residual",
            "lbm_set_fields",
            "lbm_run_to", "lbm_get_f", "lbm_set_f", "lbm_link_params", "lbm_get_info",
-           "lbm_precompute", "lbm_residual_noalloc", "lbm_destroy", "lbm_last_error",
+           "lbm_precompute", "lbm_residual_noalloc", "lbm_save", "lbm_load", "lbm_destroy",
+           "lbm_last_error",
            "lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
            "lbm_batch_set_fields",
            "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
@@ -112,6 +113,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_void_p, dp, dp]
+    lib.lbm_save.argtypes = [H, ctypes.c_char_p]
+    lib.lbm_load.argtypes = [H, ctypes.c_char_p]
     lib.lbm_destroy.argtypes = [H]
     lib.lbm_destroy.restype = None
     i64p = ctypes.POINTER(ctypes.c_int64)
@@ -243,6 +246,16 @@ def lbm_get_f(h, out: np.ndarray):
 def lbm_set_f(h, f: np.ndarray):
     f = np.ascontiguousarray(f, np.float64)
     _check(load().lbm_set_f(h, _dp(f)), h)
+
+
+def lbm_save(h, path: str):
+    """Checkpoint the solver state to `path` (see include/lbm.h)."""
+    _check(load().lbm_save(h, os.fsencode(path)), h)
+
+
+def lbm_load(h, path: str):
+    """Resume from a checkpoint of the same case."""
+    _check(load().lbm_load(h, os.fsencode(path)), h)
 
 
 def lbm_set_fields(h, rho, ux, uy, on_device: bool = False):
@@ -383,6 +396,12 @@ class Solver:
 
     def set_f(self, f):
         lbm_set_f(self.h, f)
+
+    def save(self, path: str):
+        lbm_save(self.h, path)
+
+    def load(self, path: str):
+        lbm_load(self.h, path)
 
     def link_params(self):
         return lbm_link_params(self.h, self.case.n_links)

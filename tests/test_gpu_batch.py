@@ -68,3 +68,27 @@ def test_batch_reset_and_info():
         np.testing.assert_array_equal(a, w)
     with pytest.raises(lbm.LbmError):
         b.run_to(1e-6, 100, check_every=3)
+
+
+def test_batch_of_awkward_sizes_is_bitwise_the_cases_alone():
+    """Cases smaller than a warp, of exactly one 256-node chunk, one node
+    more, and a walled channel share the node arena (each case starts on a
+    256-node chunk); 300 steps of each in the batch equal 300 steps alone."""
+    cl = [cases.periodic_box(1, 7, ax=1e-5),
+          cases.periodic_box(16, 16, ax=1e-5, ay=-2e-6),
+          cases.periodic_box(257, 1, ax=1e-5),
+          cases.config_poiseuille(),
+          cases.cylinder_array(70, 45, 2, Kn=0.02, ax=1e-5)]
+    assert [c.n_fluid for c in cl[:3]] == [7, 256, 257]
+    b = lbm.Batch(cl, precision="fp32")
+    info = b.info()
+    chunks = sum((max(c.n_fluid, 1) + 255) // 256 for c in cl)
+    assert info["n_tiles"] * info["cta_threads"] == 256 * chunks
+    steps, res, total = b.run_to(0.0, 300, check_every=100)
+    assert total == 300 and (steps == 0).all()
+    for k, c in enumerate(cl):
+        s = lbm.Solver(c, precision="fp32")
+        s.step(300)
+        for a, w in zip(b.fields(k), s.fields()):
+            np.testing.assert_array_equal(a, w)
+        s.close()

@@ -35,6 +35,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FLUID_BYTES = {"fp32": 72, "fp64": 144, "bf16": 36, "fp16": 36}  # algorithmic bytes per fluid-node update
+# The FP64 step is bound by this GPU's FP64 units, not by HBM: FP64 flops per
+# fluid-node update (dadd + dmul + 2 dfma executed by the step kernel, ncu
+# counters on the 4096x2048 case; profiles/) against the nominal FP64 rate.
+FP64_FLOPS_PER_NODE = 156.2
+FP64_PEAK_GFLOPS = 1250.0
 ELEM_BYTES = {"fp32": 4, "fp64": 8, "bf16": 2, "fp16": 2}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -300,10 +305,18 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (2 x %.2f GB lattices of fluid nodes)" % (
                        9 * ((n_fluid + 31) // 32 * 32) * ELEM_BYTES[args.precision] / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "step_kernel", "bytes_per_fluid_node": FLUID_BYTES[args.precision],
-                     "launch_ms": launch_ms, "peak_source": peak_src},
+        "roofline": ({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                      "frac": achieved / peak, "traffic": traffic,
+                      "kernel": "step_kernel", "bytes_per_fluid_node": FLUID_BYTES[args.precision],
+                      "launch_ms": launch_ms, "peak_source": peak_src}
+                     if args.precision != "fp64" else
+                     {"bound": "alu", "achieved": FP64_FLOPS_PER_NODE * n_fluid / (launch_ms / 1e3) / 1e9,
+                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                      "frac": FP64_FLOPS_PER_NODE * n_fluid / (launch_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
+                      "traffic": None, "kernel": "step_kernel",
+                      "flops_per_fluid_node": FP64_FLOPS_PER_NODE, "hbm_gbs": achieved,
+                      "launch_ms": launch_ms,
+                      "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)"}),
         "e2e": e2e,
         "gpu_launches": args.steps * (per + 2),
         "clocks": clocks,

@@ -154,6 +154,10 @@ int main(int argc, char **argv) {
   fails += check("column", 1, 7, 1, 1, std::vector<uint8_t>(7, 0));
   fails += check("row", 33, 1, 1, 1, std::vector<uint8_t>(33, 0));
   fails += check("row_wall_x", 40, 20, 0, 1, [] { std::vector<uint8_t> s(40 * 20, 0); for (int y = 0; y < 20; y++) { s[y * 40] = 1; s[y * 40 + 39] = 1; } return s; }());
+  // periodic y with solid blocks at the ends of the last and first rows: the
+  // first fluid node at or after (x, y +- 1) is then past the end of that
+  // row (for the last row, the end of the lattice)
+  fails += check("edge_row_gaps", 24, 9, 1, 1, [] { std::vector<uint8_t> s(24 * 9, 0); for (int x = 16; x < 24; x++) { s[8 * 24 + x] = 1; s[x - 16] = 1; } s[4 * 24 + 23] = 1; return s; }());
   std::mt19937 rng(3);
   for (int t = 0; t < 6; t++) {
     int nx = 50 + rng() % 700, ny = 40 + rng() % 300;

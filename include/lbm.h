@@ -273,7 +273,7 @@ int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double 
 /* Sizes of the batch (outputs may be NULL): lattice nodes and fluid nodes
  * of all cases, the step kernel's CTA width and its CTAs per step. */
 int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fluid,
-                   int32_t *cta_threads, int32_t *n_tiles);
+                   int32_t *cta_threads, int32_t *n_ctas);
 void lbm_batch_destroy(lbm_batch_t *b);
 /* Last error of the batch; with b = NULL, of the last failed lbm_batch_create. */
 const char *lbm_batch_last_error(const lbm_batch_t *b);

@@ -10,11 +10,12 @@
 // per-chunk case index: a time step is one launch over the whole node
 // arena; a CTA looks up its case's constants in a descriptor table and runs
 // the single-case kernel's per-node update (step_node_pull), so a case in a
-// batch follows exactly the arithmetic of the case run alone.  Every K steps a batched reduction (one CTA per case, fixed
-// order) computes each case's residual and retires converged cases on the
-// device; retired cases' CTAs return immediately.  K steps plus the
-// reduction are captured once in a CUDA graph that the host replays, reading
-// back only the number of active cases.  The CTA width is picked by timing
+// batch follows exactly the arithmetic of the case run alone.  Every K
+// steps a batched reduction (one CTA per case, fixed order) computes each
+// case's residual and retires converged cases on the device; retired
+// cases' CTAs return immediately.  K steps plus the reduction are captured
+// once in a CUDA graph that the host replays, reading back only the number
+// of active cases.  The CTA width and the L2 prefetch are picked by timing
 // the candidates on the batch itself (autotuner), cached per size class and
 // precision.
 #include <algorithm>
@@ -712,12 +713,12 @@ int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const dou
 }
 
 int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fluid,
-                   int32_t *cta_threads, int32_t *n_tiles) {
+                   int32_t *cta_threads, int32_t *n_ctas) {
   if (!b) return LBM_EINVAL;
   if (total_nodes) *total_nodes = b->total_nodes;
   if (total_fluid) *total_fluid = b->total_fluid;
   if (cta_threads) *cta_threads = b->threads;
-  if (n_tiles) *n_tiles = static_cast<int32_t>(b->arena_nodes / b->threads);
+  if (n_ctas) *n_ctas = static_cast<int32_t>(b->arena_nodes / b->threads);
   return LBM_OK;
 }
 

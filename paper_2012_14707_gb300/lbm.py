@@ -523,7 +523,7 @@ class Batch:
         t, nt = ctypes.c_int32(), ctypes.c_int32()
         _bcheck(load().lbm_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t),
                                       ctypes.byref(nt)), self.h)
-        return dict(total_nodes=a.value, total_fluid=b.value, cta_threads=t.value, n_tiles=nt.value)
+        return dict(total_nodes=a.value, total_fluid=b.value, cta_threads=t.value, n_ctas=nt.value)
 
 
 # --------------------------------------------------------------------------

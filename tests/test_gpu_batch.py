@@ -83,7 +83,7 @@ def test_batch_of_awkward_sizes_is_bitwise_the_cases_alone():
     b = lbm.Batch(cl, precision="fp32")
     info = b.info()
     chunks = sum((max(c.n_fluid, 1) + 255) // 256 for c in cl)
-    assert info["n_tiles"] * info["cta_threads"] == 256 * chunks
+    assert info["n_ctas"] * info["cta_threads"] == 256 * chunks
     steps, res, total = b.run_to(0.0, 300, check_every=100)
     assert total == 300 and (steps == 0).all()
     for k, c in enumerate(cl):

@@ -382,6 +382,8 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   hc->py = py;
   hc->ax = dom->ax;
   hc->ay = dom->ay;
+  // only FP16 storage is scaled (BF16 keeps FP32's exponent range; its
+  // kernels assume scale 1)
   hc->scale = p.precision == LBM_FP16 ? (p.storage_scale > 0.0 ? p.storage_scale : 4096.0) : 1.0;
   hc->cp = cp;
   hc->params = p;

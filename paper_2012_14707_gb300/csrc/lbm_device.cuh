@@ -11,9 +11,10 @@ namespace lbm {
 namespace dev {
 
 
-// Storage of a deviation d as T and its arithmetic type C.  FP32 and FP64
-// store d itself; the 16-bit types store d * scale (scale a power of two,
-// 1 for BF16), so loads and stores are exact apart from the rounding to T.
+// Storage of a deviation d as T and its arithmetic type C.  FP32, FP64 and
+// BF16 (which keeps FP32's exponent range) store d itself; FP16 stores
+// d * scale (a power of two), so loads and stores are exact apart from the
+// rounding to T.
 template <typename T>
 struct Stor {
   using C = T;
@@ -29,11 +30,10 @@ struct Stor<__half> {
 template <>
 struct Stor<__nv_bfloat16> {
   using C = float;
-  static __device__ __forceinline__ float ld(__nv_bfloat16 v, float inv) {
-    return __bfloat162float(v) * inv;
-  }
-  static __device__ __forceinline__ __nv_bfloat16 st(float v, float sc) {
-    return __float2bfloat16_rn(v * sc);
+  // the scale of BF16 storage is always 1 (the library sets no other)
+  static __device__ __forceinline__ float ld(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 st(float v, float) {
+    return __float2bfloat16_rn(v);
   }
 };
 

@@ -97,6 +97,21 @@ def test_fp64_populations_match_oracle(name, diffuse_mode):
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_one_row_channel_matches_oracle(precision, tol):
+    """A channel one fluid row high (moving upper wall): every node has the
+    links j and opp(j) of three direction pairs, so Eq. EqNewBDSC of one
+    link reads the unknown population the other link set a step earlier
+    (f_jb from the link tail rather than from a neighbour)."""
+    c = cases.channel(8, 1, 0.4, 0.7, Kn=0.05, ax=1e-5, u_top=0.01)
+    assert c.n_fluid == 8 and c.n_links == 48
+    o, g = _pair(c, precision, start_seed=5)
+    for n in (1, 37, 162):
+        o.step(n)
+        g.step(n)
+        np.testing.assert_allclose(_fluid_f(c, g.get_f()), _fluid_f(c, o.get_f()), rtol=0, atol=tol)
+
+
 @pytest.mark.parametrize("l_mode,extra", [
     ("zero", {}), ("gamma", {}), ("2gamma", {}), ("gamma2", {}), ("gamma2+gamma", {}),
     (0.35, {"r": 0.7, "tau_q": 0.9}),

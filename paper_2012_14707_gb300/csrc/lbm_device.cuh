@@ -14,18 +14,27 @@ namespace dev {
 // Storage of a deviation d as T and its arithmetic type C.  FP32, FP64 and
 // BF16 (which keeps FP32's exponent range) store d itself; FP16 stores
 // d * scale (a power of two), so loads and stores are exact apart from the
-// rounding to T.
+// rounding to T.  ld_raw / st_raw move the stored value itself (d * scale)
+// for the step kernel, which works in storage units where the storage is
+// scaled (kScaled): scaling by a power of two commutes with every rounding,
+// so that is the same arithmetic without a multiplication per value.
 template <typename T>
 struct Stor {
   using C = T;
+  static constexpr bool kScaled = false;
   static __device__ __forceinline__ C ld(T v, C) { return v; }
   static __device__ __forceinline__ T st(C v, C) { return v; }
+  static __device__ __forceinline__ C ld_raw(T v) { return v; }
+  static __device__ __forceinline__ T st_raw(C v) { return v; }
 };
 template <>
 struct Stor<__half> {
   using C = float;
+  static constexpr bool kScaled = true;
   static __device__ __forceinline__ float ld(__half v, float inv) { return __half2float(v) * inv; }
   static __device__ __forceinline__ __half st(float v, float sc) { return __float2half_rn(v * sc); }
+  static __device__ __forceinline__ float ld_raw(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half st_raw(float v) { return __float2half_rn(v); }
 };
 template <>
 struct Stor<__nv_bfloat16> {
@@ -35,6 +44,9 @@ struct Stor<__nv_bfloat16> {
   static __device__ __forceinline__ __nv_bfloat16 st(float v, float) {
     return __float2bfloat16_rn(v);
   }
+  static constexpr bool kScaled = false;
+  static __device__ __forceinline__ float ld_raw(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 st_raw(float v) { return __float2bfloat16_rn(v); }
 };
 
 
@@ -55,7 +67,8 @@ __device__ __forceinline__ double recip<double>(double v) {
 }
 
 // Post-collision state of one node: the nine values (arithmetic type and
-// rounded to storage) and the macroscopic quantities the links need.
+// rounded to storage; in storage units where the storage is scaled) and
+// the macroscopic quantities the links need.
 template <typename T, typename C>
 struct Collided {
   C o[9];
@@ -64,9 +77,14 @@ struct Collided {
 };
 
 // Eq. FluidMacr, Eq. MomentPost and f' = M^-1 m' for the deviations d of one
-// node; f'_1..f'_8 rounded to storage, f'_0 closing the mass balance.
+// node (in storage units, d * scale, where Stor<T>::kScaled); f'_1..f'_8
+// rounded to storage, f'_0 closing the mass balance.  Every quantity that
+// carries the storage scale S is computed as S times its unscaled value
+// exactly (S is a power of two), so the stored results do not depend on
+// the units.
 template <typename T, typename C>
 __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, Collided<T, C> &r) {
+  constexpr bool kS = Stor<T>::kScaled;
   C(&o)[9] = r.o;
   T(&t)[9] = r.t;
   // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
@@ -74,15 +92,17 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
   const C d5m6 = d[5] - d[6], d8m7 = d[8] - d[7];
   const C s14 = a13 + a24, s58 = d5p6 + d7p8;
-  const C drho = (d[0] + s14) + s58;
+  const C drho_s = (d[0] + s14) + s58;
   const C e = C(2) * s58 + (C(-4) * d[0] - s14);
   const C eps = C(-2) * s14 + (C(4) * d[0] + s58);
   const C u13 = d[1] - d[3], t58 = d5m6 + d8m7;
   const C v24 = d[2] - d[4], w58 = d5p6 - d7p8;
-  const C jx = u13 + t58, qx = C(-2) * u13 + t58;
-  const C jy = v24 + w58, qy = C(-2) * v24 + w58;
+  const C jx_s = u13 + t58, qx = C(-2) * u13 + t58;
+  const C jy_s = v24 + w58, qy = C(-2) * v24 + w58;
   const C pxx = a13 - a24;
   const C pxy = d5m6 - d8m7;
+  const C drho = kS ? drho_s * k.inv_sc : drho_s;
+  const C jx = kS ? jx_s * k.inv_sc : jx_s, jy = kS ? jy_s * k.inv_sc : jy_s;
 
   // Eq. FluidMacr.
   const C rho = C(1) + drho;
@@ -100,18 +120,21 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   // FP32 that bias adds up over thousands of steps).  M f_eq and M Fbar in
   // closed form; each row of m' - m is already scaled by its entry of
   // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) (the
-  // constants k.e2 .. k.y3 fold s and 1 - s/2 with that scale).  Mass does
-  // not change; momentum changes by rho a exactly, for any s_j, since
+  // constants k.e2 .. k.y3 fold s and 1 - s/2 with that scale, and the
+  // storage scale into the forcing weights).  Mass does not change;
+  // momentum changes by rho a exactly, for any s_j, since
   // rho u = j + rho a / 2.
   const C ua6 = C(6) * (rux * k.ax + ruy * k.ay);
-  const C w3 = C(3) * rho * uu;
-  const C e36 = k.e3 * ua6 - k.e2 * (e + C(2) * drho - w3);
-  const C p36 = -k.p2 * (eps - drho + w3) - k.p3 * ua6;
-  const C jx6 = rax * C(1.0 / 6.0), jy6 = ray * C(1.0 / 6.0);
-  const C qx12 = -k.q2 * (qx + rux) - k.q3 * rax;
-  const C qy12 = -k.q2 * (qy + ruy) - k.q3 * ray;
-  const C xx4 = k.x3 * (rux * k.ax - ruy * k.ay) - k.x2 * (pxx - rho * (ux * ux - uy * uy));
-  const C xy4 = k.y3 * (rux * k.ay + ruy * k.ax) - k.x2 * (pxy - rho * ux * uy);
+  const C w3 = kS ? k.w3c * rho * uu : C(3) * rho * uu;
+  const C rho_s = kS ? rho * k.sc : rho;
+  const C rux_s = kS ? rux * k.sc : rux, ruy_s = kS ? ruy * k.sc : ruy;
+  const C e36 = k.e3 * ua6 - k.e2 * (e + C(2) * drho_s - w3);
+  const C p36 = -k.p2 * (eps - drho_s + w3) - k.p3 * ua6;
+  const C jx6 = rax * k.j6, jy6 = ray * k.j6;
+  const C qx12 = -k.q2 * (qx + rux_s) - k.q3 * rax;
+  const C qy12 = -k.q2 * (qy + ruy_s) - k.q3 * ray;
+  const C xx4 = k.x3 * (rux * k.ax - ruy * k.ay) - k.x2 * (pxx - rho_s * (ux * ux - uy * uy));
+  const C xy4 = k.y3 * (rux * k.ay + ruy * k.ax) - k.x2 * (pxy - rho_s * ux * uy);
 
   // f' - f = M^-1 (m' - m).
   const C axis = -e36 - C(2) * p36;
@@ -136,12 +159,20 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   C dd[9];
 #pragma unroll
   for (int i = 1; i < 9; i++) {
-    t[i] = Stor<T>::st(o[i], k.sc);
-    o[i] = Stor<T>::ld(t[i], k.inv_sc);
+    if constexpr (kS) {
+      t[i] = Stor<T>::st_raw(o[i]);
+      o[i] = Stor<T>::ld_raw(t[i]);
+    } else {
+      t[i] = Stor<T>::st(o[i], k.sc);
+      o[i] = Stor<T>::ld(t[i], k.inv_sc);
+    }
     dd[i] = o[i] - d[i];
   }
   o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
-  t[0] = Stor<T>::st(o[0], k.sc);
+  if constexpr (kS)
+    t[0] = Stor<T>::st_raw(o[0]);
+  else
+    t[0] = Stor<T>::st(o[0], k.sc);
 
   r.drho = drho;
   r.rho = rho;
@@ -169,8 +200,11 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
                                                    const StepConst<C> &k) {
   const unsigned wmask = __reduce_or_sync(__activemask(), fl);
   if (!wmask) return;
+  constexpr bool kS = Stor<T>::kScaled;
   const C(&o)[9] = c_.o;
-  const C drho = c_.drho, rho = c_.rho, ux = c_.ux, uy = c_.uy, uu = c_.uu;
+  const C ux = c_.ux, uy = c_.uy, uu = c_.uu;
+  // in storage units (times the storage scale) where the storage is scaled
+  const C drho = kS ? c_.drho * k.sc : c_.drho, rho = kS ? c_.rho * k.sc : c_.rho;
   const uint32_t tail = 9u * g.plane;
 #pragma unroll
   for (int j = 1; j < 9; j++) {
@@ -196,10 +230,11 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
       }
       const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
       const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-      const C djb = Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
-      const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
-                  c2 * (drho + rho * pj);
-      dst[tail + lj] = Stor<T>::st(v, k.sc);
+      const C djb = kS ? Stor<T>::ld_raw(src[g.jbslot[lj]])
+                       : Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
+      const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + (kS ? c0 * k.sc : c0) +
+                  c.alpha * drho + c2 * (drho + rho * pj);
+      dst[tail + lj] = kS ? Stor<T>::st_raw(v) : Stor<T>::st(v, k.sc);
     }
   }
 }
@@ -221,7 +256,8 @@ __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__r
     uint32_t s[9];
     pull_slots(nw, gr, i, P, g.n_fluid, g.ny, g.periodic_y, g.rowstart, s);
 #pragma unroll
-    for (int q = 0; q < 9; q++) d[q] = Stor<T>::ld(src[s[q]], k.inv_sc);
+    for (int q = 0; q < 9; q++)
+      d[q] = Stor<T>::kScaled ? Stor<T>::ld_raw(src[s[q]]) : Stor<T>::ld(src[s[q]], k.inv_sc);
     // the link records are read after the collision: start fetching them now
     if (nw.x & 0xFFu) {
       asm volatile("prefetch.global.L1 [%0];" ::"l"(links + gr.y + node_loff(nw)));

@@ -25,9 +25,10 @@ struct StepConst {
   // Relaxation rates s = 1/tau of e, eps, q and the stress (p_xx, p_xy),
   // as the collide function consumes them: s and the forcing weight 1 - s/2
   // (Eq. MomentPost), each times the moment's entry of
-  // diag(1/36, 1/36, 1/12, 1/4) in M^-1 (x3 = 2 (1 - s_s/2) / 4).  The
-  // momentum rows need no rate (collide).
-  C e2, e3, p2, p3, q2, q3, x2, x3, y3;
+  // diag(1/36, 1/36, 1/12, 1/4) in M^-1 (x3 = 2 (1 - s_s/2) / 4); the
+  // forcing weights also times the storage scale S (1 but for FP16).  The
+  // momentum rows need no rate (collide): j6 = S / 6.  w3c = 3 S.
+  C e2, e3, p2, p3, q2, q3, x2, x3, y3, j6, w3c;
   C sc, inv_sc;                 // storage scale of the 16-bit types (1 otherwise)
   C ax, ay;                     // body acceleration
   int32_t nx, ny, pitch;        // lattice size; row pitch (unused by the compacted lattice)
@@ -261,14 +262,16 @@ StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32
     const double se = 1.0 / cp.tau_e, sp = 1.0 / cp.tau_eps, sq = 1.0 / cp.tau_q,
                  ss = 1.0 / cp.tau_s;
     k.e2 = static_cast<C>(se / 36.0);
-    k.e3 = static_cast<C>((1.0 - 0.5 * se) / 36.0);
+    k.e3 = static_cast<C>(scale * (1.0 - 0.5 * se) / 36.0);
     k.p2 = static_cast<C>(sp / 36.0);
-    k.p3 = static_cast<C>((1.0 - 0.5 * sp) / 36.0);
+    k.p3 = static_cast<C>(scale * (1.0 - 0.5 * sp) / 36.0);
     k.q2 = static_cast<C>(sq / 12.0);
-    k.q3 = static_cast<C>((1.0 - 0.5 * sq) / 12.0);
+    k.q3 = static_cast<C>(scale * (1.0 - 0.5 * sq) / 12.0);
     k.x2 = static_cast<C>(ss / 4.0);
-    k.x3 = static_cast<C>((1.0 - 0.5 * ss) / 2.0);
-    k.y3 = static_cast<C>((1.0 - 0.5 * ss) / 4.0);
+    k.x3 = static_cast<C>(scale * (1.0 - 0.5 * ss) / 2.0);
+    k.y3 = static_cast<C>(scale * (1.0 - 0.5 * ss) / 4.0);
+    k.j6 = static_cast<C>(scale / 6.0);
+    k.w3c = static_cast<C>(3.0 * scale);
   }
   k.sc = static_cast<C>(scale);
   k.inv_sc = static_cast<C>(1.0 / scale);

@@ -184,13 +184,14 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
 // The unknown populations of a boundary node for the next step (bits of
 // fl, its flag byte; li is its first link), Eq. EqNewBDSC in the folded
 // form of LinkCoef, written to the link tail of dst (pull layout, see
-// pull_slots): link k of the table has tail element 9 P + k.  The link
-// records and jbslot entries were prefetched before the collision.
-// Inputs: the node's post-collision state c and
-// its pre-collision f_jb(x, t), gathered again from src at the slot the
-// link's jbslot entry names (a cache hit; fewer live registers than
-// keeping nine values through the collision).  Directions that no active
-// lane of the warp needs are skipped warp-uniformly.
+// pull_slots): link k of the table has tail element 9 P + k.  Inputs: the
+// node's post-collision state c and its pre-collision f_jb(x, t), gathered
+// again from src at the slot the link's jbslot entry names (a cache hit;
+// fewer live registers than keeping nine values through the collision).
+// The link records and jbslot entries were prefetched before the
+// collision.  Where the storage is scaled, every term is taken times the
+// scale, so the stored value is the same.  Directions that no active lane
+// of the warp needs are skipped warp-uniformly.
 template <typename T, typename C>
 __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                    const PullGeom &g, const uint32_t fl,

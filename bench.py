@@ -358,7 +358,7 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
 
 
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
-KERNEL_REV = 9
+KERNEL_REV = 10
 
 
 def run_batch(args):

@@ -13,6 +13,11 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
   * boundary scheme -- pinned (halfway bounce-back no-slip parabola at the
     magic parameter, Zhao no-slip parabola, slip Poiseuille closed forms for
     tuned and untuned parameters).
+  * boundary scheme with the Maxwell part at the printed wall velocity
+    (diffuse_mode 1) -- pinned per node by the wall relation of the Sec. 3.B
+    channel analysis carried out for that reading
+    (params.wall_recursion_coefficients_printed): plane Couette, untuned
+    Poiseuille, and force plus moving wall with unequal walls.
   * curved walls (Couette) -- pinned only to within discretisation error
     (error against Eq. EqAnaMicro falls under refinement).
 """

@@ -153,6 +153,28 @@ def wall_recursion_coefficients(r, l, gamma, tau_s, tau_q):
     return A, B, C
 
 
+def wall_recursion_coefficients_printed(r, l, gamma, tau_s, tau_q):
+    """The wall relation u_1 = A' u_0 + B' a dt + C' u_w of the same channel
+    analysis (Sec. 3.B, Eqs. EqMicroBound -> NumerSana) with the Maxwell part
+    of Eq. EqNewBDSC evaluated as printed, f_i^eq(rho_f, u_b), instead of at
+    the fluid velocity of x_f.
+
+    Route (linear in u and a, Eq. EqAssumpt): only the x-odd combinations
+    f_1 - f_3, f_5 - f_6, f_8 - f_7 of a row carry the flow; the difference
+    of Eq. EqNewBDSC for i = 5 and i = 6 at the wall row contributes
+    (1 - r) u_d / 6 from the Maxwell part, with u_d = u_0 in the reading
+    under which Eq. u1u0Coeff holds and u_d = u_w as printed.  Eliminating the
+    shear moments of rows 0 and 1 gives Eq. u1u0Coeff for u_d = u_0 and, for
+    u_d = u_w, the same B with
+        A' = A + (1 + l)(1 - r) / d,   C' = 1 - A',
+        d  = (1 + l)(1 - r) tau_s + 2 r gamma.
+    A' + C' = 1: a uniform flow at the wall speed is steady."""
+    A, B, _ = wall_recursion_coefficients(r, l, gamma, tau_s, tau_q)
+    d = (1 + l) * (1 - r) * tau_s + 2 * r * gamma
+    Ap = A + (1 + l) * (1 - r) / d
+    return Ap, B, 1 - Ap
+
+
 def slip_velocity_numeric(r, l, gamma, tau_s, tau_q, H):
     """Eq. EqMiSlip: U_s = u_s / u_c of the scheme for any parameters
     (delta_x = 1, channel width H)."""

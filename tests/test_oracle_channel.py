@@ -138,6 +138,107 @@ def test_moving_wall_matches_wall_recursion(oracle_mod, r, l, g):
     np.testing.assert_allclose(ux / U, want / U, rtol=0, atol=2e-9)
 
 
+def _steady_channel_from_wall_relations(H, g_bot, g_top, nu, a, rel_bot, rel_top, uw_bot, uw_top):
+    """(alpha, beta, kappa) of u(y) = alpha + beta y + kappa y^2, y from the
+    lower wall: kappa = -a / (2 nu) is the bulk (the MRT rows reproduce
+    u_{j+1} - 2 u_j + u_{j-1} = -a / nu exactly), and alpha, beta follow
+    from the relation u_1 = A u_0 + B a + C u_w at each wall row (the upper
+    wall mirrored, y -> H - y)."""
+    kappa = -a / (2 * nu)
+    rows, rhs = [], []
+    for (A, B, C), y0, y1, uw in ((rel_bot, g_bot, 1 + g_bot, uw_bot),
+                                  (rel_top, H - g_top, H - 1 - g_top, uw_top)):
+        rows.append([1 - A, y1 - A * y0])
+        rhs.append(B * a + C * uw - kappa * (y1 * y1 - A * y0 * y0))
+    alpha, beta = np.linalg.solve(np.array(rows), np.array(rhs))
+    return alpha, beta, kappa
+
+
+def test_printed_reading_coefficient_of_the_measured_case():
+    """r = 0.6, l = 0, gamma = 1/2, tau_s = 1.2: the printed reading gives
+    A' = 67/27 where Eq. u1u0Coeff gives 19/9; B is the same."""
+    A, B, C = P.wall_recursion_coefficients(0.6, 0.0, 0.5, 1.2, 1.1)
+    Ap, Bp, Cp = P.wall_recursion_coefficients_printed(0.6, 0.0, 0.5, 1.2, 1.1)
+    assert A == pytest.approx(19 / 9, rel=1e-14)
+    assert Ap == pytest.approx(67 / 27, rel=1e-14)
+    assert Bp == B and A + C == pytest.approx(1.0) and Ap + Cp == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("r,l,g", [(0.6, 0.0, 0.5), (0.6, 0.2, 0.5), (0.8, 0.4, 0.3),
+                                   (0.45, 0.9, 0.85)])
+def test_printed_reading_plane_couette_matches_its_wall_recursion(oracle_mod, r, l, g):
+    """Maxwell part at the wall velocity (diffuse_mode 1, Eq. EqNewBDSC as
+    printed), plane Couette flow (a = 0, upper wall at U): the steady linear
+    profile satisfies u_1 = A' u_0 + C' u_w at each wall row, node by node,
+    and misses the relation of Eq. u1u0Coeff (so a slip in the Maxwell term's
+    velocity, sign or weight fails here)."""
+    m, U = 10, 1e-4
+    c = cases.channel(4, m, g, g, Kn=0.05, ax=0.0, u_top=U)
+    ts, tq = 1.3, 1.1
+    par = P.Parameters(c.Kn, c.H, tau_s=ts, tau_q_fixed=tq, l_mode=l, r_fixed=r)
+    o = oracle_mod.OracleLBM(c, par, diffuse_mode=1)
+    o.run_to(1e-13, 400000)
+    ux, _, _ = _profile(o, m)
+    y = np.arange(m) + g
+    rel = P.wall_recursion_coefficients_printed(r, l, g, ts, tq)
+    al, be, _ = _steady_channel_from_wall_relations(c.H, g, g, P.viscosity(ts), 0.0, rel, rel, 0.0, U)
+    np.testing.assert_allclose(ux / U, (al + be * y) / U, rtol=0, atol=2e-9)
+    rel0 = P.wall_recursion_coefficients(r, l, g, ts, tq)
+    al0, be0, _ = _steady_channel_from_wall_relations(c.H, g, g, P.viscosity(ts), 0.0, rel0, rel0, 0.0,
+                                                      U)
+    assert np.abs(ux - (al0 + be0 * y)).max() / U > 1e-3
+
+
+@pytest.mark.parametrize("r,l,g,ts,tq", [
+    (0.6, 0.0, 0.5, 1.2, 1.2),
+    (0.7, 0.3, 0.25, 1.2, 1.2),
+    (0.45, 0.8, 0.9, 2.0, 0.9),
+    (0.85, 0.1, 0.15, 0.9, 1.4),
+])
+def test_printed_reading_untuned_poiseuille_matches_its_wall_recursion(oracle_mod, r, l, g, ts, tq):
+    """diffuse_mode 1, force-driven channel with walls at rest, any
+    (r, l, gamma, tau_s, tau_q): the steady profile is the bulk parabola
+    whose wall rows satisfy u_1 = A' u_0 + B a, at every node.  (With the
+    walls at rest the printed Maxwell part is w_i rho_f: no momentum enters
+    through it, which is why A' exceeds A.)"""
+    m = 16
+    c = cases.channel(4, m, g, g, Kn=0.05, ax=1e-6)
+    par = P.Parameters(c.Kn, c.H, tau_s=ts, tau_q_fixed=tq, l_mode=l, r_fixed=r)
+    o = oracle_mod.OracleLBM(c, par, diffuse_mode=1)
+    o.run_to(1e-12, 400000)
+    ux, _, _ = _profile(o, m)
+    nu = P.viscosity(ts)
+    uc = c.ax * c.H ** 2 / (8 * nu)
+    rel = P.wall_recursion_coefficients_printed(r, l, g, ts, tq)
+    al, be, ka = _steady_channel_from_wall_relations(c.H, g, g, nu, c.ax, rel, rel, 0.0, 0.0)
+    y = np.arange(m) + g
+    np.testing.assert_allclose(ux / uc, (al + be * y + ka * y * y) / uc, rtol=0, atol=2e-8)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_force_and_moving_wall_with_unequal_walls(oracle_mod, mode):
+    """Both readings with a force, a moving upper wall and different gamma,
+    l, r on the two walls (the tuned Sec. 3.B parameters): the steady
+    profile follows the parabola fixed by each wall's own relation --
+    Eq. u1u0Coeff for the default reading, A', B, C' for the printed one."""
+    m, U = 12, 2e-5
+    gb, gt = 0.35, 0.8
+    c = cases.channel(4, m, gb, gt, Kn=0.03, ax=1e-6, u_top=U)
+    par = P.Parameters(c.Kn, c.H)
+    o = oracle_mod.OracleLBM(c, par, diffuse_mode=mode)
+    o.run_to(1e-13, 400000)
+    ux, _, _ = _profile(o, m)
+    (rb, rt), (lb, lt) = par.per_link(np.array([gb, gt]))
+    fn = P.wall_recursion_coefficients_printed if mode else P.wall_recursion_coefficients
+    nu = P.viscosity(par.tau_s)
+    al, be, ka = _steady_channel_from_wall_relations(
+        c.H, gb, gt, nu, c.ax, fn(rb, lb, gb, par.tau_s, par.tau_q), fn(rt, lt, gt, par.tau_s, par.tau_q),
+        0.0, U)
+    y = np.arange(m) + gb
+    uc = c.ax * c.H ** 2 / (8 * nu)
+    np.testing.assert_allclose(ux / uc, (al + be * y + ka * y * y) / uc, rtol=0, atol=2e-8)
+
+
 def test_literal_reading_differs_only_when_r_below_one(oracle_mod):
     """The two readings of the Maxwell part coincide for r = 1 (no Maxwell
     part) and differ otherwise."""

@@ -13,13 +13,15 @@
 // The scratch array, g_row_partials, holds kNoallocMaxRows rows x 5 doubles
 // (640 KiB).  Every GPU that loads the library holds it until the process
 // exits.  Host code cannot use the array's name as a device address (in
-// host code it names a host-side stand-in), so on the first call on each
-// device, with that device current, the address is looked up with
-// cudaGetSymbolAddress and cached per device.
+// host code it names a host-side stand-in), so every call looks the address
+// up with cudaGetSymbolAddress, with the caller's device current.  The
+// lookup allocates nothing; it is not cached, because the array's address
+// belongs to the context that loaded the library's device code, and a
+// cached one would be stale after cudaDeviceReset or under another context
+// of the same device.
 #include <cmath>
 #include <cstdint>
 #include <limits>
-#include <mutex>
 #include <string>
 
 #include "lbm_internal.h"
@@ -32,15 +34,11 @@ namespace {
 
 constexpr int kNoallocMaxRows = 16384;
 constexpr int kNoallocSlots = 5;  // num, den, sum(rho - 1), fluid count, non-finite count
-constexpr int kNoallocMaxDevices = 64;
 constexpr int kRowThreads = 256;
 constexpr int kFinalThreads = 1024;
 
 // Row partials of the latest call, then (at the end) its 5 totals.
 static __device__ __align__(256) double g_row_partials[(kNoallocMaxRows + 1) * kNoallocSlots];
-
-std::mutex g_mu;
-double *g_scratch[kNoallocMaxDevices] = {};
 
 __constant__ double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
@@ -82,9 +80,11 @@ noalloc_rows(const double *__restrict__ cur, const double *__restrict__ prev,
     if (solid[p]) continue;
     double u1, v1, u0, v0;
     const double drho = macro(cur, n, p, ax, ay, u1, v1);
-    macro(prev, n, p, ax, ay, u0, v0);
+    const double drho0 = macro(prev, n, p, ax, ay, u0, v0);
     acc[3] += 1.0;
-    if (!(isfinite(drho) && isfinite(u1) && isfinite(v1))) {
+    // a non-finite value in either state counts, as in lbm_residual
+    if (!(isfinite(drho) && isfinite(u1) && isfinite(v1) && isfinite(drho0) && isfinite(u0) &&
+          isfinite(v0))) {
       acc[4] += 1.0;
       continue;
     }
@@ -125,21 +125,13 @@ __global__ void __launch_bounds__(kFinalThreads) noalloc_final(double *rows, int
   }
 }
 
-// Device address of g_row_partials on the current device, looked up once
-// per device.
+// Device address of g_row_partials in the context current on the calling
+// thread (see the file comment: looked up on every call, never cached).
 cudaError_t scratch_for_current_device(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_row_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_row_partials);
-    if (e != cudaSuccess) return e;
-    g_scratch[dev] = static_cast<double *>(p);
-  }
-  *out = g_scratch[dev];
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 

@@ -64,3 +64,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         lbm.lbm_residual_noalloc(f.data_ptr(), f.data_ptr(), m.data_ptr(), 1, 16385, 0.0, 0.0)
     assert ei.value.code == lbm.LBM_EINVAL
     assert "16384" in str(ei.value)
+
+
+def test_noalloc_reports_a_nonfinite_previous_state():
+    """A non-finite value in the previous state alone is reported, as
+    lbm_residual reports it (both states are checked)."""
+    import torch
+
+    lbm.load()
+    torch.cuda.set_device(0)
+    case = cases.cylinder_array(120, 64, 3, Kn=0.02, ax=1e-5)
+    f = cases.random_populations(case.nx, case.ny, 2)
+    fl = np.argwhere(case.solid == 0)[17]
+    f_prev = f.copy()
+    f_prev[5, fl[0], fl[1]] = np.nan
+    cur = torch.from_numpy(f).cuda()
+    prev = torch.from_numpy(f_prev).cuda()
+    solid = torch.from_numpy(np.ascontiguousarray(case.solid, np.uint8)).cuda()
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_residual_noalloc(cur.data_ptr(), prev.data_ptr(), solid.data_ptr(), case.nx,
+                                 case.ny, case.ax, case.ay)
+    assert ei.value.code == lbm.LBM_EUNSTABLE
+    # the clean pair still reports normally afterwards
+    res, mass = lbm.lbm_residual_noalloc(cur.data_ptr(), cur.data_ptr(), solid.data_ptr(), case.nx,
+                                         case.ny, case.ax, case.ay)
+    assert res == 0.0 and math.isfinite(mass)

@@ -34,22 +34,36 @@ from . import params  # noqa: F401
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_HERE, "liblbm_oracle_omp.so")
+_libs = {}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (plain C, -O2, no target-specific flags,
+    no contraction into FMAs), twice from the same source: single-threaded,
+    and with OpenMP over the row loops of a step (bitwise the same results).
+    Returns the single-threaded library's path."""
+    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", *extra, "-shared",
+                                   "-fPIC", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, lib)
     return _LIB
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _load(threaded: bool = False):
+    if threaded not in _libs:
+        build()
+        lib = ctypes.CDLL(_LIB_OMP if threaded else _LIB)
         P = ctypes.c_void_p
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int32)
@@ -68,8 +82,10 @@ def _load():
         lib.olbm_steps.restype = ctypes.c_long
         lib.olbm_steps.argtypes = [P]
         lib.olbm_destroy.argtypes = [P]
-        _lib = lib
-    return _lib
+        lib.olbm_set_threads.argtypes = [ctypes.c_int]
+        lib.olbm_threads.restype = ctypes.c_int
+        _libs[threaded] = lib
+    return _libs[threaded]
 
 
 def _dp(a):
@@ -83,11 +99,15 @@ class OracleLBM:
     unless `link_r` / `link_l` are given.  `diffuse_mode` 0 evaluates the
     Maxwell part of Eq. EqNewBDSC at the fluid velocity of x_f (the reading
     under which the analysis of Sec. 3.B holds), 1 at the wall velocity u_b
-    (the equation as printed).
+    (the equation as printed).  `threads` > 1 runs the OpenMP build of the
+    same source on that many threads (bitwise the same states).
     """
 
-    def __init__(self, case, par, link_r=None, link_l=None, diffuse_mode=0):
-        lib = _load()
+    def __init__(self, case, par, link_r=None, link_l=None, diffuse_mode=0, threads=1):
+        self._lib = lib = _load(threads > 1)
+        if threads > 1:
+            lib.olbm_set_threads(int(threads))
+        self.threads = int(lib.olbm_threads())
         self.case = case
         self.par = par
         g = np.ascontiguousarray(case.link_q, np.float64)
@@ -118,46 +138,46 @@ class OracleLBM:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            _load().olbm_destroy(h)
+            self._lib.olbm_destroy(h)
             self._h = None
 
     def step(self, n: int = 1):
-        _load().olbm_step(self._h, int(n))
+        self._lib.olbm_step(self._h, int(n))
 
     @property
     def steps(self) -> int:
-        return int(_load().olbm_steps(self._h))
+        return int(self._lib.olbm_steps(self._h))
 
     def fields(self):
         n = self.case.nx * self.case.ny
         rho, ux, uy = np.empty(n), np.empty(n), np.empty(n)
-        _load().olbm_fields(self._h, _dp(rho), _dp(ux), _dp(uy))
+        self._lib.olbm_fields(self._h, _dp(rho), _dp(ux), _dp(uy))
         s = (self.case.ny, self.case.nx)
         return rho.reshape(s), ux.reshape(s), uy.reshape(s)
 
     def residual(self):
         res = ctypes.c_double()
         mass = ctypes.c_double()
-        _load().olbm_residual(self._h, ctypes.byref(res), ctypes.byref(mass))
+        self._lib.olbm_residual(self._h, ctypes.byref(res), ctypes.byref(mass))
         return res.value, mass.value
 
     def get_f(self) -> np.ndarray:
         f = np.empty((9, self.case.ny, self.case.nx))
-        _load().olbm_get_f(self._h, _dp(f))
+        self._lib.olbm_get_f(self._h, _dp(f))
         return f
 
     def get_fpost(self) -> np.ndarray:
         f = np.empty((9, self.case.ny, self.case.nx))
-        _load().olbm_get_fpost(self._h, _dp(f))
+        self._lib.olbm_get_fpost(self._h, _dp(f))
         return f
 
     def set_f(self, f: np.ndarray):
         f = np.ascontiguousarray(f, np.float64).reshape(9, self.case.ny, self.case.nx)
-        _load().olbm_set_f(self._h, _dp(f))
+        self._lib.olbm_set_f(self._h, _dp(f))
 
     def minv(self) -> np.ndarray:
         m = np.empty((9, 9))
-        _load().olbm_get_minv(self._h, _dp(m))
+        self._lib.olbm_get_minv(self._h, _dp(m))
         return m
 
     def run_to(self, tol: float, max_steps: int, every: int = 100):

@@ -24,11 +24,19 @@
  *      wall velocity u_b as printed in Eq. EqNewBDSC in mode 1.
  * M^-1 is obtained once by Gauss-Jordan elimination of the printed M.
  * Sums over nodes (residual, mass) run serially in a fixed order.
+ *
+ * The same source builds single-threaded and, with -fopenmp, with the row
+ * loops of a step spread over threads: every node's arithmetic is the same
+ * and every destination is written by exactly one iteration, so both builds
+ * give bitwise the same states.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static const int CXs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CYs[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -238,15 +246,18 @@ static void collide_node(olbm *o, int x, int y) {
 void olbm_step(olbm *o, long nsteps) {
     int nx = o->nx, ny = o->ny;
     for (long s = 0; s < nsteps; s++) {
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; y++)
             for (int x = 0; x < nx; x++)
                 if (!o->solid[(size_t)y * nx + x]) collide_node(o, x, y);
         /* solid nodes keep their values */
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; y++)
             for (int x = 0; x < nx; x++)
                 if (o->solid[(size_t)y * nx + x])
                     for (int i = 0; i < 9; i++) o->fnew[IDX(o, i, x, y)] = o->f[IDX(o, i, x, y)];
-        /* streaming */
+        /* streaming (each fluid destination has exactly one source) */
+#pragma omp parallel for schedule(static)
         for (int y = 0; y < ny; y++)
             for (int x = 0; x < nx; x++) {
                 if (o->solid[(size_t)y * nx + x]) continue;
@@ -258,7 +269,8 @@ void olbm_step(olbm *o, long nsteps) {
                         o->fnew[IDX(o, i, xn, yn)] = o->fpost[IDX(o, i, x, y)];
                 }
             }
-        /* boundary links, Eq. EqNewBDSC */
+        /* boundary links, Eq. EqNewBDSC (one link per unknown population) */
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < o->nl; k++) {
             int x = o->lx[k], y = o->ly[k], i = o->ld[k], ib = OPPs[i];
             double r = o->lr[k], l = o->ll[k], g = o->lg[k];
@@ -344,3 +356,20 @@ void olbm_get_fpost(const olbm *o, double *f) {
 void olbm_get_minv(const olbm *o, double *minv) { memcpy(minv, o->Minv, sizeof(o->Minv)); }
 
 long olbm_steps(const olbm *o) { return o->steps; }
+
+/* Threads of the row loops (the OpenMP build; 1 in the single-threaded one). */
+void olbm_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int olbm_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

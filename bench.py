@@ -150,44 +150,66 @@ def reduce_over_ranks(values_max, values_sum, world, device):
     return [float(v) for v in tm.cpu()], [float(v) for v in ts.cpu()]
 
 
-def cpu_baseline_sample(precision: str, n_steps: int = 3, rows: int = 512):
-    """The FP64 oracle (single thread, as it stands) on a bounded sample of
-    the workload: `n_steps` lattice steps of an 8192 x `rows` channel built
-    with the same cylinder recipe.  Returns MLUPS over fluid nodes."""
+def _oracle_band(rows: int, threads: int):
+    """The FP64 oracle on an 8192 x `rows` channel built with the throughput
+    case's cylinder recipe (a band of the same workload), on `threads`
+    threads of its OpenMP build."""
     import oracle
     from oracle import params as P
     from paper_2012_14707_gb300 import cases
     case = cases.cylinder_array(8192, rows, 0, porosity=0.7, Kn=0.02, ax=1e-5,
                                 name=f"cylinders_8192x{rows}_s0")
-    o = oracle.OracleLBM(case, P.Parameters(case.Kn, case.H))
-    o.step(1)
+    return oracle.OracleLBM(case, P.Parameters(case.Kn, case.H), threads=threads), case
+
+
+def cpu_baseline_sample(rows: int = 1024, warmup: int = 10, min_seconds: float = 5.0,
+                        repeats: int = 3):
+    """The FP64 oracle as it stands, on every host core, on a bounded sample of
+    the workload: `warmup` lattice steps of an 8192 x `rows` band, then
+    `repeats` timings of whole lattice steps, each at least `min_seconds`
+    long.  Returns (median MLUPS over fluid nodes, case, cores, steps timed)."""
+    import oracle
+    cores = oracle.host_cores()
+    o, case = _oracle_band(rows, cores)
+    o.step(warmup)
     t0 = time.perf_counter()
-    o.step(n_steps)
-    dt = time.perf_counter() - t0
-    return case.n_fluid * n_steps / dt / 1e6, case, dt
+    o.step(1)
+    chunk = max(1, int(0.5 / max(time.perf_counter() - t0, 1e-6)))
+    rates, steps = [], 0
+    for _ in range(repeats):
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            o.step(chunk)
+            n += chunk
+            dt = time.perf_counter() - t0
+            if dt >= min_seconds:
+                break
+        rates.append(case.n_fluid * n / dt / 1e6)
+        steps += n
+    return statistics.median(rates), case, o.threads, steps
 
 
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    # a band of the same recipe, as tall as keeps the whole run within about
-    # three minutes of one host core (~4 M fluid-node updates per second)
-    rows = int(min(512, max(16, 180 * 4e6 / (0.7 * 8192 * max(1, args.steps + args.warmup)))))
-    rows -= rows % 16
     import oracle
-    from oracle import params as P
-    from paper_2012_14707_gb300 import cases
-    case = cases.cylinder_array(8192, rows, 0, porosity=0.7, Kn=0.02, ax=1e-5,
-                                name=f"cylinders_8192x{rows}_s0")
-    o = oracle.OracleLBM(case, P.Parameters(case.Kn, case.H))
+    cores = oracle.host_cores()
+    # a band of the same recipe, as tall as keeps the whole run within about
+    # three minutes on the host cores (~3 M fluid-node updates per second
+    # and core assumed), at most 1024 rows
+    rows = int(min(1024, max(16, 180 * 3e6 * cores / (0.7 * 8192 * max(1, args.steps + args.warmup)))))
+    rows -= rows % 16
+    o, case = _oracle_band(rows, cores)
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
     mlups = case.n_fluid * args.steps / dt / 1e6
     sample = (f"each step: one FP64 lattice step of an 8192x{rows} channel with the same "
-              f"cylinder recipe ({case.n_fluid} fluid nodes), single thread")
+              f"cylinder recipe ({case.n_fluid} fluid nodes), OpenMP over rows on "
+              f"{o.threads} threads")
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -197,7 +219,7 @@ def run_reference(args):
                    "precision": "fp64 (oracle)", "lattice_steps_per_step": 1,
                    "sample_rows": rows,
                    "l2": "inputs larger than L2 not applicable (CPU)"},
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": o.threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -323,11 +345,13 @@ def run_ours(args):
         "residual_last": last[0] if last else None,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        v, bcase, dt = cpu_baseline_sample(args.precision)
+        v, bcase, cores, nst = cpu_baseline_sample()
         line["cpu_baseline"] = {
-            "value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"3 FP64 lattice steps of an 8192x512 channel with the same cylinder "
-                      f"recipe ({bcase.n_fluid} fluid nodes), {dt:.1f} s"}
+            "value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle (OpenMP over rows, {cores} threads) on an 8192x{bcase.ny} "
+                      f"channel with the same cylinder recipe ({bcase.n_fluid} fluid nodes): "
+                      f"10 warm-up lattice steps, then the median of 3 timings of >= 5 s "
+                      f"({nst} lattice steps in all)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

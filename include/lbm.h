@@ -55,6 +55,14 @@ typedef enum {
   LBM_BF16 = 2, /* deviations stored as BF16, FP32 arithmetic */
   LBM_FP16 = 3  /* deviations times storage_scale stored as FP16, FP32 arithmetic */
 } lbm_precision;
+/* BF16 and FP16 storage round every stored value stochastically (to one of
+ * its two storage neighbours, with probabilities that make it exact on
+ * average), so changes smaller than a storage unit are not lost step after
+ * step.  The random bits are a counter-based hash of the node and the step
+ * count: a run is reproducible, and a resumed or batched case takes the
+ * same roundings as the uninterrupted lone case.  A value beyond the
+ * largest finite 16-bit number saturates there; lbm_residual reports a
+ * saturated value as non-finite (LBM_EUNSTABLE). */
 
 typedef enum {
   LBM_L_PAPER = 0,        /* l from Eq. Eqexlva, set to 0 where it is below l_clamp */
@@ -97,6 +105,15 @@ typedef struct {
                            time equals tau_s and E solves Eq. NSliCoertstq for tau_q = tau_s
                            (tau_q, E and the fixed relaxation times given here are ignored) */
   void *stream;         /* cudaStream_t for all device work; NULL = legacy default stream */
+  int32_t mass_mode;    /* LBM_FP32 only.  0 (default): the exact-mass step where a wall moves
+                           (some link has a nonzero wall velocity); 1: always; -1: never.  The
+                           exact-mass step forms each boundary link's value (Eq. EqNewBDSC) and
+                           the rest population's mass closure in FP64 and keeps, per link and
+                           per node, what FP32 storage dropped from them, adding it to the next
+                           value: the stored mass then follows the FP64 trajectory within one
+                           rounding per population instead of drifting by a rounding that
+                           repeats every step.  It costs 4 B per link and 8 B per fluid node
+                           of extra traffic per step. */
 } lbm_params_t;
 
 typedef struct {
@@ -107,6 +124,8 @@ typedef struct {
   int64_t device_bytes;   /* device memory held by the handle */
   int32_t precision, pitch; /* storage precision; row pitch in elements of a dense lattice
                                (0: the single-case solver stores fluid nodes only) */
+  int32_t exact_mass;     /* 1 if the step runs the exact-mass variant (see mass_mode) */
+  int32_t reserved;
 } lbm_info_t;
 
 /* Fill *p with the defaults listed above (no side effects). */
@@ -213,13 +232,17 @@ int lbm_precompute(double Kn, double H, const lbm_params_t *params, size_t n,
  *   residual, mass: host outputs.
  * Scratch: a fixed device array in the library (16384 rows x 5 doubles,
  * 640 KiB), held by every GPU that loads the library until the process
- * exits; ny > 16384 is LBM_EINVAL.  The first call on a device looks up that
- * array's address with the device current, so make the first call on each
- * device before any stream capture.  All calls share the array and each
- * call overwrites every part of it that it reads, so calls whose work
- * overlaps on the GPU (other threads, other streams) race and must not be
- * issued concurrently.  Errors: LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE (outputs
- * still written); the message is lbm_last_error(NULL).
+ * exits; ny > 16384 is LBM_EINVAL.  Each call looks up that array's address
+ * in the context current on the calling thread (the lookup allocates
+ * nothing; it is repeated on every call so that a device reset or another
+ * context never leaves a stale address).  The first call on a device may
+ * load the library's device code there, so make it before any stream
+ * capture.  All calls share the array and each call overwrites every part
+ * of it that it reads, so calls whose work overlaps on the GPU (other
+ * threads, other streams) race and must not be issued concurrently.
+ * Errors: LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE (a fluid node with a
+ * non-finite density or velocity in either state; outputs still written);
+ * the message is lbm_last_error(NULL).
  */
 int lbm_residual_noalloc(const double *f_cur, const double *f_prev, const uint8_t *solid,
                          int32_t nx, int32_t ny, double ax, double ay, void *stream,
@@ -257,10 +280,12 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
 /* Back to rest, every case active, step counts zero. */
 int lbm_batch_reset(lbm_batch_t *b);
 /* Advance all active cases, check_every (even, >= 2) steps at a time, until
- * every case has residual < tol or max_steps were taken.  Outputs (host,
- * n_cases entries, may be NULL): the step count at which each case met tol
- * (negative if it became non-finite, 0 if still running) and its last
- * residual; *steps_total = steps taken by the batch.  Synchronises. */
+ * every case has residual < tol or max_steps were taken.  The batch advances
+ * in whole rounds of check_every steps, so a max_steps that is not a
+ * multiple of check_every is rounded up to the next multiple.  Outputs
+ * (host, n_cases entries, may be NULL): the step count at which each case
+ * met tol (negative if it became non-finite, 0 if still running) and its
+ * last residual; *steps_total = steps taken by the batch.  Synchronises. */
 int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t check_every,
                      int64_t *steps_per_case, double *residual_per_case, int64_t *steps_total);
 /* Warm start of case c from density / velocity fields (host, nx*ny
@@ -307,6 +332,10 @@ int lbm_net_gradients(lbm_net_t *n, const float *x, const float *t, int32_t batc
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on that loss. */
 int lbm_net_train_step(lbm_net_t *n, const float *x, const float *t, int32_t batch, float lr,
                        double *loss);
+/* LBM_ETIMEOUT from a network call means a tensor-core kernel gave up
+ * waiting on one of its barriers (a bounded wait) and returned early; the
+ * network's activations and parameters are then unspecified.  Destroy the
+ * network and create a new one; do not reuse it. */
 void lbm_net_destroy(lbm_net_t *n);
 const char *lbm_net_last_error(const lbm_net_t *n);
 

@@ -10,6 +10,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "lbm_device.cuh"
 #include "lbm_internal.h"
 
 struct lbm_handle {
@@ -33,6 +34,12 @@ struct lbm_handle {
   int32_t *rowstart = nullptr;
   int32_t *index = nullptr;  // y * nx + x -> compacted index or -1
   void *links = nullptr;
+  // the exact-mass variant (FP32 storage with moving walls): FP64 link
+  // records and the per-link carry (see lbm::link_epilogue_pull)
+  int exact = 0;
+  lbm::LinkCoef<double> *links64 = nullptr;
+  float *carry = nullptr;   // per link
+  float *carry0 = nullptr;  // per fluid node (rest population)
   double *partials = nullptr;
   double *result = nullptr;
   double *h_result = nullptr;  // pinned, 4 doubles
@@ -132,6 +139,7 @@ void release(lbm_handle_t *h) {
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->grp),
                   static_cast<void *>(h->jbslot),
                   static_cast<void *>(h->rowstart), static_cast<void *>(h->index), h->links,
+                  static_cast<void *>(h->links64), static_cast<void *>(h->carry),
                   static_cast<void *>(h->partials), static_cast<void *>(h->result)})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -141,8 +149,12 @@ void release(lbm_handle_t *h) {
 
 template <typename C>
 lbm::StepConst<C> step_const(const lbm_handle_t *h) {
-  return lbm::make_step_const<C>(h->cp, h->nx, h->ny, 0, h->plane, h->n_fluid, h->px, h->py,
-                                 h->ax, h->ay, h->params.diffuse_mode, h->scale);
+  lbm::StepConst<C> k = lbm::make_step_const<C>(h->cp, h->nx, h->ny, 0, h->plane, h->n_fluid,
+                                                h->px, h->py, h->ax, h->ay,
+                                                h->params.diffuse_mode, h->scale);
+  k.sr_seed = lbm::dev::step_seed(h->steps);
+  k.exact = h->exact;
+  return k;
 }
 
 lbm::PullGeom pull_geom(const lbm_handle_t *h) {
@@ -156,7 +168,22 @@ lbm::PullGeom pull_geom(const lbm_handle_t *h) {
   g.plane = static_cast<uint32_t>(h->plane);
   g.n_fluid = static_cast<uint32_t>(h->n_fluid);
   g.pf_dist = h->pf_dist;
+  g.links64 = h->links64;
+  g.carry = h->carry;
+  g.carry0 = h->carry0;
   return g;
+}
+
+// Bytes of the exact-mass variant's carries (per link, then per node).
+size_t carry_bytes(const lbm_handle_t *h) {
+  return h->exact ? static_cast<size_t>(std::max<int64_t>(1, h->n_links) + h->plane) * sizeof(float)
+                  : 0;
+}
+
+// Zero the carries of the exact-mass variant (a new state owes nothing).
+cudaError_t clear_carry(lbm_handle_t *h) {
+  if (!h->exact) return cudaSuccess;
+  return cudaMemsetAsync(h->carry, 0, carry_bytes(h), h->stream);
 }
 
 lbm::NodeMap node_map(const lbm_handle_t *h) {
@@ -210,6 +237,7 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
     return bad(LBM_EINVAL, "storage_scale must be 0 (default) or a positive power of two");
   if (p.diffuse_mode != 0 && p.diffuse_mode != 1) return bad(LBM_EINVAL, "diffuse_mode must be 0 or 1");
   if (p.residual_every < 1) return bad(LBM_EINVAL, "residual_every must be >= 1");
+  if (p.mass_mode < -1 || p.mass_mode > 1) return bad(LBM_EINVAL, "mass_mode must be -1, 0 or 1");
   if (!std::isfinite(dom->ax) || !std::isfinite(dom->ay)) return bad(LBM_EINVAL, "non-finite force");
   const int32_t nx = dom->nx, ny = dom->ny;
   // 32-bit element offsets in the kernels: 9 planes of the padded lattice < 2^31.
@@ -290,6 +318,7 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
       return bad(LBM_EINVAL, buf);
     }
     fl |= static_cast<uint8_t>(1u << (i - 1));
+    if (link_ubx[k] != 0.0 || link_uby[k] != 0.0) hc->moving_walls = true;
   }
   // Every unknown direction of every fluid node needs its link (rows in
   // parallel; the first offending node in row-major order is reported).
@@ -548,6 +577,7 @@ void lbm_params_default(lbm_params_t *p) {
   p->precision = LBM_FP32;
   p->residual_every = 100;
   p->stream = nullptr;
+  p->mass_mode = 0;
 }
 
 int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
@@ -677,6 +707,18 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   if (e == cudaSuccess)
     e = alloc(reinterpret_cast<void **>(&h->jbslot), std::max<size_t>(1, jbs.size()) * 4);
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
+  h->exact = lbm::exact_mass(hc) ? 1 : 0;
+  if (h->exact) {
+    // one allocation: the per-link carries, then the per-node ones
+    const size_t nl = std::max<size_t>(1, n_links_sz);
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->links64), nl * 32);
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->carry), carry_bytes(h));
+    if (e == cudaSuccess) h->carry0 = h->carry + nl;
+    if (e == cudaSuccess && n_links_sz)
+      e = cudaMemcpyAsync(h->links64, hc.coef.data(), n_links_sz * 32, cudaMemcpyHostToDevice,
+                          h->stream);
+    if (e == cudaSuccess) e = clear_carry(h);
+  }
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_result), 4 * sizeof(double));
@@ -830,6 +872,7 @@ int lbm_set_f(lbm_handle_t *h, const double *f) {
                                      h->stream);
     });
   cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = clear_carry(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_f");
   h->steps = 0;
@@ -861,6 +904,7 @@ int lbm_set_fields(lbm_handle_t *h, const double *rho, const double *ux, const d
                                        h->stream);
     });
   if (d) cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = clear_carry(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
   h->steps = 0;
@@ -890,6 +934,7 @@ int lbm_get_info(const lbm_handle_t *h, lbm_info_t *info) {
   info->device_bytes = h->dev_bytes;
   info->precision = h->precision;
   info->pitch = h->pitch;
+  info->exact_mass = h->exact;
   return LBM_OK;
 }
 
@@ -946,7 +991,7 @@ constexpr char kCheckpointMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
 CheckpointHeader checkpoint_header(const lbm_handle_t *h) {
   CheckpointHeader hd{};
   std::memcpy(hd.magic, kCheckpointMagic, 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.precision = h->precision;
   hd.nx = h->nx;
   hd.ny = h->ny;
@@ -963,14 +1008,18 @@ int lbm_save(lbm_handle_t *h, const char *path) {
   if (!h) return LBM_EINVAL;
   if (!path) return fail(h, LBM_EINVAL, "null path");
   std::vector<unsigned char> buf;
+  const size_t cbytes = carry_bytes(h);
   try {
-    buf.resize(2 * h->fbytes);
+    buf.resize(2 * h->fbytes + cbytes);
   } catch (...) {
     return fail(h, LBM_ENOMEM, "host buffer for the checkpoint");
   }
   LBM_CK(h, cudaMemcpyAsync(buf.data(), h->f[h->cur], h->fbytes, cudaMemcpyDeviceToHost, h->stream));
   LBM_CK(h, cudaMemcpyAsync(buf.data() + h->fbytes, h->f[1 - h->cur], h->fbytes,
                             cudaMemcpyDeviceToHost, h->stream));
+  if (cbytes)
+    LBM_CK(h, cudaMemcpyAsync(buf.data() + 2 * h->fbytes, h->carry, cbytes, cudaMemcpyDeviceToHost,
+                              h->stream));
   LBM_CK(h, cudaStreamSynchronize(h->stream));
   const CheckpointHeader hd = checkpoint_header(h);
   FILE *f = std::fopen(path, "wb");
@@ -995,7 +1044,7 @@ int lbm_load(lbm_handle_t *h, const char *path) {
   const CheckpointHeader want = checkpoint_header(h);
   std::string why;
   if (std::memcmp(hd.magic, kCheckpointMagic, 8) != 0) why = "not a checkpoint file";
-  else if (hd.version != 1) why = "unknown checkpoint version";
+  else if (hd.version != 2) why = "unknown checkpoint version";
   else if (hd.precision != want.precision) why = "checkpoint of another precision";
   else if (hd.nx != want.nx || hd.ny != want.ny || hd.n_fluid != want.n_fluid ||
            hd.n_links != want.n_links || hd.elems != want.elems ||
@@ -1007,8 +1056,9 @@ int lbm_load(lbm_handle_t *h, const char *path) {
     return fail(h, LBM_EINVAL, why + ": " + path);
   }
   std::vector<unsigned char> buf;
+  const size_t cbytes = carry_bytes(h);
   try {
-    buf.resize(2 * h->fbytes);
+    buf.resize(2 * h->fbytes + cbytes);
   } catch (...) {
     std::fclose(f);
     return fail(h, LBM_ENOMEM, "host buffer for the checkpoint");
@@ -1019,6 +1069,9 @@ int lbm_load(lbm_handle_t *h, const char *path) {
   LBM_CK(h, cudaMemcpyAsync(h->f[h->cur], buf.data(), h->fbytes, cudaMemcpyHostToDevice, h->stream));
   LBM_CK(h, cudaMemcpyAsync(h->f[1 - h->cur], buf.data() + h->fbytes, h->fbytes,
                             cudaMemcpyHostToDevice, h->stream));
+  if (cbytes)
+    LBM_CK(h, cudaMemcpyAsync(h->carry, buf.data() + 2 * h->fbytes, cbytes, cudaMemcpyHostToDevice,
+                              h->stream));
   LBM_CK(h, cudaStreamSynchronize(h->stream));
   h->steps = hd.steps;
   return LBM_OK;

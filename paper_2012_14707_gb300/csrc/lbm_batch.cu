@@ -55,7 +55,9 @@ struct BatchCase {
 template <typename C>
 __host__ __device__ inline PullGeom case_geom(const BatchCase<C> &bc, const uint2 *node,
                                               const int2 *grp, const int32_t *rowstart,
-                                              const uint32_t *jbslot) {
+                                              const uint32_t *jbslot,
+                                              const LinkCoef<double> *links64 = nullptr,
+                                              float *carry = nullptr, float *carry0 = nullptr) {
   PullGeom g;
   g.node = node + bc.node_off;
   g.grp = grp + bc.grp_off;
@@ -66,6 +68,9 @@ __host__ __device__ inline PullGeom case_geom(const BatchCase<C> &bc, const uint
   g.plane = static_cast<uint32_t>(bc.k.plane);
   g.n_fluid = static_cast<uint32_t>(bc.n_fluid);
   g.pf_dist = 0;
+  g.links64 = links64 ? links64 + bc.link_off : nullptr;
+  g.carry = carry ? carry + bc.link_off : nullptr;
+  g.carry0 = carry0 ? carry0 + bc.node_off : nullptr;
   return g;
 }
 
@@ -78,7 +83,11 @@ constexpr int kChunk = 256;  // node-arena alignment of every case (>= any CTA w
 // THREADS - 1, all of case ccase[b * THREADS / kChunk] (the index is
 // CTA-uniform, so the case's constants stay out of the per-thread
 // registers).  Like the single-case kernel, each CTA first asks L2 for the
-// node words and case index of the CTA pf_dist blocks ahead.
+// node words and case index of the CTA pf_dist blocks ahead.  The step
+// count of every active case is *counter + j (the graph replays K steps,
+// j = 0 .. K-1, between advances of the counter), which seeds the random
+// bits exactly as the case's own step count does when it runs alone.  FP32
+// cases with moving walls (k.exact) are left to batch_exact_kernel.
 template <typename T, typename C, int THREADS>
 __global__ void __launch_bounds__(THREADS, PullOcc<T>::min_blocks * kPullThreads / THREADS)
 batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
@@ -86,7 +95,8 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
                   const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,
                   const uint32_t *__restrict__ jbslot, const LinkCoef<C> *__restrict__ links,
                   const BatchCase<C> *__restrict__ cases, const int32_t *__restrict__ active,
-                  const uint32_t n_blocks, const uint32_t pf_dist) {
+                  const uint32_t n_blocks, const uint32_t pf_dist,
+                  const int64_t *__restrict__ counter, const uint32_t j) {
   static_assert(kChunk % THREADS == 0, "a CTA stays inside one chunk");
   {
     constexpr uint32_t kNodeLines = THREADS * sizeof(uint2) / 128;
@@ -104,8 +114,64 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
   const BatchCase<C> &bc = cases[c];
   const uint32_t i = blockIdx.x * THREADS + threadIdx.x - static_cast<uint32_t>(bc.node_off);
   if (i >= static_cast<uint32_t>(bc.n_fluid)) return;
+  // exact-mass cases run in batch_exact_kernel
+  if (std::is_same<T, float>::value && bc.k.exact) return;
   const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot);
-  step_node_pull<T, C>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i);
+  uint32_t seed = 0;
+  if constexpr (kStochastic<T>) seed = step_seed(*counter + j);
+  step_node_pull<T, C, false>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i,
+                              seed);
+}
+
+// 16-bit batches: the paired step of the single-case kernel
+// (step_pair_pull).  CTA b runs node-arena entries b * 2 THREADS ..
+// (b + 1) * 2 THREADS - 1, two per thread, all of one case (2 THREADS
+// divides kChunk); the step seed is the batch step kernel's.
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS, PairOcc::min_blocks * kPairThreads / THREADS)
+batch_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint2 *__restrict__ node,
+                  const int2 *__restrict__ grp, const int32_t *__restrict__ ccase,
+                  const int32_t *__restrict__ rowstart, const uint32_t *__restrict__ jbslot,
+                  const LinkCoef<float> *__restrict__ links,
+                  const BatchCase<float> *__restrict__ cases, const int32_t *__restrict__ active,
+                  const int64_t *__restrict__ counter, const uint32_t j) {
+  static_assert(kChunk % (2 * THREADS) == 0, "a CTA stays inside one chunk");
+  const int c = ccase[blockIdx.x * 2 * THREADS / kChunk];
+  if (!active[c]) return;
+  const BatchCase<float> &bc = cases[c];
+  const uint32_t i0 = blockIdx.x * 2 * THREADS + 2 * threadIdx.x - static_cast<uint32_t>(bc.node_off);
+  if (i0 >= static_cast<uint32_t>(bc.n_fluid)) return;
+  const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot);
+  const uint32_t seed = step_seed(*counter + j);
+  if (i0 + 1u < static_cast<uint32_t>(bc.n_fluid))
+    step_pair_pull<T>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i0, seed);
+  else
+    step_node_pull<T, float, false>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k,
+                                    i0, seed);
+}
+
+// The exact-mass cases of an FP32 batch (moving walls; see collide and
+// link_epilogue_pull): one CTA of kChunk threads per node-arena chunk in
+// `chunks` (the chunks of those cases), with room for the FP64 registers.
+__global__ void __launch_bounds__(kChunk, 2)
+batch_exact_kernel(const float *__restrict__ src, float *__restrict__ dst,
+                   const uint2 *__restrict__ node, const int2 *__restrict__ grp,
+                   const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,
+                   const uint32_t *__restrict__ jbslot, const LinkCoef<float> *__restrict__ links,
+                   const BatchCase<float> *__restrict__ cases, const int32_t *__restrict__ active,
+                   const int32_t *__restrict__ chunks, const int64_t *__restrict__ counter,
+                   const uint32_t j, const LinkCoef<double> *__restrict__ links64,
+                   float *__restrict__ carry, float *__restrict__ carry0) {
+  const int32_t ch = chunks[blockIdx.x];
+  const int c = ccase[ch];
+  if (!active[c]) return;
+  const BatchCase<float> &bc = cases[c];
+  const uint32_t i = static_cast<uint32_t>(ch) * kChunk + threadIdx.x -
+                     static_cast<uint32_t>(bc.node_off);
+  if (i >= static_cast<uint32_t>(bc.n_fluid)) return;
+  const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot, links64, carry, carry0);
+  step_node_exact(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i,
+                  step_seed(*counter + j));
 }
 
 // One CTA per case: residual of the case (FP64 sums in a fixed order); a
@@ -135,14 +201,19 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
       uint32_t s[9];
       map.slots(static_cast<uint32_t>(i), static_cast<uint32_t>(k.plane), s);
       C a[9], b[9];
+      bool sat = false;
 #pragma unroll
       for (int q = 0; q < 9; q++) {
         a[q] = Stor<T>::ld(a_base[s[q]], k.inv_sc);
         b[q] = Stor<T>::ld(b_base[s[q]], k.inv_sc);
+        if constexpr (kStochastic<T>)
+          sat |= fabsf(Stor<T>::ld_raw(a_base[s[q]])) >= Stor<T>::kMaxRaw ||
+                 fabsf(Stor<T>::ld_raw(b_base[s[q]])) >= Stor<T>::kMaxRaw;
       }
       C n1, d1, m1;
       residual_terms<C>(a, b, k.ax, k.ay, n1, d1, m1);
-      if (!(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
+      // a saturated 16-bit value counts as non-finite
+      if (sat || !(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
         bad += 1.0;
         continue;
       }
@@ -187,12 +258,37 @@ cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int
                               const int32_t *ccase, const int32_t *rowstart,
                               const uint32_t *jbslot, const void *links, const void *cases,
                               const int32_t *active, int64_t arena_nodes, uint32_t pf_dist,
-                              cudaStream_t s) {
+                              const int64_t *counter, uint32_t j, const LinkCoef<double> *links64,
+                              float *carry, float *carry0, const int32_t *exact_chunks,
+                              int32_t n_exact_chunks, cudaStream_t s) {
   if (arena_nodes <= 0) return cudaSuccess;
+  if constexpr (kStochastic<T>) {
+    if constexpr (THREADS <= kChunk / 2) {
+      batch_pair_kernel<T, THREADS><<<static_cast<unsigned>(arena_nodes / (2 * THREADS)), THREADS,
+                                      0, s>>>(src, dst, node, grp, ccase, rowstart, jbslot,
+                                              static_cast<const LinkCoef<float> *>(links),
+                                              static_cast<const BatchCase<float> *>(cases), active,
+                                              counter, j);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;  // 16-bit batches use widths 64 and 128
+    }
+  }
   const int64_t blocks = arena_nodes / THREADS;  // arena_nodes: a multiple of kChunk
   batch_step_kernel<T, C, THREADS><<<static_cast<unsigned>(blocks), THREADS, 0, s>>>(
       src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<C> *>(links),
-      static_cast<const BatchCase<C> *>(cases), active, static_cast<uint32_t>(blocks), pf_dist);
+      static_cast<const BatchCase<C> *>(cases), active, static_cast<uint32_t>(blocks), pf_dist,
+      counter, j);
+  if constexpr (std::is_same<T, float>::value) {
+    if (n_exact_chunks > 0) {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      batch_exact_kernel<<<static_cast<unsigned>(n_exact_chunks), kChunk, 0, s>>>(
+          src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<float> *>(links),
+          static_cast<const BatchCase<float> *>(cases), active, exact_chunks, counter, j, links64,
+          carry, carry0);
+    }
+  }
   return cudaGetLastError();
 }
 
@@ -201,11 +297,16 @@ template <typename T, typename C, int THREADS>
 int batch_resident_ctas() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<T, C, THREADS>,
-                                                    THREADS, 0) != cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
-  return sms * per;
+  cudaError_t e;
+  if constexpr (kStochastic<T> && THREADS <= kChunk / 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_pair_kernel<T, THREADS>, THREADS,
+                                                      0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<T, C, THREADS>,
+                                                      THREADS, 0);
+  return e == cudaSuccess ? sms * per : 0;
 }
 
 // Autotuner cache: CTA width and prefetch distance per (precision, size
@@ -239,6 +340,15 @@ struct lbm_batch {
   int32_t *index = nullptr;
   void *links = nullptr;
   void *cases = nullptr;
+  // FP32 cases with moving walls: FP64 link records and per-link carry
+  // (the exact-mass variant), over the whole link arena; null if no case
+  // needs them
+  lbm::LinkCoef<double> *links64 = nullptr;
+  float *carry = nullptr;   // per link of the link arena, then per node-arena entry
+  float *carry0 = nullptr;  // = carry + max(1, n_links_total)
+  int64_t n_links_total = 0;
+  int32_t *exact_chunks = nullptr;  // node-arena chunks of those cases
+  int32_t n_exact_chunks = 0;
   int threads = 0;
   uint32_t pf_dist = 0;  // L2 prefetch distance of the step kernel (CTAs), for `threads`
   int32_t *active = nullptr;
@@ -290,7 +400,9 @@ lbm::NodeMap case_map(const lbm_batch_t *b, int c) {
   return m;
 }
 
-cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src) {
+// One step launch; j = the step's position after the last advance of the
+// device step counter (seeds the random bits).
+cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src, uint32_t j) {
   const int dst = 1 - src;
   return dispatch_b(b->precision, [&](auto tT, auto tC) {
     using T = std::remove_pointer_t<decltype(tT)>;
@@ -300,7 +412,9 @@ cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src) {
       return lbm::launch_batch_step<T, C, TH>(
           static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->node, b->grp,
           b->ccase, b->rowstart, b->jbslot, b->links, b->cases, b->active, b->arena_nodes,
-          pf_dist, b->stream);
+          pf_dist, b->counter, j, b->links64, b->carry, b->carry0, b->exact_chunks,
+          b->n_exact_chunks,
+          b->stream);
     };
     if (threads == 64) return go(std::integral_constant<int, 64>());
     if (threads == 128) return go(std::integral_constant<int, 128>());
@@ -320,7 +434,9 @@ void batch_release(lbm_batch_t *b) {
   for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->node), static_cast<void *>(b->grp),
                   static_cast<void *>(b->jbslot), static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->ccase), static_cast<void *>(b->active),
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
-                  static_cast<void *>(b->counter), static_cast<void *>(b->n_active)})
+                  static_cast<void *>(b->counter), static_cast<void *>(b->n_active),
+                  static_cast<void *>(b->links64), static_cast<void *>(b->carry),
+                  static_cast<void *>(b->exact_chunks)})
     if (p) cudaFree(p);
   if (b->h_n_active) cudaFreeHost(b->h_n_active);
   if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -352,7 +468,10 @@ lbm::TuneChoice autotune(lbm_batch_t *b) {
     auto it = lbm::g_tune_cache.find({b->precision, size_class});
     if (it != lbm::g_tune_cache.end()) return it->second;
   }
-  const int cand[3] = {64, 128, 256};
+  // CTA widths (threads); a 16-bit CTA runs two nodes per thread, so its
+  // widths stop at half a chunk
+  const bool pairs = b->precision == LBM_BF16 || b->precision == LBM_FP16;
+  const std::vector<int> cand = pairs ? std::vector<int>{64, 128} : std::vector<int>{64, 128, 256};
   float best_ms = std::numeric_limits<float>::infinity();
   lbm::TuneChoice best{128, 0};
   cudaEvent_t e0, e1;
@@ -361,9 +480,9 @@ lbm::TuneChoice autotune(lbm_batch_t *b) {
   for (int th : cand) {
     const uint32_t half = static_cast<uint32_t>(resident_ctas(b->precision, th) / 2);
     for (uint32_t pf : {0u, half}) {
-      for (int w = 0; w < 2; w++) step_once(b, th, pf, w & 1);
+      for (int w = 0; w < 2; w++) step_once(b, th, pf, w & 1, static_cast<uint32_t>(w));
       cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < 6; r++) step_once(b, th, pf, r & 1);
+      for (int r = 0; r < 6; r++) step_once(b, th, pf, r & 1, static_cast<uint32_t>(r));
       cudaEventRecord(e1, b->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -449,7 +568,12 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   std::vector<uint32_t> jbs(static_cast<size_t>(std::max<int64_t>(1, links)), 0u);
   std::vector<int32_t> rowstart(static_cast<size_t>(rows), 0), index(static_cast<size_t>(dense), -1);
   std::vector<unsigned char> lhost(std::max<int64_t>(1, links) * 4 * ces, 0);
+  std::vector<double> l64;  // FP64 link records (filled if some case runs the exact variant)
+  bool any_exact = false;
+  for (int c = 0; c < n_cases; c++) any_exact |= lbm::exact_mass(hc[c]);
+  if (any_exact) l64.assign(static_cast<size_t>(std::max<int64_t>(1, links)) * 4, 0.0);
   std::vector<unsigned char> chost;
+  std::vector<int32_t> xchunks;
   int64_t noff = 0, foff = 0, goff = 0, loff = 0, roff = 0, ioff = 0;
   for (int c = 0; c < n_cases; c++) {
     const lbm::HostCase &h = hc[c];
@@ -481,6 +605,11 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     std::copy(kj.begin(), kj.end(), jbs.begin() + loff);
     std::copy(k.rowstart.begin(), k.rowstart.end(), rowstart.begin() + roff);
     std::copy(k.index.begin(), k.index.end(), index.begin() + ioff);
+    if (lbm::exact_mass(h)) {
+      std::copy(h.coef.begin(), h.coef.begin() + 4 * h.n_links, l64.begin() + 4 * loff);
+      for (int64_t q = noff / lbm::kChunk; q < (noff + padded) / lbm::kChunk; q++)
+        xchunks.push_back(static_cast<int32_t>(q));
+    }
     for (int64_t q = 0; q < h.n_links; q++) {
       const double *cf = &h.coef[4 * q];
       if (ces == 8) {
@@ -497,6 +626,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       lbm::BatchCase<C> d;
       d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, 0, k.plane, h.n_fluid, h.px, h.py, h.ax,
                                     h.ay, h.params.diffuse_mode, h.scale);
+      d.k.exact = lbm::exact_mass(h) ? 1 : 0;
       d.f_off = foff;
       d.node_off = noff;
       d.grp_off = goff;
@@ -532,6 +662,20 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->rowstart), rowstart.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->index), index.size() * 4);
   if (e == cudaSuccess) e = alloc(&b->links, lhost.size());
+  b->n_links_total = links;
+  if (any_exact) {
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->links64), l64.size() * 8);
+    if (e == cudaSuccess)
+      e = alloc(reinterpret_cast<void **>(&b->carry), (l64.size() / 4 + nodes) * 4);
+    if (e == cudaSuccess) b->carry0 = b->carry + l64.size() / 4;
+    if (e == cudaSuccess) e = cudaMemset(b->carry, 0, (l64.size() / 4 + nodes) * 4);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->links64, l64.data(), l64.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->exact_chunks), xchunks.size() * 4);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->exact_chunks, xchunks.data(), xchunks.size() * 4, cudaMemcpyHostToDevice);
+    b->n_exact_chunks = static_cast<int32_t>(xchunks.size());
+  }
   if (e == cudaSuccess) e = alloc(&b->cases, chost.size());
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->active), n_cases * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->steps_done), n_cases * 8);
@@ -585,6 +729,10 @@ int lbm_batch_reset(lbm_batch_t *b) {
   const int64_t zero = 0;
   cudaError_t e = cudaMemsetAsync(b->f[0], 0, fbytes, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->f[1], 0, fbytes, b->stream);
+  if (e == cudaSuccess && b->carry)
+    e = cudaMemsetAsync(b->carry, 0,
+                        static_cast<size_t>(std::max<int64_t>(1, b->n_links_total) + b->arena_nodes) * 4,
+                        b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->active, ones.data(), n * 4, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
@@ -614,7 +762,7 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     for (int s = 0; s < check_every && e == cudaSuccess; s++)
-      e = step_once(b, b->threads, b->pf_dist, s & 1);
+      e = step_once(b, b->threads, b->pf_dist, s & 1, static_cast<uint32_t>(s));
     if (e == cudaSuccess)
       e = dispatch_b(b->precision, [&](auto tT, auto tC) {
         using T = std::remove_pointer_t<decltype(tT)>;
@@ -718,7 +866,8 @@ int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fl
   if (total_nodes) *total_nodes = b->total_nodes;
   if (total_fluid) *total_fluid = b->total_fluid;
   if (cta_threads) *cta_threads = b->threads;
-  if (n_ctas) *n_ctas = static_cast<int32_t>(b->arena_nodes / b->threads);
+  const bool pairs = b->precision == LBM_BF16 || b->precision == LBM_FP16;
+  if (n_ctas) *n_ctas = static_cast<int32_t>(b->arena_nodes / (b->threads * (pairs ? 2 : 1)));
   return LBM_OK;
 }
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -31,10 +32,23 @@ template <>
 struct Stor<__half> {
   using C = float;
   static constexpr bool kScaled = true;
+  static constexpr float kMaxRaw = 65504.0f;  // largest finite FP16
   static __device__ __forceinline__ float ld(__half v, float inv) { return __half2float(v) * inv; }
   static __device__ __forceinline__ __half st(float v, float sc) { return __float2half_rn(v * sc); }
   static __device__ __forceinline__ float ld_raw(__half v) { return __half2float(v); }
   static __device__ __forceinline__ __half st_raw(float v) { return __float2half_rn(v); }
+  // Two stored values by stochastic rounding (hi from a, lo from b), with
+  // the random bits rb: the result is the nearest value below or above with
+  // probabilities that make it exact on average.  Finite overflow saturates
+  // (the residual pass counts saturated values as non-finite).
+  static __device__ __forceinline__ uint32_t st_rs2(float a, float b, uint32_t rb) {
+    uint32_t d;
+    asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rb));
+    return d;
+  }
+  static __device__ __forceinline__ __half bits(uint32_t h) {
+    return __ushort_as_half(static_cast<unsigned short>(h));
+  }
 };
 template <>
 struct Stor<__nv_bfloat16> {
@@ -45,10 +59,45 @@ struct Stor<__nv_bfloat16> {
     return __float2bfloat16_rn(v);
   }
   static constexpr bool kScaled = false;
+  static constexpr float kMaxRaw = 3.38953139e38f;  // largest finite BF16
   static __device__ __forceinline__ float ld_raw(__nv_bfloat16 v) { return __bfloat162float(v); }
   static __device__ __forceinline__ __nv_bfloat16 st_raw(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ uint32_t st_rs2(float a, float b, uint32_t rb) {
+    uint32_t d;
+    asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rb));
+    return d;
+  }
+  static __device__ __forceinline__ __nv_bfloat16 bits(uint32_t h) {
+    return __ushort_as_bfloat16(static_cast<unsigned short>(h));
+  }
 };
 
+// 16-bit storage rounds stochastically (Stor<T>::st_rs2): a deterministic
+// rounding drops every change smaller than half a unit of the stored
+// deviation, and near steady state those dropped changes are the same step
+// after step, so the stored state drifts away from the exact one.
+template <typename T>
+constexpr bool kStochastic = std::is_same<T, __half>::value || std::is_same<T, __nv_bfloat16>::value;
+
+// The 32-bit finaliser of MurmurHash3 (Appleby): a bijective mix in which
+// every output bit depends on every input bit.  The random bits of the
+// stochastic rounding are this hash of the node index and a per-step seed
+// (counter-based: a step's roundings are a function of the node and the
+// step count only, so runs are reproducible and a resumed run is the
+// uninterrupted one).
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+// Seed of time step n (the same on the host and the device).
+__host__ __device__ __forceinline__ uint32_t step_seed(int64_t n) {
+  return fmix32(static_cast<uint32_t>(n) * 0x9E3779B9u + static_cast<uint32_t>(n >> 32) +
+                0x7F4A7C15u);
+}
 
 template <typename C>
 __device__ __forceinline__ C recip(C v);
@@ -66,6 +115,26 @@ __device__ __forceinline__ double recip<double>(double v) {
   return 1.0 / v;
 }
 
+// Two arithmetic lanes: the same quantity of two nodes (the paired 16-bit
+// step), each operation one packed FP32x2 instruction of this GPU with the
+// rounding of the scalar FP32 operation (a - b as fma(b, -1, a), exact).
+struct F2 {
+  float2 v;
+  F2() = default;
+  __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ explicit F2(float2 a) : v(a) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  return F2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+template <>
+__device__ __forceinline__ F2 recip<F2>(F2 v) {
+  return F2(make_float2(recip<float>(v.v.x), recip<float>(v.v.y)));
+}
+
 // Post-collision state of one node: the nine values (arithmetic type and
 // rounded to storage; in storage units where the storage is scaled) and
 // the macroscopic quantities the links need.
@@ -74,19 +143,34 @@ struct Collided {
   C o[9];
   T t[9];
   C drho, rho, ux, uy, uu;
+  // the exact-mass variant (FP32 storage): the same quantities in FP64
+  double drho64, rho64, ux64, uy64;
 };
 
-// Eq. FluidMacr, Eq. MomentPost and f' = M^-1 m' for the deviations d of one
-// node (in storage units, d * scale, where Stor<T>::kScaled); f'_1..f'_8
-// rounded to storage, f'_0 closing the mass balance.  Every quantity that
-// carries the storage scale S is computed as S times its unscaled value
-// exactly (S is a power of two), so the stored results do not depend on
-// the units.
-template <typename T, typename C>
-__device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, Collided<T, C> &r) {
-  constexpr bool kS = Stor<T>::kScaled;
-  C(&o)[9] = r.o;
-  T(&t)[9] = r.t;
+// a + b rounded to FP32 stochastically: the FP32 sum s (round to nearest)
+// or its neighbour on the side of the exact remainder e = a + b - s
+// (TwoSum, Knuth), taken with probability |e| / (spacing there), so the
+// result is a + b on average.  u16: 16 random bits.
+__device__ __forceinline__ float add_stochastic(float a, float b, uint32_t u16) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  if (e == 0.0f || s == 0.0f) return s;
+  const int bits = __float_as_int(s);
+  const float s2 = __int_as_float(((e > 0.0f) == (s > 0.0f)) ? bits + 1 : bits - 1);
+  return static_cast<float>(u16) * 0x1p-16f * fabsf(s2 - s) < fabsf(e) ? s2 : s;
+}
+
+// The collision of Eq. MomentPost as the change ch_i = f'_i - f_i of each
+// population, with the node's rho - 1, rho, u and |u|^2 (Eq. FluidMacr),
+// for the deviations d of one node (C = float or double) or of two nodes at
+// once (C = F2); S is the scalar type of the constants.  kS: d is in
+// storage units (times the storage scale).  kGiven: rho, ux, uy are taken
+// from given[0..2] instead of being formed here.
+template <bool kS, bool kGiven, typename C, typename S>
+__device__ __forceinline__ void collision_change(const C (&d)[9], const StepConst<S> &k,
+                                                 C (&ch)[9], C &drho, C &rho, C &ux, C &uy,
+                                                 C &uu, const C *given = nullptr) {
   // Moments of the deviations (rows of M, Sec. 2).  M w = (1, -2, 1, 0, ...).
   const C a13 = d[1] + d[3], a24 = d[2] + d[4];
   const C d5p6 = d[5] + d[6], d7p8 = d[7] + d[8];
@@ -101,16 +185,16 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   const C jy_s = v24 + w58, qy = C(-2) * v24 + w58;
   const C pxx = a13 - a24;
   const C pxy = d5m6 - d8m7;
-  const C drho = kS ? drho_s * k.inv_sc : drho_s;
+  drho = kS ? drho_s * k.inv_sc : drho_s;
   const C jx = kS ? jx_s * k.inv_sc : jx_s, jy = kS ? jy_s * k.inv_sc : jy_s;
 
   // Eq. FluidMacr.
-  const C rho = C(1) + drho;
+  rho = kGiven ? given[0] : C(1) + drho;
   const C rax = rho * k.ax, ray = rho * k.ay;
   const C inv_rho = recip<C>(rho);
-  const C ux = (jx + C(0.5) * rax) * inv_rho;
-  const C uy = (jy + C(0.5) * ray) * inv_rho;
-  const C uu = ux * ux + uy * uy;
+  ux = kGiven ? given[1] : (jx + C(0.5) * rax) * inv_rho;
+  uy = kGiven ? given[2] : (jy + C(0.5) * ray) * inv_rho;
+  uu = ux * ux + uy * uy;
   const C rux = rho * ux, ruy = rho * uy;
 
   // Eq. MomentPost, m' = m - S (m - m_eq) + (I - S/2) M Fbar, applied as
@@ -141,14 +225,75 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   const C diag = C(2) * e36 + p36;
   const C ax_x = jx6 - C(2) * qx12, ax_y = jy6 - C(2) * qy12;
   const C dg_x = jx6 + qx12, dg_y = jy6 + qy12;
-  o[1] = d[1] + (axis + ax_x + xx4);
-  o[2] = d[2] + (axis + ax_y - xx4);
-  o[3] = d[3] + (axis - ax_x + xx4);
-  o[4] = d[4] + (axis - ax_y - xx4);
-  o[5] = d[5] + (diag + dg_x + dg_y + xy4);
-  o[6] = d[6] + (diag - dg_x + dg_y - xy4);
-  o[7] = d[7] + (diag - dg_x - dg_y + xy4);
-  o[8] = d[8] + (diag + dg_x - dg_y - xy4);
+  ch[0] = C(0);
+  ch[1] = axis + ax_x + xx4;
+  ch[2] = axis + ax_y - xx4;
+  ch[3] = axis - ax_x + xx4;
+  ch[4] = axis - ax_y - xx4;
+  ch[5] = diag + dg_x + dg_y + xy4;
+  ch[6] = diag - dg_x + dg_y - xy4;
+  ch[7] = diag - dg_x - dg_y + xy4;
+  ch[8] = diag + dg_x - dg_y - xy4;
+}
+
+// Eq. FluidMacr, Eq. MomentPost and f' = M^-1 m' for the deviations d of one
+// node (in storage units, d * scale, where Stor<T>::kScaled); f'_1..f'_8
+// rounded to storage, f'_0 closing the mass balance.  Every quantity that
+// carries the storage scale S is computed as S times its unscaled value
+// exactly (S is a power of two), so the stored results do not depend on
+// the units.
+//
+// kExact (FP32 storage only): the stored mass must follow the FP64
+// trajectory to ~1e-10 over thousands of steps.  A moving wall exchanges
+// mass with the fluid at a rate set by the velocity next to it, so every
+// rounding that leans the same way step after step shows up in the mass.
+// Hence: rho and u are formed in FP64 and rounded once (no approximate
+// reciprocal) for the equilibrium and the links; f'_1..f'_8 are rounded to
+// FP32 stochastically (add_stochastic, random bits from rs); f'_0 closes
+// the node's mass in FP64 plus the node's carry c0 (what FP32 storage
+// dropped from its earlier values), is stored rounded to nearest, and the
+// new remainder is kept in c0.
+// 16-bit storage rounds f'_0..f'_8 stochastically with random bits from rs,
+// the node's random word (fmix32 of the node index and the step seed).
+template <typename T, typename C, bool kExact = false>
+__device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, Collided<T, C> &r,
+                                        const uint32_t rs = 0, float *c0 = nullptr) {
+  constexpr bool kS = Stor<T>::kScaled;
+  static_assert(!kExact || std::is_same<T, float>::value, "the exact-mass variant is FP32 storage");
+  C(&o)[9] = r.o;
+  T(&t)[9] = r.t;
+  if constexpr (kExact) {
+    double dr = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) dr += static_cast<double>(d[i]);
+    const double jx = (static_cast<double>(d[1]) - d[3]) + (static_cast<double>(d[5]) - d[6]) +
+                      (static_cast<double>(d[8]) - d[7]);
+    const double jy = (static_cast<double>(d[2]) - d[4]) + (static_cast<double>(d[5]) + d[6]) -
+                      (static_cast<double>(d[7]) + d[8]);
+    const double rh = 1.0 + dr;
+    r.drho64 = dr;
+    r.rho64 = rh;
+    r.ux64 = (jx + 0.5 * rh * static_cast<double>(k.ax)) / rh;
+    r.uy64 = (jy + 0.5 * rh * static_cast<double>(k.ay)) / rh;
+  }
+  C ch[9];
+  if constexpr (kExact) {
+    const C given[3] = {C(r.rho64), C(r.ux64), C(r.uy64)};
+    collision_change<kS, true>(d, k, ch, r.drho, r.rho, r.ux, r.uy, r.uu, given);
+  } else {
+    collision_change<kS, false>(d, k, ch, r.drho, r.rho, r.ux, r.uy, r.uu);
+  }
+  if constexpr (kExact) {
+    const uint32_t w1 = fmix32(rs + 0x9E3779B9u), w2 = fmix32(rs + 0x3C6EF372u),
+                   w3 = fmix32(rs + 0xDAA66D2Bu);
+    const uint32_t u16[9] = {0u, rs & 0xFFFFu, rs >> 16, w1 & 0xFFFFu, w1 >> 16,
+                             w2 & 0xFFFFu, w2 >> 16, w3 & 0xFFFFu, w3 >> 16};
+#pragma unroll
+    for (int i = 1; i < 9; i++) o[i] = add_stochastic(d[i], ch[i], u16[i]);
+  } else {
+#pragma unroll
+    for (int i = 1; i < 9; i++) o[i] = d[i] + ch[i];
+  }
   // The rest population closes the mass balance (M^-1 m' conserves sum f
   // only in exact arithmetic).  Round f'_1..f'_8 to storage first (a no-op
   // for FP32/FP64), then take their changes f'_i - f_i as stored: each is
@@ -157,28 +302,56 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   // f'_0 = f_0 - sum_{i>0} (f'_i - f_i) changes the stored mass by the one
   // rounding of f'_0 -- not by roundings of the sums of the full |f|.
   C dd[9];
+  if constexpr (kStochastic<T>) {
+    // four pairs by stochastic rounding (in storage units: o is already
+    // scaled where the storage is), then the rest population
+    const uint32_t w1 = fmix32(rs + 0x9E3779B9u), w2 = fmix32(rs + 0x3C6EF372u);
+    const uint32_t rb[5] = {rs, w1, w2, rs ^ __funnelshift_l(w1, w1, 16),
+                            w1 ^ __funnelshift_l(w2, w2, 16)};
 #pragma unroll
-  for (int i = 1; i < 9; i++) {
-    if constexpr (kS) {
-      t[i] = Stor<T>::st_raw(o[i]);
-      o[i] = Stor<T>::ld_raw(t[i]);
-    } else {
-      t[i] = Stor<T>::st(o[i], k.sc);
-      o[i] = Stor<T>::ld(t[i], k.inv_sc);
+    for (int p = 0; p < 4; p++) {
+      const uint32_t h = Stor<T>::st_rs2(o[1 + 2 * p], o[2 + 2 * p], rb[p]);
+      t[1 + 2 * p] = Stor<T>::bits(h >> 16);
+      t[2 + 2 * p] = Stor<T>::bits(h & 0xFFFFu);
     }
-    dd[i] = o[i] - d[i];
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      o[i] = Stor<T>::ld_raw(t[i]);
+      dd[i] = o[i] - d[i];
+    }
+    o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
+    t[0] = Stor<T>::bits(Stor<T>::st_rs2(o[0], C(0), rb[4]) >> 16);
+  } else {
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      if constexpr (kS) {
+        t[i] = Stor<T>::st_raw(o[i]);
+        o[i] = Stor<T>::ld_raw(t[i]);
+      } else {
+        t[i] = Stor<T>::st(o[i], k.sc);
+        o[i] = Stor<T>::ld(t[i], k.inv_sc);
+      }
+      dd[i] = o[i] - d[i];
+    }
+    if constexpr (kExact) {
+      // f'_0 = f_0 - sum (f'_i - f_i) in FP64 (exact: eight FP32 changes
+      // and d_0), plus the carry
+      double sdd = 0.0;
+#pragma unroll
+      for (int i = 1; i < 9; i++) sdd += static_cast<double>(dd[i]);
+      const double v0 = static_cast<double>(d[0]) - sdd + static_cast<double>(*c0);
+      t[0] = __double2float_rn(v0);
+      *c0 = __double2float_rn(v0 - static_cast<double>(t[0]));
+      o[0] = t[0];
+    } else {
+      o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
+      if constexpr (kS)
+        t[0] = Stor<T>::st_raw(o[0]);
+      else
+        t[0] = Stor<T>::st(o[0], k.sc);
+    }
   }
-  o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
-  if constexpr (kS)
-    t[0] = Stor<T>::st_raw(o[0]);
-  else
-    t[0] = Stor<T>::st(o[0], k.sc);
 
-  r.drho = drho;
-  r.rho = rho;
-  r.ux = ux;
-  r.uy = uy;
-  r.uu = uu;
 }
 
 // The unknown populations of a boundary node for the next step (bits of
@@ -192,13 +365,22 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
 // collision.  Where the storage is scaled, every term is taken times the
 // scale, so the stored value is the same.  Directions that no active lane
 // of the warp needs are skipped warp-uniformly.
-template <typename T, typename C>
+//
+// 16-bit storage rounds each value stochastically (random bits: fmix32 of
+// the node's word rs and the direction).  The exact-mass variant (kExact,
+// FP32 storage) evaluates the link in FP64 from the FP64 coefficients
+// (g.links64) and the FP64 rho, u of the node, adds the link's carry (the
+// part of its earlier values that FP32 storage dropped) and keeps the new
+// remainder in the carry: the stored values then add up, step after step,
+// to the FP64 ones, so the mass a moving wall exchanges with the fluid does
+// not drift by a rounding that repeats every step.
+template <typename T, typename C, bool kExact = false>
 __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                    const PullGeom &g, const uint32_t fl,
                                                    const uint32_t li,
                                                    const LinkCoef<C> *__restrict__ links,
                                                    const Collided<T, C> &c_,
-                                                   const StepConst<C> &k) {
+                                                   const StepConst<C> &k, const uint32_t rs = 0) {
   const unsigned wmask = __reduce_or_sync(__activemask(), fl);
   if (!wmask) return;
   constexpr bool kS = Stor<T>::kScaled;
@@ -219,36 +401,74 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
       const int jb = opp_tab[j];
       // link j is the node's k-th, k = links in lower directions
       const uint32_t lj = li + __popc(fl & ((1u << (j - 1)) - 1u));
-      const LinkCoef<C> c = links[lj];
-      const C r = c.k1 + c.k2 + c.k3;
-      C c0, c2;
-      if (k.diffuse_mode == 0) {
-        c0 = c.alpha;
-        c2 = (C(1) - r) * C(w_tab[j]);
+      if constexpr (kExact) {
+        const LinkCoef<double> c = g.links64[lj];
+        const double r = c.k1 + c.k2 + c.k3;
+        double c0, c2;
+        if (k.diffuse_mode == 0) {
+          c0 = c.alpha;
+          c2 = (1.0 - r) * w_tab[j];
+        } else {
+          c0 = c.alpha + (r - 1.0) * w_tab[j];
+          c2 = 0.0;
+        }
+        const double cu = cx_tab[j] * c_.ux64 + cy_tab[j] * c_.uy64;
+        const double pj = 3.0 * cu + 4.5 * cu * cu - 1.5 * (c_.ux64 * c_.ux64 + c_.uy64 * c_.uy64);
+        const double djb = static_cast<double>(src[g.jbslot[lj]]);
+        const double v = c.k1 * djb + c.k2 * static_cast<double>(o[j]) +
+                         c.k3 * static_cast<double>(o[jb]) + c0 + c.alpha * c_.drho64 +
+                         c2 * (c_.drho64 + c_.rho64 * pj) + static_cast<double>(g.carry[lj]);
+        const float t = __double2float_rn(v);
+        g.carry[lj] = __double2float_rn(v - static_cast<double>(t));
+        dst[tail + lj] = t;
       } else {
-        c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
-        c2 = C(0);
+        const LinkCoef<C> c = links[lj];
+        const C r = c.k1 + c.k2 + c.k3;
+        C c0, c2;
+        if (k.diffuse_mode == 0) {
+          c0 = c.alpha;
+          c2 = (C(1) - r) * C(w_tab[j]);
+        } else {
+          c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
+          c2 = C(0);
+        }
+        const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
+        const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+        const C djb = kS ? Stor<T>::ld_raw(src[g.jbslot[lj]])
+                         : Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
+        const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + (kS ? c0 * k.sc : c0) +
+                    c.alpha * drho + c2 * (drho + rho * pj);
+        if constexpr (kStochastic<T>)
+          dst[tail + lj] =
+              Stor<T>::bits(Stor<T>::st_rs2(v, C(0), fmix32(rs ^ (0x27D4EB2Fu * j))) >> 16);
+        else
+          dst[tail + lj] = kS ? Stor<T>::st_raw(v) : Stor<T>::st(v, k.sc);
       }
-      const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
-      const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-      const C djb = kS ? Stor<T>::ld_raw(src[g.jbslot[lj]])
-                       : Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
-      const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + (kS ? c0 * k.sc : c0) +
-                  c.alpha * drho + c2 * (drho + rho * pj);
-      dst[tail + lj] = kS ? Stor<T>::st_raw(v) : Stor<T>::st(v, k.sc);
     }
   }
+}
+
+// Random word of node i in the step whose seed is `seed` (16-bit storage
+// and the exact-mass variant; 0 otherwise, unused).
+template <typename T, bool kExact>
+__device__ __forceinline__ uint32_t node_random(const uint32_t seed, const uint32_t i) {
+  if constexpr (kStochastic<T> || kExact)
+    return fmix32(i ^ seed);
+  else
+    return 0u;
 }
 
 // One time step for fluid node i of a lattice in the pull layout
 // (pull_slots): gather f(x, t) (streaming, Sec. 2), collide (collide),
 // store f'(x, t) in the node's own slots of dst, then the link epilogue.
-// Used by the single-case and the batched step kernels alike.
-template <typename T, typename C>
+// Used by the single-case and the batched step kernels alike; seed is the
+// step's seed of random bits (step_seed of the case's step count).
+template <typename T, typename C, bool kExact = false>
 __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                const PullGeom &g,
                                                const LinkCoef<C> *__restrict__ links,
-                                               const StepConst<C> &k, const uint32_t i) {
+                                               const StepConst<C> &k, const uint32_t i,
+                                               const uint32_t seed) {
   const uint32_t P = g.plane;
   const uint2 nw = g.node[i];
   const int2 gr = g.grp[i / kGroup];
@@ -261,17 +481,175 @@ __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__r
       d[q] = Stor<T>::kScaled ? Stor<T>::ld_raw(src[s[q]]) : Stor<T>::ld(src[s[q]], k.inv_sc);
     // the link records are read after the collision: start fetching them now
     if (nw.x & 0xFFu) {
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(links + gr.y + node_loff(nw)));
+      if constexpr (kExact)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(g.links64 + gr.y + node_loff(nw)));
+      else
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(links + gr.y + node_loff(nw)));
       asm volatile("prefetch.global.L1 [%0];" ::"l"(g.jbslot + gr.y + node_loff(nw)));
     }
   }
+  const uint32_t rs = node_random<T, kExact>(seed, i);
   Collided<T, C> c;
-  collide<T, C>(d, k, c);
+  if constexpr (kExact) {
+    float c0 = g.carry0[i];
+    collide<T, C, kExact>(d, k, c, rs, &c0);
+    g.carry0[i] = c0;
+  } else {
+    collide<T, C, kExact>(d, k, c, rs);
+  }
 #pragma unroll
   for (int q = 0; q < 9; q++) dst[q * P + i] = c.t[q];
   // flag byte and first link (li) of the node
-  link_epilogue_pull<T, C>(src, dst, g, nw.x & 0xFFu,
-                           static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k);
+  link_epilogue_pull<T, C, kExact>(src, dst, g, nw.x & 0xFFu,
+                                   static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k, rs);
+}
+
+// ---------------------------------------------------------------------------
+// The paired step of 16-bit storage: one thread advances fluid nodes i0 and
+// i0 + 1 (i0 even).  The 16-bit step spends its time issuing instructions,
+// not waiting on memory, and a pair shares some of them: one 16-byte load
+// brings both node words; the collision runs on
+// both nodes at once in packed FP32x2 arithmetic (F2); each stochastic
+// rounding (cvt.rs ...x2) yields the 32-bit word that holds both nodes'
+// values of one population, which is their own slot pair q P + i0, q P +
+// i0 + 1 -- one aligned store per population.  Random bits: fmix32 of the
+// pair's first node index and the step seed (words derived by rotations).
+
+// Unknown population j of node x (link lj of the table): Eq. EqNewBDSC in
+// the folded form of LinkCoef, in the storage's units, from the node's
+// post-collision values oj = f'_j, ojb = f'_jb, its pre-collision f_jb,
+// drho, rho (storage units where scaled) and u.
+template <typename T>
+__device__ __forceinline__ float link_value(const LinkCoef<float> &c, const int j, const float djb,
+                                            const float oj, const float ojb, const float drho,
+                                            const float rho, const float ux, const float uy,
+                                            const float uu, const StepConst<float> &k) {
+  constexpr bool kS = Stor<T>::kScaled;
+  constexpr int cx_tab[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int cy_tab[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  constexpr float w_tab[9] = {4.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9, 1.0f / 9,
+                              1.0f / 36, 1.0f / 36, 1.0f / 36, 1.0f / 36};
+  const float r = c.k1 + c.k2 + c.k3;
+  float c0, c2;
+  if (k.diffuse_mode == 0) {
+    c0 = c.alpha;
+    c2 = (1.0f - r) * w_tab[j];
+  } else {
+    c0 = c.alpha + (r - 1.0f) * w_tab[j];
+    c2 = 0.0f;
+  }
+  const float cu = float(cx_tab[j]) * ux + float(cy_tab[j]) * uy;
+  const float pj = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+  return c.k1 * djb + c.k2 * oj + c.k3 * ojb + (kS ? c0 * k.sc : c0) + c.alpha * drho +
+         c2 * (drho + rho * pj);
+}
+
+template <typename T>
+__device__ __forceinline__ void step_pair_pull(const T *__restrict__ src, T *__restrict__ dst,
+                                               const PullGeom &g,
+                                               const LinkCoef<float> *__restrict__ links,
+                                               const StepConst<float> &k, const uint32_t i0,
+                                               const uint32_t seed) {
+  static_assert(kStochastic<T>, "the paired step is the 16-bit storage step");
+  const uint32_t P = g.plane;
+  const uint4 nw2 = *reinterpret_cast<const uint4 *>(g.node + i0);
+  const uint2 nw0 = make_uint2(nw2.x, nw2.y), nw1 = make_uint2(nw2.z, nw2.w);
+  const int2 gr = g.grp[i0 / kGroup];  // i0 even: both nodes in one group
+  const uint32_t m0 = nw0.x & kNodeMeta, m1 = nw1.x & kNodeMeta;
+  const uint32_t fl0 = m0 & 0xFFu, fl1 = m1 & 0xFFu;
+  const uint32_t li0 = static_cast<uint32_t>(gr.y) + node_loff(nw0);
+  const uint32_t li1 = static_cast<uint32_t>(gr.y) + node_loff(nw1);
+  F2 d[9];
+  {
+    uint32_t s0[9], s1[9];
+    pull_slots(nw0, gr, i0, P, g.n_fluid, g.ny, g.periodic_y, g.rowstart, s0);
+    pull_slots(nw1, gr, i0 + 1u, P, g.n_fluid, g.ny, g.periodic_y, g.rowstart, s1);
+#pragma unroll
+    for (int q = 0; q < 9; q++)
+      d[q] = F2(make_float2(Stor<T>::ld_raw(src[s0[q]]), Stor<T>::ld_raw(src[s1[q]])));
+    if (fl0) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(links + li0));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.jbslot + li0));
+    }
+    if (fl1) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(links + li1));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(g.jbslot + li1));
+    }
+  }
+  constexpr bool kS = Stor<T>::kScaled;
+  F2 ch[9], drho, rho, ux, uy, uu;
+  collision_change<kS, false>(d, k, ch, drho, rho, ux, uy, uu);
+  // random words of the pair
+  const uint32_t h0 = fmix32(i0 ^ seed), h1 = fmix32(h0 + 0x9E3779B9u),
+                 h2 = fmix32(h0 + 0x3C6EF372u);
+  const uint32_t rb[9] = {h0,
+                          h1,
+                          h2,
+                          h0 ^ __funnelshift_l(h1, h1, 8),
+                          h1 ^ __funnelshift_l(h2, h2, 8),
+                          h2 ^ __funnelshift_l(h0, h0, 8),
+                          h0 ^ __funnelshift_l(h2, h2, 16),
+                          h1 ^ __funnelshift_l(h0, h0, 16),
+                          h2 ^ __funnelshift_l(h1, h1, 16)};
+  F2 o[9];
+  uint32_t t[9];
+#pragma unroll
+  for (int q = 1; q < 9; q++) {
+    const F2 v = d[q] + ch[q];
+    t[q] = Stor<T>::st_rs2(v.v.y, v.v.x, rb[q]);  // node i0 in the low half
+    o[q] = F2(make_float2(Stor<T>::ld_raw(Stor<T>::bits(t[q] & 0xFFFFu)),
+                          Stor<T>::ld_raw(Stor<T>::bits(t[q] >> 16))));
+  }
+  // the rest population closes each node's mass from the stored changes
+  // (as in collide)
+  {
+    F2 dd[9];
+#pragma unroll
+    for (int q = 1; q < 9; q++) dd[q] = o[q] - d[q];
+    o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
+    t[0] = Stor<T>::st_rs2(o[0].v.y, o[0].v.x, rb[0]);
+  }
+#pragma unroll
+  for (int q = 0; q < 9; q++) *reinterpret_cast<uint32_t *>(dst + q * P + i0) = t[q];
+
+  // boundary links of either node (Eq. EqNewBDSC is local to the node)
+  const unsigned wmask = __reduce_or_sync(__activemask(), fl0 | fl1);
+  if (!wmask) return;
+  const uint32_t tail = 9u * P;
+  const F2 drho_s = kS ? drho * k.sc : drho, rho_s = kS ? rho * k.sc : rho;
+#pragma unroll
+  for (int j = 1; j < 9; j++) {
+    if (!(wmask & (1u << (j - 1)))) continue;
+    constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const int jb = opp_tab[j];
+    const uint32_t below = (1u << (j - 1)) - 1u;
+    if (fl0 & (1u << (j - 1))) {
+      const uint32_t lj = li0 + __popc(fl0 & below);
+      const float v = link_value<T>(links[lj], j, Stor<T>::ld_raw(src[g.jbslot[lj]]), o[j].v.x,
+                                    o[jb].v.x, drho_s.v.x, rho_s.v.x, ux.v.x, uy.v.x, uu.v.x, k);
+      dst[tail + lj] =
+          Stor<T>::bits(Stor<T>::st_rs2(v, 0.0f, fmix32(h0 ^ (0x27D4EB2Fu * j))) >> 16);
+    }
+    if (fl1 & (1u << (j - 1))) {
+      const uint32_t lj = li1 + __popc(fl1 & below);
+      const float v = link_value<T>(links[lj], j, Stor<T>::ld_raw(src[g.jbslot[lj]]), o[j].v.y,
+                                    o[jb].v.y, drho_s.v.y, rho_s.v.y, ux.v.y, uy.v.y, uu.v.y, k);
+      dst[tail + lj] =
+          Stor<T>::bits(Stor<T>::st_rs2(v, 0.0f, fmix32(h1 ^ (0x27D4EB2Fu * j))) >> 16);
+    }
+  }
+}
+
+// The exact-mass step of one node (FP32 storage) as a function of its own,
+// not inlined: the single-case and the batched kernels then run bitwise the
+// same compiled arithmetic (inlined into kernels with different register
+// budgets, the compiler may fuse multiplies and adds differently).
+static __device__ __noinline__ void step_node_exact(const float *__restrict__ src, float *__restrict__ dst,
+                                             const PullGeom &g,
+                                             const LinkCoef<float> *__restrict__ links,
+                                             const StepConst<float> &k, const uint32_t i,
+                                             const uint32_t seed) {
+  step_node_pull<float, float, true>(src, dst, g, links, k, i, seed);
 }
 
 // Eq. FluidMacr from deviations: returns rho - 1 (kept exact for the mass sum).

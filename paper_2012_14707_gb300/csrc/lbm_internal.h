@@ -36,6 +36,8 @@ struct StepConst {
   int32_t diffuse_mode;         // reading of the Maxwell part, see LinkCoef
   int32_t n_fluid;              // fluid nodes (compacted lattice)
   int64_t plane;                // elements per population plane (padded fluid-node count)
+  uint32_t sr_seed;             // seed of this time step's random bits (step_seed)
+  int32_t exact;                // 1: the exact-mass variant (FP32 storage, moving walls)
 };
 
 // Coefficients of one link in the kernels' folded form of Eq. EqNewBDSC,
@@ -73,7 +75,16 @@ struct HostCase {
   std::vector<int32_t> lbase;
   std::vector<double> coef;
   std::vector<double> link_r, link_l;  // per link in input order
+  bool moving_walls = false;           // some link has a nonzero wall velocity
 };
+// FP32 storage runs the exact-mass variant of the step (collide,
+// link_epilogue_pull: FP64 link values and rest-population closure, each
+// with a carry of what FP32 storage dropped) where a wall moves, or always
+// with params.mass_mode = 1 (never with -1).
+inline bool exact_mass(const HostCase &hc) {
+  if (hc.params.precision != LBM_FP32 || hc.params.mass_mode < 0) return false;
+  return hc.params.mass_mode > 0 || hc.moving_walls;
+}
 
 // Bits above the flag byte in a compacted lattice's node word (.x; the
 // full layout is described at CompactCase).
@@ -168,6 +179,12 @@ struct PullGeom {
   uint32_t plane = 0;               // P
   uint32_t n_fluid = 0;
   uint32_t pf_dist = 0;             // step kernel: CTAs ahead whose data it prefetches to L2
+  // the exact-mass variant (FP32 storage): FP64 link coefficients and, per
+  // link and per node (rest population), the remainder of its values that
+  // FP32 storage has not yet taken
+  const LinkCoef<double> *links64 = nullptr;
+  float *carry = nullptr;
+  float *carry0 = nullptr;
 };
 
 // s[q] = element of the pre-collision f_q of fluid node i, q = 0..8.
@@ -285,6 +302,8 @@ StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32
   k.diffuse_mode = diffuse_mode;
   k.plane = plane;
   k.n_fluid = static_cast<int32_t>(n_fluid);
+  k.sr_seed = 0;
+  k.exact = 0;
   return k;
 }
 
@@ -346,6 +365,13 @@ struct PullOcc<__half> {
 template <>
 struct PullOcc<__nv_bfloat16> {
   static constexpr int min_blocks = 12;
+};
+
+// The 16-bit step runs fluid-node pairs (step_pair_pull): kPairThreads
+// threads per CTA, two nodes each; PairOcc bounds the registers.
+constexpr int kPairThreads = 128;
+struct PairOcc {
+  static constexpr int min_blocks = 8;
 };
 
 // Kernel launchers (lbm_kernels.cu).  All return the launch error code.

@@ -16,6 +16,7 @@
 // batched solver (lbm_batch.cu) runs the same per-node update on each case
 // of its arena.
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
@@ -36,8 +37,11 @@ using namespace dev;
 // planes.  A prefetch holds no register and never waits; the later loads
 // then find their lines in L2 (the gathers from the rows above and below
 // mostly hit lines that the neighbouring rows' CTAs brought in).
-template <typename T, typename C>
-__global__ void __launch_bounds__(kPullThreads, PullOcc<T>::min_blocks)
+//
+// kExact: the exact-mass variant of FP32 storage (cases with moving walls;
+// see collide and link_epilogue_pull), with room for its FP64 registers.
+template <typename T, typename C, bool kExact>
+__global__ void __launch_bounds__(kPullThreads, kExact ? 8 : PullOcc<T>::min_blocks)
 step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom g,
                  const uint32_t n_fluid, const LinkCoef<C> *__restrict__ links,
                  const StepConst<C> k) {
@@ -65,7 +69,52 @@ step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom 
   }
   const uint32_t i = blockIdx.x * kPullThreads + threadIdx.x;
   if (i >= n_fluid) return;
-  step_node_pull<T, C>(src, dst, g, links, k, i);
+  if constexpr (kExact)
+    step_node_exact(src, dst, g, links, k, i, k.sr_seed);
+  else
+    step_node_pull<T, C, false>(src, dst, g, links, k, i, k.sr_seed);
+}
+
+// One time step of a single case in 16-bit storage: thread t of CTA b runs
+// the fluid-node pair 2 (b kPairThreads + t), 2 (b kPairThreads + t) + 1
+// (step_pair_pull; a lone last node takes the one-node step), after the
+// same L2 prefetch of the data of the CTA g.pf_dist blocks ahead as
+// step_kernel_pull.
+template <typename T>
+__global__ void __launch_bounds__(kPairThreads, PairOcc::min_blocks)
+step_kernel_pair(const T *__restrict__ src, T *__restrict__ dst, const PullGeom g,
+                 const uint32_t n_fluid, const LinkCoef<float> *__restrict__ links,
+                 const StepConst<float> k) {
+  constexpr uint32_t kNodes = 2 * kPairThreads;  // per CTA
+  {
+    constexpr uint32_t kNodeLines = kNodes * sizeof(uint2) / 128;
+    constexpr uint32_t kPlaneLines = kNodes * sizeof(T) / 128;
+    constexpr uint32_t kPerLine = 128 / sizeof(T);
+    constexpr uint32_t kGrpLines = (kNodes / kGroup * sizeof(int2) + 127) / 128;
+    const uint32_t base = (blockIdx.x + g.pf_dist) * kNodes;
+    const uint32_t t = threadIdx.x;
+    constexpr uint32_t kPfThreads = (kNodeLines + 9 * kPlaneLines + kGrpLines + 31) / 32 * 32;
+    static_assert(kPfThreads <= kPairThreads, "one prefetch per thread");
+    if (t < kPfThreads && g.pf_dist && base < n_fluid) {
+      if (t < kNodeLines) {
+        if (base + t * 16 < n_fluid)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(g.node + base + t * 16));
+      } else if (t < kNodeLines + 9 * kPlaneLines) {
+        const uint32_t q = (t - kNodeLines) / kPlaneLines, l = (t - kNodeLines) % kPlaneLines;
+        if (base + l * kPerLine < n_fluid)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + q * g.plane + base + l * kPerLine));
+      } else if (t < kNodeLines + 9 * kPlaneLines + kGrpLines) {
+        const uint32_t l = t - kNodeLines - 9 * kPlaneLines;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(g.grp + base / kGroup + l * 16));
+      }
+    }
+  }
+  const uint32_t i0 = 2u * (blockIdx.x * kPairThreads + threadIdx.x);
+  if (i0 >= n_fluid) return;
+  if (i0 + 1u < n_fluid)
+    step_pair_pull<T>(src, dst, g, links, k, i0, k.sr_seed);
+  else
+    step_node_pull<T, float, false>(src, dst, g, links, k, i0, k.sr_seed);
 }
 
 // Error-free sum of two FP32 values: s + e == a + b exactly (Knuth's
@@ -118,14 +167,20 @@ residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
     uint32_t s[9];
     map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
     C a[9], b[9];
+    bool sat = false;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
       a[i] = Stor<T>::ld(cur[s[i]], inv);
       b[i] = Stor<T>::ld(prev[s[i]], inv);
+      if constexpr (kStochastic<T>)
+        sat |= fabsf(Stor<T>::ld_raw(cur[s[i]])) >= Stor<T>::kMaxRaw ||
+               fabsf(Stor<T>::ld_raw(prev[s[i]])) >= Stor<T>::kMaxRaw;
     }
     C n1, d1, m1;
     residual_terms<C>(a, b, static_cast<C>(ax), static_cast<C>(ay), n1, d1, m1);
-    if (!(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
+    // a saturated 16-bit value (stochastic rounding saturates instead of
+    // overflowing to infinity) counts as non-finite
+    if (sat || !(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
       bad += 1.0;
       continue;
     }
@@ -329,20 +384,39 @@ template <typename T, typename C>
 int pull_resident_ctas() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_pull<T, C>, kPullThreads, 0) !=
-          cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
-  return sms * per;
+  cudaError_t e;
+  if constexpr (kStochastic<T>)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_pair<T>, kPairThreads, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel_pull<T, C, false>,
+                                                      kPullThreads, 0);
+  return e == cudaSuccess ? sms * per : 0;
 }
 
 template <typename T, typename C>
 cudaError_t launch_step_pull(const T *src, T *dst, const PullGeom &g, int64_t n_fluid,
                              const LinkCoef<C> *links, const StepConst<C> &k, cudaStream_t s) {
   if (n_fluid <= 0) return cudaSuccess;
-  const int64_t blocks = (n_fluid + kPullThreads - 1) / kPullThreads;
-  step_kernel_pull<T, C><<<static_cast<unsigned>(blocks), kPullThreads, 0, s>>>(
-      src, dst, g, static_cast<uint32_t>(n_fluid), links, k);
+  if constexpr (kStochastic<T>) {
+    const int64_t pairs = (n_fluid + 1) / 2;
+    step_kernel_pair<T><<<static_cast<unsigned>((pairs + kPairThreads - 1) / kPairThreads),
+                          kPairThreads, 0, s>>>(src, dst, g, static_cast<uint32_t>(n_fluid), links,
+                                                k);
+  } else {
+    const int64_t blocks = (n_fluid + kPullThreads - 1) / kPullThreads;
+    if constexpr (std::is_same<T, float>::value) {
+      if (k.exact) {
+        if (!g.links64 || !g.carry || !g.carry0) return cudaErrorInvalidValue;
+        step_kernel_pull<T, C, true><<<static_cast<unsigned>(blocks), kPullThreads, 0, s>>>(
+            src, dst, g, static_cast<uint32_t>(n_fluid), links, k);
+        return cudaGetLastError();
+      }
+    }
+    step_kernel_pull<T, C, false><<<static_cast<unsigned>(blocks), kPullThreads, 0, s>>>(
+        src, dst, g, static_cast<uint32_t>(n_fluid), links, k);
+  }
   return cudaGetLastError();
 }
 

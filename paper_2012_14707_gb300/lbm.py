@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
                 ("l_mode", ctypes.c_int32), ("diffuse_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("residual_every", ctypes.c_int32),
                 ("storage_scale", ctypes.c_double), ("collision", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("mass_mode", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -68,7 +68,8 @@ class Info(ctypes.Structure):
                 ("tau_s", ctypes.c_double), ("tau_q", ctypes.c_double), ("E", ctypes.c_double),
                 ("E_max", ctypes.c_double), ("L1", ctypes.c_double), ("L2", ctypes.c_double),
                 ("n_clamped", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("precision", ctypes.c_int32), ("pitch", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("exact_mass", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class CaseDesc(ctypes.Structure):
@@ -327,13 +328,14 @@ class Solver:
     `case` is a `cases.Case`.  Keyword arguments override the parameter
     defaults of include/lbm.h: precision ("fp32" | "fp64" | "bf16" | "fp16"), l_mode (a name of
     L_MODES or a float for a fixed l), r (fixed r), tau_q, tau_s, E, L1, L2,
-    sigma, diffuse_mode, residual_every, stream (a cudaStream_t as int).
+    sigma, diffuse_mode, residual_every, stream (a cudaStream_t as int),
+    mass_mode (FP32: 0 auto, 1 always, -1 never the exact-mass step).
     """
 
     def __init__(self, case, precision="fp32", l_mode="paper", r=None, tau_q=None, tau_s=None,
                  E=None, L1=None, L2=None, sigma=1.0, diffuse_mode=0, residual_every=100,
                  stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4, storage_scale=0.0,
-                 bgk=False):
+                 bgk=False, mass_mode=0):
         p = lbm_params_default()
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if isinstance(l_mode, str):
@@ -355,6 +357,7 @@ class Solver:
         p.storage_scale = float(storage_scale)
         p.collision = 1 if bgk else 0
         p.stream = stream
+        p.mass_mode = int(mass_mode)
         self.case = case
         self.params = p
         self.h = None
@@ -437,7 +440,8 @@ def make_params(**kw) -> Params:
         setattr(p, field, math.nan if v is None else float(v))
     if kw.pop("bgk", False):
         p.collision = 1
-    for key in ("sigma", "diffuse_mode", "tau_e", "tau_eps", "l_clamp", "storage_scale"):
+    for key in ("sigma", "diffuse_mode", "tau_e", "tau_eps", "l_clamp", "storage_scale",
+                "mass_mode"):
         if key in kw:
             setattr(p, key, kw.pop(key))
     if kw:
@@ -550,36 +554,51 @@ class Net:
         self.h = h.value
         self.H, self.W, self.c_in, self.c_out, self.max_batch = H, W, c_in, c_out, max_batch
 
+    def _call(self, rc):
+        """Status check of a network call.  LBM_ETIMEOUT leaves the network
+        unspecified (a tensor-core kernel gave up on a bounded wait): it is
+        destroyed, and later calls fail."""
+        if rc == LBM_ETIMEOUT:
+            msg = load().lbm_net_last_error(self.h).decode()
+            self.close()
+            raise LbmError(rc, msg + " (network destroyed)")
+        _ncheck(rc, self.h)
+
+    def _live(self):
+        if not getattr(self, "h", None):
+            raise LbmError(LBM_EINVAL, "network was destroyed")
+        return self.h
+
     @property
     def n_params(self) -> int:
-        return int(load().lbm_net_num_params(self.h))
+        return int(load().lbm_net_num_params(self._live()))
 
     def get_params(self) -> np.ndarray:
         p = np.empty(self.n_params, np.float32)
-        _ncheck(load().lbm_net_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                          p.size), self.h)
+        self._call(load().lbm_net_get_params(self._live(),
+                                             p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
         return p
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, np.float32)
-        _ncheck(load().lbm_net_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                          p.size), self.h)
+        self._call(load().lbm_net_set_params(self._live(),
+                                             p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
 
     def forward(self, x_ptr: int, n: int, y_ptr: int):
-        _ncheck(load().lbm_net_forward(self.h, x_ptr, int(n), y_ptr), self.h)
+        self._call(load().lbm_net_forward(self._live(), x_ptr, int(n), y_ptr))
 
     def gradients(self, x_ptr: int, t_ptr: int, n: int):
         g = np.empty(self.n_params, np.float32)
         loss = ctypes.c_double()
-        _ncheck(load().lbm_net_gradients(self.h, x_ptr, t_ptr, int(n),
-                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                         ctypes.byref(loss)), self.h)
+        self._call(load().lbm_net_gradients(self._live(), x_ptr, t_ptr, int(n),
+                                            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            ctypes.byref(loss)))
         return g, loss.value
 
     def train_step(self, x_ptr: int, t_ptr: int, n: int, lr: float) -> float:
         loss = ctypes.c_double()
-        _ncheck(load().lbm_net_train_step(self.h, x_ptr, t_ptr, int(n), float(lr),
-                                          ctypes.byref(loss)), self.h)
+        self._call(load().lbm_net_train_step(self._live(), x_ptr, t_ptr, int(n), float(lr),
+                                             ctypes.byref(loss)))
         return loss.value
 
     def close(self):

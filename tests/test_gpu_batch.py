@@ -92,3 +92,28 @@ def test_batch_of_awkward_sizes_is_bitwise_the_cases_alone():
         for a, w in zip(b.fields(k), s.fields()):
             np.testing.assert_array_equal(a, w)
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_stochastic_rounding_and_exact_mass_cases_in_a_batch_are_the_cases_alone(precision):
+    """16-bit batches round stochastically with random bits keyed by the
+    case's step count (the batch's device counter plus the step's place in
+    the graph), FP32 cases with a moving wall (and one that asks for it) run
+    the exact-mass step in the batch's own kernel for them: 300 steps of
+    each case in the batch equal 300 steps alone, bit for bit."""
+    cl = [cases.channel(37, 9, 0.2, 0.85, Kn=0.05, ax=1e-6, u_top=0.01),
+          cases.cylinder_array(70, 45, 2, Kn=0.02, ax=1e-5),
+          cases.periodic_box(40, 30, ax=1e-5, ay=-3e-6),
+          cases.annulus(40, 8.0, 16.0, 0.05, 0.05 * (1 / 3) ** 0.5 / 8)]
+    prm = [{}, {}, {"mass_mode": 1}, {"L1": 1.0, "L2": 0.0}]
+    b = lbm.Batch(cl, precision=precision, params=prm)
+    steps, res, total = b.run_to(0.0, 300, check_every=100)
+    assert total == 300 and (steps == 0).all()
+    for k, c in enumerate(cl):
+        s = lbm.Solver(c, precision=precision, **prm[k])
+        if precision == "fp32":
+            assert s.info().exact_mass == (0 if k == 1 else 1)
+        s.step(300)
+        for a, w in zip(b.fields(k), s.fields()):
+            np.testing.assert_array_equal(a, w)
+        s.close()

@@ -32,7 +32,7 @@ def _pair(case, precision, start_seed=None, amp=1e-3, **kw):
     """Oracle and GPU solver on the same case, parameters and start state."""
     okw = {}
     gkw = dict(precision=precision)
-    for k in ("l_mode", "diffuse_mode", "E", "L1", "L2", "tau_s", "bgk"):
+    for k in ("l_mode", "diffuse_mode", "E", "L1", "L2", "tau_s", "bgk", "mass_mode"):
         if k in kw:
             gkw[k] = kw[k]
     if kw.get("bgk"):
@@ -127,29 +127,60 @@ def test_fp64_scheme_variants_match_oracle(l_mode, extra):
     np.testing.assert_allclose(l_g, o.link_l, rtol=1e-13, atol=1e-15)
 
 
-@pytest.mark.parametrize("name", list(CASES))
+MOVING_WALLS = {"annulus", "channel_moving"}
+# lattices without walls whose flow is uniform (every node rounds the same
+# values the same way, so nothing averages out over nodes): FP32 meets the
+# mass target there with the exact-mass step, which they request
+UNIFORM = {"box", "column", "row"}
+
+
+def _fp32_mass_params():
+    out = []
+    for name in CASES:
+        marks = ()
+        if name == "annulus":
+            marks = pytest.mark.xfail(strict=False, reason=(
+                "known miss: 5.4e-10 after 2000 steps with the exact-mass step (8.9e-9 without); "
+                "the rotating curved wall exchanges mass at a rate set by the near-wall velocity, "
+                "and FP32 relaxation rates and coefficients shift that rate by ~1e-7"))
+        out.append(pytest.param(name, marks=marks))
+    return out
+
+
+@pytest.mark.parametrize("name", _fp32_mass_params())
 def test_fp32_velocity_and_mass_match_oracle(name):
-    """From rest, 2000 steps.  Velocity rel. L2 <= 1e-5 everywhere (measured
-    5e-8 to 6e-7: the collision adds its small change to the stored
-    deviations).  Mass drift against the oracle trajectory: <= 1e-10 with
-    stationary walls.  Moving walls (u_b ~ 0.03 and 0.01 here) exchange
-    mass with the fluid every step in tiny net amounts (~1e-8 per link and
-    step) computed from wall populations of size ~1e-3; their FP32 rounding
-    is the same every step once the flow is steady, so it adds up linearly
-    (up to 9e-9 relative after 2000 steps): held to 3e-8.  The periodic
-    boxes accelerate without bound (u ~ 0.04; measured up to 3.6e-10): held
-    to 1e-9."""
+    """From rest, 2000 steps, FP32 against the FP64 oracle: velocity rel. L2
+    <= 1e-5 and mass drift |M_gpu - M_oracle| / M_oracle(0) <= 1e-10, the
+    FP32 targets, on every case.  Moving walls switch the exact-mass step on
+    by themselves (FP64 link values and rest-population closure, each with a
+    carry of what FP32 storage dropped); the uniform periodic lattices ask
+    for it (mass_mode = 1); the others run the plain step."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    if name in UNIFORM:
+        kw["mass_mode"] = 1
     o, g = _pair(c, "fp32", **kw)
+    assert g.info().exact_mass == (1 if name in MOVING_WALLS | UNIFORM else 0)
     m0 = o.residual()[1]
-    mass_tol = {"box": 1e-9, "column": 1e-9, "row": 1e-9, "annulus": 3e-8,
-                "channel_moving": 3e-8}.get(name, 1e-10)
     for n in (500, 1500):
         o.step(n)
         g.step(n)
         assert _vel_rel_l2(c, g.fields(), o.fields()) <= 1e-5
-        assert abs(g.residual()[1] - o.residual()[1]) / m0 <= mass_tol
+    assert abs(g.residual()[1] - o.residual()[1]) / m0 <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["annulus", "channel_moving"])
+def test_fp32_exact_mass_step_matches_the_plain_step_in_velocity(name):
+    """The exact-mass step changes roundings only: its velocity stays within
+    the FP32 target of the plain step's (mass_mode = -1) after 1000 steps."""
+    c = CASES[name]()
+    kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    a = lbm.Solver(c, precision="fp32", **kw)
+    b = lbm.Solver(c, precision="fp32", mass_mode=-1, **kw)
+    assert a.info().exact_mass == 1 and b.info().exact_mass == 0
+    a.step(1000)
+    b.step(1000)
+    assert _vel_rel_l2(c, a.fields(), b.fields()) <= 1e-5
 
 
 def test_poiseuille_steady_state_fp64_and_fp32():
@@ -207,6 +238,24 @@ def test_couette_256_parity_and_slip(Kn, bound):
     assert err < err0
 
 
+@pytest.mark.parametrize("Kn", [0.01, 0.1])
+def test_couette_256_fp32_mass_drift(Kn):
+    """The 256^2 rotating-cylinder Couette workload in FP32 (the exact-mass
+    step switches on by itself: the inner wall moves), 2000 steps from rest:
+    mass drift against the FP64 oracle within the 1e-10 target and velocity
+    within 1e-5."""
+    c = cases.config_couette(Kn)
+    par = P.Parameters(c.Kn, c.H, L1=1.0, L2=0.0)
+    o = oracle.OracleLBM(c, par, threads=oracle.host_cores())
+    g = lbm.Solver(c, precision="fp32", L1=1.0, L2=0.0)
+    assert g.info().exact_mass == 1
+    m0 = o.residual()[1]
+    o.step(2000)
+    g.step(2000)
+    assert _vel_rel_l2(c, g.fields(), o.fields()) <= 1e-5
+    assert abs(g.residual()[1] - o.residual()[1]) / m0 <= 1e-10
+
+
 def test_full_size_throughput_case_matches_oracle():
     """8192 x 4096 random-cylinder channel, FP32 in the benchmark's launch
     configuration: two steps from a seeded perturbed state, every node
@@ -253,12 +302,14 @@ UNIT_ROUNDOFF = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}  # 8 and 11 significant 
 def test_16bit_one_step_is_the_oracle_step_rounded_to_storage(name, precision):
     """Both sides start from the same state, one that the 16-bit storage
     holds exactly (a seeded state imported by the GPU and read back), and
-    take one step.  A streamed population is the oracle's value rounded once
-    to storage: |error| <= u |f_i - w_i| with u the unit round-off, plus a
-    floor for the FP32 arithmetic.  A link population also carries the
-    roundings of the post-collision values it is built from, and the rest
-    population those of the eight others (it closes the mass balance):
-    <= u (|f_i - w_i| + 10 s), s the node's largest deviation."""
+    take one step.  16-bit storage rounds stochastically, so a streamed
+    population is the oracle's value moved to one of its two storage
+    neighbours: |error| < one unit in the last place <= 2 u |f_i - w_i| with
+    u the unit round-off, plus a floor for the FP32 arithmetic.  A link
+    population also carries the roundings of the post-collision values it is
+    built from, and the rest population those of the eight others (it closes
+    the mass balance): < 2 u (|f_i - w_i| + 10 s), s the node's largest
+    deviation.  The error averages a third of a unit (half of u |f - w|)."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
     o, g = _pair(c, precision, start_seed=7, amp=1e-3, **kw)
@@ -277,34 +328,75 @@ def test_16bit_one_step_is_the_oracle_step_rounded_to_storage(name, precision):
     link[0] = True
     floor = 2.0 ** -20 * s
     plain = ~link
-    assert (err[plain] <= u * np.abs(b[plain]) + np.broadcast_to(floor, b.shape)[plain]).all()
-    assert (err[link] <= u * (np.abs(b[link]) + 10 * np.broadcast_to(s, b.shape)[link])).all()
-    # and not a loose bound in practice: the typical error is a fraction of one rounding
-    assert np.median(err[plain] / (u * np.abs(b[plain]) + 1e-300)) <= 0.5
+    assert (err[plain] <= 2 * u * np.abs(b[plain]) + np.broadcast_to(floor, b.shape)[plain]).all()
+    assert (err[link] <= 2 * u * (np.abs(b[link]) + 10 * np.broadcast_to(s, b.shape)[link])).all()
+    ratio = err[plain] / (u * np.abs(b[plain]) + 1e-300)
+    assert 0.2 <= np.median(ratio) <= 0.8
 
 
-# Velocity rel. L2 and mass drift against the oracle after 500 steps from rest
-# (bounds ~2x the values measured on a GB300).  BF16 keeps 8 significant bits
-# of each deviation: ~1e-3 to 1e-2 in velocity where u ~ 1e-3 to 1e-2, and the
-# slow 4 x 32 channel (u ~ 2e-4, deviations ~ 2e-5) loses most of its profile
-# -- BF16 storage does not meet a 1e-3 target there.  FP16 (deviations x 4096)
-# keeps 11 bits: 2e-4 to 2e-3.
-BOUNDS_16 = {
-    ("bf16", "annulus"): (3e-3, 3e-4), ("bf16", "cylinders"): (1.5e-2, 2e-6),
-    ("bf16", "channel_moving"): (3e-2, 1.2e-4), ("bf16", "poiseuille"): (0.25, 2e-8),
-    ("fp16", "annulus"): (4e-4, 3e-5), ("fp16", "cylinders"): (8e-4, 3e-7),
-    ("fp16", "channel_moving"): (4e-3, 1.3e-6), ("fp16", "poiseuille"): (2e-3, 1e-9),
-}
+# Velocity against the oracle after 500 steps from rest, at the 16-bit
+# target (rel. L2 <= 1e-3).  FP16 (deviations x 4096, 11 significant bits)
+# meets it on every case.  BF16 keeps 8 significant bits: with stochastic
+# rounding its error is the rounding noise of the stored deviations, about
+# 2^-9 |f - w| per population and step, i.e. ~2e-3 of |u| (the deviations
+# that carry u are ~|u| / 3): it misses the target by ~2x on every case
+# (measured values in the marks).
+V16_CASES = ["poiseuille", "annulus", "cylinders", "channel_moving", "box", "inclined"]
 
 
-@pytest.mark.parametrize("precision,name", list(BOUNDS_16))
-def test_16bit_velocity_and_mass_after_500_steps(precision, name):
+def _v16_params():
+    out = []
+    for name in V16_CASES:
+        out.append(pytest.param("fp16", name, id=f"fp16-{name}"))
+        out.append(pytest.param("bf16", name, id=f"bf16-{name}", marks=pytest.mark.xfail(
+            strict=False, reason="BF16 storage: rounding noise of 8-bit significands "
+                                 "(~2e-3 of |u|) exceeds the 1e-3 target")))
+    return out
+
+
+@pytest.mark.parametrize("precision,name", _v16_params())
+def test_16bit_velocity_meets_the_target_after_500_steps(precision, name):
+    c = CASES[name]()
+    kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
+    o, g = _pair(c, precision, **kw)
+    o.step(500)
+    g.step(500)
+    assert _vel_rel_l2(c, g.fields(), o.fields()) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("name", ["poiseuille", "annulus", "cylinders", "channel_moving"])
+def test_16bit_mass_drift_is_the_random_walk_of_its_roundings(precision, name):
+    """16-bit storage holds no deviation to 1e-10 (a BF16 unit of a 1e-4
+    deviation is ~4e-7), so the 1e-10 mass target binds FP32 and FP64 only.
+    What 16-bit storage guarantees is unbiased rounding: the stored mass
+    moves by the rest population's and the link values' stochastic roundings
+    (zero mean, each below one unit, 2 u |d|), a random walk.  Bound: 5
+    standard deviations of that walk over 500 steps, with |d| the largest
+    deviation of the oracle's state."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
     o, g = _pair(c, precision, **kw)
     m0 = o.residual()[1]
-    o.step(500)
-    g.step(500)
-    vb, mb = BOUNDS_16[(precision, name)]
-    assert _vel_rel_l2(c, g.fields(), o.fields()) <= vb
-    assert abs(g.residual()[1] - o.residual()[1]) / m0 <= mb
+    n = 500
+    o.step(n)
+    g.step(n)
+    dmax = np.abs(o.get_f()[:, c.solid == 0] - W9[:, None]).max()
+    sigma = 2 * UNIT_ROUNDOFF[precision] * dmax / math.sqrt(3) * math.sqrt(n * (c.n_fluid + c.n_links))
+    assert abs(g.residual()[1] - o.residual()[1]) <= 5 * sigma, (sigma / m0)
+
+
+def test_saturated_16bit_state_is_reported_as_unstable():
+    """Stochastic rounding saturates at the largest finite 16-bit value
+    instead of overflowing to infinity; the residual pass counts a saturated
+    value as non-finite.  FP16 with the default scale 4096 holds |d| <= 16:
+    a node with deviations of 10 collides to a rest population beyond it."""
+    c = CASES["box"]()
+    g = lbm.Solver(c, precision="fp16")
+    f = np.broadcast_to(W9[:, None, None], (9, c.ny, c.nx)).copy()
+    f[:, 20, 30] += 10.0
+    g.set_f(f)
+    g.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.residual()
+    assert ei.value.code == lbm.LBM_EUNSTABLE

@@ -35,9 +35,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FLUID_BYTES = {"fp32": 72, "fp64": 144, "bf16": 36, "fp16": 36}  # algorithmic bytes per fluid-node update
-# The FP64 step is bound by this GPU's FP64 units, not by HBM: FP64 flops per
-# fluid-node update (dadd + dmul + 2 dfma executed by the step kernel, ncu
-# counters on the 4096x2048 case; profiles/) against the nominal FP64 rate.
+# The FP64 step is bound by this GPU's FP64 units, not by HBM.  Its line is
+# reported, not judged: the flops are those the step kernel EXECUTES per
+# fluid-node update (dadd + dmul + 2 dfma, ncu counters on the 4096x2048
+# case; profiles/), not an algorithmic count, and the peak is NVIDIA's
+# nominal FP64 rate, not a measured one.
 FP64_FLOPS_PER_NODE = 156.2
 FP64_PEAK_GFLOPS = 1250.0
 ELEM_BYTES = {"fp32": 4, "fp64": 8, "bf16": 2, "fp16": 2}
@@ -294,6 +296,9 @@ def run_ours(args):
     launch_ms = kernel_ms / (args.steps * per)
     alg_bytes = FLUID_BYTES[args.precision] * n_fluid
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    # the same algorithmic bytes over the whole bench step (lattice steps,
+    # residual pass and its read-back: the time the MLUPS figure counts)
+    step_achieved = FLUID_BYTES[args.precision] * mlups * 1e6 / world / 1e9
     peak, peak_src = _peak_hbm()
     solver.close()
 
@@ -330,15 +335,21 @@ def run_ours(args):
         "roofline": ({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                       "frac": achieved / peak, "traffic": traffic,
                       "kernel": "step_kernel", "bytes_per_fluid_node": FLUID_BYTES[args.precision],
-                      "launch_ms": launch_ms, "peak_source": peak_src}
+                      "launch_ms": launch_ms, "peak_source": peak_src,
+                      "step_achieved": step_achieved, "step_frac": step_achieved / peak,
+                      "step_note": "same algorithmic bytes over the whole bench step (residual "
+                                   "pass and read-back included), the time the MLUPS value counts",
+                      "dram_gbs_ncu": (traffic / (launch_ms / 1e3) / 1e9) if traffic else None}
                      if args.precision != "fp64" else
                      {"bound": "alu", "achieved": FP64_FLOPS_PER_NODE * n_fluid / (launch_ms / 1e3) / 1e9,
                       "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
                       "frac": FP64_FLOPS_PER_NODE * n_fluid / (launch_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
                       "traffic": None, "kernel": "step_kernel",
-                      "flops_per_fluid_node": FP64_FLOPS_PER_NODE, "hbm_gbs": achieved,
-                      "launch_ms": launch_ms,
-                      "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)"}),
+                      "flops_per_fluid_node": FP64_FLOPS_PER_NODE,
+                      "flops_kind": "executed by the kernel (ncu counters), not algorithmic",
+                      "hbm_gbs": achieved, "launch_ms": launch_ms,
+                      "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s), not measured",
+                      "judged": False}),
         "e2e": e2e,
         "gpu_launches": args.steps * (per + 2),
         "clocks": clocks,
@@ -382,14 +393,19 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
 
 
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
-KERNEL_REV = 10
+KERNEL_REV = 11
 
 
 def run_batch(args):
     """The batched workload: 512 uneven cases (sizes 64x64-1024x512, slip
     channel / annulus / cylinder array, Kn log-uniform 0.001-0.1), FP32, all
-    run together to --batch-tol (capped at --batch-max-steps).  value =
-    aggregate fluid-node updates per second over the cases still running."""
+    run together to --batch-tol (default 1e-8, the workload's residual) with
+    the interval residual (the mean change per step over each check
+    interval; the one-step FP32 residual floors near 1e-8), capped at
+    --batch-max-steps.  value = aggregate fluid-node updates per second over
+    the cases still running; the line also carries the per-case steps to
+    steady state and the time to steady state of a subset solved one at a
+    time through the single-case solver."""
     import numpy as np
     import torch
 
@@ -405,8 +421,9 @@ def run_batch(args):
     lbm_build.build()
     lbm.load()
     cl = cases.batch_cases(args.batch_cases, seed=rank)
+    prm = [{"residual_mode": 1}] * len(cl)
     t0 = time.perf_counter()
-    b = lbm.Batch(cl, precision=args.precision)
+    b = lbm.Batch(cl, precision=args.precision, params=prm)
     t_create = time.perf_counter() - t0
     info = b.info()
     # warm-up: graph capture and a few hundred steps, then back to rest
@@ -430,7 +447,7 @@ def run_batch(args):
     comp = None
     if args.batch_single > 0:
         sub = cl[:args.batch_single]
-        bs = lbm.Batch(sub, precision=args.precision)
+        bs = lbm.Batch(sub, precision=args.precision, params=prm[:len(sub)])
         bs.run_to(args.batch_tol, args.lbm_steps, check_every=args.lbm_steps)
         bs.reset()
         torch.cuda.synchronize()
@@ -441,7 +458,8 @@ def run_batch(args):
         t0 = time.perf_counter()
         s_single = []
         for c in sub:
-            sv = lbm.Solver(c, precision=args.precision, residual_every=args.lbm_steps)
+            sv = lbm.Solver(c, precision=args.precision, residual_every=args.lbm_steps,
+                            residual_mode=1)
             try:
                 n, r = sv.run_to(args.batch_tol, args.batch_max_steps)
                 s_single.append(n if r < args.batch_tol else 0)
@@ -465,10 +483,13 @@ def run_batch(args):
         "config": {"workload": f"batch_{len(cl)}_cases_64-1024x64-512_Kn0.001-0.1",
                    "total_nodes": info["total_nodes"], "total_fluid": info["total_fluid"],
                    "cta_threads_autotuned": info["cta_threads"], "tol": args.batch_tol,
+                   "residual": "interval (mean change per step over each check interval)",
                    "max_steps": args.batch_max_steps, "check_every": args.lbm_steps},
         "batch": {"converged": int(conv.sum()), "unstable": int((steps < 0).sum()),
                   "steps_to_steady_median": float(np.median(steps[conv])) if conv.any() else None,
                   "steps_to_steady_p90": float(np.percentile(steps[conv], 90)) if conv.any() else None,
+                  "not_converged_Kn_max": (float(max(c.Kn for c, ok in zip(cl, conv) if not ok))
+                                           if (~conv).any() else None),
                   "create_seconds": t_create, "wall_seconds": wall},
         "time_to_steady_vs_single": comp,
         "clocks": clocks,
@@ -581,11 +602,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=("throughput", "batch", "net"), default="throughput")
     ap.add_argument("--batch-cases", type=int, default=512)
-    ap.add_argument("--batch-max-steps", type=int, default=20000)
+    ap.add_argument("--batch-max-steps", type=int, default=50000)
     ap.add_argument("--batch-single", type=int, default=32,
                     help="cases also solved one at a time for the time-to-steady comparison")
-    ap.add_argument("--batch-tol", type=float, default=1e-6,
-                    help="residual to reach; the one-step FP32 residual floors near 1e-8")
+    ap.add_argument("--batch-tol", type=float, default=1e-8,
+                    help="interval residual to reach (the batched workload's 1e-8)")
     ap.add_argument("--nx", type=int, default=0, help="profiling only: smaller lattice width")
     ap.add_argument("--ny", type=int, default=0, help="profiling only: smaller lattice height")
     args = ap.parse_args()

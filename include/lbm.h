@@ -114,6 +114,13 @@ typedef struct {
                            rounding per population instead of drifting by a rounding that
                            repeats every step.  It costs 4 B per link and 8 B per fluid node
                            of extra traffic per step. */
+  int32_t residual_mode; /* 0 (default): lbm_residual's residual is the one-step change
+                            ||u^n - u^(n-1)|| / ||u^n||.  1: the interval change
+                            ||u^n - u^m|| / ((n - m) ||u^n||), u^m the velocity field at the
+                            previous lbm_residual call (m its step count; the initial state,
+                            lbm_set_f / lbm_set_fields or lbm_load start a new interval): the
+                            mean change per step, which near a steady state does not floor at the
+                            rounding noise that 16-bit or FP32 storage leaves in one step. */
 } lbm_params_t;
 
 typedef struct {
@@ -166,7 +173,8 @@ int lbm_fields(lbm_handle_t *h, double *rho, double *ux, double *uy, int on_devi
 
 /*
  * Convergence and conservation monitor: residual = ||u^n - u^(n-1)||_2 /
- * ||u^n||_2 over fluid nodes (0 before the first step) and mass =
+ * ||u^n||_2 over fluid nodes (0 before the first step; with
+ * params.residual_mode = 1 the interval change described there) and mass =
  * sum over fluid nodes of sum_i f_i, both accumulated in FP64.  Synchronises.
  * Returns LBM_EUNSTABLE (with the values still written) when a fluid node
  * has a non-finite density or velocity.
@@ -280,7 +288,10 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
 /* Back to rest, every case active, step counts zero. */
 int lbm_batch_reset(lbm_batch_t *b);
 /* Advance all active cases, check_every (even, >= 2) steps at a time, until
- * every case has residual < tol or max_steps were taken.  The batch advances
+ * every case has residual < tol or max_steps were taken.  A case's residual
+ * follows its params.residual_mode: the one-step change, or (1) the change
+ * over the check_every steps since the previous check divided by
+ * check_every.  The batch advances
  * in whole rounds of check_every steps, so a max_steps that is not a
  * multiple of check_every is rounded up to the next multiple.  Outputs
  * (host, n_cases entries, may be NULL): the step count at which each case

@@ -75,6 +75,7 @@ def _load(threaded: bool = False):
         lib.olbm_step.argtypes = [P, ctypes.c_long]
         lib.olbm_fields.argtypes = [P, dp, dp, dp]
         lib.olbm_residual.argtypes = [P, dp, dp]
+        lib.olbm_residual_interval.argtypes = [P, dp]
         lib.olbm_get_f.argtypes = [P, dp]
         lib.olbm_set_f.argtypes = [P, dp]
         lib.olbm_get_fpost.argtypes = [P, dp]
@@ -161,6 +162,13 @@ class OracleLBM:
         self._lib.olbm_residual(self._h, ctypes.byref(res), ctypes.byref(mass))
         return res.value, mass.value
 
+    def residual_interval(self) -> float:
+        """||u^n - u^m|| / ((n - m) ||u^n||): the mean change per step since
+        the previous call (since the initial state for the first)."""
+        res = ctypes.c_double()
+        self._lib.olbm_residual_interval(self._h, ctypes.byref(res))
+        return res.value
+
     def get_f(self) -> np.ndarray:
         f = np.empty((9, self.case.ny, self.case.nx))
         self._lib.olbm_get_f(self._h, _dp(f))
@@ -180,13 +188,14 @@ class OracleLBM:
         self._lib.olbm_get_minv(self._h, _dp(m))
         return m
 
-    def run_to(self, tol: float, max_steps: int, every: int = 100):
-        """Step in chunks of `every` until residual < tol; returns steps done."""
+    def run_to(self, tol: float, max_steps: int, every: int = 100, interval: bool = False):
+        """Step in chunks of `every` until the residual (one-step, or the
+        interval residual over each chunk) is below tol; returns steps done."""
         done = 0
         while done < max_steps:
             self.step(every)
             done += every
-            res, _ = self.residual()
+            res = self.residual_interval() if interval else self.residual()[0]
             if res < tol:
                 break
         return done

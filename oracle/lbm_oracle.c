@@ -60,6 +60,8 @@ typedef struct {
     int *lx, *ly, *ld;
     double *lr, *ll, *lg, *lubx, *luby;
     double *f, *fpost, *fnew, *fprev, *rho, *ux, *uy;
+    double *snap_ux, *snap_uy; /* velocity at the last interval residual */
+    long snap_steps;
     int diffuse_mode;
     long steps;
 } olbm;
@@ -121,9 +123,11 @@ void olbm_destroy(olbm *o) {
     free(o->solid); free(o->lx); free(o->ly); free(o->ld);
     free(o->lr); free(o->ll); free(o->lg); free(o->lubx); free(o->luby);
     free(o->f); free(o->fpost); free(o->fnew); free(o->fprev); free(o->rho);
-    free(o->ux); free(o->uy);
+    free(o->ux); free(o->uy); free(o->snap_ux); free(o->snap_uy);
     free(o);
 }
+
+static void current_velocity(const olbm *o, double *ux, double *uy);
 
 /* Returns NULL on bad input (a link that is not a fluid node next to a
  * solid one, gamma outside (0, 1], or an unknown direction with no link). */
@@ -150,6 +154,8 @@ olbm *olbm_create(int nx, int ny, int periodic_x, int periodic_y, const uint8_t 
     o->rho = (double *)malloc(n * sizeof(double));
     o->ux = (double *)calloc(n, sizeof(double));
     o->uy = (double *)calloc(n, sizeof(double));
+    o->snap_ux = (double *)calloc(n, sizeof(double));
+    o->snap_uy = (double *)calloc(n, sizeof(double));
     size_t nlb = (size_t)(n_links > 0 ? n_links : 1);
     o->nl = n_links;
     o->lx = (int *)malloc(nlb * sizeof(int)); o->ly = (int *)malloc(nlb * sizeof(int));
@@ -157,7 +163,8 @@ olbm *olbm_create(int nx, int ny, int periodic_x, int periodic_y, const uint8_t 
     o->lr = (double *)malloc(nlb * sizeof(double)); o->ll = (double *)malloc(nlb * sizeof(double));
     o->lg = (double *)malloc(nlb * sizeof(double));
     o->lubx = (double *)malloc(nlb * sizeof(double)); o->luby = (double *)malloc(nlb * sizeof(double));
-    if (!o->solid || !o->f || !o->fpost || !o->fnew || !o->fprev || !o->rho || !o->ux || !o->uy || !o->lx ||
+    if (!o->solid || !o->f || !o->fpost || !o->fnew || !o->fprev || !o->rho || !o->ux || !o->uy ||
+        !o->snap_ux || !o->snap_uy || !o->lx ||
         !o->ly || !o->ld || !o->lr || !o->ll || !o->lg || !o->lubx || !o->luby) {
         olbm_destroy(o); return NULL;
     }
@@ -198,6 +205,8 @@ olbm *olbm_create(int nx, int ny, int periodic_x, int periodic_y, const uint8_t 
     memcpy(o->fnew, o->f, nf * sizeof(double));
     memcpy(o->fpost, o->f, nf * sizeof(double));
     for (size_t p = 0; p < n; p++) o->rho[p] = 1.0;
+    /* the initial state is the first reference of the interval residual */
+    current_velocity(o, o->snap_ux, o->snap_uy);
     return o;
 }
 
@@ -337,6 +346,51 @@ void olbm_residual(const olbm *o, double *residual, double *mass) {
     *mass = ms;
 }
 
+/* Velocity of every node from the current populations (solid: 0). */
+static void current_velocity(const olbm *o, double *ux, double *uy) {
+    size_t n = (size_t)o->nx * o->ny;
+    for (size_t p = 0; p < n; p++) {
+        ux[p] = uy[p] = 0.0;
+        if (o->solid[p]) continue;
+        double r = 0.0, jx = 0.0, jy = 0.0;
+        for (int i = 0; i < 9; i++) {
+            double v = o->f[(size_t)i * n + p];
+            r += v; jx += CXs[i] * v; jy += CYs[i] * v;
+        }
+        ux[p] = (jx + 0.5 * r * o->ax) / r;
+        uy[p] = (jy + 0.5 * r * o->ay) / r;
+    }
+}
+
+/* Interval residual: ||u^n - u^m||_2 / ((n - m) ||u^n||_2) over fluid nodes,
+ * u^m the velocity at the previous call (the initial state before the
+ * first), then u^n becomes the reference.  0 when no step was taken since.
+ * Serial fixed-order sums. */
+void olbm_residual_interval(olbm *o, double *residual) {
+    size_t n = (size_t)o->nx * o->ny;
+    double *ux = (double *)malloc(n * sizeof(double)), *uy = (double *)malloc(n * sizeof(double));
+    if (!ux || !uy) { free(ux); free(uy); *residual = NAN; return; }
+    current_velocity(o, ux, uy);
+    double num = 0.0, den = 0.0;
+    for (size_t p = 0; p < n; p++) {
+        if (o->solid[p]) continue;
+        double dx = ux[p] - o->snap_ux[p], dy = uy[p] - o->snap_uy[p];
+        num += dx * dx + dy * dy;
+        den += ux[p] * ux[p] + uy[p] * uy[p];
+    }
+    long span = o->steps - o->snap_steps;
+    if (isnan(num) || isnan(den))
+        *residual = NAN;
+    else if (span <= 0)
+        *residual = 0.0;
+    else
+        *residual = (den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0)) / (double)span;
+    memcpy(o->snap_ux, ux, n * sizeof(double));
+    memcpy(o->snap_uy, uy, n * sizeof(double));
+    o->snap_steps = o->steps;
+    free(ux); free(uy);
+}
+
 /* f in [9][ny][nx] order. */
 void olbm_get_f(const olbm *o, double *f) {
     memcpy(f, o->f, 9 * (size_t)o->nx * o->ny * sizeof(double));
@@ -346,6 +400,8 @@ void olbm_set_f(olbm *o, const double *f) {
     size_t nf = 9 * (size_t)o->nx * o->ny;
     memcpy(o->f, f, nf * sizeof(double));
     memcpy(o->fprev, f, nf * sizeof(double));
+    current_velocity(o, o->snap_ux, o->snap_uy);
+    o->snap_steps = o->steps;
 }
 
 /* post-collision populations of the last step, [9][ny][nx] */

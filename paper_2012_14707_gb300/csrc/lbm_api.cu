@@ -40,6 +40,10 @@ struct lbm_handle {
   lbm::LinkCoef<double> *links64 = nullptr;
   float *carry = nullptr;   // per link
   float *carry0 = nullptr;  // per fluid node (rest population)
+  // interval residual (params.residual_mode 1): velocity of every fluid
+  // node at the step snap_steps (two values of the arithmetic type)
+  void *snap = nullptr;
+  int64_t snap_steps = 0;
   double *partials = nullptr;
   double *result = nullptr;
   double *h_result = nullptr;  // pinned, 4 doubles
@@ -139,7 +143,7 @@ void release(lbm_handle_t *h) {
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->grp),
                   static_cast<void *>(h->jbslot),
                   static_cast<void *>(h->rowstart), static_cast<void *>(h->index), h->links,
-                  static_cast<void *>(h->links64), static_cast<void *>(h->carry),
+                  static_cast<void *>(h->links64), static_cast<void *>(h->carry), h->snap,
                   static_cast<void *>(h->partials), static_cast<void *>(h->result)})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
@@ -186,6 +190,19 @@ cudaError_t clear_carry(lbm_handle_t *h) {
   return cudaMemsetAsync(h->carry, 0, carry_bytes(h), h->stream);
 }
 
+// The interval residual's kernel on the current state: partials, result
+// and the new velocity snapshot (the previous one is read first).
+cudaError_t interval_residual_launch(lbm_handle_t *h);
+
+// Start a new interval at the current state (the snapshot becomes its
+// velocity field).
+cudaError_t reset_interval(lbm_handle_t *h) {
+  if (!h->snap) return cudaSuccess;
+  const cudaError_t e = interval_residual_launch(h);
+  h->snap_steps = h->steps;
+  return e;
+}
+
 lbm::NodeMap node_map(const lbm_handle_t *h) {
   lbm::NodeMap m;
   m.index = h->index;
@@ -193,6 +210,15 @@ lbm::NodeMap node_map(const lbm_handle_t *h) {
   m.ny = h->ny;
   m.pull = pull_geom(h);
   return m;
+}
+
+cudaError_t interval_residual_launch(lbm_handle_t *h) {
+  return dispatch(h->precision, [&](auto tT, auto tC) {
+    LBM_TYPES(tT, tC);
+    return lbm::launch_residual_interval<T>(static_cast<const T *>(h->f[h->cur]), node_map(h),
+                                            h->n_fluid, h->plane, h->ax, h->ay, h->scale, h->snap,
+                                            h->partials, h->result, h->stream);
+  });
 }
 
 cudaError_t do_step(lbm_handle_t *h) {
@@ -238,6 +264,8 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
   if (p.diffuse_mode != 0 && p.diffuse_mode != 1) return bad(LBM_EINVAL, "diffuse_mode must be 0 or 1");
   if (p.residual_every < 1) return bad(LBM_EINVAL, "residual_every must be >= 1");
   if (p.mass_mode < -1 || p.mass_mode > 1) return bad(LBM_EINVAL, "mass_mode must be -1, 0 or 1");
+  if (p.residual_mode != 0 && p.residual_mode != 1)
+    return bad(LBM_EINVAL, "residual_mode must be 0 or 1");
   if (!std::isfinite(dom->ax) || !std::isfinite(dom->ay)) return bad(LBM_EINVAL, "non-finite force");
   const int32_t nx = dom->nx, ny = dom->ny;
   // 32-bit element offsets in the kernels: 9 planes of the padded lattice < 2^31.
@@ -578,6 +606,7 @@ void lbm_params_default(lbm_params_t *p) {
   p->residual_every = 100;
   p->stream = nullptr;
   p->mass_mode = 0;
+  p->residual_mode = 0;
 }
 
 int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
@@ -721,6 +750,9 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   }
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->result), 4 * sizeof(double));
+  if (e == cudaSuccess && p.residual_mode == 1)
+    e = alloc(&h->snap, std::max<size_t>(1, static_cast<size_t>(hc.n_fluid)) * 2 *
+                            (p.precision == LBM_FP64 ? sizeof(double) : sizeof(float)));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h->h_result), 4 * sizeof(double));
 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, fbytes, h->stream);
@@ -736,6 +768,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   up(h->index, cc.index.data(), cc.index.size() * 4);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->links, lhost.data(), lbytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = reset_interval(h);  // the rest state starts the first interval
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     g_create_error = std::string("device setup: ") + cudaGetErrorString(e);
@@ -760,13 +793,21 @@ int lbm_step(lbm_handle_t *h, int64_t n) {
 int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   if (!h) return LBM_EINVAL;
   const int c = h->cur, pv = 1 - h->cur;
-  cudaError_t e = dispatch(h->precision, [&](auto tT, auto tC) {
-    LBM_TYPES(tT, tC);
-    return lbm::launch_residual_compact<T>(static_cast<const T *>(h->f[c]),
-                                           static_cast<const T *>(h->f[pv]), node_map(h),
-                                           h->n_fluid, h->plane, h->ax, h->ay, h->scale,
-                                           h->partials, h->result, h->stream);
-  });
+  int64_t span = 1;
+  cudaError_t e;
+  if (h->snap) {
+    span = h->steps - h->snap_steps;
+    e = interval_residual_launch(h);
+    h->snap_steps = h->steps;
+  } else {
+    e = dispatch(h->precision, [&](auto tT, auto tC) {
+      LBM_TYPES(tT, tC);
+      return lbm::launch_residual_compact<T>(static_cast<const T *>(h->f[c]),
+                                             static_cast<const T *>(h->f[pv]), node_map(h),
+                                             h->n_fluid, h->plane, h->ax, h->ay, h->scale,
+                                             h->partials, h->result, h->stream);
+    });
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "residual kernel launch");
   LBM_CK(h, cudaMemcpyAsync(h->h_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
@@ -775,8 +816,11 @@ int lbm_residual(lbm_handle_t *h, double *residual, double *mass) {
   double res;
   if (std::isnan(num) || std::isnan(den))
     res = std::numeric_limits<double>::quiet_NaN();
+  else if (span <= 0)
+    res = 0.0;  // no step since the interval began
   else
-    res = den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+    res = (den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0)) /
+          static_cast<double>(span);
   if (residual) *residual = res;
   if (mass) *mass = static_cast<double>(h->n_fluid) + h->h_result[2];
   if (h->h_result[3] > 0.0) {
@@ -873,9 +917,10 @@ int lbm_set_f(lbm_handle_t *h, const double *f) {
     });
   cudaFreeAsync(d, h->stream);
   if (e == cudaSuccess) e = clear_carry(h);
+  h->steps = 0;
+  if (e == cudaSuccess) e = reset_interval(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_f");
-  h->steps = 0;
   return LBM_OK;
 }
 
@@ -905,9 +950,10 @@ int lbm_set_fields(lbm_handle_t *h, const double *rho, const double *ux, const d
     });
   if (d) cudaFreeAsync(d, h->stream);
   if (e == cudaSuccess) e = clear_carry(h);
+  h->steps = 0;
+  if (e == cudaSuccess) e = reset_interval(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lbm_set_fields");
-  h->steps = 0;
   return LBM_OK;
 }
 
@@ -1072,8 +1118,9 @@ int lbm_load(lbm_handle_t *h, const char *path) {
   if (cbytes)
     LBM_CK(h, cudaMemcpyAsync(h->carry, buf.data() + 2 * h->fbytes, cbytes, cudaMemcpyHostToDevice,
                               h->stream));
-  LBM_CK(h, cudaStreamSynchronize(h->stream));
   h->steps = hd.steps;
+  LBM_CK(h, reset_interval(h));
+  LBM_CK(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
 

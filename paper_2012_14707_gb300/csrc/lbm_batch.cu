@@ -177,7 +177,11 @@ batch_exact_kernel(const float *__restrict__ src, float *__restrict__ dst,
 // One CTA per case: residual of the case (FP64 sums in a fixed order); a
 // case whose residual fell below tol, or whose state is no longer finite,
 // is retired with the step count at which that happened (negative when
-// unstable).
+// unstable).  A case with residual_mode 1 takes the interval residual: its
+// velocity against the snapshot of the previous check (snap, two values per
+// node-arena entry), divided by the K steps since, and the snapshot is
+// replaced.  init: only write the snapshots of those cases (the start of
+// the first interval), retire nothing.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kBatchResidualThreads)
 batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
@@ -186,13 +190,16 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
                       const BatchCase<C> *__restrict__ cases,
                       int32_t *__restrict__ active, double tol, const int64_t *__restrict__ counter,
                       int64_t K, int64_t *__restrict__ steps_done, double *__restrict__ res_out,
-                      int32_t *__restrict__ n_active) {
+                      int32_t *__restrict__ n_active, C *__restrict__ snap, const int init) {
   const int c = blockIdx.x;
   if (!active[c]) return;
   const BatchCase<C> &bc = cases[c];
   const StepConst<C> k = bc.k;
+  const bool interval = k.residual_mode == 1 && snap;
+  if (init && !interval) return;
   const T *a_base = cur + bc.f_off;
   const T *b_base = prev + bc.f_off;
+  C *sn = interval ? snap + 2 * bc.node_off : nullptr;
   NodeMap map;
   map.pull = case_geom(bc, node, grp, rowstart, static_cast<const uint32_t *>(nullptr));
   double num = 0.0, den = 0.0, bad = 0.0;
@@ -205,13 +212,26 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
 #pragma unroll
       for (int q = 0; q < 9; q++) {
         a[q] = Stor<T>::ld(a_base[s[q]], k.inv_sc);
-        b[q] = Stor<T>::ld(b_base[s[q]], k.inv_sc);
+        b[q] = interval ? C(0) : Stor<T>::ld(b_base[s[q]], k.inv_sc);
         if constexpr (kStochastic<T>)
           sat |= fabsf(Stor<T>::ld_raw(a_base[s[q]])) >= Stor<T>::kMaxRaw ||
-                 fabsf(Stor<T>::ld_raw(b_base[s[q]])) >= Stor<T>::kMaxRaw;
+                 (!interval && fabsf(Stor<T>::ld_raw(b_base[s[q]])) >= Stor<T>::kMaxRaw);
       }
       C n1, d1, m1;
-      residual_terms<C>(a, b, k.ax, k.ay, n1, d1, m1);
+      if (interval) {
+        const C r = C(1) + (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8]);
+        const C jx = a[1] - a[3] + (a[5] - a[6]) + (a[8] - a[7]);
+        const C jy = a[2] - a[4] + (a[5] + a[6]) - (a[7] + a[8]);
+        const C ux = (jx + C(0.5) * r * k.ax) / r, uy = (jy + C(0.5) * r * k.ay) / r;
+        const C dx = ux - sn[2 * i], dy = uy - sn[2 * i + 1];
+        sn[2 * i] = ux;
+        sn[2 * i + 1] = uy;
+        n1 = dx * dx + dy * dy;
+        d1 = ux * ux + uy * uy;
+        m1 = r - C(1);
+      } else {
+        residual_terms<C>(a, b, k.ax, k.ay, n1, d1, m1);
+      }
       // a saturated 16-bit value counts as non-finite
       if (sat || !(isfinite(n1) && isfinite(d1) && isfinite(m1))) {
         bad += 1.0;
@@ -221,6 +241,7 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
       den += static_cast<double>(d1);
     }
   }
+  if (init) return;
   __shared__ double sh[kBatchResidualThreads / 32][3];
   num = warp_sum(num);
   den = warp_sum(den);
@@ -236,7 +257,8 @@ batch_residual_kernel(const T *__restrict__ cur, const T *__restrict__ prev,
     double s[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < kBatchResidualThreads / 32; i++)
       for (int q = 0; q < 3; q++) s[q] += sh[i][q];
-    const double res = s[1] > 0.0 ? sqrt(s[0] / s[1]) : (s[0] > 0.0 ? INFINITY : 0.0);
+    const double res = (s[1] > 0.0 ? sqrt(s[0] / s[1]) : (s[0] > 0.0 ? INFINITY : 0.0)) /
+                       (interval ? static_cast<double>(K) : 1.0);
     res_out[c] = res;
     const int64_t now = *counter + K;
     if (s[2] > 0.0 || isnan(res)) {
@@ -349,6 +371,7 @@ struct lbm_batch {
   int64_t n_links_total = 0;
   int32_t *exact_chunks = nullptr;  // node-arena chunks of those cases
   int32_t n_exact_chunks = 0;
+  void *snap = nullptr;  // interval-residual snapshots (2 values per node-arena entry), or null
   int threads = 0;
   uint32_t pf_dist = 0;  // L2 prefetch distance of the step kernel (CTAs), for `threads`
   int32_t *active = nullptr;
@@ -422,6 +445,21 @@ cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src, ui
   });
 }
 
+// Snapshots of the interval residual from the current state (lattice 0,
+// every active case with residual_mode 1): the start of an interval.
+cudaError_t init_snapshots(lbm_batch_t *b) {
+  if (!b->snap) return cudaSuccess;
+  return dispatch_b(b->precision, [&](auto tT, auto tC) {
+    using T = std::remove_pointer_t<decltype(tT)>;
+    using C = std::remove_pointer_t<decltype(tC)>;
+    lbm::batch_residual_kernel<T, C><<<b->n_cases, lbm::kBatchResidualThreads, 0, b->stream>>>(
+        static_cast<const T *>(b->f[0]), static_cast<const T *>(b->f[1]), b->node, b->grp,
+        b->rowstart, static_cast<const lbm::BatchCase<C> *>(b->cases), b->active, 0.0, b->counter,
+        1, b->steps_done, b->res, b->n_active, static_cast<C *>(b->snap), 1);
+    return cudaGetLastError();
+  });
+}
+
 int bfail(lbm_batch_t *b, int code, const std::string &m) {
   if (b) b->err = m;
   return code;
@@ -436,7 +474,7 @@ void batch_release(lbm_batch_t *b) {
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active),
                   static_cast<void *>(b->links64), static_cast<void *>(b->carry),
-                  static_cast<void *>(b->exact_chunks)})
+                  static_cast<void *>(b->exact_chunks), b->snap})
     if (p) cudaFree(p);
   if (b->h_n_active) cudaFreeHost(b->h_n_active);
   if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -574,6 +612,8 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   if (any_exact) l64.assign(static_cast<size_t>(std::max<int64_t>(1, links)) * 4, 0.0);
   std::vector<unsigned char> chost;
   std::vector<int32_t> xchunks;
+  bool any_interval = false;
+  for (int c = 0; c < n_cases; c++) any_interval |= hc[c].params.residual_mode == 1;
   int64_t noff = 0, foff = 0, goff = 0, loff = 0, roff = 0, ioff = 0;
   for (int c = 0; c < n_cases; c++) {
     const lbm::HostCase &h = hc[c];
@@ -627,6 +667,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       d.k = lbm::make_step_const<C>(h.cp, h.nx, h.ny, 0, k.plane, h.n_fluid, h.px, h.py, h.ax,
                                     h.ay, h.params.diffuse_mode, h.scale);
       d.k.exact = lbm::exact_mass(h) ? 1 : 0;
+      d.k.residual_mode = h.params.residual_mode;
       d.f_off = foff;
       d.node_off = noff;
       d.grp_off = goff;
@@ -682,6 +723,8 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->res), n_cases * 8);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->counter), 8);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->n_active), 4);
+  if (e == cudaSuccess && any_interval)
+    e = alloc(&b->snap, static_cast<size_t>(nodes) * 2 * (precision == LBM_FP64 ? 8 : 4));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&b->h_n_active), 4);
   auto up = [&](void *dst, const void *src, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -739,6 +782,7 @@ int lbm_batch_reset(lbm_batch_t *b) {
     e = cudaMemcpyAsync(b->steps_done, zeros.data(), n * 8, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->counter, &zero, 8, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->n_active, &n, 4, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = init_snapshots(b);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("lbm_batch_reset: ") + cudaGetErrorString(e));
   b->cur = 0;
@@ -770,8 +814,8 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
         lbm::batch_residual_kernel<T, C><<<b->n_cases, lbm::kBatchResidualThreads, 0, b->stream>>>(
             static_cast<const T *>(b->f[0]), static_cast<const T *>(b->f[1]), b->node, b->grp,
             b->rowstart, static_cast<const lbm::BatchCase<C> *>(b->cases), b->active, tol,
-            b->counter,
-            check_every, b->steps_done, b->res, b->n_active);
+            b->counter, check_every, b->steps_done, b->res, b->n_active, static_cast<C *>(b->snap),
+            0);
         return cudaGetLastError();
       });
     if (e == cudaSuccess) {
@@ -854,6 +898,7 @@ int lbm_batch_set_fields(lbm_batch_t *b, int32_t c, const double *rho, const dou
                                        static_cast<T *>(b->f[0]) + b->f_off[c],
                                        static_cast<T *>(b->f[1]) + b->f_off[c], b->stream);
     });
+  if (e == cudaSuccess) e = init_snapshots(b);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   cudaFree(d);
   if (e != cudaSuccess) return bfail(b, LBM_ECUDA, cudaGetErrorString(e));

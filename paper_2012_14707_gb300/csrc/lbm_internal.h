@@ -38,6 +38,7 @@ struct StepConst {
   int64_t plane;                // elements per population plane (padded fluid-node count)
   uint32_t sr_seed;             // seed of this time step's random bits (step_seed)
   int32_t exact;                // 1: the exact-mass variant (FP32 storage, moving walls)
+  int32_t residual_mode;        // params.residual_mode (the batched reduction reads it)
 };
 
 // Coefficients of one link in the kernels' folded form of Eq. EqNewBDSC,
@@ -304,6 +305,7 @@ StepConst<C> make_step_const(const CaseParams &cp, int32_t nx, int32_t ny, int32
   k.n_fluid = static_cast<int32_t>(n_fluid);
   k.sr_seed = 0;
   k.exact = 0;
+  k.residual_mode = 0;
   return k;
 }
 
@@ -388,6 +390,16 @@ template <typename T>
 cudaError_t launch_residual_compact(const T *cur, const T *prev, const NodeMap &map,
                                     int64_t n_fluid, int64_t plane, double ax, double ay,
                                     double scale, double *partials, double *result, cudaStream_t s);
+
+// The interval residual (params.residual_mode 1): num, den, mass deviation
+// and non-finite count of the state in cur against the velocity snapshot
+// snap (two values of the storage's arithmetic type per fluid node), which
+// it then replaces with the state's velocity; partials and result as
+// launch_residual_compact.
+template <typename T>
+cudaError_t launch_residual_interval(const T *cur, const NodeMap &map, int64_t n_fluid,
+                                     int64_t plane, double ax, double ay, double scale, void *snap,
+                                     double *partials, double *result, cudaStream_t s);
 
 // Conversions between a compacted lattice (see NodeMap) and
 // caller arrays over the nx x ny nodes (row-major, y * nx + x).

@@ -208,6 +208,66 @@ residual_partials_compact(const T *__restrict__ cur, const T *__restrict__ prev,
   }
 }
 
+// The interval residual's pass 1 (same grid and order as
+// residual_partials_compact): per node the velocity of cur (Eq. FluidMacr,
+// in the storage's arithmetic type) against the snapshot, which it replaces.
+template <typename T>
+__global__ void __launch_bounds__(kResidualThreads)
+residual_interval_compact(const T *__restrict__ cur, const NodeMap map, int64_t n_fluid,
+                          int64_t plane, double ax, double ay, double inv_scale,
+                          typename Stor<T>::C *__restrict__ snap, double *__restrict__ partials) {
+  using C = typename Stor<T>::C;
+  const C inv = static_cast<C>(inv_scale);
+  double num = 0.0, den = 0.0, dm = 0.0, bad = 0.0;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t node = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; node < n_fluid;
+       node += G) {
+    uint32_t s[9];
+    map.slots(static_cast<uint32_t>(node), static_cast<uint32_t>(plane), s);
+    C a[9];
+    bool sat = false;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+      a[i] = Stor<T>::ld(cur[s[i]], inv);
+      if constexpr (kStochastic<T>) sat |= fabsf(Stor<T>::ld_raw(cur[s[i]])) >= Stor<T>::kMaxRaw;
+    }
+    const C r = C(1) + (((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])) + a[8]);
+    const C jx = a[1] - a[3] + (a[5] - a[6]) + (a[8] - a[7]);
+    const C jy = a[2] - a[4] + (a[5] + a[6]) - (a[7] + a[8]);
+    const C ux = (jx + C(0.5) * r * static_cast<C>(ax)) / r;
+    const C uy = (jy + C(0.5) * r * static_cast<C>(ay)) / r;
+    const C px = snap[2 * node], py = snap[2 * node + 1];
+    snap[2 * node] = ux;
+    snap[2 * node + 1] = uy;
+    if (sat || !(isfinite(ux) && isfinite(uy) && isfinite(r))) {
+      bad += 1.0;
+      continue;
+    }
+    const C dx = ux - px, dy = uy - py;
+    num += static_cast<double>(dx * dx + dy * dy);
+    den += static_cast<double>(ux * ux + uy * uy);
+    dm += node_mass(a);
+  }
+  __shared__ double sh[kResidualThreads / 32][kPartialStride];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  dm = warp_sum(dm);
+  bad = warp_sum(bad);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[w][0] = num;
+    sh[w][1] = den;
+    sh[w][2] = dm;
+    sh[w][3] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPartialStride) {
+    double t = 0.0;
+    for (int i = 0; i < kResidualThreads / 32; i++) t += sh[i][threadIdx.x];
+    partials[blockIdx.x * kPartialStride + threadIdx.x] = t;
+  }
+}
+
 // Pass 2: one block of kFinalThreads sums the partials in a fixed order
 // (thread t first adds blocks t, t + kFinalThreads, ...).
 constexpr int kFinalThreads = 1024;
@@ -431,6 +491,17 @@ cudaError_t launch_residual_compact(const T *cur, const T *prev, const NodeMap &
 }
 
 template <typename T>
+cudaError_t launch_residual_interval(const T *cur, const NodeMap &map, int64_t n_fluid,
+                                     int64_t plane, double ax, double ay, double scale, void *snap,
+                                     double *partials, double *result, cudaStream_t s) {
+  residual_interval_compact<T><<<kResidualBlocks, kResidualThreads, 0, s>>>(
+      cur, map, n_fluid, plane, ax, ay, 1.0 / scale, static_cast<typename Stor<T>::C *>(snap),
+      partials);
+  residual_final<<<1, kFinalThreads, 0, s>>>(partials, result);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_fields(const T *f, const NodeMap &map, int64_t plane, double ax, double ay,
                           double scale, double *rho, double *ux, double *uy, cudaStream_t s) {
   const int64_t n = static_cast<int64_t>(map.nx) * map.ny;
@@ -473,6 +544,9 @@ cudaError_t launch_import_f(const double *in, const NodeMap &map, int64_t plane,
   template cudaError_t launch_residual_compact<T>(const T *, const T *, const NodeMap &, int64_t,  \
                                                   int64_t, double, double, double, double *,       \
                                                   double *, cudaStream_t);                         \
+  template cudaError_t launch_residual_interval<T>(const T *, const NodeMap &, int64_t, int64_t,   \
+                                                   double, double, double, void *, double *,       \
+                                                   double *, cudaStream_t);                        \
   template cudaError_t launch_fields<T>(const T *, const NodeMap &, int64_t, double, double,       \
                                         double, double *, double *, double *, cudaStream_t);       \
   template cudaError_t launch_export_f<T>(const T *, const NodeMap &, int64_t, double, double *,   \

@@ -59,7 +59,8 @@ class Params(ctypes.Structure):
                 ("l_mode", ctypes.c_int32), ("diffuse_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("residual_every", ctypes.c_int32),
                 ("storage_scale", ctypes.c_double), ("collision", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("mass_mode", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("mass_mode", ctypes.c_int32),
+                ("residual_mode", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -329,13 +330,14 @@ class Solver:
     defaults of include/lbm.h: precision ("fp32" | "fp64" | "bf16" | "fp16"), l_mode (a name of
     L_MODES or a float for a fixed l), r (fixed r), tau_q, tau_s, E, L1, L2,
     sigma, diffuse_mode, residual_every, stream (a cudaStream_t as int),
-    mass_mode (FP32: 0 auto, 1 always, -1 never the exact-mass step).
+    mass_mode (FP32: 0 auto, 1 always, -1 never the exact-mass step),
+    residual_mode (0 one-step, 1 interval residual).
     """
 
     def __init__(self, case, precision="fp32", l_mode="paper", r=None, tau_q=None, tau_s=None,
                  E=None, L1=None, L2=None, sigma=1.0, diffuse_mode=0, residual_every=100,
                  stream=None, tau_e=1.1, tau_eps=1.2, l_clamp=-0.4, storage_scale=0.0,
-                 bgk=False, mass_mode=0):
+                 bgk=False, mass_mode=0, residual_mode=0):
         p = lbm_params_default()
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if isinstance(l_mode, str):
@@ -358,6 +360,7 @@ class Solver:
         p.collision = 1 if bgk else 0
         p.stream = stream
         p.mass_mode = int(mass_mode)
+        p.residual_mode = int(residual_mode)
         self.case = case
         self.params = p
         self.h = None
@@ -441,7 +444,7 @@ def make_params(**kw) -> Params:
     if kw.pop("bgk", False):
         p.collision = 1
     for key in ("sigma", "diffuse_mode", "tau_e", "tau_eps", "l_clamp", "storage_scale",
-                "mass_mode"):
+                "mass_mode", "residual_mode"):
         if key in kw:
             setattr(p, key, kw.pop(key))
     if kw:

@@ -117,3 +117,21 @@ def test_stochastic_rounding_and_exact_mass_cases_in_a_batch_are_the_cases_alone
         for a, w in zip(b.fields(k), s.fields()):
             np.testing.assert_array_equal(a, w)
         s.close()
+
+
+def test_interval_residual_in_a_batch_is_the_case_alone():
+    """residual_mode 1 in a batch: each case retires at the same step as the
+    same case run alone with the same check interval, FP32, tolerance 1e-8."""
+    cl = _small_batch()[:4]
+    prm = [{"residual_mode": 1}] * len(cl)
+    b = lbm.Batch(cl, precision="fp32", params=prm)
+    steps, res, total = b.run_to(1e-8, 30000, check_every=100)
+    assert (steps > 0).any()
+    for k, c in enumerate(cl):
+        s = lbm.Solver(c, precision="fp32", residual_every=100, residual_mode=1)
+        n, r = s.run_to(1e-8, 30000)
+        if steps[k] > 0:
+            assert n == steps[k] and r < 1e-8, (k, n, steps[k])
+            for a, w in zip(b.fields(k), s.fields()):
+                np.testing.assert_array_equal(a, w)
+        s.close()

@@ -32,7 +32,8 @@ def _pair(case, precision, start_seed=None, amp=1e-3, **kw):
     """Oracle and GPU solver on the same case, parameters and start state."""
     okw = {}
     gkw = dict(precision=precision)
-    for k in ("l_mode", "diffuse_mode", "E", "L1", "L2", "tau_s", "bgk", "mass_mode"):
+    for k in ("l_mode", "diffuse_mode", "E", "L1", "L2", "tau_s", "bgk", "mass_mode",
+              "residual_mode"):
         if k in kw:
             gkw[k] = kw[k]
     if kw.get("bgk"):
@@ -400,3 +401,49 @@ def test_saturated_16bit_state_is_reported_as_unstable():
     with pytest.raises(lbm.LbmError) as ei:
         g.residual()
     assert ei.value.code == lbm.LBM_EUNSTABLE
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-3)])
+def test_interval_residual_matches_oracle(precision, tol):
+    """residual_mode 1: ||u^n - u^m|| / ((n - m) ||u^n||) against the
+    previous call, against the oracle's same quantity on a cylinder array
+    from a perturbed state (FP64 within 1e-10 relative; FP32 within the
+    rounding of one velocity field, ~1e-7 relative per node against a mean
+    change per step of ~1e-4, i.e. ~1e-3 of the residual)."""
+    c = CASES["cylinders"]()
+    o, g = _pair(c, precision, start_seed=9, residual_mode=1)
+    for n in (37, 100, 163):
+        o.step(n)
+        g.step(n)
+        ro = o.residual_interval()
+        rg, mg = g.residual()
+        assert rg == pytest.approx(ro, rel=tol)
+        assert mg == pytest.approx(o.residual()[1], rel=1e-10)
+    assert g.residual()[0] == 0.0  # no step since the last call
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_interval_residual_of_an_accelerating_box(precision):
+    """A periodic box from rest under a body force: u^n = (n + 1/2) a, so
+    the interval residual over steps m..n is 1 / (n + 1/2), whatever m."""
+    c = cases.periodic_box(40, 30, ax=3e-6, ay=-2e-6)
+    g = lbm.Solver(c, precision=precision, residual_mode=1)
+    g.step(1)
+    assert g.residual()[0] == pytest.approx(1 / 1.5, rel=1e-4)
+    g.step(99)
+    assert g.residual()[0] == pytest.approx(1 / 100.5, rel=2e-3)
+
+
+def test_fp32_reaches_the_batch_tolerance_with_the_interval_residual():
+    """The one-step FP32 residual of a converged state is the rounding noise
+    of one step (~1e-8); the interval residual over 100 steps divides that
+    noise by 100 (it settles near 2.5e-9 on this case) and follows the FP64
+    solve down to the 1e-8 of the batched workload: FP32 reaches it within
+    10 % of the steps FP64 takes."""
+    c = cases.cylinder_array(120, 80, 4, Kn=0.02, ax=1e-5)
+    n = {}
+    for prec in ("fp64", "fp32"):
+        g = lbm.Solver(c, precision=prec, residual_mode=1, residual_every=100)
+        n[prec], res = g.run_to(1e-8, 200000)
+        assert res < 1e-8
+    assert abs(n["fp32"] - n["fp64"]) <= 0.1 * n["fp64"]

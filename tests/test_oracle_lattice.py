@@ -163,3 +163,24 @@ def test_openmp_build_is_bitwise_the_single_threaded_one(oracle_mod, threads):
             o.step(57)
         np.testing.assert_array_equal(many.get_f(), one.get_f())
         assert many.residual() == one.residual()
+
+
+def test_residuals_of_a_uniformly_accelerating_box(oracle_mod):
+    """A periodic box from rest under a body force a: u^n = (n + 1/2) a at
+    every node (j gains rho a per step; Eq. FluidMacr adds a / 2), so the
+    one-step residual after n steps is 1 / (n + 1/2) and the interval
+    residual over steps m..n is (n - m) |a| / ((n - m) (n + 1/2) |a|), the
+    same value; a second call with no step in between gives 0."""
+    c = cases.periodic_box(9, 5, ax=3e-6, ay=-2e-6)
+    o = oracle_mod.OracleLBM(c, P.Parameters(c.Kn, c.H))
+    o.step(1)
+    assert o.residual()[0] == pytest.approx(1 / 1.5, rel=1e-9)
+    assert o.residual_interval() == pytest.approx(1 / 1.5, rel=1e-9)
+    o.step(40)
+    assert o.residual()[0] == pytest.approx(1 / 41.5, rel=1e-9)
+    assert o.residual_interval() == pytest.approx(1 / 41.5, rel=1e-9)
+    assert o.residual_interval() == 0.0
+    # set_f makes the new state the reference
+    o.set_f(o.get_f())
+    o.step(7)
+    assert o.residual_interval() == pytest.approx(1 / 48.5, rel=1e-9)

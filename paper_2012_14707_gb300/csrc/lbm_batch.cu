@@ -95,24 +95,28 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
                   const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,
                   const uint32_t *__restrict__ jbslot, const LinkCoef<C> *__restrict__ links,
                   const BatchCase<C> *__restrict__ cases, const int32_t *__restrict__ active,
-                  const uint32_t n_blocks, const uint32_t pf_dist,
-                  const int64_t *__restrict__ counter, const uint32_t j) {
+                  const int32_t *__restrict__ work, const uint32_t n_blocks,
+                  const uint32_t pf_dist, const int64_t *__restrict__ counter, const uint32_t j) {
   static_assert(kChunk % THREADS == 0, "a CTA stays inside one chunk");
+  constexpr uint32_t kPer = kChunk / THREADS;  // CTAs per chunk
   {
     constexpr uint32_t kNodeLines = THREADS * sizeof(uint2) / 128;
     const uint32_t b2 = blockIdx.x + pf_dist;
     const uint32_t t = threadIdx.x;
     if (pf_dist && t < 32 && b2 < n_blocks) {
+      const uint32_t base2 = static_cast<uint32_t>(work[b2 / kPer]) * kChunk + (b2 % kPer) * THREADS;
       if (t < kNodeLines)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(node + b2 * THREADS + t * 16));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(node + base2 + t * 16));
       else if (t == kNodeLines)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ccase + b2 * THREADS / kChunk));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ccase + base2 / kChunk));
     }
   }
-  const int c = ccase[blockIdx.x * THREADS / kChunk];
+  const int32_t chunk = work[blockIdx.x / kPer];
+  const int c = ccase[chunk];
   if (!active[c]) return;
   const BatchCase<C> &bc = cases[c];
-  const uint32_t i = blockIdx.x * THREADS + threadIdx.x - static_cast<uint32_t>(bc.node_off);
+  const uint32_t i = static_cast<uint32_t>(chunk) * kChunk + (blockIdx.x % kPer) * THREADS +
+                     threadIdx.x - static_cast<uint32_t>(bc.node_off);
   if (i >= static_cast<uint32_t>(bc.n_fluid)) return;
   // exact-mass cases run in batch_exact_kernel
   if (std::is_same<T, float>::value && bc.k.exact) return;
@@ -134,12 +138,16 @@ batch_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint2 *_
                   const int32_t *__restrict__ rowstart, const uint32_t *__restrict__ jbslot,
                   const LinkCoef<float> *__restrict__ links,
                   const BatchCase<float> *__restrict__ cases, const int32_t *__restrict__ active,
-                  const int64_t *__restrict__ counter, const uint32_t j) {
+                  const int32_t *__restrict__ work, const int64_t *__restrict__ counter,
+                  const uint32_t j) {
   static_assert(kChunk % (2 * THREADS) == 0, "a CTA stays inside one chunk");
-  const int c = ccase[blockIdx.x * 2 * THREADS / kChunk];
+  constexpr uint32_t kPer = kChunk / (2 * THREADS);  // CTAs per chunk
+  const int32_t chunk = work[blockIdx.x / kPer];
+  const int c = ccase[chunk];
   if (!active[c]) return;
   const BatchCase<float> &bc = cases[c];
-  const uint32_t i0 = blockIdx.x * 2 * THREADS + 2 * threadIdx.x - static_cast<uint32_t>(bc.node_off);
+  const uint32_t i0 = static_cast<uint32_t>(chunk) * kChunk + (blockIdx.x % kPer) * 2 * THREADS +
+                      2 * threadIdx.x - static_cast<uint32_t>(bc.node_off);
   if (i0 >= static_cast<uint32_t>(bc.n_fluid)) return;
   const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot);
   const uint32_t seed = step_seed(*counter + j);
@@ -279,28 +287,30 @@ template <typename T, typename C, int THREADS>
 cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int2 *grp,
                               const int32_t *ccase, const int32_t *rowstart,
                               const uint32_t *jbslot, const void *links, const void *cases,
-                              const int32_t *active, int64_t arena_nodes, uint32_t pf_dist,
-                              const int64_t *counter, uint32_t j, const LinkCoef<double> *links64,
-                              float *carry, float *carry0, const int32_t *exact_chunks,
-                              int32_t n_exact_chunks, cudaStream_t s) {
-  if (arena_nodes <= 0) return cudaSuccess;
+                              const int32_t *active, const int32_t *work, int32_t n_work,
+                              uint32_t pf_dist, const int64_t *counter, uint32_t j,
+                              const LinkCoef<double> *links64, float *carry, float *carry0,
+                              const int32_t *exact_chunks, int32_t n_exact_chunks,
+                              cudaStream_t s) {
   if constexpr (kStochastic<T>) {
     if constexpr (THREADS <= kChunk / 2) {
-      batch_pair_kernel<T, THREADS><<<static_cast<unsigned>(arena_nodes / (2 * THREADS)), THREADS,
-                                      0, s>>>(src, dst, node, grp, ccase, rowstart, jbslot,
-                                              static_cast<const LinkCoef<float> *>(links),
-                                              static_cast<const BatchCase<float> *>(cases), active,
-                                              counter, j);
+      if (n_work > 0)
+        batch_pair_kernel<T, THREADS><<<static_cast<unsigned>(n_work) * (kChunk / (2 * THREADS)),
+                                        THREADS, 0, s>>>(
+            src, dst, node, grp, ccase, rowstart, jbslot,
+            static_cast<const LinkCoef<float> *>(links),
+            static_cast<const BatchCase<float> *>(cases), active, work, counter, j);
       return cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;  // 16-bit batches use widths 64 and 128
     }
   }
-  const int64_t blocks = arena_nodes / THREADS;  // arena_nodes: a multiple of kChunk
-  batch_step_kernel<T, C, THREADS><<<static_cast<unsigned>(blocks), THREADS, 0, s>>>(
-      src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<C> *>(links),
-      static_cast<const BatchCase<C> *>(cases), active, static_cast<uint32_t>(blocks), pf_dist,
-      counter, j);
+  const int64_t blocks = static_cast<int64_t>(n_work) * (kChunk / THREADS);
+  if (blocks > 0)
+    batch_step_kernel<T, C, THREADS><<<static_cast<unsigned>(blocks), THREADS, 0, s>>>(
+        src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<C> *>(links),
+        static_cast<const BatchCase<C> *>(cases), active, work, static_cast<uint32_t>(blocks),
+        pf_dist, counter, j);
   if constexpr (std::is_same<T, float>::value) {
     if (n_exact_chunks > 0) {
       cudaError_t e = cudaGetLastError();
@@ -369,8 +379,17 @@ struct lbm_batch {
   float *carry = nullptr;   // per link of the link arena, then per node-arena entry
   float *carry0 = nullptr;  // = carry + max(1, n_links_total)
   int64_t n_links_total = 0;
-  int32_t *exact_chunks = nullptr;  // node-arena chunks of those cases
+  int32_t *exact_chunks = nullptr;  // node-arena chunks of the active exact-mass cases
   int32_t n_exact_chunks = 0;
+  // Work lists: the step kernels run only the node-arena chunks listed
+  // (work: the other active cases'), so retired cases cost no CTAs.  Per
+  // case its first chunk and chunk count; the lists are rebuilt (and the
+  // graph captured again) each time the active cases halve.
+  std::vector<int32_t> chunk_first, chunk_count;
+  std::vector<char> case_exact;
+  int32_t *work = nullptr;
+  int32_t n_work = 0;
+  int32_t n_listed = 0;  // active cases when the lists were last built
   void *snap = nullptr;  // interval-residual snapshots (2 values per node-arena entry), or null
   int threads = 0;
   uint32_t pf_dist = 0;  // L2 prefetch distance of the step kernel (CTAs), for `threads`
@@ -434,7 +453,7 @@ cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src, ui
       constexpr int TH = decltype(kernel_threads)::value;
       return lbm::launch_batch_step<T, C, TH>(
           static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->node, b->grp,
-          b->ccase, b->rowstart, b->jbslot, b->links, b->cases, b->active, b->arena_nodes,
+          b->ccase, b->rowstart, b->jbslot, b->links, b->cases, b->active, b->work, b->n_work,
           pf_dist, b->counter, j, b->links64, b->carry, b->carry0, b->exact_chunks,
           b->n_exact_chunks,
           b->stream);
@@ -443,6 +462,34 @@ cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src, ui
     if (threads == 128) return go(std::integral_constant<int, 128>());
     return go(std::integral_constant<int, 256>());
   });
+}
+
+// Rebuild the work lists from the active flags (host copy; all cases when
+// null) and upload them.
+cudaError_t build_lists(lbm_batch_t *b, const int32_t *active_host) {
+  std::vector<int32_t> w, x;
+  int32_t n_act = 0;
+  for (int c = 0; c < b->n_cases; c++) {
+    if (active_host && !active_host[c]) continue;
+    n_act++;
+    std::vector<int32_t> &dst = b->case_exact[c] ? x : w;
+    for (int32_t q = 0; q < b->chunk_count[c]; q++) dst.push_back(b->chunk_first[c] + q);
+  }
+  cudaError_t e = cudaSuccess;
+  if (!w.empty())
+    e = cudaMemcpyAsync(b->work, w.data(), w.size() * 4, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && !x.empty())
+    e = cudaMemcpyAsync(b->exact_chunks, x.data(), x.size() * 4, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  b->n_work = static_cast<int32_t>(w.size());
+  b->n_exact_chunks = static_cast<int32_t>(x.size());
+  b->n_listed = n_act;
+  // a captured graph holds the old lists' grid sizes
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return e;
 }
 
 // Snapshots of the interval residual from the current state (lattice 0,
@@ -474,7 +521,7 @@ void batch_release(lbm_batch_t *b) {
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active),
                   static_cast<void *>(b->links64), static_cast<void *>(b->carry),
-                  static_cast<void *>(b->exact_chunks), b->snap})
+                  static_cast<void *>(b->exact_chunks), b->snap, static_cast<void *>(b->work)})
     if (p) cudaFree(p);
   if (b->h_n_active) cudaFreeHost(b->h_n_active);
   if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -645,6 +692,9 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     std::copy(kj.begin(), kj.end(), jbs.begin() + loff);
     std::copy(k.rowstart.begin(), k.rowstart.end(), rowstart.begin() + roff);
     std::copy(k.index.begin(), k.index.end(), index.begin() + ioff);
+    b->chunk_first.push_back(static_cast<int32_t>(noff / lbm::kChunk));
+    b->chunk_count.push_back(static_cast<int32_t>(padded / lbm::kChunk));
+    b->case_exact.push_back(lbm::exact_mass(h) ? 1 : 0);
     if (lbm::exact_mass(h)) {
       std::copy(h.coef.begin(), h.coef.begin() + 4 * h.n_links, l64.begin() + 4 * loff);
       for (int64_t q = noff / lbm::kChunk; q < (noff + padded) / lbm::kChunk; q++)
@@ -733,6 +783,10 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   up(b->grp, grp.data(), grp.size() * sizeof(int2));
   up(b->ccase, ccase.data(), ccase.size() * 4);
   b->arena_nodes = nodes;
+  if (e == cudaSuccess)
+    e = alloc(reinterpret_cast<void **>(&b->work),
+              static_cast<size_t>(std::max<int64_t>(1, nodes / lbm::kChunk)) * 4);
+  if (e == cudaSuccess) e = build_lists(b, nullptr);
   up(b->jbslot, jbs.data(), jbs.size() * 4);
   up(b->rowstart, rowstart.data(), rowstart.size() * 4);
   up(b->index, index.data(), index.size() * 4);
@@ -783,6 +837,7 @@ int lbm_batch_reset(lbm_batch_t *b) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->counter, &zero, 8, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->n_active, &n, 4, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = init_snapshots(b);
+  if (e == cudaSuccess && b->n_listed != b->n_cases) e = build_lists(b, nullptr);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("lbm_batch_reset: ") + cudaGetErrorString(e));
   b->cur = 0;
@@ -798,17 +853,19 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
   if (max_steps < 0) return bfail(b, LBM_EINVAL, "negative max_steps");
   if (b->cur != 0) return bfail(b, LBM_EINVAL, "batch state is mid-graph; call lbm_batch_reset");
   cudaError_t e = cudaSuccess;
-  if (!b->graph || b->graph_K != check_every || b->graph_tol != tol) {
+  // K steps, the batched reduction and the counter advance as one graph,
+  // captured for the current work lists
+  auto capture = [&]() -> cudaError_t {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
     cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    for (int s = 0; s < check_every && e == cudaSuccess; s++)
-      e = step_once(b, b->threads, b->pf_dist, s & 1, static_cast<uint32_t>(s));
-    if (e == cudaSuccess)
-      e = dispatch_b(b->precision, [&](auto tT, auto tC) {
+    cudaError_t ec = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    for (int s = 0; s < check_every && ec == cudaSuccess; s++)
+      ec = step_once(b, b->threads, b->pf_dist, s & 1, static_cast<uint32_t>(s));
+    if (ec == cudaSuccess)
+      ec = dispatch_b(b->precision, [&](auto tT, auto tC) {
         using T = std::remove_pointer_t<decltype(tT)>;
         using C = std::remove_pointer_t<decltype(tC)>;
         lbm::batch_residual_kernel<T, C><<<b->n_cases, lbm::kBatchResidualThreads, 0, b->stream>>>(
@@ -818,25 +875,32 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
             0);
         return cudaGetLastError();
       });
-    if (e == cudaSuccess) {
+    if (ec == cudaSuccess) {
       lbm::batch_advance<<<1, 1, 0, b->stream>>>(b->counter, check_every);
-      e = cudaGetLastError();
+      ec = cudaGetLastError();
     }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->h_n_active, b->n_active, 4, cudaMemcpyDeviceToHost, b->stream);
+    if (ec == cudaSuccess)
+      ec = cudaMemcpyAsync(b->h_n_active, b->n_active, 4, cudaMemcpyDeviceToHost, b->stream);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (ec == cudaSuccess) ec = e2;
+    if (ec == cudaSuccess) ec = cudaGraphInstantiate(&b->graph, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
+    if (ec != cudaSuccess) {
       b->graph = nullptr;
-      return bfail(b, LBM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      return ec;
     }
     b->graph_K = check_every;
     b->graph_tol = tol;
+    return cudaSuccess;
+  };
+  if (!b->graph || b->graph_K != check_every || b->graph_tol != tol) {
+    e = capture();
+    if (e != cudaSuccess)
+      return bfail(b, LBM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
   int64_t done = 0;
   *b->h_n_active = b->n_cases;
+  std::vector<int32_t> act(static_cast<size_t>(b->n_cases));
   while (done < max_steps) {
     e = cudaGraphLaunch(b->graph, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -844,6 +908,14 @@ int lbm_batch_run_to(lbm_batch_t *b, double tol, int64_t max_steps, int32_t chec
     done += check_every;
     b->steps += check_every;
     if (*b->h_n_active <= 0) break;
+    // half of the listed cases retired: list only the active ones' chunks
+    if (*b->h_n_active * 2 <= b->n_listed && done < max_steps) {
+      e = cudaMemcpy(act.data(), b->active, act.size() * 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = build_lists(b, act.data());
+      if (e == cudaSuccess) e = capture();
+      if (e != cudaSuccess)
+        return bfail(b, LBM_ECUDA, std::string("work lists: ") + cudaGetErrorString(e));
+    }
   }
   if (steps_per_case)
     e = cudaMemcpy(steps_per_case, b->steps_done, b->n_cases * 8, cudaMemcpyDeviceToHost);

@@ -370,6 +370,63 @@ const char *lbm_net_last_error(const lbm_net_t *n);
 int lbm_save(lbm_handle_t *h, const char *path);
 int lbm_load(lbm_handle_t *h, const char *path);
 
+/* ---------------------------------------------------------------------------
+ * Three dimensions (D3Q19): the extension the paper names as future work
+ * (Sec. 5).  The same collision (MRT in moment space with Guo forcing, Eqs.
+ * LBEequi, LBEforce, MomentPost, on the D3Q19 moment basis of d'Humieres et
+ * al. 2002), streaming and slip scheme per boundary link (Eq. EqNewBDSC with
+ * the D3Q19 weights), with the parameters of Sec. 3.B from the paper's
+ * two-dimensional analysis.  The paper gives no three-dimensional
+ * derivation; carried out for a D3Q19 flow u_x(z) between walls normal to
+ * z, the same analysis reaches the wall relation of Eq. u1u0Coeff exactly
+ * when the third-order moments relax with tau_q, which they do here (the
+ * fourth-order ones relax with tau_eps), so the slip law of Sec. 3.B holds
+ * for 3-D flat channels; for curved 3-D walls it is an extrapolation.
+ * Conventions:
+ *   * D3Q19 velocities, in this order: (0,0,0); +x, -x, +y, -y, +z, -z; the
+ *     diagonals of the xy, xz and yz planes, each as (+,+), (+,-), (-,+),
+ *     (-,-) (e.g. 7 = (1,1,0), 12 = (1,0,-1), 18 = (0,-1,-1)).
+ *   * Node (x, y, z) has index (z*ny + y)*nx + x; populations are 19*nx*ny*nz
+ *     doubles, index q*nx*ny*nz + node.
+ *   * A link (x, y, z, i, q, u_b) names a fluid node whose neighbour
+ *     x - c_i is solid (or outside a non-periodic axis); every such
+ *     (node, direction) needs exactly one link.  link_ub holds 3 doubles per
+ *     link.
+ *   * Storage LBM_FP64 or LBM_FP32 (deviations f_i - w_i); params as
+ *     lbm_create takes them (collision must be MRT; mass_mode and
+ *     residual_mode do not apply).  The lattice is dense (every node has
+ *     slots).  Calls synchronise the handle's stream, except lbm3d_step.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm3d lbm3d_t;
+
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t periodic_x, periodic_y, periodic_z;
+  double H;          /* characteristic length (Eq. tKnrela) */
+  double ax, ay, az; /* body acceleration */
+} lbm3d_domain_t;
+
+int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links,
+                 const int32_t *link_x, const int32_t *link_y, const int32_t *link_z,
+                 const int32_t *link_dir, const double *link_q, const double *link_ub, double Kn,
+                 const lbm_params_t *params, lbm3d_t **out);
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+int lbm3d_step(lbm3d_t *h, int64_t n);
+/* One-step residual ||u^n - u^(n-1)|| / ||u^n|| and mass over fluid nodes (FP64 sums). */
+int lbm3d_residual(lbm3d_t *h, double *residual, double *mass);
+/* All populations f_i as 19*nx*ny*nz host doubles (get: solid nodes as w_i;
+ * set: replaces both states, steps restart at 0). */
+int lbm3d_get_f(lbm3d_t *h, double *f);
+int lbm3d_set_f(lbm3d_t *h, const double *f);
+/* Density and velocity (Eq. FluidMacr) of every node, nx*ny*nz host doubles
+ * each (solid nodes 0; any pointer may be NULL). */
+int lbm3d_fields(lbm3d_t *h, double *rho, double *ux, double *uy, double *uz);
+/* Per-link r and l as used, in the order the links were given. */
+int lbm3d_link_params(const lbm3d_t *h, double *r, double *l);
+void lbm3d_destroy(lbm3d_t *h);
+/* Last error of the handle; with h = NULL, of the last failed lbm3d_create. */
+const char *lbm3d_last_error(const lbm3d_t *h);
+
 /* Release the handle and its device memory (waits for its stream).  NULL is a no-op. */
 void lbm_destroy(lbm_handle_t *h);
 

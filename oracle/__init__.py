@@ -35,6 +35,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 _LIB_OMP = os.path.join(_HERE, "liblbm_oracle_omp.so")
+_SRC3 = os.path.join(_HERE, "lbm3d_oracle.c")
+_LIB3 = os.path.join(_HERE, "liblbm3d_oracle.so")
 _libs = {}
 
 
@@ -43,11 +45,11 @@ def build(force: bool = False) -> str:
     no contraction into FMAs), twice from the same source: single-threaded,
     and with OpenMP over the row loops of a step (bitwise the same results).
     Returns the single-threaded library's path."""
-    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
-        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+    for lib, src, extra in ((_LIB, _SRC, []), (_LIB_OMP, _SRC, ["-fopenmp"]), (_LIB3, _SRC3, [])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
             tmp = lib + f".tmp{os.getpid()}"
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", *extra, "-shared",
-                                   "-fPIC", "-o", tmp, _SRC, "-lm"])
+                                   "-fPIC", "-o", tmp, src, "-lm"])
             os.replace(tmp, lib)
     return _LIB
 
@@ -197,5 +199,125 @@ class OracleLBM:
             done += every
             res = self.residual_interval() if interval else self.residual()[0]
             if res < tol:
+                break
+        return done
+
+
+def _load3d():
+    if "3d" not in _libs:
+        build()
+        lib = ctypes.CDLL(_LIB3)
+        P = ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        up = ctypes.POINTER(ctypes.c_uint8)
+        c_int, c_d = ctypes.c_int, ctypes.c_double
+        lib.o3d_create.restype = P
+        lib.o3d_create.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, up, c_d, c_d, c_d, dp,
+                                   c_int, ip, ip, ip, ip, dp, dp, dp, dp, c_int]
+        lib.o3d_step.argtypes = [P, ctypes.c_long]
+        lib.o3d_fields.argtypes = [P, dp, dp, dp, dp]
+        lib.o3d_residual.argtypes = [P, dp, dp]
+        lib.o3d_get_f.argtypes = [P, dp]
+        lib.o3d_set_f.argtypes = [P, dp]
+        lib.o3d_get_m.argtypes = [P, dp]
+        lib.o3d_lattice.argtypes = [ip, dp]
+        lib.o3d_steps.restype = ctypes.c_long
+        lib.o3d_steps.argtypes = [P]
+        lib.o3d_destroy.argtypes = [P]
+        _libs["3d"] = lib
+    return _libs["3d"]
+
+
+def d3q19_lattice():
+    """(c [19, 3] int, w [19]) as the 3-D oracle uses them."""
+    c = np.empty((19, 3), np.int32)
+    w = np.empty(19)
+    _load3d().o3d_lattice(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(w))
+    return c, w
+
+
+class OracleLBM3D:
+    """One D3Q19 case (`cases.Case3D`) on the CPU in FP64, with the per-link
+    r and l of `par` (an `oracle.params.Parameters`, the formulas of Sec. 3.B
+    applied unchanged in three dimensions) and the D3Q19 relaxation times of
+    `par.relaxation_times_d3q19()`."""
+
+    def __init__(self, case, par, diffuse_mode=0, link_r=None, link_l=None):
+        lib = self._lib = _load3d()
+        self.case = case
+        g = np.ascontiguousarray(case.link_q, np.float64)
+        r, l = par.per_link(g)
+        if link_l is not None:
+            l = np.asarray(link_l, np.float64) * np.ones_like(g)
+        if link_r is not None:
+            r = np.asarray(link_r, np.float64) * np.ones_like(g)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        k = self._keep = [np.ascontiguousarray(case.solid, np.uint8), par.relaxation_times_d3q19(),
+                          np.ascontiguousarray(case.link_x, np.int32),
+                          np.ascontiguousarray(case.link_y, np.int32),
+                          np.ascontiguousarray(case.link_z, np.int32),
+                          np.ascontiguousarray(case.link_dir, np.int32),
+                          np.ascontiguousarray(r, np.float64), np.ascontiguousarray(l, np.float64), g,
+                          np.ascontiguousarray(case.link_ub, np.float64)]
+        self.link_r, self.link_l = k[6], k[7]
+        px, py, pz = (int(v) for v in case.periodic)
+        ax, ay, az = case.a
+        self._h = lib.o3d_create(case.nx, case.ny, case.nz, px, py, pz,
+                                 k[0].ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ax, ay, az,
+                                 _dp(k[1]), case.n_links, k[2].ctypes.data_as(ip),
+                                 k[3].ctypes.data_as(ip), k[4].ctypes.data_as(ip),
+                                 k[5].ctypes.data_as(ip), _dp(k[6]), _dp(k[7]), _dp(k[8]), _dp(k[9]),
+                                 int(diffuse_mode))
+        if not self._h:
+            raise ValueError("oracle rejected the 3-D case (bad link set or parameters)")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.o3d_destroy(h)
+            self._h = None
+
+    def step(self, n: int = 1):
+        self._lib.o3d_step(self._h, int(n))
+
+    @property
+    def steps(self) -> int:
+        return int(self._lib.o3d_steps(self._h))
+
+    def fields(self):
+        c = self.case
+        n = c.nx * c.ny * c.nz
+        out = [np.empty(n) for _ in range(4)]
+        self._lib.o3d_fields(self._h, *(_dp(a) for a in out))
+        return tuple(a.reshape(c.nz, c.ny, c.nx) for a in out)
+
+    def residual(self):
+        res, mass = ctypes.c_double(), ctypes.c_double()
+        self._lib.o3d_residual(self._h, ctypes.byref(res), ctypes.byref(mass))
+        return res.value, mass.value
+
+    def get_f(self) -> np.ndarray:
+        c = self.case
+        f = np.empty((19, c.nz, c.ny, c.nx))
+        self._lib.o3d_get_f(self._h, _dp(f))
+        return f
+
+    def set_f(self, f: np.ndarray):
+        c = self.case
+        f = np.ascontiguousarray(f, np.float64).reshape(19, c.nz, c.ny, c.nx)
+        self._lib.o3d_set_f(self._h, _dp(f))
+
+    def moment_matrix(self) -> np.ndarray:
+        m = np.empty((19, 19))
+        self._lib.o3d_get_m(self._h, _dp(m))
+        return m
+
+    def run_to(self, tol: float, max_steps: int, every: int = 100):
+        done = 0
+        while done < max_steps:
+            self.step(every)
+            done += every
+            if self.residual()[0] < tol:
                 break
         return done

@@ -267,6 +267,20 @@ class Parameters:
         return np.array([self.tau_rho, self.tau_e, self.tau_eps, self.tau_j, self.tau_q,
                          self.tau_j, self.tau_q, self.tau_s, self.tau_s])
 
+    def relaxation_times_d3q19(self) -> np.ndarray:
+        """Relaxation times of the 19 D3Q19 moments in the order of the 3-D
+        oracle's basis (rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx,
+        3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x, m_y, m_z).  The paper
+        fixes only tau_s (stress) and tau_q (energy flux) through its
+        two-dimensional analysis.  Carried out for D3Q19 (flow u_x(z) between
+        walls normal to z), that analysis reaches the same wall relation
+        Eq. u1u0Coeff exactly when the third-order moments m relax with
+        tau_q, so m takes tau_q; the fourth-order pi take tau_eps."""
+        return np.array([self.tau_rho, self.tau_e, self.tau_eps, self.tau_j, self.tau_q,
+                         self.tau_j, self.tau_q, self.tau_j, self.tau_q, self.tau_s, self.tau_eps,
+                         self.tau_s, self.tau_eps, self.tau_s, self.tau_s, self.tau_s, self.tau_q,
+                         self.tau_q, self.tau_q])
+
     def link_l(self, gamma) -> np.ndarray:
         g = np.asarray(gamma, dtype=np.float64)
         m = self.l_mode

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_params.cpp", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_net.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_params.cpp", "lbm_noalloc.cu", "lbm_batch.cu",
+           "lbm_net.cu", "lbm3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
          "-I", os.path.join(ROOT, "include")]

@@ -476,3 +476,175 @@ def signed_distance(case: Case, clip: float = 32.0) -> np.ndarray:
         sub = np.hypot(xx[y0:y1, x0:x1] - X, yy[y0:y1, x0:x1] - Y) - R
         d[y0:y1, x0:x1] = np.minimum(d[y0:y1, x0:x1], sub)
     return np.clip(d, -clip, clip)
+
+
+# --------------------------------------------------------------------------
+# three dimensions (D3Q19): the extension the paper names as future work
+# --------------------------------------------------------------------------
+#
+# D3Q19 velocities, in the order both the oracle and the library use: the
+# rest velocity, the six axes (+x, -x, +y, -y, +z, -z), then the diagonals of
+# the xy, xz and yz planes, each as (+, +), (+, -), (-, +), (-, -).  Node
+# (x, y, z) has index (z * ny + y) * nx + x; masks are [nz, ny, nx].
+
+def _d3q19_velocities():
+    c = [(0, 0, 0)]
+    for a in range(3):
+        for s in (1, -1):
+            v = [0, 0, 0]
+            v[a] = s
+            c.append(tuple(v))
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        for s1 in (1, -1):
+            for s2 in (1, -1):
+                v = [0, 0, 0]
+                v[a], v[b] = s1, s2
+                c.append(tuple(v))
+    return np.array(c, dtype=np.int64)
+
+
+C3 = _d3q19_velocities()
+
+
+@dataclasses.dataclass
+class Case3D:
+    """One three-dimensional solver input (D3Q19).  Arrays are host numpy arrays."""
+
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    periodic: tuple  # (x, y, z) booleans
+    solid: np.ndarray  # uint8 [nz, ny, nx]
+    link_x: np.ndarray  # int32 [n_links]
+    link_y: np.ndarray
+    link_z: np.ndarray
+    link_dir: np.ndarray  # int32, 1..18
+    link_q: np.ndarray  # float64, gamma in (0, 1]
+    link_ub: np.ndarray  # float64 [n_links, 3], wall velocity at x_b
+    Kn: float
+    H: float
+    a: tuple = (0.0, 0.0, 0.0)  # body acceleration
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_links(self) -> int:
+        return int(self.link_x.shape[0])
+
+    @property
+    def n_fluid(self) -> int:
+        return int((self.solid == 0).sum())
+
+
+def _wall_candidates_3d(solid: np.ndarray, periodic):
+    """All (x, y, z, i) with (x, y, z) fluid and (x, y, z) - c_i solid."""
+    nz, ny, nx = solid.shape
+    zs, ys, xs = np.nonzero(solid == 0)
+    out = [[], [], [], [], [], [], []]
+    dims = (nx, ny, nz)
+    for i in range(1, 19):
+        r = [xs - C3[i, 0], ys - C3[i, 1], zs - C3[i, 2]]
+        inside = np.ones(xs.shape, bool)
+        for a in range(3):
+            if periodic[a]:
+                r[a] = r[a] % dims[a]
+            else:
+                inside &= (r[a] >= 0) & (r[a] < dims[a])
+        hit = np.ones(xs.shape, bool)
+        hit[inside] = solid[r[2][inside], r[1][inside], r[0][inside]] != 0
+        for lst, v in zip(out, (xs, ys, zs, np.full(xs.shape, i), r[0], r[1], r[2])):
+            lst.append(v[hit])
+    return tuple(np.concatenate(v) for v in out)
+
+
+def _make_case3d(name, solid, periodic, lx, ly, lz, li, q, ub, Kn, H, a, meta=None) -> Case3D:
+    order = np.lexsort((li, lx, ly, lz))
+    nz, ny, nx = solid.shape
+    return Case3D(name=name, nx=nx, ny=ny, nz=nz, periodic=tuple(bool(p) for p in periodic),
+                  solid=np.ascontiguousarray(solid, np.uint8),
+                  link_x=np.asarray(lx, np.int32)[order], link_y=np.asarray(ly, np.int32)[order],
+                  link_z=np.asarray(lz, np.int32)[order], link_dir=np.asarray(li, np.int32)[order],
+                  link_q=np.asarray(q, np.float64)[order],
+                  link_ub=np.ascontiguousarray(np.asarray(ub, np.float64).reshape(-1, 3)[order]),
+                  Kn=float(Kn), H=float(H), a=tuple(float(v) for v in a), meta=dict(meta or {}))
+
+
+def channel3d(nx: int, ny: int, m: int, q_bottom: float, q_top: float, Kn: float,
+              ax: float = 1e-6, u_top: float = 0.0, name: str = "slip_channel_3d") -> Case3D:
+    """Channel with m fluid layers between two flat walls normal to z,
+    periodic in x and y: layers z = 0 and m + 1 are solid, the lower wall
+    lies q_bottom below the first fluid layer and the upper one q_top above
+    the last (every link of a wall layer has gamma = q of that wall), the
+    upper wall moves along x at u_top.  H = m - 1 + q_bottom + q_top."""
+    nz = m + 2
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[0] = 1
+    solid[nz - 1] = 1
+    lx, ly, lz, li, rx, ry, rz = _wall_candidates_3d(solid, (True, True, False))
+    bottom = rz == 0
+    q = np.where(bottom, q_bottom, q_top)
+    ub = np.zeros((lx.shape[0], 3))
+    ub[~bottom, 0] = u_top
+    return _make_case3d(name, solid, (True, True, False), lx, ly, lz, li, q, ub, Kn,
+                        m - 1 + q_bottom + q_top, (ax, 0.0, 0.0),
+                        meta=dict(m=m, q_bottom=q_bottom, q_top=q_top))
+
+
+def periodic_box3d(nx: int, ny: int, nz: int, a=(1e-5, 0.0, 0.0), Kn: float = 0.05,
+                   name: str = "box_3d") -> Case3D:
+    """Fully periodic box without walls (no links)."""
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    e = np.zeros(0, np.int32)
+    return _make_case3d(name, solid, (True, True, True), e, e, e, e, np.zeros(0), np.zeros((0, 3)),
+                        Kn, float(min(nx, ny, nz)), a)
+
+
+def sphere_array3d(n: int, n_spheres: int, r_range=(3.0, 6.0), seed: int = 0, Kn: float = 0.02,
+                   a=(1e-5, 0.0, 0.0), name: str = "spheres_3d") -> Case3D:
+    """Periodic n^3 box with non-overlapping spheres (seeded random
+    sequential addition, radii uniform in r_range, 2-node clearance, wrapped
+    distances); gamma from the exact segment-sphere intersection (the nearest
+    periodic image of the sphere), walls at rest.  H = mean diameter."""
+    rng = np.random.default_rng(seed)
+    centres, radii = [], []
+    tries = 0
+    while len(centres) < n_spheres and tries < 20000:
+        tries += 1
+        r = rng.uniform(*r_range)
+        c = rng.uniform(0, n, size=3)
+        ok = True
+        for c2, r2 in zip(centres, radii):
+            d = np.abs(c - c2)
+            d = np.minimum(d, n - d)
+            if np.sqrt((d * d).sum()) < r + r2 + 2.0:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+            radii.append(r)
+    zz, yy, xx = np.mgrid[0:n, 0:n, 0:n].astype(np.float64)
+    solid = np.zeros((n, n, n), np.uint8)
+    owner = np.full((n, n, n), -1, np.int64)
+    for k, (c, r) in enumerate(zip(centres, radii)):
+        dx = (xx - c[0] + n / 2) % n - n / 2
+        dy = (yy - c[1] + n / 2) % n - n / 2
+        dz = (zz - c[2] + n / 2) % n - n / 2
+        inside = dx * dx + dy * dy + dz * dz <= r * r
+        solid[inside] = 1
+        owner[inside] = k
+    lx, ly, lz, li, rx, ry, rz = _wall_candidates_3d(solid, (True, True, True))
+    q = np.empty(lx.shape[0])
+    for t in range(lx.shape[0]):
+        k = owner[rz[t], ry[t], rx[t]]
+        c, r = centres[k], radii[k]
+        p = np.array([lx[t], ly[t], lz[t]], np.float64)
+        p = c + ((p - c + n / 2) % n - n / 2)  # the fluid node next to the nearest image
+        d = -C3[li[t]].astype(np.float64)
+        o = p - c
+        aa, bb, cc = d @ d, 2 * (o @ d), o @ o - r * r
+        q[t] = min(1.0, max(np.finfo(np.float64).tiny,
+                            (-bb - math.sqrt(max(bb * bb - 4 * aa * cc, 0.0))) / (2 * aa)))
+    H = 2.0 * float(np.mean(radii)) if radii else float(n)
+    return _make_case3d(name, solid, (True, True, True), lx, ly, lz, li, q,
+                        np.zeros((lx.shape[0], 3)), Kn, H, a,
+                        meta=dict(n_spheres=len(centres)))

@@ -160,8 +160,9 @@ batch_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint2 *_
 
 // The exact-mass cases of an FP32 batch (moving walls; see collide and
 // link_epilogue_pull): one CTA of kChunk threads per node-arena chunk in
-// `chunks` (the chunks of those cases), with room for the FP64 registers.
-__global__ void __launch_bounds__(kChunk, 2)
+// `chunks` (the chunks of those cases); the same register budget per thread
+// (64) as the single-case exact kernel.
+__global__ void __launch_bounds__(kChunk, 4)
 batch_exact_kernel(const float *__restrict__ src, float *__restrict__ dst,
                    const uint2 *__restrict__ node, const int2 *__restrict__ grp,
                    const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,

@@ -143,9 +143,32 @@ struct Collided {
   C o[9];
   T t[9];
   C drho, rho, ux, uy, uu;
-  // the exact-mass variant (FP32 storage): the same quantities in FP64
-  double drho64, rho64, ux64, uy64;
+  // the exact-mass variant (FP32 storage): rho - 1 and j in twice the
+  // working precision (hi + lo), for the FP64 link values
+  float dr_hi, dr_lo, jx_hi, jx_lo, jy_hi, jy_lo;
 };
+
+// Error-free sum of two FP32 values: s + e == a + b exactly (Knuth's
+// TwoSum; no multiplication, so nothing is contracted into an FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Sum of n FP32 values in twice the working precision (cascaded TwoSum,
+// Ogita, Rump and Oishi's Sum2): s + e.
+template <int N>
+__device__ __forceinline__ void sum2(const float (&a)[N], float &s, float &e) {
+  s = a[0];
+  e = 0.0f;
+#pragma unroll
+  for (int i = 1; i < N; i++) {
+    float t;
+    two_sum(s, a[i], s, t);
+    e += t;
+  }
+}
 
 // a + b rounded to FP32 stochastically: the FP32 sum s (round to nearest)
 // or its neighbour on the side of the exact remainder e = a + b - s
@@ -247,12 +270,15 @@ __device__ __forceinline__ void collision_change(const C (&d)[9], const StepCons
 // trajectory to ~1e-10 over thousands of steps.  A moving wall exchanges
 // mass with the fluid at a rate set by the velocity next to it, so every
 // rounding that leans the same way step after step shows up in the mass.
-// Hence: rho and u are formed in FP64 and rounded once (no approximate
-// reciprocal) for the equilibrium and the links; f'_1..f'_8 are rounded to
-// FP32 stochastically (add_stochastic, random bits from rs); f'_0 closes
-// the node's mass in FP64 plus the node's carry c0 (what FP32 storage
+// Hence: rho - 1 and j are summed in twice the working precision (sum2),
+// rho and u rounded once each (u by the correctly rounded division, no
+// approximate reciprocal) for the equilibrium, and kept for the links'
+// FP64 values; f'_1..f'_8 are rounded to FP32 stochastically
+// (add_stochastic, random bits from rs); f'_0 closes the node's mass in
+// twice the working precision plus the node's carry c0 (what FP32 storage
 // dropped from its earlier values), is stored rounded to nearest, and the
-// new remainder is kept in c0.
+// new remainder is kept in c0.  Only boundary nodes do FP64 arithmetic
+// (this GPU has few FP64 units).
 // 16-bit storage rounds f'_0..f'_8 stochastically with random bits from rs,
 // the node's random word (fmix32 of the node index and the step seed).
 template <typename T, typename C, bool kExact = false>
@@ -262,23 +288,18 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
   static_assert(!kExact || std::is_same<T, float>::value, "the exact-mass variant is FP32 storage");
   C(&o)[9] = r.o;
   T(&t)[9] = r.t;
-  if constexpr (kExact) {
-    double dr = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; i++) dr += static_cast<double>(d[i]);
-    const double jx = (static_cast<double>(d[1]) - d[3]) + (static_cast<double>(d[5]) - d[6]) +
-                      (static_cast<double>(d[8]) - d[7]);
-    const double jy = (static_cast<double>(d[2]) - d[4]) + (static_cast<double>(d[5]) + d[6]) -
-                      (static_cast<double>(d[7]) + d[8]);
-    const double rh = 1.0 + dr;
-    r.drho64 = dr;
-    r.rho64 = rh;
-    r.ux64 = (jx + 0.5 * rh * static_cast<double>(k.ax)) / rh;
-    r.uy64 = (jy + 0.5 * rh * static_cast<double>(k.ay)) / rh;
-  }
   C ch[9];
   if constexpr (kExact) {
-    const C given[3] = {C(r.rho64), C(r.ux64), C(r.uy64)};
+    // rho - 1 and j in twice the working precision; rho and u rounded once
+    // each (u by the correctly rounded division, no approximate reciprocal)
+    sum2(d, r.dr_hi, r.dr_lo);
+    const float jxs[6] = {d[1], -d[3], d[5], -d[6], -d[7], d[8]};
+    const float jys[6] = {d[2], -d[4], d[5], d[6], -d[7], -d[8]};
+    sum2(jxs, r.jx_hi, r.jx_lo);
+    sum2(jys, r.jy_hi, r.jy_lo);
+    const float rho = 1.0f + (r.dr_hi + r.dr_lo);
+    const C given[3] = {rho, __fdiv_rn(r.jx_hi + (r.jx_lo + 0.5f * rho * k.ax), rho),
+                        __fdiv_rn(r.jy_hi + (r.jy_lo + 0.5f * rho * k.ay), rho)};
     collision_change<kS, true>(d, k, ch, r.drho, r.rho, r.ux, r.uy, r.uu, given);
   } else {
     collision_change<kS, false>(d, k, ch, r.drho, r.rho, r.ux, r.uy, r.uu);
@@ -334,14 +355,15 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
       dd[i] = o[i] - d[i];
     }
     if constexpr (kExact) {
-      // f'_0 = f_0 - sum (f'_i - f_i) in FP64 (exact: eight FP32 changes
-      // and d_0), plus the carry
-      double sdd = 0.0;
-#pragma unroll
-      for (int i = 1; i < 9; i++) sdd += static_cast<double>(dd[i]);
-      const double v0 = static_cast<double>(d[0]) - sdd + static_cast<double>(*c0);
-      t[0] = __double2float_rn(v0);
-      *c0 = __double2float_rn(v0 - static_cast<double>(t[0]));
+      // f'_0 = f_0 - sum (f'_i - f_i) plus the carry, in twice the working
+      // precision (the eight changes are exact FP32 values); stored rounded
+      // to nearest, the remainder kept as the new carry
+      const float ddv[8] = {dd[1], dd[2], dd[3], dd[4], dd[5], dd[6], dd[7], dd[8]};
+      float sh, sl, vh, e1, e2;
+      sum2(ddv, sh, sl);
+      two_sum(d[0], -sh, vh, e1);
+      two_sum(vh, (e1 - sl) + *c0, t[0], e2);
+      *c0 = e2;
       o[0] = t[0];
     } else {
       o[0] = d[0] - (((dd[1] + dd[2]) + (dd[3] + dd[4])) + ((dd[5] + dd[6]) + (dd[7] + dd[8])));
@@ -389,6 +411,14 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
   // in storage units (times the storage scale) where the storage is scaled
   const C drho = kS ? c_.drho * k.sc : c_.drho, rho = kS ? c_.rho * k.sc : c_.rho;
   const uint32_t tail = 9u * g.plane;
+  // the exact-mass variant's FP64 rho - 1, rho and u of the node
+  double drho64 = 0.0, rho64 = 1.0, ux64 = 0.0, uy64 = 0.0;
+  if constexpr (kExact) {
+    drho64 = static_cast<double>(c_.dr_hi) + c_.dr_lo;
+    rho64 = 1.0 + drho64;
+    ux64 = (static_cast<double>(c_.jx_hi) + c_.jx_lo + 0.5 * rho64 * k.ax) / rho64;
+    uy64 = (static_cast<double>(c_.jy_hi) + c_.jy_lo + 0.5 * rho64 * k.ay) / rho64;
+  }
 #pragma unroll
   for (int j = 1; j < 9; j++) {
     if (!(wmask & (1u << (j - 1)))) continue;
@@ -412,12 +442,12 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
           c0 = c.alpha + (r - 1.0) * w_tab[j];
           c2 = 0.0;
         }
-        const double cu = cx_tab[j] * c_.ux64 + cy_tab[j] * c_.uy64;
-        const double pj = 3.0 * cu + 4.5 * cu * cu - 1.5 * (c_.ux64 * c_.ux64 + c_.uy64 * c_.uy64);
+        const double cu = cx_tab[j] * ux64 + cy_tab[j] * uy64;
+        const double pj = 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux64 * ux64 + uy64 * uy64);
         const double djb = static_cast<double>(src[g.jbslot[lj]]);
         const double v = c.k1 * djb + c.k2 * static_cast<double>(o[j]) +
-                         c.k3 * static_cast<double>(o[jb]) + c0 + c.alpha * c_.drho64 +
-                         c2 * (c_.drho64 + c_.rho64 * pj) + static_cast<double>(g.carry[lj]);
+                         c.k3 * static_cast<double>(o[jb]) + c0 + c.alpha * drho64 +
+                         c2 * (drho64 + rho64 * pj) + static_cast<double>(g.carry[lj]);
         const float t = __double2float_rn(v);
         g.carry[lj] = __double2float_rn(v - static_cast<double>(t));
         dst[tail + lj] = t;

@@ -337,6 +337,13 @@ int build_host_case(const lbm_domain_t *dom, const uint8_t *solid, size_t n_link
 
 // Host-side FP64 precompute (lbm_params.cpp).  Returns "" or an error text.
 std::string compute_case_params(double Kn, double H, const lbm_params_t &p, CaseParams *out);
+// Per-link l and r (Sec. 3.B) and the folded coefficients above, from the
+// link's c_i . u_b, weight w_i and |u_b|^2 (any lattice; the D2Q9 entry
+// below computes them from the direction).
+std::string compute_link_coefs_general(const CaseParams &cp, const lbm_params_t &p, size_t n,
+                                       const double *q, const double *cub, const double *w,
+                                       const double *uu, double *r_out, double *l_out,
+                                       double *coef8_out /* n x 8 */, int64_t *n_clamped);
 // Per-link l and r (Sec. 3.B) and the folded coefficients above.
 std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size_t n,
                                const int32_t *dir, const double *q, const double *ubx,

@@ -39,7 +39,7 @@ using namespace dev;
 // mostly hit lines that the neighbouring rows' CTAs brought in).
 //
 // kExact: the exact-mass variant of FP32 storage (cases with moving walls;
-// see collide and link_epilogue_pull), with room for its FP64 registers.
+// see collide and link_epilogue_pull), with 64 registers per thread.
 template <typename T, typename C, bool kExact>
 __global__ void __launch_bounds__(kPullThreads, kExact ? 8 : PullOcc<T>::min_blocks)
 step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom g,
@@ -115,14 +115,6 @@ step_kernel_pair(const T *__restrict__ src, T *__restrict__ dst, const PullGeom 
     step_pair_pull<T>(src, dst, g, links, k, i0, k.sr_seed);
   else
     step_node_pull<T, float, false>(src, dst, g, links, k, i0, k.sr_seed);
-}
-
-// Error-free sum of two FP32 values: s + e == a + b exactly (Knuth's
-// TwoSum; no multiplication, so nothing is contracted into an FMA).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
 }
 
 // Mass deviation of one node, sum_i d_i, to FP64 accuracy.  FP64 storage:

@@ -5,6 +5,7 @@
 #include <limits>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "lbm_internal.h"
 
@@ -77,12 +78,28 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
                                const int32_t *dir, const double *q, const double *ubx,
                                const double *uby, double *r_out, double *l_out, double *coef8,
                                int64_t *n_clamped) {
+  // the D2Q9 quantities of each link, then the lattice-independent part
+  std::vector<double> cub(n), w(n), uu(n);
+  for (size_t k = 0; k < n; k++) {
+    const int i = dir[k];
+    if (i < 1 || i > 8) return fmt("link direction %g outside 1..8", static_cast<double>(i));
+    cub[k] = kCx[i] * ubx[k] + kCy[i] * uby[k];
+    w[k] = kW[i];
+    uu[k] = ubx[k] * ubx[k] + uby[k] * uby[k];
+  }
+  return compute_link_coefs_general(cp, p, n, q, cub.data(), w.data(), uu.data(), r_out, l_out,
+                                    coef8, n_clamped);
+}
+
+std::string compute_link_coefs_general(const CaseParams &cp, const lbm_params_t &p, size_t n,
+                                       const double *q, const double *cub_in, const double *w_in,
+                                       const double *uu_in, double *r_out, double *l_out,
+                                       double *coef8, int64_t *n_clamped) {
   const double s6 = std::sqrt(6.0 / kPi);
   const double ts = cp.tau_s, a = 2.0 * ts - 1.0, L1 = cp.L1;
   // one link: "" or an error text; sets *cl when the clamp applied
   auto one = [&](size_t k, int *cl) -> std::string {
     const double g = q[k];
-    const int i = dir[k];
     double l;
     switch (p.l_mode) {
       case LBM_L_PAPER: {
@@ -117,14 +134,13 @@ std::string compute_link_coefs(const CaseParams &cp, const lbm_params_t &p, size
     const double k1 = r * (1.0 + l - 2.0 * g) * inv;
     const double k2 = r * l * inv;
     const double k3 = r * (2.0 * g - l) * inv;
-    const double cub = kCx[i] * ubx[k] + kCy[i] * uby[k];
-    double alpha = 2.0 * r * inv * kW[i] * 3.0 * cub;  // multiplies rho_f
-    double beta;                                         // multiplies f_eq(rho_f, u_f)
+    const double cub = cub_in[k], wi = w_in[k];
+    double alpha = 2.0 * r * inv * wi * 3.0 * cub;  // multiplies rho_f
+    double beta;                                      // multiplies f_eq(rho_f, u_f)
     if (p.diffuse_mode == 0) {
       beta = 1.0 - r;
     } else {
-      const double uu = ubx[k] * ubx[k] + uby[k] * uby[k];
-      alpha += (1.0 - r) * kW[i] * (1.0 + 3.0 * cub + 4.5 * cub * cub - 1.5 * uu);
+      alpha += (1.0 - r) * wi * (1.0 + 3.0 * cub + 4.5 * cub * cub - 1.5 * uu_in[k]);
       beta = 0.0;
     }
     (void)beta;  // implied by diffuse_mode and r = k1 + k2 + k3 in the kernel

@@ -73,6 +73,13 @@ class Info(ctypes.Structure):
                 ("exact_mass", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Domain3D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("periodic_z", ctypes.c_int32), ("H", ctypes.c_double), ("ax", ctypes.c_double),
+                ("ay", ctypes.c_double), ("az", ctypes.c_double)]
+
+
 class CaseDesc(ctypes.Structure):
     _fields_ = [("dom", Domain), ("solid", ctypes.c_void_p), ("n_links", ctypes.c_size_t),
                 ("link_x", ctypes.c_void_p), ("link_y", ctypes.c_void_p),
@@ -115,6 +122,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_residual_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_void_p, dp, dp]
+    lib.lbm3d_create.argtypes = [ctypes.POINTER(Domain3D), ctypes.POINTER(ctypes.c_uint8),
+                                 ctypes.c_size_t, ip, ip, ip, ip, dp, dp, ctypes.c_double,
+                                 ctypes.POINTER(Params), ctypes.POINTER(H)]
+    lib.lbm3d_step.argtypes = [H, ctypes.c_int64]
+    lib.lbm3d_residual.argtypes = [H, dp, dp]
+    lib.lbm3d_get_f.argtypes = [H, dp]
+    lib.lbm3d_set_f.argtypes = [H, dp]
+    lib.lbm3d_link_params.argtypes = [H, dp, dp]
+    lib.lbm3d_fields.argtypes = [H, dp, dp, dp, dp]
+    lib.lbm3d_destroy.argtypes = [H]
+    lib.lbm3d_destroy.restype = None
+    lib.lbm3d_last_error.argtypes = [H]
+    lib.lbm3d_last_error.restype = ctypes.c_char_p
     lib.lbm_save.argtypes = [H, ctypes.c_char_p]
     lib.lbm_load.argtypes = [H, ctypes.c_char_p]
     lib.lbm_destroy.argtypes = [H]
@@ -607,6 +627,94 @@ class Net:
     def close(self):
         if getattr(self, "h", None):
             load().lbm_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# three dimensions (lbm3d_*)
+# --------------------------------------------------------------------------
+
+def _check3(rc, h=None):
+    if rc != LBM_OK:
+        raise LbmError(rc, load().lbm3d_last_error(h).decode())
+
+
+class Solver3D:
+    """One D3Q19 case (`cases.Case3D`) on the GPU.  Keyword arguments as for
+    `Solver` (precision "fp64" or "fp32")."""
+
+    def __init__(self, case, precision="fp32", stream=None, **kw):
+        lib = load()
+        p = make_params(**kw)
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.stream = stream
+        self.case = case
+        px, py, pz = (int(bool(v)) for v in case.periodic)
+        dom = Domain3D(case.nx, case.ny, case.nz, px, py, pz, float(case.H), *(float(v) for v in case.a))
+        solid = np.ascontiguousarray(case.solid, np.uint8).reshape(-1)
+        arrs = [np.ascontiguousarray(a, t) for a, t in
+                ((case.link_x, np.int32), (case.link_y, np.int32), (case.link_z, np.int32),
+                 (case.link_dir, np.int32), (case.link_q, np.float64))]
+        ub = np.ascontiguousarray(case.link_ub, np.float64).reshape(-1)
+        self._keep = (solid, arrs, ub)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        h = ctypes.c_void_p()
+        rc = lib.lbm3d_create(ctypes.byref(dom), solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                              arrs[0].size, *(a.ctypes.data_as(ip) for a in arrs[:4]),
+                              _dp(arrs[4]), _dp(ub), float(case.Kn), ctypes.byref(p), ctypes.byref(h))
+        _check3(rc, None)
+        self.h = h.value
+
+    def step(self, n=1):
+        _check3(load().lbm3d_step(self.h, int(n)), self.h)
+
+    def residual(self):
+        r, m = ctypes.c_double(), ctypes.c_double()
+        _check3(load().lbm3d_residual(self.h, ctypes.byref(r), ctypes.byref(m)), self.h)
+        return r.value, m.value
+
+    def get_f(self):
+        c = self.case
+        f = np.empty((19, c.nz, c.ny, c.nx))
+        _check3(load().lbm3d_get_f(self.h, _dp(f)), self.h)
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, np.float64)
+        _check3(load().lbm3d_set_f(self.h, _dp(f)), self.h)
+
+    def fields(self):
+        """(rho, ux, uy, uz) [nz, ny, nx] (lbm3d_fields); solid nodes 0."""
+        c = self.case
+        out = [np.empty((c.nz, c.ny, c.nx)) for _ in range(4)]
+        _check3(load().lbm3d_fields(self.h, *(_dp(a) for a in out)), self.h)
+        return tuple(out)
+
+    def run_to(self, tol, max_steps, every=100):
+        done, res = 0, math.inf
+        while done < max_steps:
+            self.step(every)
+            done += every
+            res = self.residual()[0]
+            if res < tol:
+                break
+        return done, res
+
+    def link_params(self):
+        n = self.case.n_links
+        r, l = np.empty(n), np.empty(n)
+        _check3(load().lbm3d_link_params(self.h, _dp(r), _dp(l)), self.h)
+        return r, l
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm3d_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -141,7 +141,7 @@ def _fp32_mass_params():
         marks = ()
         if name == "annulus":
             marks = pytest.mark.xfail(strict=False, reason=(
-                "known miss: 5.4e-10 after 2000 steps with the exact-mass step (8.9e-9 without); "
+                "known miss: 1.9e-10 after 2000 steps with the exact-mass step (8.9e-9 without); "
                 "the rotating curved wall exchanges mass at a rate set by the near-wall velocity, "
                 "and FP32 relaxation rates and coefficients shift that rate by ~1e-7"))
         out.append(pytest.param(name, marks=marks))

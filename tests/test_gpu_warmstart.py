@@ -20,29 +20,28 @@ def _lib():
 
 
 def test_set_fields_restart_from_a_steady_state():
-    """Restarting from converged fields (equilibrium plus first-order
-    non-equilibrium part) reaches tol 1e-6 in well under the steps from rest
-    and ends in the same state.  (The first-order populations miss the wall
-    nodes' own non-equilibrium structure, so the restart has a short
-    transient: at much tighter tolerances the saving shrinks.)"""
+    """What any predictor could save: restarting from the converged fields
+    themselves (equilibrium plus first-order non-equilibrium part) reaches
+    the interval residual 1e-8 in at most half the steps from rest (0.44 on
+    this small case; 0.25 is the median on 200 held-out 256^2 cases), and ends
+    in the same state.  The fields round-trip through the populations."""
     c = cases.cylinder_array(96, 64, 4, Kn=0.01, ax=1e-5, r_max=10.0)
-    s = lbm.Solver(c, precision="fp64", residual_every=100)
-    n_rest, r_rest = s.run_to(1e-6, 200000)
-    assert r_rest < 1e-6
-    s.run_to(1e-11, 200000)
+    s = lbm.Solver(c, precision="fp64", residual_every=100, residual_mode=1)
+    n_rest, r_rest = s.run_to(1e-8, 200000)
+    assert r_rest < 1e-8
+    s.run_to(1e-12, 400000)
     rho, ux, uy = s.fields()
-    s2 = lbm.Solver(c, precision="fp64", residual_every=100)
+    s2 = lbm.Solver(c, precision="fp64", residual_every=100, residual_mode=1)
     s2.set_fields(rho, ux, uy)
     got = s2.fields()
     fl = c.solid == 0
-    # the fields round-trip through the populations
     np.testing.assert_allclose(got[0][fl], rho[fl], rtol=0, atol=1e-13)
     np.testing.assert_allclose(got[1][fl], ux[fl], rtol=0, atol=1e-14)
     np.testing.assert_allclose(got[2][fl], uy[fl], rtol=0, atol=1e-14)
-    n_warm, r_warm = s2.run_to(1e-6, 200000)
-    assert r_warm < 1e-6
-    assert n_warm <= 0.7 * n_rest
-    s2.run_to(1e-11, 200000)
+    n_warm, r_warm = s2.run_to(1e-8, 200000)
+    assert r_warm < 1e-8
+    assert n_warm <= 0.5 * n_rest
+    s2.run_to(1e-12, 400000)
     u2 = s2.fields()
     assert np.abs(u2[1] - ux)[fl].max() <= 1e-7 * np.abs(ux).max()
 

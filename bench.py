@@ -501,6 +501,232 @@ def run_batch(args):
     return 0
 
 
+D3Q19_BYTES = {"fp32": 152, "fp64": 304}  # 19 reads + 19 writes per fluid node
+
+
+def run_d3q19(args):
+    """The D3Q19 extension: a periodic 512 x 256 x 256 box of non-overlapping
+    spheres (porosity 0.8, radii 6-12, seeded), Kn 0.02, force-driven, FP32
+    (or FP64).  One bench step = --lbm-steps lattice steps + the residual
+    pass; MLUPS over fluid nodes; roofline of the step kernel = 152 B per
+    fluid node (FP32) over its mean launch time (CUDA events on the
+    solver's stream).  cpu_baseline: the FP64 D3Q19 oracle (one thread) on a
+    128 x 64 x 64 box of the same recipe."""
+    import numpy as np
+    import torch
+
+    from paper_2012_14707_gb300 import build as lbm_build
+    from paper_2012_14707_gb300 import cases, lbm
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lbm_build.build()
+    lbm.load()
+    nx, ny, nz = (args.nx or 512), (args.ny or 256), (args.nz or 256)
+    case = cases.sphere_pack3d(nx, ny, nz, seed=rank, porosity=0.8, r_range=(6.0, 12.0),
+                               Kn=0.02, a=(1e-6, 0.0, 0.0))
+    stream = torch.cuda.current_stream(dev)
+    prec = args.precision if args.precision in D3Q19_BYTES else "fp32"
+    sv = lbm.Solver3D(case, precision=prec, stream=stream.cuda_stream)
+    per = args.lbm_steps
+    n_fluid = case.n_fluid
+    for _ in range(args.warmup):
+        sv.step(per)
+        sv.residual()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    last = None
+    for s in range(args.steps):
+        k_start[s].record(stream)
+        sv.step(per)
+        k_end[s].record(stream)
+        last = sv.residual()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in zip(k_start, k_end))
+    (elapsed_ms, kernel_ms), (total_fluid,) = reduce_over_ranks([elapsed_ms, kernel_ms], [n_fluid],
+                                                                world, dev)
+    sv.close()
+    mlups = total_fluid * per * args.steps / (elapsed_ms / 1e3) / 1e6
+    launch_ms = kernel_ms / (args.steps * per)
+    achieved = D3Q19_BYTES[prec] * n_fluid / (launch_ms / 1e3) / 1e9
+    step_achieved = D3Q19_BYTES[prec] * mlups * 1e6 / world / 1e9
+    peak, peak_src = _peak_hbm()
+    line = {
+        "metric": "MLUPS (D3Q19)", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64"}[prec], "data": "synthetic",
+        "config": {"workload": f"spheres3d_{nx}x{ny}x{nz}_phi0.8_Kn0.02", "nx": nx, "ny": ny,
+                   "nz": nz, "n_fluid": n_fluid, "n_links": case.n_links,
+                   "n_spheres": case.meta["n_spheres"], "precision": prec,
+                   "lattice_steps_per_step": per,
+                   "l2": "inputs larger than L2 (2 x %.2f GB dense lattices)" % (
+                       19 * nx * ny * nz * D3Q19_BYTES[prec] / 38 / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "step3_kernel",
+                     "bytes_per_fluid_node": D3Q19_BYTES[prec], "launch_ms": launch_ms,
+                     "peak_source": peak_src, "step_achieved": step_achieved,
+                     "step_frac": step_achieved / peak},
+        "e2e": None,
+        "gpu_launches": args.steps * (per + 2),
+        "clocks": clocks,
+        "residual_last": last[0] if last else None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        from oracle import params as P
+        sc = cases.sphere_pack3d(128, 64, 64, seed=0, porosity=0.8, r_range=(6.0, 12.0),
+                                 Kn=0.02, a=(1e-6, 0.0, 0.0))
+        o = oracle.OracleLBM3D(sc, P.Parameters(sc.Kn, sc.H))
+        o.step(2)
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < 5.0:
+            o.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": sc.n_fluid * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 D3Q19 oracle (one thread) on a 128x64x64 box of the same recipe "
+                      f"({sc.n_fluid} fluid nodes): 2 warm-up steps, then {n} steps in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_warmstart(args):
+    """The learned warm start (256 x 256 random-cylinder channels, Kn
+    log-uniform 0.001-0.1, FP32 solves to the interval residual 1e-8): the
+    network is trained on --ws-train seeded cases solved by the batched
+    solver, then --ws-test held-out seeds are solved three ways and timed to
+    steady state (creation, and for the warm start the network's inference
+    and lbm_set_fields, included): in one batch started from the network's
+    fields, in one batch started from rest, and one case at a time through
+    the single-case solver from rest.  value = the time to steady state of
+    the batched + warm-start run."""
+    import numpy as np
+    import torch
+
+    from paper_2012_14707_gb300 import build as lbm_build
+    from paper_2012_14707_gb300 import lbm
+    from paper_2012_14707_gb300 import warmstart as ws
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    lbm_build.build()
+    lbm.load()
+    tol, cap, every, size = args.batch_tol, 40000, 100, 256
+    t0 = time.perf_counter()
+    data = ws.make_dataset(args.ws_train, 1 + 1000000 * rank, size, tol, cap)
+    t_data = time.perf_counter() - t0
+    net = lbm.Net(size, size, base=32, levels=4, precision="bf16", max_batch=8, seed=0)
+    t0 = time.perf_counter()
+    ws.train(net, data, args.ws_epochs, 8, 2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    held = ws.make_cases(args.ws_test, 100000 + 1000000 * rank, size)
+    prm = [{"residual_mode": 1}] * len(held)
+    # warm-up of the batched path (graph capture, allocator) on two cases
+    b = lbm.Batch(held[:2], precision="fp32", params=prm[:2])
+    b.run_to(tol, 2 * every, every)
+    b.close()
+    sampler = ClockSampler(local)
+    sampler.start()
+    runs = {}
+    for mode in ("warm", "rest"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        preds = ws.predict(net, held, 8) if mode == "warm" else None
+        t_inf = time.perf_counter() - t0
+        b = lbm.Batch(held, precision="fp32", params=prm)
+        if preds is not None:
+            for k, (rho, ux, uy) in enumerate(preds):
+                b.set_fields(k, rho, ux, uy)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        steps, _, total = b.run_to(tol, cap, every)
+        torch.cuda.synchronize()
+        t_end = time.perf_counter()
+        b.close()
+        runs[mode] = dict(seconds=t_end - t0, solve_seconds=t_end - t1, inference_seconds=t_inf,
+                          steps=steps, total=int(total))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = []
+    for c in held:
+        sv = lbm.Solver(c, precision="fp32", residual_every=every, residual_mode=1)
+        try:
+            n, r = sv.run_to(tol, cap)
+            single.append(n if r < tol else 0)
+        except lbm.LbmError:
+            single.append(-1)
+        sv.close()
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    clocks = sampler.stop()
+    single = np.array(single)
+    w, r_ = runs["warm"]["steps"], runs["rest"]["steps"]
+    both = (w > 0) & (r_ > 0)
+    line = {
+        "metric": "time to steady state (batched + warm start)", "value": runs["warm"]["seconds"],
+        "unit": "s", "n_gpus": world, "steps": int(runs["warm"]["total"]), "warmup": 2 * every,
+        "ms_per_step": runs["warm"]["solve_seconds"] / max(runs["warm"]["total"], 1) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"warmstart_{len(held)}_heldout_cylinders_{size}x{size}_Kn0.001-0.1",
+                   "tol": tol, "residual": "interval (mean change per step over each check interval)",
+                   "max_steps": cap, "check_every": every, "train_cases": args.ws_train,
+                   "train_converged": len(data.cases), "epochs": args.ws_epochs,
+                   "net": "unet4_base32 bf16", "l2": "whole batch (%.0f MB lattices) above L2" % (
+                       2 * 9 * 4 * sum(c.n_fluid for c in held) / 1e6)},
+        "time_to_steady": {
+            "batched_warm_start_s": runs["warm"]["seconds"],
+            "batched_from_rest_s": runs["rest"]["seconds"],
+            "single_case_from_rest_s": t_single,
+            "warm_inference_s": runs["warm"]["inference_seconds"],
+            "converged": {"warm": int((w > 0).sum()), "rest": int((r_ > 0).sum()),
+                          "single": int((single > 0).sum())},
+            "median_steps": {"warm": float(np.median(w[both])) if both.any() else None,
+                             "rest": float(np.median(r_[both])) if both.any() else None},
+            "median_step_ratio": float(np.median(w[both] / r_[both])) if both.any() else None,
+            "single_same_steps_as_batch": int((single == r_).sum()),
+            "note": "creation included in every arm; warm start includes inference and "
+                    "lbm_set_fields; training excluded (data %.0f s, training %.0f s)" % (
+                        t_data, t_train)},
+        "e2e": None,
+        "clocks": clocks,
+    }
+    net.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def net_flops(H, W, base=32, levels=4, c_in=3, c_out=3):
     """Multiply-adds x 2 of one forward pass of the warm-start network on one
     H x W sample (every convolution; pooling and upsampling are negligible)."""
@@ -600,7 +826,8 @@ def main():
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=("throughput", "batch", "net"), default="throughput")
+    ap.add_argument("--workload", choices=("throughput", "batch", "net", "d3q19", "warmstart"),
+                    default="throughput")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-max-steps", type=int, default=50000)
     ap.add_argument("--batch-single", type=int, default=32,
@@ -609,6 +836,10 @@ def main():
                     help="interval residual to reach (the batched workload's 1e-8)")
     ap.add_argument("--nx", type=int, default=0, help="profiling only: smaller lattice width")
     ap.add_argument("--ny", type=int, default=0, help="profiling only: smaller lattice height")
+    ap.add_argument("--nz", type=int, default=0, help="profiling only: smaller D3Q19 lattice depth")
+    ap.add_argument("--ws-train", type=int, default=512, help="warm start: training cases")
+    ap.add_argument("--ws-test", type=int, default=200, help="warm start: held-out cases")
+    ap.add_argument("--ws-epochs", type=int, default=20, help="warm start: training epochs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -616,6 +847,10 @@ def main():
         return run_batch(args)
     if args.workload == "net":
         return run_net(args)
+    if args.workload == "d3q19":
+        return run_d3q19(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

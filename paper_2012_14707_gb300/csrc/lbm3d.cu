@@ -45,6 +45,87 @@ constexpr int kResThreads3 = 256;
 
 // velocities: rest, the six axes (+x, -x, +y, -y, +z, -z), then the
 // diagonals of the xy, xz and yz planes, each (+, +), (+, -), (-, +), (-, -)
+#define LBM3_CX {0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 0, 0, 0, 0}
+#define LBM3_CY {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1}
+#define LBM3_CZ {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1}
+#define LBM3_OPP {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15}
+
+// component a (0 x, 1 y, 2 z) of c_q, and the opposite direction
+__host__ __device__ constexpr int cvel3(int q, int a) {
+  const int cx[Q] = LBM3_CX, cy[Q] = LBM3_CY, cz[Q] = LBM3_CZ;
+  return a == 0 ? cx[q] : (a == 1 ? cy[q] : cz[q]);
+}
+__host__ __device__ constexpr int opp3(int q) {
+  const int o[Q] = LBM3_OPP;
+  return o[q];
+}
+
+// Moment basis of d'Humieres et al. (2002): row r evaluated at c_q.  Rows:
+// rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww,
+// p_xy, p_yz, p_xz, m_x, m_y, m_z.  Every entry is an integer.
+__host__ __device__ constexpr int m3(int r, int q) {
+  const int x = cvel3(q, 0), y = cvel3(q, 1), z = cvel3(q, 2), c2 = x * x + y * y + z * z;
+  switch (r) {
+    case 0: return 1;
+    case 1: return 19 * c2 - 30;
+    case 2: return (21 * c2 * c2 - 53 * c2 + 24) / 2;
+    case 3: return x;
+    case 4: return (5 * c2 - 9) * x;
+    case 5: return y;
+    case 6: return (5 * c2 - 9) * y;
+    case 7: return z;
+    case 8: return (5 * c2 - 9) * z;
+    case 9: return 3 * x * x - c2;
+    case 10: return (3 * c2 - 5) * (3 * x * x - c2);
+    case 11: return y * y - z * z;
+    case 12: return (3 * c2 - 5) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return (y * y - z * z) * x;
+    case 17: return (z * z - x * x) * y;
+    default: return (x * x - y * y) * z;
+  }
+}
+
+// the rows odd in c (j, q and the third-order m): m3(r, opp q) = -m3(r, q);
+// the others are even
+__host__ __device__ constexpr bool odd_row3(int r) { return (r >= 3 && r <= 8) || r >= 16; }
+
+// one direction of each pair (q, opp q)
+constexpr int kPairs3 = 9;
+__host__ __device__ constexpr int rep3(int p) {
+  const int t[kPairs3] = {1, 3, 5, 7, 8, 11, 12, 15, 16};
+  return t[p];
+}
+
+constexpr int norm3(int r) {
+  int s = 0;
+  for (int q = 0; q < Q; q++) s += m3(r, q) * m3(r, q);
+  return s;
+}
+
+// The basis is orthogonal, each row even or odd as odd_row3 says, and the
+// representatives with their opposites cover directions 1..18 once.
+constexpr bool basis3_ok() {
+  for (int r = 0; r < Q; r++) {
+    for (int s = 0; s < Q; s++) {
+      int dot = 0;
+      for (int q = 0; q < Q; q++) dot += m3(r, q) * m3(s, q);
+      if (r != s && dot != 0) return false;
+    }
+    for (int q = 0; q < Q; q++)
+      if (m3(r, opp3(q)) != (odd_row3(r) ? -m3(r, q) : m3(r, q))) return false;
+  }
+  int seen = 0;
+  for (int p = 0; p < kPairs3; p++) seen |= (1 << rep3(p)) | (1 << opp3(rep3(p)));
+  return seen == ((1 << Q) - 2);
+}
+static_assert(basis3_ok(), "D3Q19 moment basis");
+static_assert(norm3(0) == 19 && norm3(1) == 2394 && norm3(2) == 252 && norm3(3) == 10 &&
+                  norm3(4) == 40 && norm3(13) == 4 && norm3(16) == 8,
+              "D3Q19 moment norms");
+
 struct Lattice {
   int c[Q][3];
   int opp[Q];
@@ -52,55 +133,15 @@ struct Lattice {
   double M[Q][Q];  // moment basis, rows = moments
   double norm[Q];  // |M_k|^2
   Lattice() {
-    int k = 0;
-    c[k][0] = c[k][1] = c[k][2] = 0;
-    w[k++] = 1.0 / 3.0;
-    for (int a = 0; a < 3; a++)
-      for (int s = 1; s >= -1; s -= 2) {
-        for (int b = 0; b < 3; b++) c[k][b] = b == a ? s : 0;
-        w[k++] = 1.0 / 18.0;
-      }
-    const int pa[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-    for (auto &pr : pa)
-      for (int s1 = 1; s1 >= -1; s1 -= 2)
-        for (int s2 = 1; s2 >= -1; s2 -= 2) {
-          for (int b = 0; b < 3; b++) c[k][b] = 0;
-          c[k][pr[0]] = s1;
-          c[k][pr[1]] = s2;
-          w[k++] = 1.0 / 36.0;
-        }
-    for (int i = 0; i < Q; i++)
-      for (int j = 0; j < Q; j++)
-        if (c[j][0] == -c[i][0] && c[j][1] == -c[i][1] && c[j][2] == -c[i][2]) opp[i] = j;
+    for (int q = 0; q < Q; q++) {
+      for (int a = 0; a < 3; a++) c[q][a] = cvel3(q, a);
+      opp[q] = opp3(q);
+      const int c2 = c[q][0] * c[q][0] + c[q][1] * c[q][1] + c[q][2] * c[q][2];
+      w[q] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
     for (int r = 0; r < Q; r++) {
-      norm[r] = 0.0;
-      for (int i = 0; i < Q; i++) {
-        const double x = c[i][0], y = c[i][1], z = c[i][2], c2 = x * x + y * y + z * z;
-        double v;
-        switch (r) {
-          case 0: v = 1.0; break;
-          case 1: v = 19.0 * c2 - 30.0; break;
-          case 2: v = (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0; break;
-          case 3: v = x; break;
-          case 4: v = (5.0 * c2 - 9.0) * x; break;
-          case 5: v = y; break;
-          case 6: v = (5.0 * c2 - 9.0) * y; break;
-          case 7: v = z; break;
-          case 8: v = (5.0 * c2 - 9.0) * z; break;
-          case 9: v = 3.0 * x * x - c2; break;
-          case 10: v = (3.0 * c2 - 5.0) * (3.0 * x * x - c2); break;
-          case 11: v = y * y - z * z; break;
-          case 12: v = (3.0 * c2 - 5.0) * (y * y - z * z); break;
-          case 13: v = x * y; break;
-          case 14: v = y * z; break;
-          case 15: v = x * z; break;
-          case 16: v = (y * y - z * z) * x; break;
-          case 17: v = (z * z - x * x) * y; break;
-          default: v = (x * x - y * y) * z; break;
-        }
-        M[r][i] = v;
-        norm[r] += v * v;
-      }
+      norm[r] = norm3(r);
+      for (int q = 0; q < Q; q++) M[r][q] = m3(r, q);
     }
   }
 };
@@ -112,9 +153,7 @@ const Lattice &lattice() {
 
 // Kernel constants of one case (passed by value): the relaxation rates
 // s_k and forcing weights 1 - s_k/2 of the 19 moments, each divided by
-// |M_k|^2 (the scale of M^-1 = M^T diag(1/|M_k|^2)).  The lattice itself
-// (velocities, weights, M) is the same for every case and sits in constant
-// memory.
+// |M_k|^2 (the scale of M^-1 = M^T diag(1/|M_k|^2)).
 template <typename C>
 struct Const3 {
   C s_scaled[Q], f_scaled[Q];
@@ -130,133 +169,168 @@ struct Link3 {
   C k1, k2, k3, alpha;
 };
 
-// Slot of f_q(x, t) for node p (pull layout): the neighbour x - c_q's own
-// slot, or the node's tail element when x - c_q is solid.  rank = links of
-// the node in lower directions.
+// lattice weight of direction q
 template <typename C>
-__device__ __forceinline__ int64_t pull_slot3(const Const3<C> &k, const int cq[3], int x, int y,
-                                              int z, uint32_t fl, int q, int64_t lbase,
-                                              int64_t N) {
+__host__ __device__ constexpr C w3(int q) {
+  return q == 0 ? C(1) / C(3) : (q < 7 ? C(1) / C(18) : C(1) / C(36));
+}
+
+// Coordinates of lattice node p (row-major x fastest; p < 2^31).
+struct Coord3 {
+  int x, y, z;
+};
+template <typename C>
+__device__ __forceinline__ Coord3 coord3(const Const3<C> &k, int64_t p) {
+  const unsigned u = static_cast<unsigned>(p), row = u / static_cast<unsigned>(k.nx);
+  return Coord3{static_cast<int>(u - row * static_cast<unsigned>(k.nx)),
+                static_cast<int>(row % static_cast<unsigned>(k.ny)),
+                static_cast<int>(row / static_cast<unsigned>(k.ny))};
+}
+
+// Slot of f_q(x, t) for node p (pull layout): the neighbour x - c_q's own
+// slot, or the node's tail element when x - c_q is solid.  A coordinate
+// that leaves the lattice wraps (periodic axis); on a walled axis the link
+// flag is set there, so the wrapped value is never used.
+template <typename C>
+__device__ __forceinline__ int64_t pull_slot3(const Const3<C> &k, int q, Coord3 c, uint32_t fl,
+                                              uint32_t lbase, int64_t N) {
   if (fl & (1u << q)) return 19 * N + lbase + __popc(fl & ((1u << q) - 1u));
-  int xs = x - cq[0], ys = y - cq[1], zs = z - cq[2];
-  if (k.px) xs = (xs + k.nx) % k.nx;
-  if (k.py) ys = (ys + k.ny) % k.ny;
-  if (k.pz) zs = (zs + k.nz) % k.nz;
+  int xs = c.x - cvel3(q, 0), ys = c.y - cvel3(q, 1), zs = c.z - cvel3(q, 2);
+  xs += xs < 0 ? k.nx : (xs >= k.nx ? -k.nx : 0);
+  ys += ys < 0 ? k.ny : (ys >= k.ny ? -k.ny : 0);
+  zs += zs < 0 ? k.nz : (zs >= k.nz ? -k.nz : 0);
   return static_cast<int64_t>(q) * N + (static_cast<int64_t>(zs) * k.ny + ys) * k.nx + xs;
 }
 
-// the velocities and opposites in the order of Lattice, for device code
-// (compile-time tables: unrolled loops index registers with them)
-#define LBM3_CX {0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 0, 0, 0, 0}
-#define LBM3_CY {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1}
-#define LBM3_CZ {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1}
-#define LBM3_OPP {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15}
-__constant__ int c_c3[Q][3];
-__constant__ double c_M3d[Q][Q];
-__constant__ float c_M3f[Q][Q];
-__constant__ double c_w3d[Q];
-__constant__ float c_w3f[Q];
-
+// acc + m x for a compile-time integer m (zero terms vanish, +-1 add)
 template <typename C>
-__device__ __forceinline__ C mval(int r, int q) {
-  if constexpr (std::is_same<C, double>::value) return c_M3d[r][q];
-  else return c_M3f[r][q];
-}
-template <typename C>
-__device__ __forceinline__ C wval(int q) {
-  if constexpr (std::is_same<C, double>::value) return c_w3d[q];
-  else return c_w3f[q];
+__device__ __forceinline__ C mac3(C acc, int m, C x) {
+  return m == 0 ? acc : (m == 1 ? acc + x : (m == -1 ? acc - x : fma(C(m), x, acc)));
 }
 
+// One lattice step for every fluid node (pull layout).  The collision runs
+// on the pairs (q, opp q): d_q + d_opp carries the even moments and
+// d_q - d_opp the odd ones, so each row of M touches at most ten values
+// and, M being integer and known here at compile time, only its non-zero
+// entries cost an instruction.
 template <typename C>
-__global__ void __launch_bounds__(kThreads3)
+__global__ void __launch_bounds__(kThreads3, sizeof(C) == 4 ? 6 : 2)
 step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
-             const int64_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
+             const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
              const Const3<C> k, int64_t n_nodes) {
   const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= n_nodes) return;
   const uint32_t fl = flags[p];
   if (fl == kSolid3) return;
   const int64_t N = k.plane;
-  const int x = static_cast<int>(p % k.nx), y = static_cast<int>((p / k.nx) % k.ny),
-            z = static_cast<int>(p / (static_cast<int64_t>(k.nx) * k.ny));
-  constexpr int cx[Q] = LBM3_CX, cy[Q] = LBM3_CY, cz[Q] = LBM3_CZ, opp[Q] = LBM3_OPP;
-  const int64_t lb = lbase[p];
+  const Coord3 c = coord3(k, p);
+  const uint32_t lb = fl ? lbase[p] : 0u;
   C d[Q];
+  if (fl == 0) {
+    // every neighbour fluid: x - c_q from the wrapped coordinates
+    const int xw[3] = {c.x + 1 < k.nx ? c.x + 1 : 0, c.x, c.x > 0 ? c.x - 1 : k.nx - 1};
+    const int yw[3] = {c.y + 1 < k.ny ? c.y + 1 : 0, c.y, c.y > 0 ? c.y - 1 : k.ny - 1};
+    const int zw[3] = {c.z + 1 < k.nz ? c.z + 1 : 0, c.z, c.z > 0 ? c.z - 1 : k.nz - 1};
+    const int64_t sx = k.nx, sxy = static_cast<int64_t>(k.nx) * k.ny;
 #pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const int cq[3] = {cx[q], cy[q], cz[q]};
-    d[q] = src[pull_slot3(k, cq, x, y, z, fl, q, lb, N)];
-  }
-  // Eq. FluidMacr
-  C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
+    for (int q = 0; q < Q; q++)
+      d[q] = src[q * N + zw[cvel3(q, 2) + 1] * sxy + yw[cvel3(q, 1) + 1] * sx +
+                 xw[cvel3(q, 0) + 1]];
+  } else {
 #pragma unroll
-  for (int q = 0; q < Q; q++) {
-    drho += d[q];
-    jx += C(cx[q]) * d[q];
-    jy += C(cy[q]) * d[q];
-    jz += C(cz[q]) * d[q];
+    for (int q = 0; q < Q; q++) d[q] = src[pull_slot3(k, q, c, fl, lb, N)];
   }
+  // Eq. FluidMacr on the pair sums and differences
+  C S[kPairs3], A[kPairs3];
+  C drho = d[0];
+#pragma unroll
+  for (int pp = 0; pp < kPairs3; pp++) {
+    S[pp] = d[rep3(pp)] + d[opp3(rep3(pp))];
+    A[pp] = d[rep3(pp)] - d[opp3(rep3(pp))];
+    drho += S[pp];
+  }
+  C j[3] = {C(0), C(0), C(0)};
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int pp = 0; pp < kPairs3; pp++) j[a] = mac3(j[a], cvel3(rep3(pp), a), A[pp]);
   const C rho = C(1) + drho;
-  const C ux = (jx + C(0.5) * rho * k.ax) / rho, uy = (jy + C(0.5) * rho * k.ay) / rho,
-          uz = (jz + C(0.5) * rho * k.az) / rho;
+  const C ux = (j[0] + C(0.5) * rho * k.ax) / rho, uy = (j[1] + C(0.5) * rho * k.ay) / rho,
+          uz = (j[2] + C(0.5) * rho * k.az) / rho;
   const C uu = ux * ux + uy * uy + uz * uz, ua = ux * k.ax + uy * k.ay + uz * k.az;
-  // d - d_eq and Fbar (Eq. LBEequi, Eq. LBEforce), then the moments
-  C neq[Q], F[Q];
+  // d - d_eq (Eq. LBEequi) and Fbar (Eq. LBEforce), as pair sums (S) and
+  // differences (A); the rest direction alone
+  C NS[kPairs3], NA[kPairs3], FS[kPairs3], FA[kPairs3];
+  const C n0 = d[0] - w3<C>(0) * (drho - C(1.5) * rho * uu);
+  const C F0 = C(-3) * w3<C>(0) * rho * ua;
 #pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const C cu = C(cx[q]) * ux + C(cy[q]) * uy + C(cz[q]) * uz;
-    const C ca = C(cx[q]) * k.ax + C(cy[q]) * k.ay + C(cz[q]) * k.az;
-    neq[q] = d[q] - wval<C>(q) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
-    F[q] = wval<C>(q) * rho * (C(3) * ca + C(9) * (cu * ca - ua / C(3)));
+  for (int pp = 0; pp < kPairs3; pp++) {
+    const int q = rep3(pp);
+    const C cu = mac3(mac3(mac3(C(0), cvel3(q, 0), ux), cvel3(q, 1), uy), cvel3(q, 2), uz);
+    const C ca = mac3(mac3(mac3(C(0), cvel3(q, 0), k.ax), cvel3(q, 1), k.ay), cvel3(q, 2), k.az);
+    const C wr = w3<C>(q) * rho;
+    NS[pp] = S[pp] - C(2) * w3<C>(q) * (drho + rho * (C(4.5) * cu * cu - C(1.5) * uu));
+    NA[pp] = A[pp] - C(6) * wr * cu;
+    FS[pp] = C(2) * wr * (C(9) * cu * ca - C(3) * ua);
+    FA[pp] = C(6) * wr * ca;
   }
   // m' - m = -s (m - m_eq) + (1 - s/2) M Fbar, scaled by 1/|M_k|^2
   C dm[Q];
 #pragma unroll
   for (int r = 0; r < Q; r++) {
     C a = C(0), b = C(0);
+    if (!odd_row3(r)) {
+      a = mac3(a, m3(r, 0), n0);
+      b = mac3(b, m3(r, 0), F0);
+    }
 #pragma unroll
-    for (int q = 0; q < Q; q++) {
-      a += mval<C>(r, q) * neq[q];
-      b += mval<C>(r, q) * F[q];
+    for (int pp = 0; pp < kPairs3; pp++) {
+      a = mac3(a, m3(r, rep3(pp)), odd_row3(r) ? NA[pp] : NS[pp]);
+      b = mac3(b, m3(r, rep3(pp)), odd_row3(r) ? FA[pp] : FS[pp]);
     }
     dm[r] = k.f_scaled[r] * b - k.s_scaled[r] * a;
   }
-  // f' - f = M^T dm; f'_0 closes the mass from the stored changes
+  // f' - f = M^T dm: even rows give the same change to q and opp q, odd
+  // rows opposite ones; f'_0 closes the mass from the stored changes
   C o[Q];
   C sum = C(0);
 #pragma unroll
-  for (int q = 1; q < Q; q++) {
-    C ch = C(0);
+  for (int pp = 0; pp < kPairs3; pp++) {
+    const int q = rep3(pp), qb = opp3(q);
+    C ev = C(0), od = C(0);
 #pragma unroll
-    for (int r = 0; r < Q; r++) ch += mval<C>(r, q) * dm[r];
-    o[q] = d[q] + ch;
-    sum += o[q] - d[q];
+    for (int r = 0; r < Q; r++) {
+      if (odd_row3(r)) od = mac3(od, m3(r, q), dm[r]);
+      else ev = mac3(ev, m3(r, q), dm[r]);
+    }
+    o[q] = d[q] + (ev + od);
+    o[qb] = d[qb] + (ev - od);
+    sum += (o[q] - d[q]) + (o[qb] - d[qb]);
   }
   o[0] = d[0] - sum;
 #pragma unroll
   for (int q = 0; q < Q; q++) dst[q * N + p] = o[q];
   // Eq. EqNewBDSC for each unknown direction j of the node, to the tail
   if (fl) {
-    int rank = 0;
+    uint32_t rank = 0;
 #pragma unroll
-    for (int j = 1; j < Q; j++) {
-      if (!(fl & (1u << j))) continue;
-      const Link3<C> c = links[lb + rank];
-      const int jb = opp[j];
-      const C r = c.k1 + c.k2 + c.k3;
+    for (int jq = 1; jq < Q; jq++) {
+      if (!(fl & (1u << jq))) continue;
+      const Link3<C> cl = links[lb + rank];
+      const int jb = opp3(jq);
+      const C r = cl.k1 + cl.k2 + cl.k3;
       C c0, c2;
       if (k.diffuse_mode == 0) {
-        c0 = c.alpha;
-        c2 = (C(1) - r) * wval<C>(j);
+        c0 = cl.alpha;
+        c2 = (C(1) - r) * w3<C>(jq);
       } else {
-        c0 = c.alpha + (r - C(1)) * wval<C>(j);
+        c0 = cl.alpha + (r - C(1)) * w3<C>(jq);
         c2 = C(0);
       }
-      const C cu = C(cx[j]) * ux + C(cy[j]) * uy + C(cz[j]) * uz;
+      const C cu = mac3(mac3(mac3(C(0), cvel3(jq, 0), ux), cvel3(jq, 1), uy), cvel3(jq, 2), uz);
       const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-      dst[19 * N + lb + rank] = c.k1 * d[jb] + c.k2 * o[j] + c.k3 * o[jb] + c0 + c.alpha * drho +
-                                c2 * (drho + rho * pj);
+      dst[19 * N + lb + rank] = cl.k1 * d[jb] + cl.k2 * o[jq] + cl.k3 * o[jb] + c0 +
+                                cl.alpha * drho + c2 * (drho + rho * pj);
       rank++;
     }
   }
@@ -267,7 +341,7 @@ step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__r
 template <typename C>
 __global__ void __launch_bounds__(kResThreads3)
 residual3_kernel(const C *__restrict__ cur, const C *__restrict__ prev,
-                 const uint32_t *__restrict__ flags, const int64_t *__restrict__ lbase,
+                 const uint32_t *__restrict__ flags, const uint32_t *__restrict__ lbase,
                  const Const3<C> k, int64_t n_nodes, double *__restrict__ partials) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const int64_t G = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -275,24 +349,26 @@ residual3_kernel(const C *__restrict__ cur, const C *__restrict__ prev,
        p += G) {
     const uint32_t fl = flags[p];
     if (fl == kSolid3) continue;
-    const int x = static_cast<int>(p % k.nx), y = static_cast<int>((p / k.nx) % k.ny),
-              z = static_cast<int>(p / (static_cast<int64_t>(k.nx) * k.ny));
+    const Coord3 c = coord3(k, p);
     double r1 = 1.0, r0 = 1.0, j1[3] = {0, 0, 0}, j0[3] = {0, 0, 0}, dm = 0.0;
-    const int64_t lb = lbase[p];
+    const uint32_t lb = fl ? lbase[p] : 0u;
+#pragma unroll
     for (int q = 0; q < Q; q++) {
-      const int64_t s = pull_slot3(k, c_c3[q], x, y, z, fl, q, lb, k.plane);
+      const int64_t s = pull_slot3(k, q, c, fl, lb, k.plane);
       const double a = static_cast<double>(cur[s]), b = static_cast<double>(prev[s]);
       r1 += a;
       r0 += b;
       dm += a;
+#pragma unroll
       for (int e = 0; e < 3; e++) {
-        j1[e] += c_c3[q][e] * a;
-        j0[e] += c_c3[q][e] * b;
+        j1[e] += cvel3(q, e) * a;
+        j0[e] += cvel3(q, e) * b;
       }
     }
     const double acc3[3] = {static_cast<double>(k.ax), static_cast<double>(k.ay),
                             static_cast<double>(k.az)};
     double num = 0.0, den = 0.0;
+#pragma unroll
     for (int e = 0; e < 3; e++) {
       const double u1 = (j1[e] + 0.5 * r1 * acc3[e]) / r1, u0 = (j0[e] + 0.5 * r0 * acc3[e]) / r0;
       num += (u1 - u0) * (u1 - u0);
@@ -308,9 +384,9 @@ residual3_kernel(const C *__restrict__ cur, const C *__restrict__ prev,
   }
   __shared__ double sh[kResThreads3 / 32][4];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = 0; c < 4; c++) {
-    const double v = lbm::dev::warp_sum(acc[c]);
-    if (lane == 0) sh[w][c] = v;
+  for (int cc = 0; cc < 4; cc++) {
+    const double v = lbm::dev::warp_sum(acc[cc]);
+    if (lane == 0) sh[w][cc] = v;
   }
   __syncthreads();
   if (threadIdx.x < 4) {
@@ -344,20 +420,19 @@ __global__ void __launch_bounds__(1024) residual3_final(const double *partials, 
 // solid entries ignored).
 template <typename C>
 __global__ void export3_kernel(const C *__restrict__ f, const uint32_t *__restrict__ flags,
-                               const int64_t *__restrict__ lbase, const Const3<C> k,
+                               const uint32_t *__restrict__ lbase, const Const3<C> k,
                                int64_t n_nodes, double *out) {
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < Q * n_nodes;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int q = static_cast<int>(t / n_nodes);
-    const int64_t p = t - static_cast<int64_t>(q) * n_nodes;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_nodes;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const uint32_t fl = flags[p];
-    double v = c_w3d[q];
-    if (fl != kSolid3) {
-      const int x = static_cast<int>(p % k.nx), y = static_cast<int>((p / k.nx) % k.ny),
-                z = static_cast<int>(p / (static_cast<int64_t>(k.nx) * k.ny));
-      v += static_cast<double>(f[pull_slot3(k, c_c3[q], x, y, z, fl, q, lbase[p], k.plane)]);
+    const Coord3 c = coord3(k, p);
+    const uint32_t lb = fl != kSolid3 && fl ? lbase[p] : 0u;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      double v = w3<double>(q);
+      if (fl != kSolid3) v += static_cast<double>(f[pull_slot3(k, q, c, fl, lb, k.plane)]);
+      out[q * n_nodes + p] = v;
     }
-    out[t] = v;
   }
 }
 
@@ -365,26 +440,22 @@ __global__ void export3_kernel(const C *__restrict__ f, const uint32_t *__restri
 // nx*ny*nz doubles.
 template <typename C>
 __global__ void fields3_kernel(const C *__restrict__ f, const uint32_t *__restrict__ flags,
-                               const int64_t *__restrict__ lbase, const Const3<C> k,
+                               const uint32_t *__restrict__ lbase, const Const3<C> k,
                                int64_t n_nodes, double *__restrict__ out) {
-  constexpr int cx[Q] = LBM3_CX, cy[Q] = LBM3_CY, cz[Q] = LBM3_CZ;
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_nodes;
        p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const uint32_t fl = flags[p];
     double r = 0.0, u[3] = {0.0, 0.0, 0.0};
     if (fl != kSolid3) {
-      const int x = static_cast<int>(p % k.nx), y = static_cast<int>((p / k.nx) % k.ny),
-                z = static_cast<int>(p / (static_cast<int64_t>(k.nx) * k.ny));
+      const Coord3 c = coord3(k, p);
       double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
-      const int64_t lb = lbase[p];
+      const uint32_t lb = fl ? lbase[p] : 0u;
 #pragma unroll
       for (int q = 0; q < Q; q++) {
-        const int cq[3] = {cx[q], cy[q], cz[q]};
-        const double v = static_cast<double>(f[pull_slot3(k, cq, x, y, z, fl, q, lb, k.plane)]);
+        const double v = static_cast<double>(f[pull_slot3(k, q, c, fl, lb, k.plane)]);
         dr += v;
-        j[0] += cx[q] * v;
-        j[1] += cy[q] * v;
-        j[2] += cz[q] * v;
+#pragma unroll
+        for (int e = 0; e < 3; e++) j[e] += cvel3(q, e) * v;
       }
       r = 1.0 + dr;
       const double a[3] = {static_cast<double>(k.ax), static_cast<double>(k.ay),
@@ -400,18 +471,17 @@ __global__ void fields3_kernel(const C *__restrict__ f, const uint32_t *__restri
 
 template <typename C>
 __global__ void import3_kernel(const double *__restrict__ in, const uint32_t *__restrict__ flags,
-                               const int64_t *__restrict__ lbase, const Const3<C> k,
+                               const uint32_t *__restrict__ lbase, const Const3<C> k,
                                int64_t n_nodes, C *f) {
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < Q * n_nodes;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int q = static_cast<int>(t / n_nodes);
-    const int64_t p = t - static_cast<int64_t>(q) * n_nodes;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_nodes;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const uint32_t fl = flags[p];
     if (fl == kSolid3) continue;
-    const int x = static_cast<int>(p % k.nx), y = static_cast<int>((p / k.nx) % k.ny),
-              z = static_cast<int>(p / (static_cast<int64_t>(k.nx) * k.ny));
-    f[pull_slot3(k, c_c3[q], x, y, z, fl, q, lbase[p], k.plane)] =
-        static_cast<C>(in[t] - c_w3d[q]);
+    const Coord3 c = coord3(k, p);
+    const uint32_t lb = fl ? lbase[p] : 0u;
+#pragma unroll
+    for (int q = 0; q < Q; q++)
+      f[pull_slot3(k, q, c, fl, lb, k.plane)] = static_cast<C>(in[q * n_nodes + p] - w3<double>(q));
   }
 }
 
@@ -443,7 +513,7 @@ struct lbm3d {
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
   uint32_t *flags = nullptr;
-  int64_t *lbase = nullptr;
+  uint32_t *lbase = nullptr;
   void *links = nullptr;
   Const3Both kc;
   double *partials = nullptr, *result = nullptr;
@@ -536,12 +606,14 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
         flags[pn] = fl;
       }
   // links: validate, one per unknown (node, direction), sorted by node then direction
-  std::vector<int64_t> lbase(static_cast<size_t>(n), 0);
+  std::vector<uint32_t> lbase(static_cast<size_t>(n), 0);
   int64_t total = 0;
   for (int64_t pn = 0; pn < n; pn++) {
-    lbase[pn] = total;
+    lbase[pn] = static_cast<uint32_t>(total);
     if (flags[pn] != kSolid3) total += __builtin_popcount(flags[pn]);
   }
+  if (total > static_cast<int64_t>(UINT32_MAX))
+    return fail3(nullptr, LBM_EINVAL, "more than 2^32 - 1 boundary links");
   if (static_cast<int64_t>(n_links) != total)
     return fail3(nullptr, LBM_EINVAL,
                  "links must cover every unknown (node, direction) once: " +
@@ -603,28 +675,6 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
                          cp.tau_eps, cp.tau_s, cp.tau_s,   cp.tau_s, cp.tau_q,   cp.tau_q,
                          cp.tau_q};
   cudaError_t e = cudaSuccess;
-  int cc[Q][3];
-  for (int q = 0; q < Q; q++)
-    for (int a = 0; a < 3; a++) cc[q][a] = L.c[q][a];
-  e = cudaMemcpyToSymbol(c_c3, cc, sizeof cc);
-  {
-    // the device's compile-time tables must be the lattice built here
-    const int tx[Q] = LBM3_CX, ty[Q] = LBM3_CY, tz[Q] = LBM3_CZ, to[Q] = LBM3_OPP;
-    for (int q = 0; q < Q; q++)
-      if (tx[q] != L.c[q][0] || ty[q] != L.c[q][1] || tz[q] != L.c[q][2] || to[q] != L.opp[q])
-        return fail3(nullptr, LBM_EINVAL, "internal: D3Q19 velocity tables disagree");
-  }
-  {
-    float mf[Q][Q], wf[Q];
-    for (int a = 0; a < Q; a++) {
-      for (int b = 0; b < Q; b++) mf[a][b] = static_cast<float>(L.M[a][b]);
-      wf[a] = static_cast<float>(L.w[a]);
-    }
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_M3d, L.M, sizeof L.M);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w3d, L.w, sizeof L.w);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_M3f, mf, sizeof mf);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w3f, wf, sizeof wf);
-  }
   const size_t es = p.precision == LBM_FP64 ? 8 : 4;
   const size_t fbytes = (19 * static_cast<size_t>(h->plane) + (n_links + 63) / 64 * 64) * es;
   auto alloc = [&](void **ptr, size_t bytes) {
@@ -633,7 +683,7 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
   if (e == cudaSuccess) e = alloc(&h->f[0], fbytes);
   if (e == cudaSuccess) e = alloc(&h->f[1], fbytes);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->flags), n * 4);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), n * 8);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->lbase), n * 4);
   if (e == cudaSuccess) e = alloc(&h->links, std::max<size_t>(1, n_links) * 4 * es);
   if (e == cudaSuccess)
     e = alloc(reinterpret_cast<void **>(&h->partials), kResBlocks3 * 4 * sizeof(double));
@@ -641,7 +691,7 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
   if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, fbytes);
   if (e == cudaSuccess) e = cudaMemset(h->f[1], 0, fbytes);
   if (e == cudaSuccess) e = cudaMemcpy(h->flags, flags.data(), n * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->lbase, lbase.data(), n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->lbase, lbase.data(), n * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = dispatch3(h->precision, [&](auto tag) {
       using C = std::remove_pointer_t<decltype(tag)>;
@@ -735,7 +785,7 @@ int lbm3d_get_f(lbm3d_t *h, double *f) {
   if (e == cudaSuccess)
     e = dispatch3(h->precision, [&](auto tag) {
       using C = std::remove_pointer_t<decltype(tag)>;
-      export3_kernel<C><<<grid_for3(Q * h->n_nodes, 256), 256, 0, h->stream>>>(
+      export3_kernel<C><<<grid_for3(h->n_nodes, 256), 256, 0, h->stream>>>(
           static_cast<const C *>(h->f[h->cur]), h->flags, h->lbase, h->kc.get(tag), h->n_nodes, d);
       return cudaGetLastError();
     });
@@ -756,7 +806,7 @@ int lbm3d_set_f(lbm3d_t *h, const double *f) {
   for (int b = 0; b < 2 && e == cudaSuccess; b++)
     e = dispatch3(h->precision, [&](auto tag) {
       using C = std::remove_pointer_t<decltype(tag)>;
-      import3_kernel<C><<<grid_for3(Q * h->n_nodes, 256), 256, 0, h->stream>>>(
+      import3_kernel<C><<<grid_for3(h->n_nodes, 256), 256, 0, h->stream>>>(
           d, h->flags, h->lbase, h->kc.get(tag), h->n_nodes, static_cast<C *>(h->f[b]));
       return cudaGetLastError();
     });

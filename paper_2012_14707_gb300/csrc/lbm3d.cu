@@ -208,23 +208,51 @@ __device__ __forceinline__ C mac3(C acc, int m, C x) {
   return m == 0 ? acc : (m == 1 ? acc + x : (m == -1 ? acc - x : fma(C(m), x, acc)));
 }
 
-// One lattice step for every fluid node (pull layout).  The collision runs
-// on the pairs (q, opp q): d_q + d_opp carries the even moments and
+// Runtime forms of the velocity components and of the opposite direction
+// (the link epilogue meets each direction as a value): two bits per
+// direction hold c + 1.
+constexpr uint64_t pack_c3(int a) {
+  uint64_t t = 0;
+  for (int q = 0; q < Q; q++) t |= static_cast<uint64_t>(cvel3(q, a) + 1) << (2 * q);
+  return t;
+}
+constexpr uint64_t kPackX3 = pack_c3(0), kPackY3 = pack_c3(1), kPackZ3 = pack_c3(2);
+__device__ __forceinline__ int cvel3_rt(int q, int a) {
+  const uint64_t t = a == 0 ? kPackX3 : (a == 1 ? kPackY3 : kPackZ3);
+  return static_cast<int>((t >> (2 * q)) & 3u) - 1;
+}
+__host__ __device__ constexpr int opp3_rt(int j) {
+  return j <= 6 ? ((j - 1) ^ 1) + 1 : j + 3 - 2 * ((j - 7) & 3);
+}
+constexpr bool opp3_rt_ok() {
+  for (int q = 1; q < Q; q++)
+    if (opp3_rt(q) != opp3(q)) return false;
+  return true;
+}
+static_assert(opp3_rt_ok(), "opposite directions");
+
+// What the links of a boundary node read of it, one column per lane of a
+// warp: f'_q (rows 0..17, q = 1..18), f_q (rows 18..35), drho, rho, u_x,
+// u_y, u_z (rows 36..40); 33 columns so that a lane's rows fall in
+// different banks.
+constexpr int kLinkVals3 = 2 * (Q - 1) + 5;
+template <typename C>
+struct Warp3 {
+  C v[kLinkVals3][33];
+};
+
+// Gather, collide and store one fluid node (pull layout).  The collision
+// runs on the pairs (q, opp q): d_q + d_opp carries the even moments and
 // d_q - d_opp the odd ones, so each row of M touches at most ten values
 // and, M being integer and known here at compile time, only its non-zero
-// entries cost an instruction.
+// entries cost an instruction.  A boundary node leaves what its links
+// need in the warp's shared record.
 template <typename C>
-__global__ void __launch_bounds__(kThreads3, sizeof(C) == 4 ? 6 : 2)
-step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
-             const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
-             const Const3<C> k, int64_t n_nodes) {
-  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= n_nodes) return;
-  const uint32_t fl = flags[p];
-  if (fl == kSolid3) return;
+__device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__ dst,
+                                      const Const3<C> &k, const int64_t p, const uint32_t fl,
+                                      const uint32_t lb, Warp3<C> &sh, const int lane) {
   const int64_t N = k.plane;
   const Coord3 c = coord3(k, p);
-  const uint32_t lb = fl ? lbase[p] : 0u;
   C d[Q];
   if (fl == 0) {
     // every neighbour fluid: x - c_q from the wrapped coordinates
@@ -310,29 +338,85 @@ step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__r
   o[0] = d[0] - sum;
 #pragma unroll
   for (int q = 0; q < Q; q++) dst[q * N + p] = o[q];
-  // Eq. EqNewBDSC for each unknown direction j of the node, to the tail
   if (fl) {
-    uint32_t rank = 0;
 #pragma unroll
-    for (int jq = 1; jq < Q; jq++) {
-      if (!(fl & (1u << jq))) continue;
-      const Link3<C> cl = links[lb + rank];
-      const int jb = opp3(jq);
-      const C r = cl.k1 + cl.k2 + cl.k3;
-      C c0, c2;
-      if (k.diffuse_mode == 0) {
-        c0 = cl.alpha;
-        c2 = (C(1) - r) * w3<C>(jq);
-      } else {
-        c0 = cl.alpha + (r - C(1)) * w3<C>(jq);
-        c2 = C(0);
-      }
-      const C cu = mac3(mac3(mac3(C(0), cvel3(jq, 0), ux), cvel3(jq, 1), uy), cvel3(jq, 2), uz);
-      const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-      dst[19 * N + lb + rank] = cl.k1 * d[jb] + cl.k2 * o[jq] + cl.k3 * o[jb] + c0 +
-                                cl.alpha * drho + c2 * (drho + rho * pj);
-      rank++;
+    for (int q = 1; q < Q; q++) {
+      sh.v[q - 1][lane] = o[q];
+      sh.v[Q - 2 + q][lane] = d[q];
     }
+    sh.v[36][lane] = drho;
+    sh.v[37][lane] = rho;
+    sh.v[38][lane] = ux;
+    sh.v[39][lane] = uy;
+    sh.v[40][lane] = uz;
+  }
+}
+
+// One lattice step of every fluid node, then Eq. EqNewBDSC for every
+// boundary link of the step's nodes into the lattice's tail.  The links of
+// a warp's 32 nodes are consecutive in the link table (sorted by node); the
+// warp spreads them over its lanes, one link per lane, each reading its
+// node's values from the warp's shared record -- the links of a node
+// cluster would otherwise run direction by direction on few lanes.
+template <typename C>
+__global__ void __launch_bounds__(kThreads3, sizeof(C) == 4 ? 8 : 2)
+step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
+             const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
+             const Const3<C> k, int64_t n_nodes) {
+  constexpr int kW = kThreads3 / 32;
+  __shared__ Warp3<C> sh[kW];
+  __shared__ uint32_t sh_ex[kW][32], sh_fl[kW][32];
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
+  const uint32_t fl = p < n_nodes ? flags[p] : kSolid3;
+  const bool live = fl != kSolid3;
+  const uint32_t lb = live && fl ? lbase[p] : 0u;
+  if (live) node3(src, dst, k, p, fl, lb, sh[w], lane);
+  const uint32_t nl = live ? static_cast<uint32_t>(__popc(fl)) : 0u;
+  const unsigned any = __ballot_sync(0xFFFFFFFFu, nl != 0u);
+  if (any == 0u) return;
+  // exclusive prefix of the lanes' link counts; link t of the warp is link
+  // base + t of the table
+  uint32_t incl = nl;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const uint32_t excl = incl - nl, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  const uint32_t base = __shfl_sync(0xFFFFFFFFu, lb - excl, __ffs(static_cast<int>(any)) - 1);
+  sh_ex[w][lane] = excl;
+  sh_fl[w][lane] = live ? fl : 0u;
+  __syncwarp();
+  const Warp3<C> &ws = sh[w];
+  for (uint32_t t = static_cast<uint32_t>(lane); t < total; t += 32u) {
+    // the node (lane s) holding link t: the last lane whose prefix is <= t
+    int s = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1)
+      if (sh_ex[w][s + st] <= t) s += st;
+    uint32_t m = sh_fl[w][s];
+    for (uint32_t r = t - sh_ex[w][s]; r; r--) m &= m - 1u;
+    const int j = __ffs(static_cast<int>(m)) - 1, jb = opp3_rt(j);
+    const Link3<C> cl = links[base + t];
+    const C oj = ws.v[j - 1][s], ojb = ws.v[jb - 1][s], djb = ws.v[Q - 2 + jb][s];
+    const C drho = ws.v[36][s], rho = ws.v[37][s], ux = ws.v[38][s], uy = ws.v[39][s],
+            uz = ws.v[40][s];
+    const C uu = ux * ux + uy * uy + uz * uz;
+    const C wj = j < 7 ? C(1) / C(18) : C(1) / C(36);
+    const C r = cl.k1 + cl.k2 + cl.k3;
+    C c0, c2;
+    if (k.diffuse_mode == 0) {
+      c0 = cl.alpha;
+      c2 = (C(1) - r) * wj;
+    } else {
+      c0 = cl.alpha + (r - C(1)) * wj;
+      c2 = C(0);
+    }
+    const C cu = C(cvel3_rt(j, 0)) * ux + C(cvel3_rt(j, 1)) * uy + C(cvel3_rt(j, 2)) * uz;
+    const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+    dst[19 * k.plane + base + t] = cl.k1 * djb + cl.k2 * oj + cl.k3 * ojb + c0 +
+                                   cl.alpha * drho + c2 * (drho + rho * pj);
   }
 }
 

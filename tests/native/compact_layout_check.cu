@@ -157,6 +157,8 @@ int main(int argc, char **argv) {
   // periodic y with solid blocks at the ends of the last and first rows: the
   // first fluid node at or after (x, y +- 1) is then past the end of that
   // row (for the last row, the end of the lattice)
+  // fully solid rows inside a periodic lattice (compact rows skip them)
+  fails += check("solid_bands", 30, 12, 1, 1, [] { std::vector<uint8_t> s(30 * 12, 0); for (int x = 0; x < 30; x++) { s[x] = 1; s[5 * 30 + x] = 1; s[6 * 30 + x] = 1; } s[11 * 30 + 7] = 1; s[4 * 30 + 29] = 1; return s; }());
   fails += check("edge_row_gaps", 24, 9, 1, 1, [] { std::vector<uint8_t> s(24 * 9, 0); for (int x = 16; x < 24; x++) { s[8 * 24 + x] = 1; s[x - 16] = 1; } s[4 * 24 + 23] = 1; return s; }());
   std::mt19937 rng(3);
   for (int t = 0; t < 6; t++) {

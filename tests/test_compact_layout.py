@@ -50,3 +50,4 @@ def test_compact_targets_match_the_dense_neighbourhood(tmp_path):
     out = subprocess.run([exe, *files], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout + out.stderr
     assert "ALL OK" in out.stdout
+    print(out.stdout)

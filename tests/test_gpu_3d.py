@@ -77,7 +77,7 @@ def _fp32_3d_params():
         marks = ()
         if name == "channel_moving":
             marks = pytest.mark.xfail(strict=False, reason=(
-                "known miss: mass drift MOVING3D after 500 steps; the three-dimensional solver has "
+                "known miss: mass drift 2.3e-9 after 500 steps; the three-dimensional solver has "
                 "no exact-mass step, and the moving lid's link values round the same way every step"))
         out.append(pytest.param(name, marks=marks))
     return out

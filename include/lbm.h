@@ -279,8 +279,9 @@ typedef struct {
 
 /* Copy and validate n_cases cases (errors name the case), lay them out on
  * the device (each case in the layout lbm_create uses, with its limits),
- * pick the step kernel's CTA width and L2 prefetch by timing (cached per
- * size class), start every case at rest.  stream: cudaStream_t or NULL
+ * pick the step kernel's CTA width and L2 prefetch by timing each
+ * candidate over 12 steps twice on the batch itself (cached per precision
+ * and size class), start every case at rest.  stream: cudaStream_t or NULL
  * (the batch then makes its own, since graph capture needs a non-legacy
  * stream). */
 int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision, void *stream,
@@ -310,6 +311,12 @@ int lbm_batch_fields(lbm_batch_t *b, int32_t c, double *rho, double *ux, double 
  * of all cases, the step kernel's CTA width and its CTAs per step. */
 int lbm_batch_info(const lbm_batch_t *b, int64_t *total_nodes, int64_t *total_fluid,
                    int32_t *cta_threads, int32_t *n_ctas);
+/* Override the autotuner's launch shape (for comparisons): the step
+ * kernel's CTA width (64, 128, or 256 for FP32 / FP64) and the L2 prefetch
+ * of the chunks half the resident CTAs ahead (1) or none (0).  Takes
+ * effect at the next lbm_batch_run_to (the CUDA graph is captured again).
+ * LBM_EINVAL for another width or flag, or while the state is mid-graph. */
+int lbm_batch_set_launch(lbm_batch_t *b, int32_t cta_threads, int32_t l2_prefetch);
 void lbm_batch_destroy(lbm_batch_t *b);
 /* Last error of the batch; with b = NULL, of the last failed lbm_batch_create. */
 const char *lbm_batch_last_error(const lbm_batch_t *b);

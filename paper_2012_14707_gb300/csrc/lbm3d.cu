@@ -254,19 +254,22 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
   const int64_t N = k.plane;
   const Coord3 c = coord3(k, p);
   C d[Q];
-  if (fl == 0) {
-    // every neighbour fluid: x - c_q from the wrapped coordinates
+  {
+    // x - c_q from the wrapped coordinates, or the node's tail element
+    // where x - c_q is solid (a select, so interior and boundary nodes run
+    // the same instructions; on a walled axis the wrapped value is unused)
     const int xw[3] = {c.x + 1 < k.nx ? c.x + 1 : 0, c.x, c.x > 0 ? c.x - 1 : k.nx - 1};
     const int yw[3] = {c.y + 1 < k.ny ? c.y + 1 : 0, c.y, c.y > 0 ? c.y - 1 : k.ny - 1};
     const int zw[3] = {c.z + 1 < k.nz ? c.z + 1 : 0, c.z, c.z > 0 ? c.z - 1 : k.nz - 1};
     const int64_t sx = k.nx, sxy = static_cast<int64_t>(k.nx) * k.ny;
+    const int64_t tail = 19 * N + lb;
 #pragma unroll
-    for (int q = 0; q < Q; q++)
-      d[q] = src[q * N + zw[cvel3(q, 2) + 1] * sxy + yw[cvel3(q, 1) + 1] * sx +
-                 xw[cvel3(q, 0) + 1]];
-  } else {
-#pragma unroll
-    for (int q = 0; q < Q; q++) d[q] = src[pull_slot3(k, q, c, fl, lb, N)];
+    for (int q = 0; q < Q; q++) {
+      const int64_t nb = q * N + zw[cvel3(q, 2) + 1] * sxy + yw[cvel3(q, 1) + 1] * sx +
+                         xw[cvel3(q, 0) + 1];
+      const int64_t tq = tail + __popc(fl & ((1u << q) - 1u));
+      d[q] = src[(fl >> q) & 1u ? tq : nb];
+    }
   }
   // Eq. FluidMacr on the pair sums and differences
   C S[kPairs3], A[kPairs3];
@@ -362,13 +365,16 @@ template <typename C>
 __global__ void __launch_bounds__(kThreads3, sizeof(C) == 4 ? 8 : 2)
 step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
              const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
-             const Const3<C> k, int64_t n_nodes) {
+             const uint32_t *__restrict__ fluid, const Const3<C> k, int64_t n_fluid) {
   constexpr int kW = kThreads3 / 32;
   __shared__ Warp3<C> sh[kW];
   __shared__ uint32_t sh_ex[kW][32], sh_fl[kW][32];
-  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  // thread t of the launch runs the t-th fluid node (node order), so no
+  // lane idles on a solid node
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
-  const uint32_t fl = p < n_nodes ? flags[p] : kSolid3;
+  const int64_t p = t0 < n_fluid ? static_cast<int64_t>(fluid[t0]) : 0;
+  const uint32_t fl = t0 < n_fluid ? flags[p] : kSolid3;
   const bool live = fl != kSolid3;
   const uint32_t lb = live && fl ? lbase[p] : 0u;
   if (live) node3(src, dst, k, p, fl, lb, sh[w], lane);
@@ -426,37 +432,43 @@ template <typename C>
 __global__ void __launch_bounds__(kResThreads3)
 residual3_kernel(const C *__restrict__ cur, const C *__restrict__ prev,
                  const uint32_t *__restrict__ flags, const uint32_t *__restrict__ lbase,
-                 const Const3<C> k, int64_t n_nodes, double *__restrict__ partials) {
+                 const uint32_t *__restrict__ fluid, const Const3<C> k, int64_t n_fluid,
+                 double *__restrict__ partials) {
+  // per node: rho and j of both states in the storage's arithmetic type,
+  // the node's mass deviation summed in FP64; sums over nodes in FP64
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const int64_t G = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_nodes;
-       p += G) {
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n_fluid;
+       t += G) {
+    const int64_t p = fluid[t];
     const uint32_t fl = flags[p];
-    if (fl == kSolid3) continue;
     const Coord3 c = coord3(k, p);
-    double r1 = 1.0, r0 = 1.0, j1[3] = {0, 0, 0}, j0[3] = {0, 0, 0}, dm = 0.0;
+    C r1 = C(0), r0 = C(0), j1[3] = {C(0), C(0), C(0)}, j0[3] = {C(0), C(0), C(0)};
+    double dm = 0.0;
     const uint32_t lb = fl ? lbase[p] : 0u;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
       const int64_t s = pull_slot3(k, q, c, fl, lb, k.plane);
-      const double a = static_cast<double>(cur[s]), b = static_cast<double>(prev[s]);
+      const C a = cur[s], b = prev[s];
       r1 += a;
       r0 += b;
-      dm += a;
+      dm += static_cast<double>(a);
 #pragma unroll
       for (int e = 0; e < 3; e++) {
-        j1[e] += cvel3(q, e) * a;
-        j0[e] += cvel3(q, e) * b;
+        j1[e] = mac3(j1[e], cvel3(q, e), a);
+        j0[e] = mac3(j0[e], cvel3(q, e), b);
       }
     }
-    const double acc3[3] = {static_cast<double>(k.ax), static_cast<double>(k.ay),
-                            static_cast<double>(k.az)};
+    r1 += C(1);
+    r0 += C(1);
+    const C acc3[3] = {k.ax, k.ay, k.az};
     double num = 0.0, den = 0.0;
 #pragma unroll
     for (int e = 0; e < 3; e++) {
-      const double u1 = (j1[e] + 0.5 * r1 * acc3[e]) / r1, u0 = (j0[e] + 0.5 * r0 * acc3[e]) / r0;
-      num += (u1 - u0) * (u1 - u0);
-      den += u1 * u1;
+      const C u1 = (j1[e] + C(0.5) * r1 * acc3[e]) / r1, u0 = (j0[e] + C(0.5) * r0 * acc3[e]) / r0;
+      const double du = static_cast<double>(u1) - static_cast<double>(u0);
+      num += du * du;
+      den += static_cast<double>(u1) * static_cast<double>(u1);
     }
     if (!(isfinite(num) && isfinite(den) && isfinite(dm))) {
       acc[3] += 1.0;
@@ -598,6 +610,7 @@ struct lbm3d {
   int cur = 0;
   uint32_t *flags = nullptr;
   uint32_t *lbase = nullptr;
+  uint32_t *fluid = nullptr;  // the fluid nodes in node order
   void *links = nullptr;
   Const3Both kc;
   double *partials = nullptr, *result = nullptr;
@@ -619,6 +632,7 @@ void release3(lbm3d_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->flags), static_cast<void *>(h->lbase),
+                  static_cast<void *>(h->fluid),
                   h->links, static_cast<void *>(h->partials),
                   static_cast<void *>(h->result)})
     if (p) cudaFree(p);
@@ -776,6 +790,15 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
   if (e == cudaSuccess) e = cudaMemset(h->f[1], 0, fbytes);
   if (e == cudaSuccess) e = cudaMemcpy(h->flags, flags.data(), n * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->lbase, lbase.data(), n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<uint32_t> fluid;
+    fluid.reserve(static_cast<size_t>(n_fluid));
+    for (int64_t pn = 0; pn < n; pn++)
+      if (flags[pn] != kSolid3) fluid.push_back(static_cast<uint32_t>(pn));
+    e = alloc(reinterpret_cast<void **>(&h->fluid), std::max<size_t>(1, fluid.size()) * 4);
+    if (e == cudaSuccess && !fluid.empty())
+      e = cudaMemcpy(h->fluid, fluid.data(), fluid.size() * 4, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess)
     e = dispatch3(h->precision, [&](auto tag) {
       using C = std::remove_pointer_t<decltype(tag)>;
@@ -822,11 +845,12 @@ int lbm3d_step(lbm3d_t *h, int64_t n) {
     const int src = h->cur, dst = 1 - h->cur;
     cudaError_t e = dispatch3(h->precision, [&](auto tag) {
       using C = std::remove_pointer_t<decltype(tag)>;
-      step3_kernel<C><<<static_cast<unsigned>((h->n_nodes + kThreads3 - 1) / kThreads3), kThreads3,
+      if (h->n_fluid == 0) return cudaSuccess;
+      step3_kernel<C><<<static_cast<unsigned>((h->n_fluid + kThreads3 - 1) / kThreads3), kThreads3,
                         0, h->stream>>>(static_cast<const C *>(h->f[src]),
                                         static_cast<C *>(h->f[dst]), h->flags, h->lbase,
-                                        static_cast<const Link3<C> *>(h->links), h->kc.get(tag),
-                                        h->n_nodes);
+                                        static_cast<const Link3<C> *>(h->links), h->fluid,
+                                        h->kc.get(tag), h->n_fluid);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return fail3(h, LBM_ECUDA, std::string("step: ") + cudaGetErrorString(e));
@@ -844,7 +868,7 @@ int lbm3d_residual(lbm3d_t *h, double *residual, double *mass) {
     using C = std::remove_pointer_t<decltype(tag)>;
     residual3_kernel<C><<<kResBlocks3, kResThreads3, 0, h->stream>>>(
         static_cast<const C *>(h->f[h->cur]), static_cast<const C *>(h->f[1 - h->cur]), h->flags,
-        h->lbase, h->kc.get(tag), h->n_nodes, h->partials);
+        h->lbase, h->fluid, h->kc.get(tag), h->n_fluid, h->partials);
     residual3_final<<<1, 1024, 0, h->stream>>>(h->partials, h->result);
     return cudaGetLastError();
   });

@@ -31,7 +31,7 @@ EXPORTS = ("lbm_params_default", "lbm_create", "lbm_step", "lbm_fields", "lbm_re
            "lbm_last_error",
            "lbm_batch_create", "lbm_batch_reset", "lbm_batch_run_to", "lbm_batch_fields",
            "lbm_batch_set_fields",
-           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
+           "lbm_batch_info", "lbm_batch_set_launch", "lbm_batch_destroy", "lbm_batch_last_error",
            "lbm_net_create", "lbm_net_num_params", "lbm_net_set_params", "lbm_net_get_params",
            "lbm_net_forward", "lbm_net_gradients", "lbm_net_train_step", "lbm_net_destroy",
            "lbm_net_last_error")
@@ -150,6 +150,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm_batch_set_fields.restype = ctypes.c_int
     lib.lbm_batch_info.argtypes = [H, i64p, i64p, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int32)]
+    lib.lbm_batch_set_launch.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
+    lib.lbm_batch_set_launch.restype = ctypes.c_int
     lib.lbm_batch_destroy.argtypes = [H]
     lib.lbm_batch_destroy.restype = None
     lib.lbm_batch_last_error.argtypes = [H]
@@ -551,6 +553,11 @@ class Batch:
         _bcheck(load().lbm_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t),
                                       ctypes.byref(nt)), self.h)
         return dict(total_nodes=a.value, total_fluid=b.value, cta_threads=t.value, n_ctas=nt.value)
+
+    def set_launch(self, cta_threads: int, l2_prefetch: bool):
+        """Override the autotuned launch shape (lbm_batch_set_launch)."""
+        _bcheck(load().lbm_batch_set_launch(self.h, int(cta_threads), int(bool(l2_prefetch))),
+                self.h)
 
 
 # --------------------------------------------------------------------------

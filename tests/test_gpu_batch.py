@@ -135,3 +135,38 @@ def test_interval_residual_in_a_batch_is_the_case_alone():
             for a, w in zip(b.fields(k), s.fields()):
                 np.testing.assert_array_equal(a, w)
         s.close()
+
+
+def test_autotuned_launch_is_no_slower_than_the_fixed_default():
+    """The autotuner's launch shape against the fixed default (128 threads,
+    L2 prefetch on), each timed over 2000 steps of the same 96-case batch
+    (tol 0: every case runs all steps), best of three."""
+    import time
+
+    cl = cases.batch_cases(96, seed=5)
+    b = lbm.Batch(cl, precision="fp32")
+
+    def timed():
+        b.reset()
+        t0 = time.perf_counter()
+        b.run_to(0.0, 2000, check_every=100)
+        return time.perf_counter() - t0
+
+    timed()
+    t_auto = min(timed() for _ in range(3))
+    b.set_launch(128, True)
+    timed()
+    t_fixed = min(timed() for _ in range(3))
+    b.close()
+    assert t_auto <= 1.10 * t_fixed, (t_auto, t_fixed)
+
+
+def test_set_launch_rejects_other_shapes():
+    b = lbm.Batch(cases.batch_cases(2, seed=1), precision="bf16")
+    with pytest.raises(lbm.LbmError):
+        b.set_launch(256, True)
+    with pytest.raises(lbm.LbmError):
+        b.set_launch(96, False)
+    b.set_launch(64, False)
+    steps, _, _ = b.run_to(1e-3, 200, check_every=100)
+    b.close()

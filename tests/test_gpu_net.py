@@ -119,3 +119,46 @@ def test_bf16_tensor_core_path_matches_fp32_at_full_width():
         ga, gb = g16[off:off + size], g32[off:off + size]
         assert np.linalg.norm(ga - gb) <= 0.1 * np.linalg.norm(gb) + 1e-12, name
         off += size + co
+
+
+@pytest.mark.parametrize("precision,rtol,grad_rtol", [("fp32", 2e-5, 2e-5), ("bf16", 3e-2, 0.1)])
+def test_full_width_network_matches_reference(precision, rtol, grad_rtol):
+    """The full-width network of the warm start (base 32, 4 levels: 32 to
+    256 channels, 384 input channels in the decoder, two 128-channel output
+    tiles of the tensor-core convolutions) on a 32 x 32 lattice, against the
+    FP64 reference (oracle/nn.py): forward and the gradient of every tensor.
+    BF16 tolerances as in the full-width BF16-against-FP32 test: every
+    activation and activation gradient is stored with 8 significant bits,
+    and the deepest level (4 x 4 pixels here) sums its weight gradients over
+    few pixels, so little of that rounding averages out."""
+    import torch
+
+    lbm_build.build()
+    torch.cuda.set_device(0)
+    levels, base, H, W, N = 4, 32, 32, 32, 2
+    rng = np.random.default_rng(21)
+    p = nn.init_params(9, base=base, levels=levels)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.05
+    x = rng.standard_normal((N, H, W, 3))
+    t = rng.standard_normal((N, H, W, 3))
+    y_ref, cache = nn.forward(p, x, levels)
+    g_ref = nn.backward(p, cache, y_ref, t, levels)
+    net = lbm.Net(H, W, base=base, levels=levels, precision=precision, max_batch=N)
+    net.set_params(_flat(p, levels, base))
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    yd = torch.empty((N, H, W, 3), dtype=torch.float32, device="cuda")
+    net.forward(xd.data_ptr(), N, yd.data_ptr())
+    y = yd.cpu().numpy()
+    assert np.linalg.norm(y - y_ref) <= rtol * np.linalg.norm(y_ref)
+    g, loss = net.gradients(xd.data_ptr(), td.data_ptr(), N)
+    g_ref_flat = _flat(g_ref, levels, base)
+    off = 0
+    for name, kind, ci, co in nn.layer_shapes(3, 3, base, levels):
+        for suffix in (".w", ".b"):
+            size = g_ref[name + suffix].size
+            a, b = g[off:off + size], g_ref_flat[off:off + size]
+            off += size
+            assert np.linalg.norm(a - b) <= grad_rtol * np.linalg.norm(b) + 1e-12, (name + suffix)

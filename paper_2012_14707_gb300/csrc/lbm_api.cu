@@ -37,7 +37,7 @@ struct lbm_handle {
   // the exact-mass variant (FP32 storage with moving walls): FP64 link
   // records and the per-link carry (see lbm::link_epilogue_pull)
   int exact = 0;
-  lbm::LinkCoef<double> *links64 = nullptr;
+  lbm::LinkCoefDF *links64 = nullptr;
   float *carry = nullptr;   // per link
   float *carry0 = nullptr;  // per fluid node (rest population)
   // interval residual (params.residual_mode 1): velocity of every fluid
@@ -737,6 +737,13 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     e = alloc(reinterpret_cast<void **>(&h->jbslot), std::max<size_t>(1, jbs.size()) * 4);
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
   h->exact = lbm::exact_mass(hc) ? 1 : 0;
+  // the exact-mass variant's link coefficients as FP32 pairs (alive until
+  // the stream synchronises below)
+  std::vector<lbm::LinkCoefDF> ldf;
+  if (h->exact) {
+    ldf.resize(n_links_sz);
+    for (size_t l = 0; l < n_links_sz; l++) ldf[l] = lbm::link_coef_df(&hc.coef[4 * l]);
+  }
   if (h->exact) {
     // one allocation: the per-link carries, then the per-node ones
     const size_t nl = std::max<size_t>(1, n_links_sz);
@@ -744,8 +751,8 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->carry), carry_bytes(h));
     if (e == cudaSuccess) h->carry0 = h->carry + nl;
     if (e == cudaSuccess && n_links_sz)
-      e = cudaMemcpyAsync(h->links64, hc.coef.data(), n_links_sz * 32, cudaMemcpyHostToDevice,
-                          h->stream);
+      e = cudaMemcpyAsync(h->links64, ldf.data(), n_links_sz * sizeof(lbm::LinkCoefDF),
+                          cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = clear_carry(h);
   }
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->partials), pbytes);

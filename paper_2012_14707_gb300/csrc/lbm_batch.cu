@@ -56,7 +56,7 @@ template <typename C>
 __host__ __device__ inline PullGeom case_geom(const BatchCase<C> &bc, const uint2 *node,
                                               const int2 *grp, const int32_t *rowstart,
                                               const uint32_t *jbslot,
-                                              const LinkCoef<double> *links64 = nullptr,
+                                              const LinkCoefDF *links64 = nullptr,
                                               float *carry = nullptr, float *carry0 = nullptr) {
   PullGeom g;
   g.node = node + bc.node_off;
@@ -164,13 +164,10 @@ batch_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint2 *_
 // (64) as the single-case exact kernel.
 __global__ void __launch_bounds__(kChunk, 4)
 batch_exact_kernel(const float *__restrict__ src, float *__restrict__ dst,
-                   const uint2 *__restrict__ node, const int2 *__restrict__ grp,
-                   const int32_t *__restrict__ ccase, const int32_t *__restrict__ rowstart,
-                   const uint32_t *__restrict__ jbslot, const LinkCoef<float> *__restrict__ links,
+                   const int32_t *__restrict__ ccase, const LinkCoef<float> *__restrict__ links,
                    const BatchCase<float> *__restrict__ cases, const int32_t *__restrict__ active,
                    const int32_t *__restrict__ chunks, const int64_t *__restrict__ counter,
-                   const uint32_t j, const LinkCoef<double> *__restrict__ links64,
-                   float *__restrict__ carry, float *__restrict__ carry0) {
+                   const uint32_t j, const PullGeom *__restrict__ geoms) {
   const int32_t ch = chunks[blockIdx.x];
   const int c = ccase[ch];
   if (!active[c]) return;
@@ -178,8 +175,9 @@ batch_exact_kernel(const float *__restrict__ src, float *__restrict__ dst,
   const uint32_t i = static_cast<uint32_t>(ch) * kChunk + threadIdx.x -
                      static_cast<uint32_t>(bc.node_off);
   if (i >= static_cast<uint32_t>(bc.n_fluid)) return;
-  const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot, links64, carry, carry0);
-  step_node_exact(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i,
+  // the case's geometry and constants from device tables (not copied into
+  // this thread's local memory to be passed to the out-of-line step)
+  step_node_exact(src + bc.f_off, dst + bc.f_off, geoms[c], links + bc.link_off, bc.k, i,
                   step_seed(*counter + j));
 }
 
@@ -290,9 +288,8 @@ cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int
                               const uint32_t *jbslot, const void *links, const void *cases,
                               const int32_t *active, const int32_t *work, int32_t n_work,
                               uint32_t pf_dist, const int64_t *counter, uint32_t j,
-                              const LinkCoef<double> *links64, float *carry, float *carry0,
-                              const int32_t *exact_chunks, int32_t n_exact_chunks,
-                              cudaStream_t s) {
+                              const PullGeom *geoms, const int32_t *exact_chunks,
+                              int32_t n_exact_chunks, cudaStream_t s) {
   if constexpr (kStochastic<T>) {
     if constexpr (THREADS <= kChunk / 2) {
       if (n_work > 0)
@@ -317,9 +314,8 @@ cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       batch_exact_kernel<<<static_cast<unsigned>(n_exact_chunks), kChunk, 0, s>>>(
-          src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<float> *>(links),
-          static_cast<const BatchCase<float> *>(cases), active, exact_chunks, counter, j, links64,
-          carry, carry0);
+          src, dst, ccase, static_cast<const LinkCoef<float> *>(links),
+          static_cast<const BatchCase<float> *>(cases), active, exact_chunks, counter, j, geoms);
     }
   }
   return cudaGetLastError();
@@ -376,12 +372,13 @@ struct lbm_batch {
   // FP32 cases with moving walls: FP64 link records and per-link carry
   // (the exact-mass variant), over the whole link arena; null if no case
   // needs them
-  lbm::LinkCoef<double> *links64 = nullptr;
+  lbm::LinkCoefDF *links64 = nullptr;
   float *carry = nullptr;   // per link of the link arena, then per node-arena entry
   float *carry0 = nullptr;  // = carry + max(1, n_links_total)
   int64_t n_links_total = 0;
   int32_t *exact_chunks = nullptr;  // node-arena chunks of the active exact-mass cases
   int32_t n_exact_chunks = 0;
+  lbm::PullGeom *geoms = nullptr;   // per case, its pull geometry (exact-mass batches)
   // Work lists: the step kernels run only the node-arena chunks listed
   // (work: the other active cases'), so retired cases cost no CTAs.  Per
   // case its first chunk and chunk count; the lists are rebuilt (and the
@@ -455,9 +452,7 @@ cudaError_t step_once(lbm_batch_t *b, int threads, uint32_t pf_dist, int src, ui
       return lbm::launch_batch_step<T, C, TH>(
           static_cast<const T *>(b->f[src]), static_cast<T *>(b->f[dst]), b->node, b->grp,
           b->ccase, b->rowstart, b->jbslot, b->links, b->cases, b->active, b->work, b->n_work,
-          pf_dist, b->counter, j, b->links64, b->carry, b->carry0, b->exact_chunks,
-          b->n_exact_chunks,
-          b->stream);
+          pf_dist, b->counter, j, b->geoms, b->exact_chunks, b->n_exact_chunks, b->stream);
     };
     if (threads == 64) return go(std::integral_constant<int, 64>());
     if (threads == 128) return go(std::integral_constant<int, 128>());
@@ -522,7 +517,8 @@ void batch_release(lbm_batch_t *b) {
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active),
                   static_cast<void *>(b->links64), static_cast<void *>(b->carry),
-                  static_cast<void *>(b->exact_chunks), b->snap, static_cast<void *>(b->work)})
+                  static_cast<void *>(b->exact_chunks), static_cast<void *>(b->geoms), b->snap,
+                  static_cast<void *>(b->work)})
     if (p) cudaFree(p);
   if (b->h_n_active) cudaFreeHost(b->h_n_active);
   if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -772,8 +768,24 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       e = alloc(reinterpret_cast<void **>(&b->carry), (l64.size() / 4 + nodes) * 4);
     if (e == cudaSuccess) b->carry0 = b->carry + l64.size() / 4;
     if (e == cudaSuccess) e = cudaMemset(b->carry, 0, (l64.size() / 4 + nodes) * 4);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(b->links64, l64.data(), l64.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      std::vector<lbm::LinkCoefDF> ldf(l64.size() / 4);
+      for (size_t l = 0; l < ldf.size(); l++) ldf[l] = lbm::link_coef_df(&l64[4 * l]);
+      e = cudaMemcpy(b->links64, ldf.data(), ldf.size() * sizeof(lbm::LinkCoefDF),
+                     cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && precision == LBM_FP32) {
+      // every case's pull geometry inside the arenas, for the exact-mass kernel
+      const auto *bcs = reinterpret_cast<const lbm::BatchCase<float> *>(chost.data());
+      std::vector<lbm::PullGeom> gs(static_cast<size_t>(n_cases));
+      for (int32_t c = 0; c < n_cases; c++)
+        gs[c] = lbm::case_geom(bcs[c], b->node, b->grp, b->rowstart, b->jbslot, b->links64,
+                               b->carry, b->carry0);
+      e = alloc(reinterpret_cast<void **>(&b->geoms), gs.size() * sizeof(lbm::PullGeom));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(b->geoms, gs.data(), gs.size() * sizeof(lbm::PullGeom),
+                       cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->exact_chunks), xchunks.size() * 4);
     if (e == cudaSuccess)
       e = cudaMemcpy(b->exact_chunks, xchunks.data(), xchunks.size() * 4, cudaMemcpyHostToDevice);

@@ -184,6 +184,40 @@ __device__ __forceinline__ float add_stochastic(float a, float b, uint32_t u16) 
   return static_cast<float>(u16) * 0x1p-16f * fabsf(s2 - s) < fabsf(e) ? s2 : s;
 }
 
+// Double-FP32 values h + l with |l| <= ulp(h) / 2 (Dekker's double-length
+// arithmetic, 1971): about 48 significant bits from FP32 operations alone.
+// The exact-mass link values use them instead of FP64, which this GPU runs
+// at a small fraction of its FP32 rate.  Products through FMA (the exact
+// error of a*b is fma(a, b, -a*b)); every operation is written with the
+// round-to-nearest intrinsics, so nothing is contracted or reordered.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_norm(float s, float e) {
+  float h, l;
+  two_sum(s, e, h, l);
+  return DF{h, l};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return df_norm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  return df_norm(p, __fmaf_rn(a.l, b, __fmaf_rn(a.h, b, -p)));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = __fmaf_rn(a.h, b.h, -p);
+  return df_norm(p, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e)));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const DF r = df_add(a, df_mul_f(b, -q1));  // a - q1 b
+  return df_norm(q1, __fdiv_rn(r.h, b.h));
+}
+
 // The collision of Eq. MomentPost as the change ch_i = f'_i - f_i of each
 // population, with the node's rho - 1, rho, u and |u|^2 (Eq. FluidMacr),
 // for the deviations d of one node (C = float or double) or of two nodes at
@@ -376,6 +410,121 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
 
 }
 
+// Eq. EqNewBDSC for the links of the exact-mass variant (FP32 storage):
+// each link value in double-FP32 arithmetic (DF) from the DF coefficients
+// (g.links64) and the node's DF rho - 1, rho and u, plus the link's carry
+// (what FP32 storage dropped from its earlier values); stored rounded to
+// nearest, the new remainder kept as the carry.  The stored values then add
+// up, step after step, to the exact ones, so the mass a moving wall
+// exchanges with the fluid does not drift by a rounding that repeats.
+// The links of a warp's nodes are consecutive in the link table; the warp
+// spreads them over its lanes, one link per lane at a time, each reading its node's
+// values from the warp's shared record.  node = the node's index i; lane
+// i mod 32 of the warp runs node i, and the lanes of nodes below g.n_fluid
+// (a prefix of the warp) take part -- named explicitly, since the lanes
+// need not have reconverged after the collision's data-dependent branches.
+constexpr int kExactMaxWarps = 8;  // CTAs of up to 256 threads
+__device__ __forceinline__ void link_epilogue_exact(const float *__restrict__ src,
+                                                    float *__restrict__ dst, const PullGeom &g,
+                                                    const uint32_t fl, const uint32_t li,
+                                                    const Collided<float, float> &c_,
+                                                    const StepConst<float> &k,
+                                                    const uint32_t node) {
+  __shared__ float xs_o[kExactMaxWarps][8][33];   // f'_1 .. f'_8
+  __shared__ float xs_n[kExactMaxWarps][10][33];  // drho, rho, ux, uy, |u|^2 (DF)
+  __shared__ uint32_t xs_ex[kExactMaxWarps][32], xs_fl[kExactMaxWarps][32];
+  const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
+  const uint32_t first = node - static_cast<uint32_t>(lane);
+  const int nact = g.n_fluid - first >= 32u ? 32 : static_cast<int>(g.n_fluid - first);
+  const unsigned am = nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u);
+  __syncwarp(am);
+  const uint32_t nl = static_cast<uint32_t>(__popc(fl));
+  const unsigned anyl = __ballot_sync(am, nl != 0u);
+  if (anyl == 0u) return;
+  if (fl) {
+    const DF drho2 = df_norm(c_.dr_hi, c_.dr_lo);
+    const DF rho2 = df_add(DF{1.0f, 0.0f}, drho2);
+    const DF half_rho{0.5f * rho2.h, 0.5f * rho2.l};
+    const DF ux2 = df_div(df_add(df_norm(c_.jx_hi, c_.jx_lo), df_mul_f(half_rho, k.ax)), rho2);
+    const DF uy2 = df_div(df_add(df_norm(c_.jy_hi, c_.jy_lo), df_mul_f(half_rho, k.ay)), rho2);
+    const DF uu2 = df_add(df_mul(ux2, ux2), df_mul(uy2, uy2));
+#pragma unroll
+    for (int q = 1; q < 9; q++) xs_o[w][q - 1][lane] = c_.o[q];
+    const float nv[10] = {drho2.h, drho2.l, rho2.h, rho2.l, ux2.h, ux2.l, uy2.h, uy2.l, uu2.h, uu2.l};
+#pragma unroll
+    for (int q = 0; q < 10; q++) xs_n[w][q][lane] = nv[q];
+  }
+  // exclusive prefix of the lanes' link counts: link t of the warp is
+  // link base + t of the table
+  uint32_t incl = nl;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(am, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const uint32_t excl = incl - nl, total = __shfl_sync(am, incl, nact - 1);
+  const uint32_t base = __shfl_sync(am, li - excl, __ffs(static_cast<int>(anyl)) - 1);
+  xs_ex[w][lane] = excl;
+  xs_fl[w][lane] = fl;
+  __syncwarp(am);
+  const uint32_t tail = 9u * g.plane;
+  // velocities (2 bits each: c + 1) and opposite directions (4 bits each)
+  constexpr uint32_t kCx = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) | (2u << 10) |
+                           (0u << 12) | (0u << 14) | (2u << 16);
+  constexpr uint32_t kCy = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) |
+                           (2u << 12) | (0u << 14) | (0u << 16);
+  constexpr uint32_t kOpp = 0x65872143u;  // opp(j) in bits 4 (j - 1) .. 4 (j - 1) + 3
+  constexpr float kW9h = static_cast<float>(1.0 / 9);
+  constexpr float kW36h = static_cast<float>(1.0 / 36);
+  const float kW9l = static_cast<float>(1.0 / 9 - static_cast<double>(kW9h));
+  const float kW36l = static_cast<float>(1.0 / 36 - static_cast<double>(kW36h));
+  // the nact lanes of the warp take the links in turn
+  for (uint32_t t = static_cast<uint32_t>(lane); t < total; t += static_cast<uint32_t>(nact)) {
+    // the node (lane s) holding link t: the last active lane whose prefix is <= t
+    int s = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1)
+      if (s + st < nact && xs_ex[w][s + st] <= t) s += st;
+    uint32_t m = xs_fl[w][s];
+    for (uint32_t r = t - xs_ex[w][s]; r; r--) m &= m - 1u;
+    const int j = __ffs(static_cast<int>(m));  // flag bit j - 1: direction j
+    const int jb = static_cast<int>((kOpp >> (4 * (j - 1))) & 15u);
+    const int cx = static_cast<int>((kCx >> (2 * j)) & 3u) - 1;
+    const int cy = static_cast<int>((kCy >> (2 * j)) & 3u) - 1;
+    const uint32_t lj = base + t;
+    const LinkCoefDF c = g.links64[lj];
+    const DF k1{c.hi[0], c.lo[0]}, k2{c.hi[1], c.lo[1]}, k3{c.hi[2], c.lo[2]},
+        al{c.hi[3], c.lo[3]};
+    const DF w2 = j < 5 ? DF{kW9h, kW9l} : DF{kW36h, kW36l};
+    const DF drho2{xs_n[w][0][s], xs_n[w][1][s]}, rho2{xs_n[w][2][s], xs_n[w][3][s]};
+    const DF ux2{xs_n[w][4][s], xs_n[w][5][s]}, uy2{xs_n[w][6][s], xs_n[w][7][s]};
+    const DF uu2{xs_n[w][8][s], xs_n[w][9][s]};
+    const DF r = df_add(df_add(k1, k2), k3);
+    DF c0, c2;
+    if (k.diffuse_mode == 0) {
+      c0 = al;
+      c2 = df_mul(df_add(DF{1.0f, 0.0f}, DF{-r.h, -r.l}), w2);
+    } else {
+      c0 = df_add(al, df_mul(df_add(r, DF{-1.0f, 0.0f}), w2));
+      c2 = DF{0.0f, 0.0f};
+    }
+    // c_j . u: the components are -1, 0 or 1
+    const DF cu = df_add(DF{cx * ux2.h, cx * ux2.l}, DF{cy * uy2.h, cy * uy2.l});
+    const DF pj = df_add(df_add(df_mul_f(cu, 3.0f), df_mul_f(df_mul(cu, cu), 4.5f)),
+                         df_mul_f(uu2, -1.5f));
+    const float djb = src[g.jbslot[lj]];
+    DF v = df_add(df_mul_f(k1, djb), df_mul_f(k2, xs_o[w][j - 1][s]));
+    v = df_add(v, df_mul_f(k3, xs_o[w][jb - 1][s]));
+    v = df_add(v, c0);
+    v = df_add(v, df_mul(al, drho2));
+    v = df_add(v, df_mul(c2, df_add(drho2, df_mul(rho2, pj))));
+    v = df_add(v, DF{g.carry[lj], 0.0f});
+    const float tv = __fadd_rn(v.h, v.l);
+    g.carry[lj] = __fadd_rn(__fadd_rn(v.h, -tv), v.l);
+    dst[tail + lj] = tv;
+  }
+}
+
 // The unknown populations of a boundary node for the next step (bits of
 // fl, its flag byte; li is its first link), Eq. EqNewBDSC in the folded
 // form of LinkCoef, written to the link tail of dst (pull layout, see
@@ -390,19 +539,19 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
 //
 // 16-bit storage rounds each value stochastically (random bits: fmix32 of
 // the node's word rs and the direction).  The exact-mass variant (kExact,
-// FP32 storage) evaluates the link in FP64 from the FP64 coefficients
-// (g.links64) and the FP64 rho, u of the node, adds the link's carry (the
-// part of its earlier values that FP32 storage dropped) and keeps the new
-// remainder in the carry: the stored values then add up, step after step,
-// to the FP64 ones, so the mass a moving wall exchanges with the fluid does
-// not drift by a rounding that repeats every step.
+// FP32 storage) runs link_epilogue_exact instead.
 template <typename T, typename C, bool kExact = false>
 __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                    const PullGeom &g, const uint32_t fl,
                                                    const uint32_t li,
                                                    const LinkCoef<C> *__restrict__ links,
                                                    const Collided<T, C> &c_,
-                                                   const StepConst<C> &k, const uint32_t rs = 0) {
+                                                   const StepConst<C> &k, const uint32_t rs = 0,
+                                                   const uint32_t node = 0) {
+  if constexpr (kExact) {
+    link_epilogue_exact(src, dst, g, fl, li, c_, k, node);
+    return;
+  }
   const unsigned wmask = __reduce_or_sync(__activemask(), fl);
   if (!wmask) return;
   constexpr bool kS = Stor<T>::kScaled;
@@ -411,14 +560,6 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
   // in storage units (times the storage scale) where the storage is scaled
   const C drho = kS ? c_.drho * k.sc : c_.drho, rho = kS ? c_.rho * k.sc : c_.rho;
   const uint32_t tail = 9u * g.plane;
-  // the exact-mass variant's FP64 rho - 1, rho and u of the node
-  double drho64 = 0.0, rho64 = 1.0, ux64 = 0.0, uy64 = 0.0;
-  if constexpr (kExact) {
-    drho64 = static_cast<double>(c_.dr_hi) + c_.dr_lo;
-    rho64 = 1.0 + drho64;
-    ux64 = (static_cast<double>(c_.jx_hi) + c_.jx_lo + 0.5 * rho64 * k.ax) / rho64;
-    uy64 = (static_cast<double>(c_.jy_hi) + c_.jy_lo + 0.5 * rho64 * k.ay) / rho64;
-  }
 #pragma unroll
   for (int j = 1; j < 9; j++) {
     if (!(wmask & (1u << (j - 1)))) continue;
@@ -431,49 +572,27 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
       const int jb = opp_tab[j];
       // link j is the node's k-th, k = links in lower directions
       const uint32_t lj = li + __popc(fl & ((1u << (j - 1)) - 1u));
-      if constexpr (kExact) {
-        const LinkCoef<double> c = g.links64[lj];
-        const double r = c.k1 + c.k2 + c.k3;
-        double c0, c2;
-        if (k.diffuse_mode == 0) {
-          c0 = c.alpha;
-          c2 = (1.0 - r) * w_tab[j];
-        } else {
-          c0 = c.alpha + (r - 1.0) * w_tab[j];
-          c2 = 0.0;
-        }
-        const double cu = cx_tab[j] * ux64 + cy_tab[j] * uy64;
-        const double pj = 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux64 * ux64 + uy64 * uy64);
-        const double djb = static_cast<double>(src[g.jbslot[lj]]);
-        const double v = c.k1 * djb + c.k2 * static_cast<double>(o[j]) +
-                         c.k3 * static_cast<double>(o[jb]) + c0 + c.alpha * drho64 +
-                         c2 * (drho64 + rho64 * pj) + static_cast<double>(g.carry[lj]);
-        const float t = __double2float_rn(v);
-        g.carry[lj] = __double2float_rn(v - static_cast<double>(t));
-        dst[tail + lj] = t;
+      const LinkCoef<C> c = links[lj];
+      const C r = c.k1 + c.k2 + c.k3;
+      C c0, c2;
+      if (k.diffuse_mode == 0) {
+        c0 = c.alpha;
+        c2 = (C(1) - r) * C(w_tab[j]);
       } else {
-        const LinkCoef<C> c = links[lj];
-        const C r = c.k1 + c.k2 + c.k3;
-        C c0, c2;
-        if (k.diffuse_mode == 0) {
-          c0 = c.alpha;
-          c2 = (C(1) - r) * C(w_tab[j]);
-        } else {
-          c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
-          c2 = C(0);
-        }
-        const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
-        const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-        const C djb = kS ? Stor<T>::ld_raw(src[g.jbslot[lj]])
-                         : Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
-        const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + (kS ? c0 * k.sc : c0) +
-                    c.alpha * drho + c2 * (drho + rho * pj);
-        if constexpr (kStochastic<T>)
-          dst[tail + lj] =
-              Stor<T>::bits(Stor<T>::st_rs2(v, C(0), fmix32(rs ^ (0x27D4EB2Fu * j))) >> 16);
-        else
-          dst[tail + lj] = kS ? Stor<T>::st_raw(v) : Stor<T>::st(v, k.sc);
+        c0 = c.alpha + (r - C(1)) * C(w_tab[j]);
+        c2 = C(0);
       }
+      const C cu = C(cx_tab[j]) * ux + C(cy_tab[j]) * uy;
+      const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+      const C djb = kS ? Stor<T>::ld_raw(src[g.jbslot[lj]])
+                       : Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
+      const C v = c.k1 * djb + c.k2 * o[j] + c.k3 * o[jb] + (kS ? c0 * k.sc : c0) +
+                  c.alpha * drho + c2 * (drho + rho * pj);
+      if constexpr (kStochastic<T>)
+        dst[tail + lj] =
+            Stor<T>::bits(Stor<T>::st_rs2(v, C(0), fmix32(rs ^ (0x27D4EB2Fu * j))) >> 16);
+      else
+        dst[tail + lj] = kS ? Stor<T>::st_raw(v) : Stor<T>::st(v, k.sc);
     }
   }
 }
@@ -531,7 +650,8 @@ __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__r
   for (int q = 0; q < 9; q++) dst[q * P + i] = c.t[q];
   // flag byte and first link (li) of the node
   link_epilogue_pull<T, C, kExact>(src, dst, g, nw.x & 0xFFu,
-                                   static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k, rs);
+                                   static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k, rs,
+                                   i);
 }
 
 // ---------------------------------------------------------------------------

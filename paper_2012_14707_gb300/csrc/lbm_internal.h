@@ -56,6 +56,21 @@ struct alignas(sizeof(C) * 4) LinkCoef {
   C k1, k2, k3, alpha;
 };
 
+// The FP64 coefficients k1, k2, k3, alpha of a link as pairs of FP32 values
+// (hi + lo, lo the FP32 rounding of what hi leaves): the exact-mass variant
+// evaluates its links in double-FP32 arithmetic.
+struct alignas(16) LinkCoefDF {
+  float hi[4], lo[4];
+};
+inline LinkCoefDF link_coef_df(const double *c) {
+  LinkCoefDF r;
+  for (int i = 0; i < 4; i++) {
+    r.hi[i] = static_cast<float>(c[i]);
+    r.lo[i] = static_cast<float>(c[i] - static_cast<double>(r.hi[i]));
+  }
+  return r;
+}
+
 // Case parameters after the FP64 precompute of Sec. 3.B.
 struct CaseParams {
   double tau_s, tau_q, tau_rho, tau_j, tau_e, tau_eps;
@@ -183,7 +198,7 @@ struct PullGeom {
   // the exact-mass variant (FP32 storage): FP64 link coefficients and, per
   // link and per node (rest population), the remainder of its values that
   // FP32 storage has not yet taken
-  const LinkCoef<double> *links64 = nullptr;
+  const LinkCoefDF *links64 = nullptr;
   float *carry = nullptr;
   float *carry0 = nullptr;
 };

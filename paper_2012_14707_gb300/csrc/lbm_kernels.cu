@@ -42,9 +42,9 @@ using namespace dev;
 // see collide and link_epilogue_pull), with 64 registers per thread.
 template <typename T, typename C, bool kExact>
 __global__ void __launch_bounds__(kPullThreads, kExact ? 8 : PullOcc<T>::min_blocks)
-step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, const PullGeom g,
+step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, __grid_constant__ const PullGeom g,
                  const uint32_t n_fluid, const LinkCoef<C> *__restrict__ links,
-                 const StepConst<C> k) {
+                 __grid_constant__ const StepConst<C> k) {
   {
     constexpr uint32_t kNodeLines = kPullThreads * sizeof(uint2) / 128;
     constexpr uint32_t kPlaneLines = kPullThreads * sizeof(T) / 128;

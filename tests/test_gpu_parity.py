@@ -141,21 +141,24 @@ def _fp32_mass_params():
         marks = ()
         if name == "annulus":
             marks = pytest.mark.xfail(strict=False, reason=(
-                "known miss: 1.9e-10 after 2000 steps with the exact-mass step (8.9e-9 without); "
-                "the rotating curved wall exchanges mass at a rate set by the near-wall velocity, "
-                "and FP32 relaxation rates and coefficients shift that rate by ~1e-7"))
+                "known miss: with the exact-mass step the drift stays bounded but reaches "
+                "2.9e-10 after 500 steps (at most 4.0e-10 over 4000 steps; 8.9e-9 after 2000 "
+                "steps without it); the rotating curved wall exchanges mass at a rate set by the "
+                "near-wall velocity, and FP32 relaxation rates and coefficients shift that rate "
+                "by ~1e-7"))
         out.append(pytest.param(name, marks=marks))
     return out
 
 
 @pytest.mark.parametrize("name", _fp32_mass_params())
 def test_fp32_velocity_and_mass_match_oracle(name):
-    """From rest, 2000 steps, FP32 against the FP64 oracle: velocity rel. L2
-    <= 1e-5 and mass drift |M_gpu - M_oracle| / M_oracle(0) <= 1e-10, the
-    FP32 targets, on every case.  Moving walls switch the exact-mass step on
-    by themselves (FP64 link values and rest-population closure, each with a
-    carry of what FP32 storage dropped); the uniform periodic lattices ask
-    for it (mass_mode = 1); the others run the plain step."""
+    """From rest, FP32 against the FP64 oracle after 500 and after 2000
+    steps: velocity rel. L2 <= 1e-5 and mass drift |M_gpu - M_oracle| /
+    M_oracle(0) <= 1e-10, the FP32 targets, on every case.  Moving walls
+    switch the exact-mass step on by themselves (link values in double-FP32
+    arithmetic and the rest population's closure, each with a carry of what
+    FP32 storage dropped); the uniform periodic lattices ask for it
+    (mass_mode = 1); the others run the plain step."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
     if name in UNIFORM:
@@ -167,7 +170,9 @@ def test_fp32_velocity_and_mass_match_oracle(name):
         o.step(n)
         g.step(n)
         assert _vel_rel_l2(c, g.fields(), o.fields()) <= 1e-5
-    assert abs(g.residual()[1] - o.residual()[1]) / m0 <= 1e-10
+        drift = abs(g.residual()[1] - o.residual()[1]) / m0
+        print(f"{name} after {o.steps} steps: FP32 mass drift {drift:.2e}")
+        assert drift <= 1e-10
 
 
 @pytest.mark.parametrize("name", ["annulus", "channel_moving"])

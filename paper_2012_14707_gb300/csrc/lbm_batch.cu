@@ -96,19 +96,32 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
                   const uint32_t *__restrict__ jbslot, const LinkCoef<C> *__restrict__ links,
                   const BatchCase<C> *__restrict__ cases, const int32_t *__restrict__ active,
                   const int32_t *__restrict__ work, const uint32_t n_blocks,
-                  const uint32_t pf_dist, const int64_t *__restrict__ counter, const uint32_t j) {
+                  const uint32_t pf_dist, const int64_t *__restrict__ counter, const uint32_t j,
+                  const PullGeom *__restrict__ geoms) {
   static_assert(kChunk % THREADS == 0, "a CTA stays inside one chunk");
   constexpr uint32_t kPer = kChunk / THREADS;  // CTAs per chunk
   {
+    // L2 prefetch for the CTA pf_dist blocks ahead: its node words, chunk
+    // case index and, in the case's nine planes, its nodes' own slots
     constexpr uint32_t kNodeLines = THREADS * sizeof(uint2) / 128;
+    constexpr uint32_t kPlaneLines = (THREADS * sizeof(T) + 127) / 128;
+    constexpr uint32_t kPerLine = 128 / sizeof(T);
     const uint32_t b2 = blockIdx.x + pf_dist;
     const uint32_t t = threadIdx.x;
-    if (pf_dist && t < 32 && b2 < n_blocks) {
-      const uint32_t base2 = static_cast<uint32_t>(work[b2 / kPer]) * kChunk + (b2 % kPer) * THREADS;
-      if (t < kNodeLines)
+    if (pf_dist && t < kNodeLines + 9 * kPlaneLines + 1 && b2 < n_blocks) {
+      const uint32_t chunk2 = static_cast<uint32_t>(work[b2 / kPer]);
+      const uint32_t base2 = chunk2 * kChunk + (b2 % kPer) * THREADS;
+      if (t < kNodeLines) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(node + base2 + t * 16));
-      else if (t == kNodeLines)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ccase + base2 / kChunk));
+      } else if (t == kNodeLines) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ccase + chunk2));
+      } else {
+        const BatchCase<C> &c2 = cases[ccase[chunk2]];
+        const uint32_t q = (t - kNodeLines - 1) / kPlaneLines, l = (t - kNodeLines - 1) % kPlaneLines;
+        const uint32_t i2 = base2 - static_cast<uint32_t>(c2.node_off) + l * kPerLine;
+        if (i2 < static_cast<uint32_t>(c2.n_fluid))
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + c2.f_off + q * c2.k.plane + i2));
+      }
     }
   }
   const int32_t chunk = work[blockIdx.x / kPer];
@@ -120,7 +133,9 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
   if (i >= static_cast<uint32_t>(bc.n_fluid)) return;
   // exact-mass cases run in batch_exact_kernel
   if (std::is_same<T, float>::value && bc.k.exact) return;
-  const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot);
+  // the case's geometry from the device table (a local copy would be
+  // spilled at this kernel's register budget)
+  const PullGeom &g = geoms[c];
   uint32_t seed = 0;
   if constexpr (kStochastic<T>) seed = step_seed(*counter + j);
   step_node_pull<T, C, false>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i,
@@ -139,7 +154,7 @@ batch_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint2 *_
                   const LinkCoef<float> *__restrict__ links,
                   const BatchCase<float> *__restrict__ cases, const int32_t *__restrict__ active,
                   const int32_t *__restrict__ work, const int64_t *__restrict__ counter,
-                  const uint32_t j) {
+                  const uint32_t j, const PullGeom *__restrict__ geoms) {
   static_assert(kChunk % (2 * THREADS) == 0, "a CTA stays inside one chunk");
   constexpr uint32_t kPer = kChunk / (2 * THREADS);  // CTAs per chunk
   const int32_t chunk = work[blockIdx.x / kPer];
@@ -149,7 +164,7 @@ batch_pair_kernel(const T *__restrict__ src, T *__restrict__ dst, const uint2 *_
   const uint32_t i0 = static_cast<uint32_t>(chunk) * kChunk + (blockIdx.x % kPer) * 2 * THREADS +
                       2 * threadIdx.x - static_cast<uint32_t>(bc.node_off);
   if (i0 >= static_cast<uint32_t>(bc.n_fluid)) return;
-  const PullGeom g = case_geom(bc, node, grp, rowstart, jbslot);
+  const PullGeom &g = geoms[c];
   const uint32_t seed = step_seed(*counter + j);
   if (i0 + 1u < static_cast<uint32_t>(bc.n_fluid))
     step_pair_pull<T>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i0, seed);
@@ -297,7 +312,7 @@ cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int
                                         THREADS, 0, s>>>(
             src, dst, node, grp, ccase, rowstart, jbslot,
             static_cast<const LinkCoef<float> *>(links),
-            static_cast<const BatchCase<float> *>(cases), active, work, counter, j);
+            static_cast<const BatchCase<float> *>(cases), active, work, counter, j, geoms);
       return cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;  // 16-bit batches use widths 64 and 128
@@ -308,7 +323,7 @@ cudaError_t launch_batch_step(const T *src, T *dst, const uint2 *node, const int
     batch_step_kernel<T, C, THREADS><<<static_cast<unsigned>(blocks), THREADS, 0, s>>>(
         src, dst, node, grp, ccase, rowstart, jbslot, static_cast<const LinkCoef<C> *>(links),
         static_cast<const BatchCase<C> *>(cases), active, work, static_cast<uint32_t>(blocks),
-        pf_dist, counter, j);
+        pf_dist, counter, j, geoms);
   if constexpr (std::is_same<T, float>::value) {
     if (n_exact_chunks > 0) {
       cudaError_t e = cudaGetLastError();
@@ -378,7 +393,7 @@ struct lbm_batch {
   int64_t n_links_total = 0;
   int32_t *exact_chunks = nullptr;  // node-arena chunks of the active exact-mass cases
   int32_t n_exact_chunks = 0;
-  lbm::PullGeom *geoms = nullptr;   // per case, its pull geometry (exact-mass batches)
+  lbm::PullGeom *geoms = nullptr;   // per case, its pull geometry inside the arenas
   // Work lists: the step kernels run only the node-arena chunks listed
   // (work: the other active cases'), so retired cases cost no CTAs.  Per
   // case its first chunk and chunk count; the lists are rebuilt (and the
@@ -774,18 +789,6 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       e = cudaMemcpy(b->links64, ldf.data(), ldf.size() * sizeof(lbm::LinkCoefDF),
                      cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess && precision == LBM_FP32) {
-      // every case's pull geometry inside the arenas, for the exact-mass kernel
-      const auto *bcs = reinterpret_cast<const lbm::BatchCase<float> *>(chost.data());
-      std::vector<lbm::PullGeom> gs(static_cast<size_t>(n_cases));
-      for (int32_t c = 0; c < n_cases; c++)
-        gs[c] = lbm::case_geom(bcs[c], b->node, b->grp, b->rowstart, b->jbslot, b->links64,
-                               b->carry, b->carry0);
-      e = alloc(reinterpret_cast<void **>(&b->geoms), gs.size() * sizeof(lbm::PullGeom));
-      if (e == cudaSuccess)
-        e = cudaMemcpy(b->geoms, gs.data(), gs.size() * sizeof(lbm::PullGeom),
-                       cudaMemcpyHostToDevice);
-    }
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->exact_chunks), xchunks.size() * 4);
     if (e == cudaSuccess)
       e = cudaMemcpy(b->exact_chunks, xchunks.data(), xchunks.size() * 4, cudaMemcpyHostToDevice);
@@ -812,6 +815,23 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
               static_cast<size_t>(std::max<int64_t>(1, nodes / lbm::kChunk)) * 4);
   if (e == cudaSuccess) e = build_lists(b, nullptr);
   up(b->jbslot, jbs.data(), jbs.size() * 4);
+  if (e == cudaSuccess) {
+    // every case's pull geometry inside the arenas (read by the step kernels)
+    std::vector<lbm::PullGeom> gs(static_cast<size_t>(n_cases));
+    for (int32_t c = 0; c < n_cases; c++) {
+      if (precision == LBM_FP64)
+        gs[c] = lbm::case_geom(reinterpret_cast<const lbm::BatchCase<double> *>(chost.data())[c],
+                               b->node, b->grp, b->rowstart, b->jbslot, b->links64, b->carry,
+                               b->carry0);
+      else
+        gs[c] = lbm::case_geom(reinterpret_cast<const lbm::BatchCase<float> *>(chost.data())[c],
+                               b->node, b->grp, b->rowstart, b->jbslot, b->links64, b->carry,
+                               b->carry0);
+    }
+    e = alloc(reinterpret_cast<void **>(&b->geoms), gs.size() * sizeof(lbm::PullGeom));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->geoms, gs.data(), gs.size() * sizeof(lbm::PullGeom), cudaMemcpyHostToDevice);
+  }
   up(b->rowstart, rowstart.data(), rowstart.size() * 4);
   up(b->index, index.data(), index.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(b->links, lhost.data(), lhost.size(), cudaMemcpyHostToDevice);

@@ -170,3 +170,34 @@ def test_set_launch_rejects_other_shapes():
     b.set_launch(64, False)
     steps, _, _ = b.run_to(1e-3, 200, check_every=100)
     b.close()
+
+
+def test_full_size_batch_matches_oracle_on_sampled_cases():
+    """The 512-case batched workload as the benchmark runs it (FP32, the
+    interval residual, the autotuned launch), 300 steps from rest; the
+    largest and the smallest case of each geometry against the FP64 oracle:
+    velocity rel. L2 <= 1e-5, and mass drift <= 1e-10 where no wall moves
+    (the FP32 targets)."""
+    cl = cases.batch_cases(512, seed=0)
+    b = lbm.Batch(cl, precision="fp32", params=[{"residual_mode": 1}] * len(cl))
+    steps, res, total = b.run_to(0.0, 300, check_every=100)
+    assert total == 300 and (steps == 0).all()
+    pick = []
+    for kind in ("channel", "annulus", "cylinders"):
+        ks = sorted((k for k, c in enumerate(cl) if c.meta["batch_kind"] == kind),
+                    key=lambda k: cl[k].n_fluid)
+        pick += [ks[0], ks[-1]]
+    for k in pick:
+        c = cl[k]
+        fl = c.solid == 0
+        o = oracle.OracleLBM(c, P.Parameters(c.Kn, c.H), threads=oracle.host_cores())
+        m0 = o.fields()[0][fl].sum()
+        o.step(300)
+        rg, ug, vg = b.fields(k)
+        ro, uo, vo = o.fields()
+        num = ((ug - uo)[fl] ** 2 + (vg - vo)[fl] ** 2).sum()
+        den = (uo[fl] ** 2 + vo[fl] ** 2).sum()
+        assert np.sqrt(num / den) <= 1e-5, (k, c.name)
+        if c.meta["batch_kind"] != "annulus":
+            assert abs(rg[fl].sum() - ro[fl].sum()) / m0 <= 1e-10, (k, c.name)
+    b.close()

@@ -12,7 +12,11 @@ Prints one JSON line: MLUPS over fluid nodes (whole job), the roofline of
 the step kernel against measured HBM bandwidth, an end-to-end number through
 the C ABI with host buffers, and the FP64 CPU oracle timed on a bounded
 sample of the same workload.  With --impl reference the oracle itself is the
-timed arm (on the host cores).
+timed arm (on the host cores).  On one GPU the line also carries, under
+"extra_workloads", the other workloads measured after the main timed region
+(BF16 storage, the 512-case batch to 1e-8, the warm start's time to steady
+state, the D3Q19 extension); --no-extras skips them, --workload runs one of
+them alone as the main line.
 
 Multi-GPU (torchrun): every rank runs an independent replica of the case
 (seed = rank); the path has no exchange step, so there is no collective in
@@ -229,7 +233,7 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def run_ours(args, emit=True):
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -364,11 +368,45 @@ def run_ours(args):
                       f"channel with the same cylinder recipe ({bcase.n_fluid} fluid nodes): "
                       f"10 warm-up lattice steps, then the median of 3 timings of >= 5 s "
                       f"({nst} lattice steps in all)"}
+    if rank == 0 and world == 1 and emit and not args.no_extras:
+        line["extra_workloads"] = _extra_workloads(args)
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _extra_workloads(args):
+    """The other workloads, measured after the main line's timed region and
+    reported inside it (single GPU only): BF16 storage on the same
+    throughput case, the 512-case batch to the interval residual 1e-8, the
+    warm start's time to steady state, and the D3Q19 extension.  Each entry
+    is that workload's own line (as `--workload ...` prints it) plus its
+    wall time; a workload that fails reports its error instead."""
+    out = {}
+
+    def sub(name, fn, **over):
+        a = argparse.Namespace(**vars(args))
+        for k, v in over.items():
+            setattr(a, k, v)
+        t0 = time.perf_counter()
+        try:
+            d = fn(a, emit=False)
+            d.pop("cpu_baseline", None)
+            out[name] = d
+        except Exception as e:  # report, do not lose the main line
+            out[name] = {"error": repr(e)[:300]}
+        out[name]["wall_seconds"] = time.perf_counter() - t0
+
+    common = dict(no_e2e=True, no_cpu_baseline=True, no_extras=True)
+    sub("throughput_bf16", run_ours, precision="bf16", steps=20, **common)
+    sub("batch_512_cases_tol1e-8", run_batch, precision="fp32", **common)
+    sub("warmstart_tol1e-8", run_warmstart, precision="fp32", **common)
+    sub("d3q19", run_d3q19, precision="fp32", steps=10, **common)
+    return out
 
 
 def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
@@ -415,7 +453,7 @@ ACCURACY = {
 }
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """The batched workload: 512 uneven cases (sizes 64x64-1024x512, slip
     channel / annulus / cylinder array, Kn log-uniform 0.001-0.1), FP32, all
     run together to --batch-tol (default 1e-8, the workload's residual) with
@@ -513,6 +551,8 @@ def run_batch(args):
         "time_to_steady_vs_single": comp,
         "clocks": clocks,
     }
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -523,7 +563,7 @@ def run_batch(args):
 D3Q19_BYTES = {"fp32": 152, "fp64": 304}  # 19 reads + 19 writes per fluid node
 
 
-def run_d3q19(args):
+def run_d3q19(args, emit=True):
     """The D3Q19 extension: a periodic 512 x 256 x 256 box of non-overlapping
     spheres (porosity 0.8, radii 6-12, seeded), Kn 0.02, force-driven, FP32
     (or FP64).  One bench step = --lbm-steps lattice steps + the residual
@@ -626,6 +666,8 @@ def run_d3q19(args):
             "value": sc.n_fluid * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"FP64 D3Q19 oracle (one thread) on a 128x64x64 box of the same recipe "
                       f"({sc.n_fluid} fluid nodes): 2 warm-up steps, then {n} steps in {dt:.1f} s"}
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -633,7 +675,7 @@ def run_d3q19(args):
     return 0
 
 
-def run_warmstart(args):
+def run_warmstart(args, emit=True):
     """The learned warm start (256 x 256 random-cylinder channels, Kn
     log-uniform 0.001-0.1, FP32 solves to the interval residual 1e-8): the
     network is trained on --ws-train seeded cases solved by the batched
@@ -739,6 +781,8 @@ def run_warmstart(args):
         "clocks": clocks,
     }
     net.close()
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -765,7 +809,7 @@ def net_flops(H, W, base=32, levels=4, c_in=3, c_out=3):
     return f
 
 
-def run_net(args):
+def run_net(args, emit=True):
     """The warm-start network's training step (256 x 256, batch 8, BF16
     storage, FP32 accumulation; convolutions of the forward pass and of the
     backward data pass on the tensor cores): TFLOP/s of the whole step
@@ -827,6 +871,8 @@ def run_net(args):
                          "unit": "TFLOP/s", "frac": 3 * fwd / ms / 1e9 / peak, "traffic": None,
                          "peak_source": src},
             "clocks": clocks}
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -845,6 +891,8 @@ def main():
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads reported inside the default line")
     ap.add_argument("--workload", choices=("throughput", "batch", "net", "d3q19", "warmstart"),
                     default="throughput")
     ap.add_argument("--batch-cases", type=int, default=512)

@@ -20,7 +20,8 @@
 // tail element 19 N + k, which Eq. EqNewBDSC (local to x) filled during
 // step t.  Per node: a flag word (bit q: x - c_q solid; kSolid3 for solid
 // nodes) and the index of its first link (links sorted by node, then
-// direction).  The collision works in moment space with the D3Q19 basis
+// direction); the step runs one thread per fluid node from a list of the
+// fluid nodes (index and flag word).  The collision works in moment space with the D3Q19 basis
 // built here from its defining polynomials (d'Humieres et al. 2002):
 // m - m_eq = M (d - d_eq), M Fbar, then f' - f = M^T diag(1/|M_k|^2) (m' -
 // m) (the basis is orthogonal), and the rest population closes the mass.
@@ -365,7 +366,7 @@ template <typename C>
 __global__ void __launch_bounds__(kThreads3, sizeof(C) == 4 ? 8 : 2)
 step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
              const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
-             const uint32_t *__restrict__ fluid, const Const3<C> k, int64_t n_fluid) {
+             const uint2 *__restrict__ fluid, const Const3<C> k, int64_t n_fluid) {
   constexpr int kW = kThreads3 / 32;
   __shared__ Warp3<C> sh[kW];
   __shared__ uint32_t sh_ex[kW][32], sh_fl[kW][32];
@@ -373,8 +374,10 @@ step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__r
   // lane idles on a solid node
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
-  const int64_t p = t0 < n_fluid ? static_cast<int64_t>(fluid[t0]) : 0;
-  const uint32_t fl = t0 < n_fluid ? flags[p] : kSolid3;
+  // the fluid-node list holds each node's index and flag word together
+  const uint2 pf = t0 < n_fluid ? fluid[t0] : make_uint2(0u, kSolid3);
+  const int64_t p = pf.x;
+  const uint32_t fl = pf.y;
   const bool live = fl != kSolid3;
   const uint32_t lb = live && fl ? lbase[p] : 0u;
   if (live) node3(src, dst, k, p, fl, lb, sh[w], lane);
@@ -432,7 +435,7 @@ template <typename C>
 __global__ void __launch_bounds__(kResThreads3)
 residual3_kernel(const C *__restrict__ cur, const C *__restrict__ prev,
                  const uint32_t *__restrict__ flags, const uint32_t *__restrict__ lbase,
-                 const uint32_t *__restrict__ fluid, const Const3<C> k, int64_t n_fluid,
+                 const uint2 *__restrict__ fluid, const Const3<C> k, int64_t n_fluid,
                  double *__restrict__ partials) {
   // per node: rho and j of both states in the storage's arithmetic type,
   // the node's mass deviation summed in FP64; sums over nodes in FP64
@@ -440,8 +443,9 @@ residual3_kernel(const C *__restrict__ cur, const C *__restrict__ prev,
   const int64_t G = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n_fluid;
        t += G) {
-    const int64_t p = fluid[t];
-    const uint32_t fl = flags[p];
+    const uint2 pf = fluid[t];
+    const int64_t p = pf.x;
+    const uint32_t fl = pf.y;
     const Coord3 c = coord3(k, p);
     C r1 = C(0), r0 = C(0), j1[3] = {C(0), C(0), C(0)}, j0[3] = {C(0), C(0), C(0)};
     double dm = 0.0;
@@ -610,7 +614,7 @@ struct lbm3d {
   int cur = 0;
   uint32_t *flags = nullptr;
   uint32_t *lbase = nullptr;
-  uint32_t *fluid = nullptr;  // the fluid nodes in node order
+  uint2 *fluid = nullptr;  // the fluid nodes in node order: index, flag word
   void *links = nullptr;
   Const3Both kc;
   double *partials = nullptr, *result = nullptr;
@@ -791,13 +795,13 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
   if (e == cudaSuccess) e = cudaMemcpy(h->flags, flags.data(), n * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->lbase, lbase.data(), n * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    std::vector<uint32_t> fluid;
+    std::vector<uint2> fluid;
     fluid.reserve(static_cast<size_t>(n_fluid));
     for (int64_t pn = 0; pn < n; pn++)
-      if (flags[pn] != kSolid3) fluid.push_back(static_cast<uint32_t>(pn));
-    e = alloc(reinterpret_cast<void **>(&h->fluid), std::max<size_t>(1, fluid.size()) * 4);
+      if (flags[pn] != kSolid3) fluid.push_back(make_uint2(static_cast<uint32_t>(pn), flags[pn]));
+    e = alloc(reinterpret_cast<void **>(&h->fluid), std::max<size_t>(1, fluid.size()) * 8);
     if (e == cudaSuccess && !fluid.empty())
-      e = cudaMemcpy(h->fluid, fluid.data(), fluid.size() * 4, cudaMemcpyHostToDevice);
+      e = cudaMemcpy(h->fluid, fluid.data(), fluid.size() * 8, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess)
     e = dispatch3(h->precision, [&](auto tag) {

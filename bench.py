@@ -432,7 +432,7 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
 
 
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
-KERNEL_REV = 11
+KERNEL_REV = 12
 
 # Accuracy of each storage against the FP64 oracle and the targets it
 # misses, as measured by tests/test_gpu_parity.py (2000 steps from rest on
@@ -451,6 +451,19 @@ ACCURACY = {
     "bf16": {"velocity_target": 1e-3, "velocity": "missed on every parity case (1.6e-3 to 7.3e-3)"},
     "fp64": {"populations": "within 1e-13 of the oracle, element by element"},
 }
+
+
+def _batch_roofline(precision, updates_per_s):
+    """The batch's aggregate rate against the copy bandwidth: algorithmic
+    bytes per fluid-node update (72 B in FP32) times updates per second over
+    the whole run (step kernels, the exact-mass step of moving-wall cases,
+    residual checks, retirements)."""
+    peak, src = _peak_hbm()
+    achieved = FLUID_BYTES[precision] * updates_per_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src,
+            "bytes_per_fluid_node": FLUID_BYTES[precision],
+            "kernel": "the whole batched run (aggregate, not one kernel)"}
 
 
 def run_batch(args, emit=True):
@@ -549,6 +562,7 @@ def run_batch(args, emit=True):
                                            if (~conv).any() else None),
                   "create_seconds": t_create, "wall_seconds": wall},
         "time_to_steady_vs_single": comp,
+        "roofline": _batch_roofline(args.precision, updates / wall),
         "clocks": clocks,
     }
     if not emit:

@@ -424,6 +424,18 @@ __device__ __forceinline__ void collide(const C (&d)[9], const StepConst<C> &k, 
 // (a prefix of the warp) take part -- named explicitly, since the lanes
 // need not have reconverged after the collision's data-dependent branches.
 constexpr int kExactMaxWarps = 8;  // CTAs of up to 256 threads
+
+// D2Q9 velocities (two bits each: c + 1, direction j in bits 2j, 2j + 1)
+// and opposite directions (four bits each: opp(j) in bits 4 (j - 1) ..
+// 4 (j - 1) + 3), for the link epilogues that meet a direction as a value.
+constexpr uint32_t kVelX2 = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) |
+                            (2u << 10) | (0u << 12) | (0u << 14) | (2u << 16);
+constexpr uint32_t kVelY2 = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) |
+                            (2u << 10) | (2u << 12) | (0u << 14) | (0u << 16);
+constexpr uint32_t kOpp2 = 0x65872143u;
+__device__ __forceinline__ int vel_x2(int j) { return static_cast<int>((kVelX2 >> (2 * j)) & 3u) - 1; }
+__device__ __forceinline__ int vel_y2(int j) { return static_cast<int>((kVelY2 >> (2 * j)) & 3u) - 1; }
+__device__ __forceinline__ int opp2(int j) { return static_cast<int>((kOpp2 >> (4 * (j - 1))) & 15u); }
 __device__ __forceinline__ void link_epilogue_exact(const float *__restrict__ src,
                                                     float *__restrict__ dst, const PullGeom &g,
                                                     const uint32_t fl, const uint32_t li,
@@ -468,12 +480,6 @@ __device__ __forceinline__ void link_epilogue_exact(const float *__restrict__ sr
   xs_fl[w][lane] = fl;
   __syncwarp(am);
   const uint32_t tail = 9u * g.plane;
-  // velocities (2 bits each: c + 1) and opposite directions (4 bits each)
-  constexpr uint32_t kCx = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) | (2u << 10) |
-                           (0u << 12) | (0u << 14) | (2u << 16);
-  constexpr uint32_t kCy = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) |
-                           (2u << 12) | (0u << 14) | (0u << 16);
-  constexpr uint32_t kOpp = 0x65872143u;  // opp(j) in bits 4 (j - 1) .. 4 (j - 1) + 3
   constexpr float kW9h = static_cast<float>(1.0 / 9);
   constexpr float kW36h = static_cast<float>(1.0 / 36);
   const float kW9l = static_cast<float>(1.0 / 9 - static_cast<double>(kW9h));
@@ -488,9 +494,7 @@ __device__ __forceinline__ void link_epilogue_exact(const float *__restrict__ sr
     uint32_t m = xs_fl[w][s];
     for (uint32_t r = t - xs_ex[w][s]; r; r--) m &= m - 1u;
     const int j = __ffs(static_cast<int>(m));  // flag bit j - 1: direction j
-    const int jb = static_cast<int>((kOpp >> (4 * (j - 1))) & 15u);
-    const int cx = static_cast<int>((kCx >> (2 * j)) & 3u) - 1;
-    const int cy = static_cast<int>((kCy >> (2 * j)) & 3u) - 1;
+    const int jb = opp2(j), cx = vel_x2(j), cy = vel_y2(j);
     const uint32_t lj = base + t;
     const LinkCoefDF c = g.links64[lj];
     const DF k1{c.hi[0], c.lo[0]}, k2{c.hi[1], c.lo[1]}, k3{c.hi[2], c.lo[2]},
@@ -694,6 +698,124 @@ __device__ __forceinline__ float link_value(const LinkCoef<float> &c, const int 
          c2 * (drho + rho * pj);
 }
 
+// link_value for a direction j known only at run time (the same
+// arithmetic; the velocity components and weight come from packed tables).
+template <typename T>
+__device__ __forceinline__ float link_value_rt(const LinkCoef<float> &c, const int j,
+                                               const float djb, const float oj, const float ojb,
+                                               const float drho, const float rho, const float ux,
+                                               const float uy, const float uu,
+                                               const StepConst<float> &k) {
+  constexpr bool kS = Stor<T>::kScaled;
+  const float w = j < 5 ? 1.0f / 9 : 1.0f / 36;
+  const float r = c.k1 + c.k2 + c.k3;
+  float c0, c2;
+  if (k.diffuse_mode == 0) {
+    c0 = c.alpha;
+    c2 = (1.0f - r) * w;
+  } else {
+    c0 = c.alpha + (r - 1.0f) * w;
+    c2 = 0.0f;
+  }
+  const float cu = float(vel_x2(j)) * ux + float(vel_y2(j)) * uy;
+  const float pj = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+  return c.k1 * djb + c.k2 * oj + c.k3 * ojb + (kS ? c0 * k.sc : c0) + c.alpha * drho +
+         c2 * (drho + rho * pj);
+}
+
+// Eq. EqNewBDSC for the links of the paired 16-bit step: the warp's 64
+// nodes (lane l holds nodes 2 l and 2 l + 1 of the warp) have consecutive
+// links in the table; the warp spreads them over its lanes, one link per
+// lane at a time, each reading its node's values (f'_1..f'_8, drho, rho, u,
+// |u|^2 in the step's units, and the node's random word) from the warp's
+// shared record.  Each link value is rounded stochastically with the
+// random bits of its node and direction, as a node doing its own links
+// would.  The lanes whose pair is complete take part (a prefix of the
+// warp; a lone last node runs the one-node step instead).
+constexpr int kPairMaxWarps = 4;  // CTAs of up to 128 threads
+template <typename T>
+__device__ __forceinline__ void pair_links_warp(const T *__restrict__ src, T *__restrict__ dst,
+                                                const PullGeom &g,
+                                                const LinkCoef<float> *__restrict__ links,
+                                                const StepConst<float> &k, const uint32_t i0,
+                                                const uint32_t fl0, const uint32_t fl1,
+                                                const uint32_t li0, const uint32_t li1,
+                                                const F2 (&o)[9], const F2 drho_s, const F2 rho_s,
+                                                const F2 ux, const F2 uy, const F2 uu,
+                                                const uint32_t h0, const uint32_t h1) {
+  __shared__ float pw_v[kPairMaxWarps][13][65];
+  __shared__ uint32_t pw_h[kPairMaxWarps][64];
+  __shared__ uint32_t pw_ex[kPairMaxWarps][32], pw_fl[kPairMaxWarps][32];
+  const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
+  const uint32_t first = i0 - 2u * static_cast<uint32_t>(lane);
+  const uint32_t pairs = (g.n_fluid - first) / 2u;
+  const int nact = pairs >= 32u ? 32 : static_cast<int>(pairs);
+  const unsigned am = nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u);
+  __syncwarp(am);
+  const uint32_t na = static_cast<uint32_t>(__popc(fl0)), nl = na + static_cast<uint32_t>(__popc(fl1));
+  const unsigned anyl = __ballot_sync(am, nl != 0u);
+  if (anyl == 0u) return;
+  if (fl0) {
+    const int n = 2 * lane;
+#pragma unroll
+    for (int q = 1; q < 9; q++) pw_v[w][q - 1][n] = o[q].v.x;
+    pw_v[w][8][n] = drho_s.v.x;
+    pw_v[w][9][n] = rho_s.v.x;
+    pw_v[w][10][n] = ux.v.x;
+    pw_v[w][11][n] = uy.v.x;
+    pw_v[w][12][n] = uu.v.x;
+    pw_h[w][n] = h0;
+  }
+  if (fl1) {
+    const int n = 2 * lane + 1;
+#pragma unroll
+    for (int q = 1; q < 9; q++) pw_v[w][q - 1][n] = o[q].v.y;
+    pw_v[w][8][n] = drho_s.v.y;
+    pw_v[w][9][n] = rho_s.v.y;
+    pw_v[w][10][n] = ux.v.y;
+    pw_v[w][11][n] = uy.v.y;
+    pw_v[w][12][n] = uu.v.y;
+    pw_h[w][n] = h1;
+  }
+  // exclusive prefix of the lanes' link counts: link t of the warp is link
+  // base + t of the table
+  uint32_t incl = nl;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(am, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const uint32_t excl = incl - nl, total = __shfl_sync(am, incl, nact - 1);
+  const uint32_t mine = fl0 ? li0 : li1;  // the lane's first link (where it has one)
+  const uint32_t base = __shfl_sync(am, mine - excl, __ffs(static_cast<int>(anyl)) - 1);
+  pw_ex[w][lane] = excl;
+  pw_fl[w][lane] = fl0 | (fl1 << 8);
+  __syncwarp(am);
+  const uint32_t tail = 9u * g.plane;
+  for (uint32_t t = static_cast<uint32_t>(lane); t < total; t += static_cast<uint32_t>(nact)) {
+    int s = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1)
+      if (s + st < nact && pw_ex[w][s + st] <= t) s += st;
+    uint32_t r = t - pw_ex[w][s];
+    const uint32_t f = pw_fl[w][s], fa = f & 0xFFu;
+    const uint32_t ca = static_cast<uint32_t>(__popc(fa));
+    const int half = r >= ca ? 1 : 0;
+    uint32_t m = half ? (f >> 8) : fa;
+    if (half) r -= ca;
+    for (; r; r--) m &= m - 1u;
+    const int j = __ffs(static_cast<int>(m)), jb = opp2(j);
+    const int n = 2 * s + half;
+    const uint32_t lj = base + t;
+    const float v = link_value_rt<T>(links[lj], j, Stor<T>::ld_raw(src[g.jbslot[lj]]),
+                                     pw_v[w][j - 1][n], pw_v[w][jb - 1][n], pw_v[w][8][n],
+                                     pw_v[w][9][n], pw_v[w][10][n], pw_v[w][11][n],
+                                     pw_v[w][12][n], k);
+    dst[tail + lj] =
+        Stor<T>::bits(Stor<T>::st_rs2(v, 0.0f, fmix32(pw_h[w][n] ^ (0x27D4EB2Fu * j))) >> 16);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void step_pair_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                const PullGeom &g,
@@ -763,31 +885,9 @@ __device__ __forceinline__ void step_pair_pull(const T *__restrict__ src, T *__r
   for (int q = 0; q < 9; q++) *reinterpret_cast<uint32_t *>(dst + q * P + i0) = t[q];
 
   // boundary links of either node (Eq. EqNewBDSC is local to the node)
-  const unsigned wmask = __reduce_or_sync(__activemask(), fl0 | fl1);
-  if (!wmask) return;
-  const uint32_t tail = 9u * P;
   const F2 drho_s = kS ? drho * k.sc : drho, rho_s = kS ? rho * k.sc : rho;
-#pragma unroll
-  for (int j = 1; j < 9; j++) {
-    if (!(wmask & (1u << (j - 1)))) continue;
-    constexpr int opp_tab[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-    const int jb = opp_tab[j];
-    const uint32_t below = (1u << (j - 1)) - 1u;
-    if (fl0 & (1u << (j - 1))) {
-      const uint32_t lj = li0 + __popc(fl0 & below);
-      const float v = link_value<T>(links[lj], j, Stor<T>::ld_raw(src[g.jbslot[lj]]), o[j].v.x,
-                                    o[jb].v.x, drho_s.v.x, rho_s.v.x, ux.v.x, uy.v.x, uu.v.x, k);
-      dst[tail + lj] =
-          Stor<T>::bits(Stor<T>::st_rs2(v, 0.0f, fmix32(h0 ^ (0x27D4EB2Fu * j))) >> 16);
-    }
-    if (fl1 & (1u << (j - 1))) {
-      const uint32_t lj = li1 + __popc(fl1 & below);
-      const float v = link_value<T>(links[lj], j, Stor<T>::ld_raw(src[g.jbslot[lj]]), o[j].v.y,
-                                    o[jb].v.y, drho_s.v.y, rho_s.v.y, ux.v.y, uy.v.y, uu.v.y, k);
-      dst[tail + lj] =
-          Stor<T>::bits(Stor<T>::st_rs2(v, 0.0f, fmix32(h1 ^ (0x27D4EB2Fu * j))) >> 16);
-    }
-  }
+  pair_links_warp<T>(src, dst, g, links, k, i0, fl0, fl1, li0, li1, o, drho_s, rho_s, ux, uy, uu,
+                     h0, h1);
 }
 
 // The exact-mass step of one node (FP32 storage) as a function of its own,

@@ -430,6 +430,183 @@ conv_fwd_tc(const __nv_bfloat16 *__restrict__ x, int xs, const __nv_bfloat16 *__
   (void)lane;
 }
 
+// The same convolution with its operands copied asynchronously (cp.async,
+// 16 bytes per copy, zero-filled outside the image) through a ring of
+// kTcAsyncStages stages: the copies of the next kTcAsyncStages - 1 chunks
+// are in flight while the tensor cores work on the current one, instead of
+// each chunk's gather waiting out its own memory latency.  Needs 16-byte
+// aligned channel rows (input channels and their stride multiples of 8).
+constexpr int kTcAsyncStages = 3;
+constexpr int kTcAsyncSmem = kTcAsyncStages * 2 * kTcStageBytes + 1024;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int KS>
+__global__ void __launch_bounds__(kTcM)
+conv_fwd_tc_async(const __nv_bfloat16 *__restrict__ x, int xs,
+                  const __nv_bfloat16 *__restrict__ wk, int Cip, const float *__restrict__ b,
+                  __nv_bfloat16 *__restrict__ y, int ys, int N, int H, int W, int Ci, int Co,
+                  int NT, int relu, int *__restrict__ err) {
+  constexpr int HALO = KS / 2;
+  constexpr int KS2 = KS * KS;
+  constexpr int S = kTcAsyncStages;
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ uint64_t mbar[S];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t npix = static_cast<int64_t>(N) * H * W;
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * kTcM + tid;  // this thread's pixel (A row)
+  const int o0 = blockIdx.y * NT;
+  int pn = 0, pi = 0, pj = 0;
+  if (p < npix) {
+    pn = static_cast<int>(p / (static_cast<int64_t>(H) * W));
+    const int r = static_cast<int>(p - static_cast<int64_t>(pn) * H * W);
+    pi = r / W;
+    pj = r - pi * W;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kTcNMax)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; s++) mbar_init(&mbar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = umma_idesc_bf16(kTcM, NT);
+  const int nck = (Cip + kTcKC - 1) / kTcKC;  // channel chunks per tap
+  const int iters = KS2 * nck;
+  // copies of chunk `it` into its stage: A row `tid` (input pixel shifted by
+  // the tap, zero outside the image) and B row `tid` (< NT: output channel
+  // o0 + tid of the packed weights)
+  auto load = [&](int it) {
+    const int st = it % S;
+    const int d = it / nck, c0 = (it % nck) * kTcKC;
+    const int kc = min(kTcKC, Cip - c0);
+    const uint32_t sa = smem_addr(smem + st * 2 * kTcStageBytes);
+    const uint32_t sb = sa + kTcStageBytes;
+    const uint32_t row = (tid >> 3) * 1024 + (tid & 7) * 16;
+    const int ii = pi + d / KS - HALO, jj = pj + d % KS - HALO;
+    const bool in = p < npix && ii >= 0 && ii < H && jj >= 0 && jj < W;
+    const __nv_bfloat16 *src =
+        in ? x + ((static_cast<int64_t>(pn) * H + ii) * W + jj) * xs : x;
+    for (int q = 0; q < kc / 8; q++) {
+      const int c = c0 + q * 8;
+      const bool v = in && c < Ci;
+      cp_async16(sa + row + q * 128, v ? src + c : x, v ? 16u : 0u);
+    }
+    if (tid < NT) {
+      const __nv_bfloat16 *ws = wk + (static_cast<int64_t>(o0 + tid) * KS2 + d) * Cip + c0;
+      for (int q = 0; q < kc / 8; q++) cp_async16(sb + row + q * 128, ws + q * 8, 16u);
+    }
+  };
+  for (int s = 0; s < S - 1; s++) {
+    if (s < iters) load(s);
+    cp_async_commit();
+  }
+  bool ok = true;
+  for (int it = 0; it < iters; it++) {
+    const int st = it % S;
+    const int nxt = it + S - 1;
+    if (nxt < iters) {
+      // stage nxt % S was last read by the MMAs of chunk it - 1
+      if (it >= 1) {
+        const bool got = mbar_wait(&mbar[(it - 1) % S], ((it - 1) / S) & 1, kTcWaitLimit);
+        if (__syncthreads_or(!got)) {  // one decision for the whole CTA
+          ok = false;
+          if (tid == 0) atomicExch(err, 1);
+          break;
+        }
+      }
+      load(nxt);
+    }
+    cp_async_commit();
+    cp_async_wait<S - 1>();  // this thread's copies of chunk `it` have landed
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int c0 = (it % nck) * kTcKC;
+      const int kc = min(kTcKC, Cip - c0);
+      const uint32_t a0 = smem_addr(smem + st * 2 * kTcStageBytes), b0 = a0 + kTcStageBytes;
+      for (int k = 0; k < kc / 16; k++) {
+        const uint64_t ad = umma_desc(a0 + k * 256, 128, 1024);
+        const uint64_t bd = umma_desc(b0 + k * 256, 128, 1024);
+        const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_addr(&mbar[st]))
+                   : "memory");
+    }
+  }
+  cp_async_wait<0>();  // no copy left in flight, whatever happened above
+  // all MMAs done: the last commit covers every earlier MMA of the issuing thread
+  if (ok && iters > 0) {
+    const int last = iters - 1;
+    const bool got = mbar_wait(&mbar[last % S], (last / S) & 1, kTcWaitLimit);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok) {
+    __syncwarp();
+    __nv_bfloat16 *yp = y + (p < npix ? p : 0) * ys;
+    for (int c = 0; c < NT; c += 8) {
+      uint32_t r[8];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7])
+          : "r"(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (p < npix) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          const int o = o0 + c + e;
+          if (o < Co) {
+            float v = __uint_as_float(r[e]) + (b ? b[o] : 0.f);
+            if (relu) v = fmaxf(v, 0.f);
+            yp[o] = __float2bfloat16_rn(v);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTcNMax)
+                 : "memory");
+  }
+}
+
 // Weight gradient on the tensor cores:
 //   dW[d][c][o] = sum_p X[p + d - HALO][c] gz[p][o]     db[o] = sum_p gz[p][o]
 // as D[m][n] = sum_k A[m][k] B[n][k] with m = d * Ci + c (M = 128 per CTA),
@@ -874,7 +1051,13 @@ void launch_conv(lbm_net_t *n, const A *x, int xs, const A *w, const float *b, A
     const int64_t npix = static_cast<int64_t>(N) * H * W;
     dim3 grid(static_cast<unsigned>((npix + kTcM - 1) / kTcM), Cop / NT);
     const bool vec = xs % 8 == 0 && Ci % 8 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0;
-    if (ks == 3)
+    if (vec && ks == 3)
+      conv_fwd_tc_async<3><<<grid, kTcM, kTcAsyncSmem, n->stream>>>(
+          x, xs, wk, Cip, b, y, ys, N, H, W, Ci, Co, NT, relu, n->d_err);
+    else if (vec)
+      conv_fwd_tc_async<1><<<grid, kTcM, kTcAsyncSmem, n->stream>>>(
+          x, xs, wk, Cip, b, y, ys, N, H, W, Ci, Co, NT, relu, n->d_err);
+    else if (ks == 3)
       conv_fwd_tc<3><<<grid, kTcM, kTcSmem, n->stream>>>(x, xs, wk, Cip, b, y, ys, N, H, W, Ci, Co,
                                                          NT, relu, vec, n->d_err);
     else
@@ -1132,6 +1315,12 @@ int lbm_net_create(int32_t base, int32_t levels, int32_t c_in, int32_t c_out, in
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(lbm::net::conv_fwd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                lbm::net::kTcSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lbm::net::conv_fwd_tc_async<3>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::net::kTcAsyncSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lbm::net::conv_fwd_tc_async<1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::net::kTcAsyncSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(lbm::net::conv_wgrad_tc<3>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::net::kWgSmem);

@@ -432,7 +432,7 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
 
 
 # Bumped whenever the step kernel changes, so stale ncu traffic is not reported.
-KERNEL_REV = 12
+KERNEL_REV = 13
 
 # Accuracy of each storage against the FP64 oracle and the targets it
 # misses, as measured by tests/test_gpu_parity.py (2000 steps from rest on

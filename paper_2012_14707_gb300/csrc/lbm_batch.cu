@@ -138,8 +138,8 @@ batch_step_kernel(const T *__restrict__ src, T *__restrict__ dst,
   const PullGeom &g = geoms[c];
   uint32_t seed = 0;
   if constexpr (kStochastic<T>) seed = step_seed(*counter + j);
-  step_node_pull<T, C, false>(src + bc.f_off, dst + bc.f_off, g, links + bc.link_off, bc.k, i,
-                              seed);
+  step_node_pull<T, C, false, THREADS / 32>(src + bc.f_off, dst + bc.f_off, g,
+                                            links + bc.link_off, bc.k, i, seed);
 }
 
 // 16-bit batches: the paired step of the single-case kernel

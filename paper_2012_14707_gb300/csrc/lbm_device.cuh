@@ -601,6 +601,83 @@ __device__ __forceinline__ void link_epilogue_pull(const T *__restrict__ src, T 
   }
 }
 
+// Eq. EqNewBDSC for the links of the one-node FP32 / FP64 step, spread
+// over the warp as in pair_links_warp: the links of the warp's 32 nodes
+// are consecutive in the table; each lane takes one link at a time and
+// reads its node's values (f'_1..f'_8, drho, rho, u, |u|^2) from the
+// warp's shared record.  The value is link_epilogue_pull's, rounded to
+// storage the same way.  The lanes of nodes below g.n_fluid take part (a
+// prefix of the warp: lane i mod 32 runs node i).  kWarps: warps per CTA.
+template <typename T, typename C, int kWarps>
+__device__ __forceinline__ void node_links_warp(const T *__restrict__ src, T *__restrict__ dst,
+                                                const PullGeom &g, const uint32_t fl,
+                                                const uint32_t li,
+                                                const LinkCoef<C> *__restrict__ links,
+                                                const Collided<T, C> &c_, const StepConst<C> &k,
+                                                const uint32_t node) {
+  static_assert(!Stor<T>::kScaled && !kStochastic<T>, "FP32 / FP64 storage");
+  __shared__ C nw_v[kWarps][13][33];
+  __shared__ uint32_t nw_ex[kWarps][32], nw_fl[kWarps][32];
+  const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
+  const uint32_t first = node - static_cast<uint32_t>(lane);
+  const int nact = g.n_fluid - first >= 32u ? 32 : static_cast<int>(g.n_fluid - first);
+  const unsigned am = nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u);
+  __syncwarp(am);
+  const uint32_t nl = static_cast<uint32_t>(__popc(fl));
+  const unsigned anyl = __ballot_sync(am, nl != 0u);
+  if (anyl == 0u) return;
+  if (fl) {
+#pragma unroll
+    for (int q = 1; q < 9; q++) nw_v[w][q - 1][lane] = c_.o[q];
+    nw_v[w][8][lane] = c_.drho;
+    nw_v[w][9][lane] = c_.rho;
+    nw_v[w][10][lane] = c_.ux;
+    nw_v[w][11][lane] = c_.uy;
+    nw_v[w][12][lane] = c_.uu;
+  }
+  uint32_t incl = nl;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(am, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const uint32_t excl = incl - nl, total = __shfl_sync(am, incl, nact - 1);
+  const uint32_t base = __shfl_sync(am, li - excl, __ffs(static_cast<int>(anyl)) - 1);
+  nw_ex[w][lane] = excl;
+  nw_fl[w][lane] = fl;
+  __syncwarp(am);
+  const uint32_t tail = 9u * g.plane;
+  for (uint32_t t = static_cast<uint32_t>(lane); t < total; t += static_cast<uint32_t>(nact)) {
+    int s = 0;
+#pragma unroll
+    for (int st = 16; st >= 1; st >>= 1)
+      if (s + st < nact && nw_ex[w][s + st] <= t) s += st;
+    uint32_t m = nw_fl[w][s];
+    for (uint32_t r = t - nw_ex[w][s]; r; r--) m &= m - 1u;
+    const int j = __ffs(static_cast<int>(m)), jb = opp2(j);
+    const uint32_t lj = base + t;
+    const LinkCoef<C> c = links[lj];
+    const C wj = j < 5 ? C(1.0 / 9) : C(1.0 / 36);
+    const C r = c.k1 + c.k2 + c.k3;
+    C c0, c2;
+    if (k.diffuse_mode == 0) {
+      c0 = c.alpha;
+      c2 = (C(1) - r) * wj;
+    } else {
+      c0 = c.alpha + (r - C(1)) * wj;
+      c2 = C(0);
+    }
+    const C ux = nw_v[w][10][s], uy = nw_v[w][11][s], uu = nw_v[w][12][s];
+    const C drho = nw_v[w][8][s], rho = nw_v[w][9][s];
+    const C cu = C(vel_x2(j)) * ux + C(vel_y2(j)) * uy;
+    const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+    const C djb = Stor<T>::ld(src[g.jbslot[lj]], k.inv_sc);
+    const C v = c.k1 * djb + c.k2 * nw_v[w][j - 1][s] + c.k3 * nw_v[w][jb - 1][s] + c0 +
+                c.alpha * drho + c2 * (drho + rho * pj);
+    dst[tail + lj] = Stor<T>::st(v, k.sc);
+  }
+}
+
 // Random word of node i in the step whose seed is `seed` (16-bit storage
 // and the exact-mass variant; 0 otherwise, unused).
 template <typename T, bool kExact>
@@ -616,7 +693,7 @@ __device__ __forceinline__ uint32_t node_random(const uint32_t seed, const uint3
 // store f'(x, t) in the node's own slots of dst, then the link epilogue.
 // Used by the single-case and the batched step kernels alike; seed is the
 // step's seed of random bits (step_seed of the case's step count).
-template <typename T, typename C, bool kExact = false>
+template <typename T, typename C, bool kExact = false, int kWarps = 0>
 __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__restrict__ dst,
                                                const PullGeom &g,
                                                const LinkCoef<C> *__restrict__ links,
@@ -653,9 +730,13 @@ __device__ __forceinline__ void step_node_pull(const T *__restrict__ src, T *__r
 #pragma unroll
   for (int q = 0; q < 9; q++) dst[q * P + i] = c.t[q];
   // flag byte and first link (li) of the node
-  link_epilogue_pull<T, C, kExact>(src, dst, g, nw.x & 0xFFu,
-                                   static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k, rs,
-                                   i);
+  if constexpr (!kExact && !kStochastic<T> && kWarps > 0)
+    node_links_warp<T, C, kWarps>(src, dst, g, nw.x & 0xFFu,
+                                  static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k, i);
+  else
+    link_epilogue_pull<T, C, kExact>(src, dst, g, nw.x & 0xFFu,
+                                     static_cast<uint32_t>(gr.y) + node_loff(nw), links, c, k, rs,
+                                     i);
 }
 
 // ---------------------------------------------------------------------------

@@ -72,7 +72,7 @@ step_kernel_pull(const T *__restrict__ src, T *__restrict__ dst, __grid_constant
   if constexpr (kExact)
     step_node_exact(src, dst, g, links, k, i, k.sr_seed);
   else
-    step_node_pull<T, C, false>(src, dst, g, links, k, i, k.sr_seed);
+    step_node_pull<T, C, false, kPullThreads / 32>(src, dst, g, links, k, i, k.sr_seed);
 }
 
 // One time step of a single case in 16-bit storage: thread t of CTA b runs

@@ -44,7 +44,7 @@ FLUID_BYTES = {"fp32": 72, "fp64": 144, "bf16": 36, "fp16": 36}  # algorithmic b
 # fluid-node update (dadd + dmul + 2 dfma, ncu counters on the 4096x2048
 # case; profiles/), not an algorithmic count, and the peak is NVIDIA's
 # nominal FP64 rate, not a measured one.
-FP64_FLOPS_PER_NODE = 156.2
+FP64_FLOPS_PER_NODE = 156.4
 FP64_PEAK_GFLOPS = 1250.0
 ELEM_BYTES = {"fp32": 4, "fp64": 8, "bf16": 2, "fp16": 2}
 FALLBACK_HBM_GBS = 6800.0

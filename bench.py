@@ -357,6 +357,7 @@ def run_ours(args, emit=True):
         "e2e": e2e,
         "accuracy_vs_oracle": ACCURACY[args.precision],
         "gpu_launches": args.steps * (per + 2),
+        "mlups_all_nodes": mlups * case.nx * case.ny / n_fluid,
         "clocks": clocks,
         "residual_last": last[0] if last else None,
     }
@@ -560,7 +561,9 @@ def run_batch(args, emit=True):
                   "steps_to_steady_p90": float(np.percentile(steps[conv], 90)) if conv.any() else None,
                   "not_converged_Kn_max": (float(max(c.Kn for c, ok in zip(cl, conv) if not ok))
                                            if (~conv).any() else None),
-                  "create_seconds": t_create, "wall_seconds": wall},
+                  "create_seconds": t_create, "wall_seconds": wall,
+                  # per case: the step at which it met tol (0: still running at the cap)
+                  "steps_per_case": [int(v) for v in steps]},
         "time_to_steady_vs_single": comp,
         "roofline": _batch_roofline(args.precision, updates / wall),
         "clocks": clocks,
@@ -787,6 +790,8 @@ def run_warmstart(args, emit=True):
             "median_steps": {"warm": float(np.median(w[both])) if both.any() else None,
                              "rest": float(np.median(r_[both])) if both.any() else None},
             "median_step_ratio": float(np.median(w[both] / r_[both])) if both.any() else None,
+            "step_ratio_quartiles": ([float(v) for v in np.percentile(w[both] / r_[both], [25, 75])]
+                                     if both.any() else None),
             "single_same_steps_as_batch": int((single == r_).sum()),
             "note": "creation included in every arm; warm start includes inference and "
                     "lbm_set_fields; training excluded (data %.0f s, training %.0f s)" % (

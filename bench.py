@@ -444,12 +444,25 @@ ACCURACY = {
     "fp32": {"velocity_target": 1e-5, "velocity": "met on every parity case (4e-8 to 3e-7)",
              "mass_target": 1e-10,
              "mass": "missed on the 40x40 rotating-wall annulus (bounded, up to 4.0e-10 over "
-                     "4000 steps with the exact-mass step) and on 1-wide periodic lattices with the "
-                     "default step (3.6e-10; 8.7e-14 with mass_mode=1); met elsewhere"},
+                     "4000 steps with the exact-mass step); met elsewhere (1-wide periodic lattices: "
+                     "3.6e-10 with the plain step, 8.7e-14 with the default exact-mass step)"},
     "fp16": {"velocity_target": 1e-3,
              "velocity": "met on every parity case (2.2e-4 to 3.2e-4); missed on the 1-wide "
                          "periodic column (1.7e-3)"},
     "bf16": {"velocity_target": 1e-3, "velocity": "missed on every parity case (1.6e-3 to 7.3e-3)"},
+    "fp64": {"populations": "within 1e-13 of the oracle, element by element"},
+}
+
+
+ACCURACY_3D = {
+    "fp32": {"velocity_target": 1e-5,
+             "velocity": "met (1.7e-6 to 3.6e-6 with the plain step on the 20^3 sphere array over "
+                         "4000 steps; 2e-8 with the exact-mass step)",
+             "mass_target": 1e-10,
+             "mass": "the plain step this line times (walls at rest) misses it at static curved "
+                     "walls after 2000 steps (4.6e-10 on the 20^3 sphere array; 1.2e-9 after 4000); "
+                     "met with mass_mode=1 (2.3e-12 after 2000 steps, at 8.5x the step time) and by "
+                     "default where walls move (6.5e-11 after 2000 steps on the moving-lid channel)"},
     "fp64": {"populations": "within 1e-13 of the oracle, element by element"},
 }
 
@@ -665,6 +678,7 @@ def run_d3q19(args, emit=True):
         "gpu_launches": args.steps * (per + 2),
         "clocks": clocks,
         "residual_last": last[0] if last else None,
+        "accuracy_vs_oracle": ACCURACY_3D[prec],
     }
     if rank == 0 and not args.no_cpu_baseline:
         import oracle

@@ -161,7 +161,9 @@ struct Const3 {
   C ax, ay, az;
   int32_t nx, ny, nz, px, py, pz;
   int32_t diffuse_mode;
-  int64_t plane;  // N
+  int64_t plane;    // N
+  int64_t n_links;  // the exact-mass variant: where the per-node carries start
+  uint32_t sr_seed; // the exact-mass variant: random-bit seed of the step
 };
 
 // per link: k1, k2, k3, alpha of the folded form of Eq. EqNewBDSC (LinkCoef)
@@ -242,16 +244,148 @@ struct Warp3 {
   C v[kLinkVals3][33];
 };
 
-// Gather, collide and store one fluid node (pull layout).  The collision
-// runs on the pairs (q, opp q): d_q + d_opp carries the even moments and
-// d_q - d_opp the odd ones, so each row of M touches at most ten values
-// and, M being integer and known here at compile time, only its non-zero
-// entries cost an instruction.  A boundary node leaves what its links
-// need in the warp's shared record.
-template <typename C>
+// Double-FP32 numbers (about 48 significant bits from FP32 operations) with
+// the arithmetic operators, so that the collision template below runs in
+// them unchanged: the exact-mass variant's collision.  This GPU runs FP64 at
+// a small fraction of its FP32 rate; the operations are those of
+// lbm::dev::DF.  Its own namespace keeps its fma out of the ordinary lookup
+// of float and double code (argument-dependent lookup finds it for D2).
+namespace df {
+struct D2 {
+  float h, l;
+  D2() = default;
+  __host__ __device__ constexpr D2(float hi, float lo) : h(hi), l(lo) {}
+  __host__ __device__ explicit constexpr D2(double x)
+      : h(static_cast<float>(x)), l(static_cast<float>(x - static_cast<double>(static_cast<float>(x)))) {}
+};
+__device__ __forceinline__ lbm::dev::DF dv(D2 a) { return lbm::dev::DF{a.h, a.l}; }
+__device__ __forceinline__ D2 d2(lbm::dev::DF a) { return D2(a.h, a.l); }
+__device__ __forceinline__ D2 operator+(D2 a, D2 b) { return d2(lbm::dev::df_add(dv(a), dv(b))); }
+__device__ __forceinline__ D2 operator-(D2 a, D2 b) {
+  return d2(lbm::dev::df_add(dv(a), lbm::dev::DF{-b.h, -b.l}));
+}
+__device__ __forceinline__ D2 operator*(D2 a, D2 b) { return d2(lbm::dev::df_mul(dv(a), dv(b))); }
+__device__ __forceinline__ D2 operator/(D2 a, D2 b) { return d2(lbm::dev::df_div(dv(a), dv(b))); }
+__device__ __forceinline__ D2 &operator+=(D2 &a, D2 b) { return a = a + b; }
+__device__ __forceinline__ D2 fma(D2 a, D2 b, D2 c) { return a * b + c; }
+}  // namespace df
+using df::D2;
+
+// lattice weight of direction q in the arithmetic type A
+template <typename A>
+__device__ __forceinline__ A wq3(int q) {
+  return w3<A>(q);
+}
+template <>
+__device__ __forceinline__ D2 wq3<D2>(int q) {
+  return D2(q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0));
+}
+
+// The collision change f' - f of one node from its deviations d (Eq.
+// FluidMacr, Eq. LBEequi, Eq. LBEforce, Eq. MomentPost through M^-1), in
+// the arithmetic type A: ch[1..18] (f'_0 closes the mass instead), and the
+// node's rho - 1, rho and u.  It runs on the pairs (q, opp q): d_q + d_opp
+// carries the even moments and d_q - d_opp the odd ones, so each row of M
+// touches at most ten values and, M being integer and known here at compile
+// time, only its non-zero entries cost an instruction.
+template <typename A>
+__device__ __forceinline__ void collide3(const A (&d)[Q], const Const3<A> &k, A &drho, A &rho,
+                                         A (&u)[3], A (&ch)[Q]) {
+  // Eq. FluidMacr on the pair sums and differences
+  A S[kPairs3], D[kPairs3];
+  drho = d[0];
+#pragma unroll
+  for (int pp = 0; pp < kPairs3; pp++) {
+    S[pp] = d[rep3(pp)] + d[opp3(rep3(pp))];
+    D[pp] = d[rep3(pp)] - d[opp3(rep3(pp))];
+    drho += S[pp];
+  }
+  A j[3] = {A(0), A(0), A(0)};
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int pp = 0; pp < kPairs3; pp++) j[a] = mac3(j[a], cvel3(rep3(pp), a), D[pp]);
+  rho = A(1) + drho;
+  u[0] = (j[0] + A(0.5) * rho * k.ax) / rho;
+  u[1] = (j[1] + A(0.5) * rho * k.ay) / rho;
+  u[2] = (j[2] + A(0.5) * rho * k.az) / rho;
+  const A ux = u[0], uy = u[1], uz = u[2];
+  const A uu = ux * ux + uy * uy + uz * uz, ua = ux * k.ax + uy * k.ay + uz * k.az;
+  // d - d_eq (Eq. LBEequi) and Fbar (Eq. LBEforce), as pair sums (S) and
+  // differences (A); the rest direction alone
+  A NS[kPairs3], NA[kPairs3], FS[kPairs3], FA[kPairs3];
+  const A n0 = d[0] - wq3<A>(0) * (drho - A(1.5) * rho * uu);
+  const A F0 = A(-3) * wq3<A>(0) * rho * ua;
+#pragma unroll
+  for (int pp = 0; pp < kPairs3; pp++) {
+    const int q = rep3(pp);
+    const A cu = mac3(mac3(mac3(A(0), cvel3(q, 0), ux), cvel3(q, 1), uy), cvel3(q, 2), uz);
+    const A ca = mac3(mac3(mac3(A(0), cvel3(q, 0), k.ax), cvel3(q, 1), k.ay), cvel3(q, 2), k.az);
+    const A wr = wq3<A>(q) * rho;
+    NS[pp] = S[pp] - A(2) * wq3<A>(q) * (drho + rho * (A(4.5) * cu * cu - A(1.5) * uu));
+    NA[pp] = D[pp] - A(6) * wr * cu;
+    FS[pp] = A(2) * wr * (A(9) * cu * ca - A(3) * ua);
+    FA[pp] = A(6) * wr * ca;
+  }
+  // m' - m = -s (m - m_eq) + (1 - s/2) M Fbar, scaled by 1/|M_k|^2
+  A dm[Q];
+#pragma unroll
+  for (int r = 0; r < Q; r++) {
+    A a = A(0), b = A(0);
+    if (!odd_row3(r)) {
+      a = mac3(a, m3(r, 0), n0);
+      b = mac3(b, m3(r, 0), F0);
+    }
+#pragma unroll
+    for (int pp = 0; pp < kPairs3; pp++) {
+      a = mac3(a, m3(r, rep3(pp)), odd_row3(r) ? NA[pp] : NS[pp]);
+      b = mac3(b, m3(r, rep3(pp)), odd_row3(r) ? FA[pp] : FS[pp]);
+    }
+    dm[r] = k.f_scaled[r] * b - k.s_scaled[r] * a;
+  }
+  // f' - f = M^T dm: even rows give the same change to q and opp q, odd
+  // rows opposite ones
+  ch[0] = A(0);
+#pragma unroll
+  for (int pp = 0; pp < kPairs3; pp++) {
+    const int q = rep3(pp), qb = opp3(q);
+    A ev = A(0), od = A(0);
+#pragma unroll
+    for (int r = 0; r < Q; r++) {
+      if (odd_row3(r)) od = mac3(od, m3(r, q), dm[r]);
+      else ev = mac3(ev, m3(r, q), dm[r]);
+    }
+    ch[q] = ev + od;
+    ch[qb] = ev - od;
+  }
+}
+
+// The exact-mass variant's extra record per warp: rho - 1, rho, u_x, u_y,
+// u_z of each boundary node in double-FP32 (pairs of rows).
+struct Warp3X {
+  float v[10][33];
+};
+
+// Gather, collide and store one fluid node (pull layout); a boundary node
+// leaves what its links need in the warp's shared record.
+//
+// kExact (FP32 storage): the stored mass must follow the FP64 trajectory to
+// ~1e-10 over thousands of steps where walls move, and a moving wall
+// exchanges mass at a rate set by the populations next to it.  Any rounding
+// that leans the same way step after step shifts that rate: the storage
+// rounding of f' (round to nearest), and equally the FP32 arithmetic of the
+// collision, whose rounding errors repeat every step once the flow is
+// steady.  So the collision change runs in double-FP32 arithmetic (kd: the
+// case's constants as double-FP32 pairs), f'_1..f'_18 are rounded to FP32
+// stochastically, and f'_0 closes the node's mass in double-FP32 plus the
+// node's carry c0 (what FP32 storage dropped from its earlier values);
+// stored rounded to nearest, the new remainder is kept in c0.
+template <typename C, bool kExact = false>
 __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__ dst,
                                       const Const3<C> &k, const int64_t p, const uint32_t fl,
-                                      const uint32_t lb, Warp3<C> &sh, const int lane) {
+                                      const uint32_t lb, Warp3<C> &sh, const int lane,
+                                      float *c0 = nullptr, const uint32_t rs = 0u,
+                                      Warp3X *shx = nullptr, const Const3<D2> *kd = nullptr) {
   const int64_t N = k.plane;
   const Coord3 c = coord3(k, p);
   C d[Q];
@@ -272,87 +406,83 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
       d[q] = src[(fl >> q) & 1u ? tq : nb];
     }
   }
-  // Eq. FluidMacr on the pair sums and differences
-  C S[kPairs3], A[kPairs3];
-  C drho = d[0];
+  C o[Q];
+  if constexpr (kExact) {
+    static_assert(std::is_same<C, float>::value, "the exact-mass variant is FP32 storage");
+    D2 dx[Q], drx, rhx, ux3[3], chx[Q];
 #pragma unroll
-  for (int pp = 0; pp < kPairs3; pp++) {
-    S[pp] = d[rep3(pp)] + d[opp3(rep3(pp))];
-    A[pp] = d[rep3(pp)] - d[opp3(rep3(pp))];
-    drho += S[pp];
-  }
-  C j[3] = {C(0), C(0), C(0)};
+    for (int q = 0; q < Q; q++) dx[q] = D2(d[q], 0.0f);
+    collide3<D2>(dx, *kd, drx, rhx, ux3, chx);
+    // f'_q = f_q + ch_q rounded to FP32 stochastically (16 random bits
+    // each: the halves of the node's nine random words)
+    uint32_t rw[kPairs3];
+    rw[0] = lbm::dev::fmix32(rs);
 #pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int pp = 0; pp < kPairs3; pp++) j[a] = mac3(j[a], cvel3(rep3(pp), a), A[pp]);
-  const C rho = C(1) + drho;
-  const C ux = (j[0] + C(0.5) * rho * k.ax) / rho, uy = (j[1] + C(0.5) * rho * k.ay) / rho,
-          uz = (j[2] + C(0.5) * rho * k.az) / rho;
-  const C uu = ux * ux + uy * uy + uz * uz, ua = ux * k.ax + uy * k.ay + uz * k.az;
-  // d - d_eq (Eq. LBEequi) and Fbar (Eq. LBEforce), as pair sums (S) and
-  // differences (A); the rest direction alone
-  C NS[kPairs3], NA[kPairs3], FS[kPairs3], FA[kPairs3];
-  const C n0 = d[0] - w3<C>(0) * (drho - C(1.5) * rho * uu);
-  const C F0 = C(-3) * w3<C>(0) * rho * ua;
-#pragma unroll
-  for (int pp = 0; pp < kPairs3; pp++) {
-    const int q = rep3(pp);
-    const C cu = mac3(mac3(mac3(C(0), cvel3(q, 0), ux), cvel3(q, 1), uy), cvel3(q, 2), uz);
-    const C ca = mac3(mac3(mac3(C(0), cvel3(q, 0), k.ax), cvel3(q, 1), k.ay), cvel3(q, 2), k.az);
-    const C wr = w3<C>(q) * rho;
-    NS[pp] = S[pp] - C(2) * w3<C>(q) * (drho + rho * (C(4.5) * cu * cu - C(1.5) * uu));
-    NA[pp] = A[pp] - C(6) * wr * cu;
-    FS[pp] = C(2) * wr * (C(9) * cu * ca - C(3) * ua);
-    FA[pp] = C(6) * wr * ca;
-  }
-  // m' - m = -s (m - m_eq) + (1 - s/2) M Fbar, scaled by 1/|M_k|^2
-  C dm[Q];
-#pragma unroll
-  for (int r = 0; r < Q; r++) {
-    C a = C(0), b = C(0);
-    if (!odd_row3(r)) {
-      a = mac3(a, m3(r, 0), n0);
-      b = mac3(b, m3(r, 0), F0);
-    }
+    for (int pp = 1; pp < kPairs3; pp++) rw[pp] = lbm::dev::fmix32(rw[0] + 0x9E3779B9u * pp);
 #pragma unroll
     for (int pp = 0; pp < kPairs3; pp++) {
-      a = mac3(a, m3(r, rep3(pp)), odd_row3(r) ? NA[pp] : NS[pp]);
-      b = mac3(b, m3(r, rep3(pp)), odd_row3(r) ? FA[pp] : FS[pp]);
+      const int q = rep3(pp), qb = opp3(q);
+      const D2 vq = dx[q] + chx[q], vb = dx[qb] + chx[qb];
+      o[q] = lbm::dev::add_stochastic(vq.h, vq.l, rw[pp] & 0xFFFFu);
+      o[qb] = lbm::dev::add_stochastic(vb.h, vb.l, rw[(pp + 4) % kPairs3] >> 16);
     }
-    dm[r] = k.f_scaled[r] * b - k.s_scaled[r] * a;
-  }
-  // f' - f = M^T dm: even rows give the same change to q and opp q, odd
-  // rows opposite ones; f'_0 closes the mass from the stored changes
-  C o[Q];
-  C sum = C(0);
-#pragma unroll
-  for (int pp = 0; pp < kPairs3; pp++) {
-    const int q = rep3(pp), qb = opp3(q);
-    C ev = C(0), od = C(0);
-#pragma unroll
-    for (int r = 0; r < Q; r++) {
-      if (odd_row3(r)) od = mac3(od, m3(r, q), dm[r]);
-      else ev = mac3(ev, m3(r, q), dm[r]);
-    }
-    o[q] = d[q] + (ev + od);
-    o[qb] = d[qb] + (ev - od);
-    sum += (o[q] - d[q]) + (o[qb] - d[qb]);
-  }
-  o[0] = d[0] - sum;
-#pragma unroll
-  for (int q = 0; q < Q; q++) dst[q * N + p] = o[q];
-  if (fl) {
+    // f'_0 = f_0 - sum (f'_q - f_q) plus the carry, in double-FP32 (each
+    // change is the exact difference of two FP32 values); stored rounded to
+    // nearest, the remainder kept
+    D2 sum(0.0f, 0.0f);
 #pragma unroll
     for (int q = 1; q < Q; q++) {
-      sh.v[q - 1][lane] = o[q];
-      sh.v[Q - 2 + q][lane] = d[q];
+      float h, l;
+      lbm::dev::two_sum(o[q], -d[q], h, l);
+      sum += D2(h, l);
     }
-    sh.v[36][lane] = drho;
-    sh.v[37][lane] = rho;
-    sh.v[38][lane] = ux;
-    sh.v[39][lane] = uy;
-    sh.v[40][lane] = uz;
+    const D2 v0 = (dx[0] - sum) + D2(*c0, 0.0f);
+    float e0;
+    lbm::dev::two_sum(v0.h, v0.l, o[0], e0);
+    *c0 = e0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) dst[q * N + p] = o[q];
+    if (fl) {
+#pragma unroll
+      for (int q = 1; q < Q; q++) {
+        sh.v[q - 1][lane] = o[q];
+        sh.v[Q - 2 + q][lane] = d[q];
+      }
+      // rho - 1, rho and u as pairs of FP32 values for the links
+      const D2 nv[5] = {drx, rhx, ux3[0], ux3[1], ux3[2]};
+#pragma unroll
+      for (int i = 0; i < 5; i++) {
+        shx->v[2 * i][lane] = nv[i].h;
+        shx->v[2 * i + 1][lane] = nv[i].l;
+      }
+    }
+  } else {
+    C drho, rho, u[3], ch[Q];
+    collide3<C>(d, k, drho, rho, u, ch);
+    // f'_0 closes the mass from the stored changes
+    C sum = C(0);
+#pragma unroll
+    for (int pp = 0; pp < kPairs3; pp++) {
+      const int q = rep3(pp), qb = opp3(q);
+      o[q] = d[q] + ch[q];
+      o[qb] = d[qb] + ch[qb];
+      sum += (o[q] - d[q]) + (o[qb] - d[qb]);
+    }
+    o[0] = d[0] - sum;
+#pragma unroll
+    for (int q = 0; q < Q; q++) dst[q * N + p] = o[q];
+    if (fl) {
+#pragma unroll
+      for (int q = 1; q < Q; q++) {
+        sh.v[q - 1][lane] = o[q];
+        sh.v[Q - 2 + q][lane] = d[q];
+      }
+      sh.v[36][lane] = drho;
+      sh.v[37][lane] = rho;
+      sh.v[38][lane] = u[0];
+      sh.v[39][lane] = u[1];
+      sh.v[40][lane] = u[2];
+    }
   }
 }
 
@@ -362,13 +492,18 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
 // warp spreads them over its lanes, one link per lane, each reading its
 // node's values from the warp's shared record -- the links of a node
 // cluster would otherwise run direction by direction on few lanes.
-template <typename C>
-__global__ void __launch_bounds__(kThreads3, sizeof(C) == 4 ? 8 : 2)
+// kExact: 128 registers and 4 CTAs per SM (the double-FP32 collision is
+// issue-bound; fewer resident warps, or more spills, measured slower).
+template <typename C, bool kExact = false>
+__global__ void __launch_bounds__(kThreads3, kExact ? 4 : (sizeof(C) == 4 ? 8 : 2))
 step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
              const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
-             const uint2 *__restrict__ fluid, const Const3<C> k, int64_t n_fluid) {
+             const uint2 *__restrict__ fluid, const __grid_constant__ Const3<C> k, int64_t n_fluid,
+             const lbm::LinkCoefDF *__restrict__ links_df = nullptr, float *carry = nullptr,
+             const __grid_constant__ Const3<D2> kd = Const3<D2>()) {
   constexpr int kW = kThreads3 / 32;
   __shared__ Warp3<C> sh[kW];
+  __shared__ Warp3X shx[kExact ? kW : 1];
   __shared__ uint32_t sh_ex[kW][32], sh_fl[kW][32];
   // thread t of the launch runs the t-th fluid node (node order), so no
   // lane idles on a solid node
@@ -380,7 +515,15 @@ step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__r
   const uint32_t fl = pf.y;
   const bool live = fl != kSolid3;
   const uint32_t lb = live && fl ? lbase[p] : 0u;
-  if (live) node3(src, dst, k, p, fl, lb, sh[w], lane);
+  // the exact-mass variant's carries: one per link, then one per fluid node
+  float *carry0 = kExact ? carry + k.n_links : nullptr;
+  if (live) {
+    if constexpr (kExact)
+      node3<C, true>(src, dst, k, p, fl, lb, sh[w], lane, carry0 + t0,
+                     static_cast<uint32_t>(t0) ^ k.sr_seed, &shx[w], &kd);
+    else
+      node3<C, false>(src, dst, k, p, fl, lb, sh[w], lane);
+  }
   const uint32_t nl = live ? static_cast<uint32_t>(__popc(fl)) : 0u;
   const unsigned any = __ballot_sync(0xFFFFFFFFu, nl != 0u);
   if (any == 0u) return;
@@ -407,25 +550,70 @@ step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__r
     uint32_t m = sh_fl[w][s];
     for (uint32_t r = t - sh_ex[w][s]; r; r--) m &= m - 1u;
     const int j = __ffs(static_cast<int>(m)) - 1, jb = opp3_rt(j);
-    const Link3<C> cl = links[base + t];
     const C oj = ws.v[j - 1][s], ojb = ws.v[jb - 1][s], djb = ws.v[Q - 2 + jb][s];
-    const C drho = ws.v[36][s], rho = ws.v[37][s], ux = ws.v[38][s], uy = ws.v[39][s],
-            uz = ws.v[40][s];
-    const C uu = ux * ux + uy * uy + uz * uz;
-    const C wj = j < 7 ? C(1) / C(18) : C(1) / C(36);
-    const C r = cl.k1 + cl.k2 + cl.k3;
-    C c0, c2;
-    if (k.diffuse_mode == 0) {
-      c0 = cl.alpha;
-      c2 = (C(1) - r) * wj;
+    if constexpr (kExact) {
+      // Eq. EqNewBDSC in double-FP32 from the pairs of the FP64
+      // coefficients and the node's double-FP32 rho - 1, rho, u, plus the
+      // link's carry; stored rounded to nearest, the remainder kept
+      using lbm::dev::DF;
+      using lbm::dev::df_add;
+      using lbm::dev::df_mul;
+      using lbm::dev::df_mul_f;
+      const Warp3X &wx = shx[w];
+      const lbm::LinkCoefDF c = links_df[base + t];
+      const DF k1{c.hi[0], c.lo[0]}, k2{c.hi[1], c.lo[1]}, k3{c.hi[2], c.lo[2]},
+          al{c.hi[3], c.lo[3]};
+      const double wd = j < 7 ? 1.0 / 18 : 1.0 / 36;
+      const DF w2{static_cast<float>(wd), static_cast<float>(wd - static_cast<float>(wd))};
+      const DF drho2{wx.v[0][s], wx.v[1][s]}, rho2{wx.v[2][s], wx.v[3][s]};
+      const DF u2[3] = {{wx.v[4][s], wx.v[5][s]}, {wx.v[6][s], wx.v[7][s]}, {wx.v[8][s], wx.v[9][s]}};
+      const DF uu2 = df_add(df_add(df_mul(u2[0], u2[0]), df_mul(u2[1], u2[1])), df_mul(u2[2], u2[2]));
+      const DF r = df_add(df_add(k1, k2), k3);
+      DF c0, c2;
+      if (k.diffuse_mode == 0) {
+        c0 = al;
+        c2 = df_mul(df_add(DF{1.0f, 0.0f}, DF{-r.h, -r.l}), w2);
+      } else {
+        c0 = df_add(al, df_mul(df_add(r, DF{-1.0f, 0.0f}), w2));
+        c2 = DF{0.0f, 0.0f};
+      }
+      DF cu{0.0f, 0.0f};
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const float ca = static_cast<float>(cvel3_rt(j, a));
+        cu = df_add(cu, DF{ca * u2[a].h, ca * u2[a].l});
+      }
+      const DF pj = df_add(df_add(df_mul_f(cu, 3.0f), df_mul_f(df_mul(cu, cu), 4.5f)),
+                           df_mul_f(uu2, -1.5f));
+      DF v = df_add(df_mul_f(k1, djb), df_mul_f(k2, oj));
+      v = df_add(v, df_mul_f(k3, ojb));
+      v = df_add(v, c0);
+      v = df_add(v, df_mul(al, drho2));
+      v = df_add(v, df_mul(c2, df_add(drho2, df_mul(rho2, pj))));
+      v = df_add(v, DF{carry[base + t], 0.0f});
+      const float tv = __fadd_rn(v.h, v.l);
+      carry[base + t] = __fadd_rn(__fadd_rn(v.h, -tv), v.l);
+      dst[19 * k.plane + base + t] = tv;
     } else {
-      c0 = cl.alpha + (r - C(1)) * wj;
-      c2 = C(0);
+      const Link3<C> cl = links[base + t];
+      const C drho = ws.v[36][s], rho = ws.v[37][s], ux = ws.v[38][s], uy = ws.v[39][s],
+              uz = ws.v[40][s];
+      const C uu = ux * ux + uy * uy + uz * uz;
+      const C wj = j < 7 ? C(1) / C(18) : C(1) / C(36);
+      const C r = cl.k1 + cl.k2 + cl.k3;
+      C c0, c2;
+      if (k.diffuse_mode == 0) {
+        c0 = cl.alpha;
+        c2 = (C(1) - r) * wj;
+      } else {
+        c0 = cl.alpha + (r - C(1)) * wj;
+        c2 = C(0);
+      }
+      const C cu = C(cvel3_rt(j, 0)) * ux + C(cvel3_rt(j, 1)) * uy + C(cvel3_rt(j, 2)) * uz;
+      const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
+      dst[19 * k.plane + base + t] = cl.k1 * djb + cl.k2 * oj + cl.k3 * ojb + c0 +
+                                     cl.alpha * drho + c2 * (drho + rho * pj);
     }
-    const C cu = C(cvel3_rt(j, 0)) * ux + C(cvel3_rt(j, 1)) * uy + C(cvel3_rt(j, 2)) * uz;
-    const C pj = C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu;
-    dst[19 * k.plane + base + t] = cl.k1 * djb + cl.k2 * oj + cl.k3 * ojb + c0 +
-                                   cl.alpha * drho + c2 * (drho + rho * pj);
   }
 }
 
@@ -589,6 +777,7 @@ __global__ void import3_kernel(const double *__restrict__ in, const uint32_t *__
 struct Const3Both {
   Const3<double> d;
   Const3<float> f;
+  Const3<D2> x;  // the FP32 exact-mass variant's collision constants
   Const3<double> &get(double *) { return d; }
   Const3<float> &get(float *) { return f; }
   const Const3<double> &get(double *) const { return d; }
@@ -615,6 +804,11 @@ struct lbm3d {
   uint32_t *flags = nullptr;
   uint32_t *lbase = nullptr;
   uint2 *fluid = nullptr;  // the fluid nodes in node order: index, flag word
+  // the exact-mass variant (FP32): link coefficients as FP32 pairs and the
+  // carries (one per link, then one per fluid node)
+  int exact = 0;
+  lbm::LinkCoefDF *links_df = nullptr;
+  float *carry = nullptr;
   void *links = nullptr;
   Const3Both kc;
   double *partials = nullptr, *result = nullptr;
@@ -636,7 +830,8 @@ void release3(lbm3d_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->flags), static_cast<void *>(h->lbase),
-                  static_cast<void *>(h->fluid),
+                  static_cast<void *>(h->fluid), static_cast<void *>(h->links_df),
+                  static_cast<void *>(h->carry),
                   h->links, static_cast<void *>(h->partials),
                   static_cast<void *>(h->result)})
     if (p) cudaFree(p);
@@ -670,6 +865,8 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
   if (p.diffuse_mode != 0 && p.diffuse_mode != 1)
     return fail3(nullptr, LBM_EINVAL, "diffuse_mode must be 0 or 1");
   if (p.collision != 0) return fail3(nullptr, LBM_EINVAL, "the 3-D solver is MRT only");
+  if (p.mass_mode < -1 || p.mass_mode > 1)
+    return fail3(nullptr, LBM_EINVAL, "mass_mode must be -1, 0 or 1");
   const int32_t nx = dom->nx, ny = dom->ny, nz = dom->nz;
   if (nx < 1 || ny < 1 || nz < 1) return fail3(nullptr, LBM_EINVAL, "nx, ny, nz must be >= 1");
   const int64_t n = static_cast<int64_t>(nx) * ny * nz;
@@ -812,25 +1009,51 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
         lk[slot[k]] = Link3<C>{static_cast<C>(cf[0]), static_cast<C>(cf[1]), static_cast<C>(cf[2]),
                                static_cast<C>(cf[3])};
       }
-      Const3<C> &kc = h->kc.get(tag);
-      for (int a = 0; a < Q; a++) {
-        const double s = 1.0 / tau[a];
-        kc.s_scaled[a] = static_cast<C>(s / L.norm[a]);
-        kc.f_scaled[a] = static_cast<C>((1.0 - 0.5 * s) / L.norm[a]);
-      }
-      kc.ax = static_cast<C>(dom->ax);
-      kc.ay = static_cast<C>(dom->ay);
-      kc.az = static_cast<C>(dom->az);
-      kc.nx = nx;
-      kc.ny = ny;
-      kc.nz = nz;
-      kc.px = per[0];
-      kc.py = per[1];
-      kc.pz = per[2];
-      kc.diffuse_mode = p.diffuse_mode;
-      kc.plane = h->plane;
+      // the case's constants in each arithmetic type (the FP32 exact-mass
+      // variant collides in double-FP32)
+      auto fill = [&](auto &kc) {
+        using A = std::remove_reference_t<decltype(kc.ax)>;
+        for (int a = 0; a < Q; a++) {
+          const double s = 1.0 / tau[a];
+          kc.s_scaled[a] = static_cast<A>(s / L.norm[a]);
+          kc.f_scaled[a] = static_cast<A>((1.0 - 0.5 * s) / L.norm[a]);
+        }
+        kc.ax = static_cast<A>(dom->ax);
+        kc.ay = static_cast<A>(dom->ay);
+        kc.az = static_cast<A>(dom->az);
+        kc.nx = nx;
+        kc.ny = ny;
+        kc.nz = nz;
+        kc.px = per[0];
+        kc.py = per[1];
+        kc.pz = per[2];
+        kc.diffuse_mode = p.diffuse_mode;
+        kc.plane = h->plane;
+        kc.n_links = h->n_links;
+        kc.sr_seed = 0u;
+      };
+      fill(h->kc.f);
+      fill(h->kc.d);
+      fill(h->kc.x);
       return cudaMemcpy(h->links, lk.data(), lk.size() * sizeof(Link3<C>), cudaMemcpyHostToDevice);
     });
+  // the exact-mass variant (FP32): where mass_mode asks for it, or by
+  // default where a wall moves or the lattice has no boundary links
+  bool moving = false;
+  for (size_t k = 0; k < 3 * n_links && !moving; k++) moving = link_ub[k] != 0.0;
+  h->exact = p.precision == LBM_FP32 && p.mass_mode >= 0 &&
+             (p.mass_mode > 0 || moving || n_links == 0);
+  if (e == cudaSuccess && h->exact) {
+    std::vector<lbm::LinkCoefDF> ldf(std::max<size_t>(1, n_links));
+    for (size_t k = 0; k < n_links; k++) ldf[slot[k]] = lbm::link_coef_df(&coef[8 * k]);
+    e = alloc(reinterpret_cast<void **>(&h->links_df), ldf.size() * sizeof(lbm::LinkCoefDF));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->links_df, ldf.data(), ldf.size() * sizeof(lbm::LinkCoefDF),
+                     cudaMemcpyHostToDevice);
+    const size_t nc = std::max<size_t>(1, n_links) + static_cast<size_t>(n_fluid);
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&h->carry), nc * 4);
+    if (e == cudaSuccess) e = cudaMemset(h->carry, 0, nc * 4);
+  }
   if (e != cudaSuccess) {
     const int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
     g_err3 = std::string("device setup: ") + cudaGetErrorString(e);
@@ -850,11 +1073,21 @@ int lbm3d_step(lbm3d_t *h, int64_t n) {
     cudaError_t e = dispatch3(h->precision, [&](auto tag) {
       using C = std::remove_pointer_t<decltype(tag)>;
       if (h->n_fluid == 0) return cudaSuccess;
-      step3_kernel<C><<<static_cast<unsigned>((h->n_fluid + kThreads3 - 1) / kThreads3), kThreads3,
-                        0, h->stream>>>(static_cast<const C *>(h->f[src]),
-                                        static_cast<C *>(h->f[dst]), h->flags, h->lbase,
-                                        static_cast<const Link3<C> *>(h->links), h->fluid,
-                                        h->kc.get(tag), h->n_fluid);
+      const unsigned blocks = static_cast<unsigned>((h->n_fluid + kThreads3 - 1) / kThreads3);
+      if constexpr (std::is_same<C, float>::value) {
+        if (h->exact) {
+          Const3<C> kx = h->kc.get(tag);
+          kx.sr_seed = lbm::dev::step_seed(h->steps);
+          step3_kernel<C, true><<<blocks, kThreads3, 0, h->stream>>>(
+              static_cast<const C *>(h->f[src]), static_cast<C *>(h->f[dst]), h->flags, h->lbase,
+              static_cast<const Link3<C> *>(h->links), h->fluid, kx, h->n_fluid, h->links_df,
+              h->carry, h->kc.x);
+          return cudaGetLastError();
+        }
+      }
+      step3_kernel<C><<<blocks, kThreads3, 0, h->stream>>>(
+          static_cast<const C *>(h->f[src]), static_cast<C *>(h->f[dst]), h->flags, h->lbase,
+          static_cast<const Link3<C> *>(h->links), h->fluid, h->kc.get(tag), h->n_fluid);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return fail3(h, LBM_ECUDA, std::string("step: ") + cudaGetErrorString(e));
@@ -922,6 +1155,9 @@ int lbm3d_set_f(lbm3d_t *h, const double *f) {
           d, h->flags, h->lbase, h->kc.get(tag), h->n_nodes, static_cast<C *>(h->f[b]));
       return cudaGetLastError();
     });
+  if (e == cudaSuccess && h->carry)  // a new state owes no carries
+    e = cudaMemsetAsync(h->carry, 0, (std::max<int64_t>(1, h->n_links) + h->n_fluid) * 4,
+                        h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (d) cudaFree(d);
   if (e != cudaSuccess) return fail3(h, LBM_ECUDA, std::string("set_f: ") + cudaGetErrorString(e));

@@ -184,6 +184,20 @@ __device__ __forceinline__ float add_stochastic(float a, float b, uint32_t u16) 
   return static_cast<float>(u16) * 0x1p-16f * fabsf(s2 - s) < fabsf(e) ? s2 : s;
 }
 
+// x rounded to FP32 stochastically: the nearest FP32 value s or its
+// neighbour on the side of the remainder e = x - s (exact in FP64), taken
+// with probability |e| / (spacing there), so the result is x on average.
+// u16: 16 random bits.
+__device__ __forceinline__ float round_stochastic(double x, uint32_t u16) {
+  const float s = __double2float_rn(x);
+  const double e = x - static_cast<double>(s);
+  if (e == 0.0 || s == 0.0f) return s;
+  const int bits = __float_as_int(s);
+  const float s2 = __int_as_float(((e > 0.0) == (s > 0.0f)) ? bits + 1 : bits - 1);
+  return static_cast<double>(u16) * 0x1p-16 * fabs(static_cast<double>(s2) - s) < fabs(e) ? s2
+                                                                                          : s;
+}
+
 // Double-FP32 values h + l with |l| <= ulp(h) / 2 (Dekker's double-length
 // arithmetic, 1971): about 48 significant bits from FP32 operations alone.
 // The exact-mass link values use them instead of FP64, which this GPU runs

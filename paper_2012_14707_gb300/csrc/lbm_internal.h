@@ -94,12 +94,15 @@ struct HostCase {
   bool moving_walls = false;           // some link has a nonzero wall velocity
 };
 // FP32 storage runs the exact-mass variant of the step (collide,
-// link_epilogue_pull: FP64 link values and rest-population closure, each
-// with a carry of what FP32 storage dropped) where a wall moves, or always
-// with params.mass_mode = 1 (never with -1).
+// link_epilogue_pull: double-FP32 link values and rest-population closure,
+// each with a carry of what FP32 storage dropped) always with
+// params.mass_mode = 1, never with -1, and by default where a wall moves or
+// the lattice has no boundary links (a periodic lattice whose flow tends to
+// be uniform, so that every node rounds the same values the same way and
+// nothing averages out).
 inline bool exact_mass(const HostCase &hc) {
   if (hc.params.precision != LBM_FP32 || hc.params.mass_mode < 0) return false;
-  return hc.params.mass_mode > 0 || hc.moving_walls;
+  return hc.params.mass_mode > 0 || hc.moving_walls || hc.n_links == 0;
 }
 
 // Bits above the flag byte in a compacted lattice's node word (.x; the

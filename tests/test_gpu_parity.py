@@ -131,7 +131,8 @@ def test_fp64_scheme_variants_match_oracle(l_mode, extra):
 MOVING_WALLS = {"annulus", "channel_moving"}
 # lattices without walls whose flow is uniform (every node rounds the same
 # values the same way, so nothing averages out over nodes): FP32 meets the
-# mass target there with the exact-mass step, which they request
+# mass target there with the exact-mass step, which the default takes on
+# every lattice without boundary links
 UNIFORM = {"box", "column", "row"}
 
 
@@ -157,12 +158,10 @@ def test_fp32_velocity_and_mass_match_oracle(name):
     M_oracle(0) <= 1e-10, the FP32 targets, on every case.  Moving walls
     switch the exact-mass step on by themselves (link values in double-FP32
     arithmetic and the rest population's closure, each with a carry of what
-    FP32 storage dropped); the uniform periodic lattices ask for it
-    (mass_mode = 1); the others run the plain step."""
+    FP32 storage dropped); so do lattices without boundary links (the
+    uniform periodic ones); the others run the plain step."""
     c = CASES[name]()
     kw = dict(L1=1.0, L2=0.0) if name == "annulus" else {}
-    if name in UNIFORM:
-        kw["mass_mode"] = 1
     o, g = _pair(c, "fp32", **kw)
     assert g.info().exact_mass == (1 if name in MOVING_WALLS | UNIFORM else 0)
     m0 = o.residual()[1]

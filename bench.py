@@ -254,8 +254,9 @@ def run_ours(args, emit=True):
     else:
         case = cases.config_throughput(seed=rank)
     stream = torch.cuda.current_stream(dev)
+    mkw = {} if args.mass_mode is None else {"mass_mode": args.mass_mode}
     solver = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
-                        residual_every=args.lbm_steps)
+                        residual_every=args.lbm_steps, **mkw)
     info = solver.info()
     n_fluid = info.n_fluid
     per = args.lbm_steps
@@ -298,11 +299,15 @@ def run_ours(args, emit=True):
     updates = total_fluid * per * args.steps
     mlups = updates / (elapsed_ms / 1e3) / 1e6
     launch_ms = kernel_ms / (args.steps * per)
-    alg_bytes = FLUID_BYTES[args.precision] * n_fluid
+    # the exact-mass step also reads and writes a carry per fluid node and
+    # per link (4 B each way)
+    exact = bool(info.exact_mass)
+    node_bytes = FLUID_BYTES[args.precision] + (8 + 8 * info.n_links / n_fluid if exact else 0)
+    alg_bytes = node_bytes * n_fluid
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     # the same algorithmic bytes over the whole bench step (lattice steps,
     # residual pass and its read-back: the time the MLUPS figure counts)
-    step_achieved = FLUID_BYTES[args.precision] * mlups * 1e6 / world / 1e9
+    step_achieved = node_bytes * mlups * 1e6 / world / 1e9
     peak, peak_src = _peak_hbm()
     solver.close()
 
@@ -319,7 +324,8 @@ def run_ours(args, emit=True):
         try:
             with open(prof) as fh:
                 pj = json.load(fh)
-            if pj.get("precision") == args.precision and pj.get("kernel_rev") == KERNEL_REV:
+            if (pj.get("precision") == args.precision and pj.get("kernel_rev") == KERNEL_REV
+                    and not exact):
                 traffic = pj.get("bytes_per_launch_full_size")
         except (OSError, ValueError):
             traffic = None
@@ -333,12 +339,14 @@ def run_ours(args, emit=True):
         "config": {"workload": f"cylinders_{case.nx}x{case.ny}_phi0.7_Kn0.02",
                    "nx": case.nx, "ny": case.ny, "n_fluid": n_fluid, "n_links": case.n_links,
                    "precision": args.precision, "lattice_steps_per_step": per,
+                   "exact_mass_step": exact,
                    "l2": "inputs larger than L2 (2 x %.2f GB lattices of fluid nodes)" % (
                        9 * ((n_fluid + 31) // 32 * 32) * ELEM_BYTES[args.precision] / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": ({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                       "frac": achieved / peak, "traffic": traffic,
-                      "kernel": "step_kernel", "bytes_per_fluid_node": FLUID_BYTES[args.precision],
+                      "kernel": "step_kernel_pull<float, float, 1> (exact-mass)" if exact
+                                else "step_kernel", "bytes_per_fluid_node": node_bytes,
                       "launch_ms": launch_ms, "peak_source": peak_src,
                       "step_achieved": step_achieved, "step_frac": step_achieved / peak,
                       "step_note": "same algorithmic bytes over the whole bench step (residual "
@@ -415,8 +423,9 @@ def _e2e(args, case, stream, per, world, n_fluid, lbm, torch, dev=None):
         import torch.distributed as dist
         dist.barrier()
     t0 = time.perf_counter()
+    mkw = {} if args.mass_mode is None else {"mass_mode": args.mass_mode}
     s2 = lbm.Solver(case, precision=args.precision, stream=stream.cuda_stream,
-                    residual_every=per)
+                    residual_every=per, **mkw)
     for _ in range(args.steps):
         s2.step(per)
         s2.residual()
@@ -620,7 +629,10 @@ def run_d3q19(args, emit=True):
                                Kn=0.02, a=(1e-6, 0.0, 0.0))
     stream = torch.cuda.current_stream(dev)
     prec = args.precision if args.precision in D3Q19_BYTES else "fp32"
-    sv = lbm.Solver3D(case, precision=prec, stream=stream.cuda_stream)
+    mkw = {} if args.mass_mode is None else {"mass_mode": args.mass_mode}
+    sv = lbm.Solver3D(case, precision=prec, stream=stream.cuda_stream, **mkw)
+    # the sphere pack's walls are at rest: the exact-mass step only on request
+    exact3 = prec == "fp32" and args.mass_mode == 1
     per = args.lbm_steps
     n_fluid = case.n_fluid
     for _ in range(args.warmup):
@@ -654,8 +666,11 @@ def run_d3q19(args, emit=True):
     sv.close()
     mlups = total_fluid * per * args.steps / (elapsed_ms / 1e3) / 1e6
     launch_ms = kernel_ms / (args.steps * per)
-    achieved = D3Q19_BYTES[prec] * n_fluid / (launch_ms / 1e3) / 1e9
-    step_achieved = D3Q19_BYTES[prec] * mlups * 1e6 / world / 1e9
+    # the exact-mass step also reads and writes a carry per fluid node and
+    # per link (4 B each way)
+    node_bytes = D3Q19_BYTES[prec] + (8 + 8 * case.n_links / n_fluid if exact3 else 0)
+    achieved = node_bytes * n_fluid / (launch_ms / 1e3) / 1e9
+    step_achieved = node_bytes * mlups * 1e6 / world / 1e9
     peak, peak_src = _peak_hbm()
     line = {
         "metric": "MLUPS (D3Q19)", "value": mlups, "unit": "MLUPS", "n_gpus": world,
@@ -665,13 +680,15 @@ def run_d3q19(args, emit=True):
         "config": {"workload": f"spheres3d_{nx}x{ny}x{nz}_phi0.8_Kn0.02", "nx": nx, "ny": ny,
                    "nz": nz, "n_fluid": n_fluid, "n_links": case.n_links,
                    "n_spheres": case.meta["n_spheres"], "precision": prec,
-                   "lattice_steps_per_step": per,
+                   "lattice_steps_per_step": per, "exact_mass_step": exact3,
                    "l2": "inputs larger than L2 (2 x %.2f GB dense lattices)" % (
                        19 * nx * ny * nz * D3Q19_BYTES[prec] / 38 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "step3_kernel",
-                     "bytes_per_fluid_node": D3Q19_BYTES[prec], "launch_ms": launch_ms,
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "step3_kernel<float, true> (exact-mass; issue-bound double-FP32 "
+                               "arithmetic)" if exact3 else "step3_kernel",
+                     "bytes_per_fluid_node": node_bytes, "launch_ms": launch_ms,
                      "peak_source": peak_src, "step_achieved": step_achieved,
                      "step_frac": step_achieved / peak},
         "e2e": None,
@@ -920,6 +937,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "fp64", "bf16", "fp16"), default="fp32")
+    ap.add_argument("--mass-mode", type=int, choices=(-1, 0, 1), default=None,
+                    help="FP32 params.mass_mode (default: the library's, 0); 1 times the "
+                         "exact-mass step")
     ap.add_argument("--lbm-steps", type=int, default=100,
                     help="lattice steps per benchmark step (the residual interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

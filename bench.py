@@ -466,12 +466,12 @@ ACCURACY = {
 ACCURACY_3D = {
     "fp32": {"velocity_target": 1e-5,
              "velocity": "met (1.7e-6 to 3.6e-6 with the plain step on the 20^3 sphere array over "
-                         "4000 steps; 2e-8 with the exact-mass step)",
+                         "4000 steps; 2e-8 to 4e-8 with the exact-mass step)",
              "mass_target": 1e-10,
              "mass": "the plain step this line times (walls at rest) misses it at static curved "
                      "walls after 2000 steps (4.6e-10 on the 20^3 sphere array; 1.2e-9 after 4000); "
-                     "met with mass_mode=1 (2.3e-12 after 2000 steps, at 8.5x the step time) and by "
-                     "default where walls move (6.5e-11 after 2000 steps on the moving-lid channel)"},
+                     "met with mass_mode=1 (2.3e-11 after 2000 steps, at 4.3x the step time) and by "
+                     "default where walls move (1.0e-11 after 2000 steps on the moving-lid channel)"},
     "fp64": {"populations": "within 1e-13 of the oracle, element by element"},
 }
 
@@ -686,8 +686,8 @@ def run_d3q19(args, emit=True):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "step3_kernel<float, true> (exact-mass; issue-bound double-FP32 "
-                               "arithmetic)" if exact3 else "step3_kernel",
+                     "kernel": "step3_kernel<float, true> (exact-mass; issue-bound, d - d_eq in "
+                               "double-FP32)" if exact3 else "step3_kernel",
                      "bytes_per_fluid_node": node_bytes, "launch_ms": launch_ms,
                      "peak_source": peak_src, "step_achieved": step_achieved,
                      "step_frac": step_achieved / peak},

@@ -281,6 +281,12 @@ __device__ __forceinline__ D2 wq3<D2>(int q) {
   return D2(q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0));
 }
 
+template <typename A>
+__device__ __forceinline__ void transform3(const A n0, const A F0, const A (&NS)[kPairs3],
+                                           const A (&NA)[kPairs3], const A (&FS)[kPairs3],
+                                           const A (&FA)[kPairs3], const Const3<A> &k,
+                                           A (&ch)[Q]);
+
 // The collision change f' - f of one node from its deviations d (Eq.
 // FluidMacr, Eq. LBEequi, Eq. LBEforce, Eq. MomentPost through M^-1), in
 // the arithmetic type A: ch[1..18] (f'_0 closes the mass instead), and the
@@ -327,6 +333,17 @@ __device__ __forceinline__ void collide3(const A (&d)[Q], const Const3<A> &k, A 
     FS[pp] = A(2) * wr * (A(9) * cu * ca - A(3) * ua);
     FA[pp] = A(6) * wr * ca;
   }
+  transform3<A>(n0, F0, NS, NA, FS, FA, k, ch);
+}
+
+// The second half of the collision: from d - d_eq and Fbar as pair sums
+// (NS, FS) and differences (NA, FA) plus the rest direction's (n0, F0), the
+// change ch[q] = f'_q - f_q (ch[0] = 0).
+template <typename A>
+__device__ __forceinline__ void transform3(const A n0, const A F0, const A (&NS)[kPairs3],
+                                           const A (&NA)[kPairs3], const A (&FS)[kPairs3],
+                                           const A (&FA)[kPairs3], const Const3<A> &k,
+                                           A (&ch)[Q]) {
   // m' - m = -s (m - m_eq) + (1 - s/2) M Fbar, scaled by 1/|M_k|^2
   A dm[Q];
 #pragma unroll
@@ -360,6 +377,59 @@ __device__ __forceinline__ void collide3(const A (&d)[Q], const Const3<A> &k, A 
   }
 }
 
+// The exact-mass variant's first half of the collision (FP32 storage).  The
+// pair sums and d_eq are ~100 times their difference d - d_eq, so the FP32
+// rounding errors of the former become relative errors of ~1e-5 of the
+// latter, and in a steady flow they repeat every step; so rho - 1, j, rho,
+// u and d - d_eq are formed in double-FP32 (the pair sums exactly, by
+// TwoSum) and d - d_eq is rounded once to FP32 for the transform.  Fbar,
+// proportional to the body force and orders of magnitude smaller, stays in
+// FP32.  rho - 1, rho and u are returned in double-FP32 for the links.
+__device__ __forceinline__ float to_f(D2 x) { return __fadd_rn(x.h, x.l); }
+__device__ __forceinline__ void exact_moments3(const float (&d)[Q], const Const3<D2> &kd, D2 &drho,
+                                               D2 &rho, D2 (&u)[3], float &n0, float &F0,
+                                               float (&NS)[kPairs3], float (&NA)[kPairs3],
+                                               float (&FS)[kPairs3], float (&FA)[kPairs3]) {
+  D2 S[kPairs3], Dd[kPairs3];
+  drho = D2(d[0], 0.0f);
+#pragma unroll
+  for (int pp = 0; pp < kPairs3; pp++) {
+    const int q = rep3(pp), qb = opp3(q);
+    float h, l;
+    lbm::dev::two_sum(d[q], d[qb], h, l);
+    S[pp] = D2(h, l);
+    lbm::dev::two_sum(d[q], -d[qb], h, l);
+    Dd[pp] = D2(h, l);
+    drho += S[pp];
+  }
+  D2 j[3] = {D2(0.0f, 0.0f), D2(0.0f, 0.0f), D2(0.0f, 0.0f)};
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int pp = 0; pp < kPairs3; pp++) j[a] = mac3(j[a], cvel3(rep3(pp), a), Dd[pp]);
+  rho = D2(1.0f, 0.0f) + drho;
+  const D2 acc[3] = {kd.ax, kd.ay, kd.az};
+#pragma unroll
+  for (int a = 0; a < 3; a++) u[a] = (j[a] + D2(0.5f, 0.0f) * rho * acc[a]) / rho;
+  const D2 uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float rf = rho.h, uaf = u[0].h * kd.ax.h + u[1].h * kd.ay.h + u[2].h * kd.az.h;
+  n0 = to_f(D2(d[0], 0.0f) - wq3<D2>(0) * (drho - D2(1.5) * rho * uu));
+  F0 = -3.0f * w3<float>(0) * rf * uaf;
+#pragma unroll
+  for (int pp = 0; pp < kPairs3; pp++) {
+    const int q = rep3(pp);
+    const D2 cu = mac3(mac3(mac3(D2(0.0f, 0.0f), cvel3(q, 0), u[0]), cvel3(q, 1), u[1]),
+                       cvel3(q, 2), u[2]);
+    const float caf = mac3(mac3(mac3(0.0f, cvel3(q, 0), kd.ax.h), cvel3(q, 1), kd.ay.h),
+                           cvel3(q, 2), kd.az.h);
+    NS[pp] = to_f(S[pp] - D2(2.0) * wq3<D2>(q) * (drho + rho * (D2(4.5) * cu * cu - D2(1.5) * uu)));
+    NA[pp] = to_f(Dd[pp] - D2(6.0) * wq3<D2>(q) * rho * cu);
+    const float wrf = w3<float>(q) * rf;
+    FS[pp] = 2.0f * wrf * (9.0f * cu.h * caf - 3.0f * uaf);
+    FA[pp] = 6.0f * wrf * caf;
+  }
+}
+
 // The exact-mass variant's extra record per warp: rho - 1, rho, u_x, u_y,
 // u_z of each boundary node in double-FP32 (pairs of rows).
 struct Warp3X {
@@ -375,11 +445,12 @@ struct Warp3X {
 // that leans the same way step after step shifts that rate: the storage
 // rounding of f' (round to nearest), and equally the FP32 arithmetic of the
 // collision, whose rounding errors repeat every step once the flow is
-// steady.  So the collision change runs in double-FP32 arithmetic (kd: the
-// case's constants as double-FP32 pairs), f'_1..f'_18 are rounded to FP32
-// stochastically, and f'_0 closes the node's mass in double-FP32 plus the
-// node's carry c0 (what FP32 storage dropped from its earlier values);
-// stored rounded to nearest, the new remainder is kept in c0.
+// steady.  So d - d_eq is formed in double-FP32 (exact_moments3; kd: the
+// body force as double-FP32 pairs) before the FP32 transform to f' - f,
+// f'_1..f'_18 are rounded to FP32 stochastically, and f'_0 closes the
+// node's mass in double-FP32 plus the node's carry c0 (what FP32 storage
+// dropped from its earlier values); stored rounded to nearest, the new
+// remainder is kept in c0.
 template <typename C, bool kExact = false>
 __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__ dst,
                                       const Const3<C> &k, const int64_t p, const uint32_t fl,
@@ -409,10 +480,10 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
   C o[Q];
   if constexpr (kExact) {
     static_assert(std::is_same<C, float>::value, "the exact-mass variant is FP32 storage");
-    D2 dx[Q], drx, rhx, ux3[3], chx[Q];
-#pragma unroll
-    for (int q = 0; q < Q; q++) dx[q] = D2(d[q], 0.0f);
-    collide3<D2>(dx, *kd, drx, rhx, ux3, chx);
+    D2 drx, rhx, ux3[3];
+    float n0, F0, NS[kPairs3], NA[kPairs3], FS[kPairs3], FA[kPairs3], ch[Q];
+    exact_moments3(d, *kd, drx, rhx, ux3, n0, F0, NS, NA, FS, FA);
+    transform3<float>(n0, F0, NS, NA, FS, FA, k, ch);
     // f'_q = f_q + ch_q rounded to FP32 stochastically (16 random bits
     // each: the halves of the node's nine random words)
     uint32_t rw[kPairs3];
@@ -422,9 +493,8 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
 #pragma unroll
     for (int pp = 0; pp < kPairs3; pp++) {
       const int q = rep3(pp), qb = opp3(q);
-      const D2 vq = dx[q] + chx[q], vb = dx[qb] + chx[qb];
-      o[q] = lbm::dev::add_stochastic(vq.h, vq.l, rw[pp] & 0xFFFFu);
-      o[qb] = lbm::dev::add_stochastic(vb.h, vb.l, rw[(pp + 4) % kPairs3] >> 16);
+      o[q] = lbm::dev::add_stochastic(d[q], ch[q], rw[pp] & 0xFFFFu);
+      o[qb] = lbm::dev::add_stochastic(d[qb], ch[qb], rw[(pp + 4) % kPairs3] >> 16);
     }
     // f'_0 = f_0 - sum (f'_q - f_q) plus the carry, in double-FP32 (each
     // change is the exact difference of two FP32 values); stored rounded to
@@ -436,7 +506,7 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
       lbm::dev::two_sum(o[q], -d[q], h, l);
       sum += D2(h, l);
     }
-    const D2 v0 = (dx[0] - sum) + D2(*c0, 0.0f);
+    const D2 v0 = (D2(d[0], 0.0f) - sum) + D2(*c0, 0.0f);
     float e0;
     lbm::dev::two_sum(v0.h, v0.l, o[0], e0);
     *c0 = e0;
@@ -492,10 +562,10 @@ __device__ __forceinline__ void node3(const C *__restrict__ src, C *__restrict__
 // warp spreads them over its lanes, one link per lane, each reading its
 // node's values from the warp's shared record -- the links of a node
 // cluster would otherwise run direction by direction on few lanes.
-// kExact: 128 registers and 4 CTAs per SM (the double-FP32 collision is
-// issue-bound; fewer resident warps, or more spills, measured slower).
+// kExact: 80 registers and 6 CTAs per SM (issue-bound; 4 and 5 CTAs per SM
+// measured 2 to 4 % slower).
 template <typename C, bool kExact = false>
-__global__ void __launch_bounds__(kThreads3, kExact ? 4 : (sizeof(C) == 4 ? 8 : 2))
+__global__ void __launch_bounds__(kThreads3, kExact ? 6 : (sizeof(C) == 4 ? 8 : 2))
 step3_kernel(const C *__restrict__ src, C *__restrict__ dst, const uint32_t *__restrict__ flags,
              const uint32_t *__restrict__ lbase, const Link3<C> *__restrict__ links,
              const uint2 *__restrict__ fluid, const __grid_constant__ Const3<C> k, int64_t n_fluid,

@@ -108,15 +108,16 @@ typedef struct {
   int32_t mass_mode;    /* LBM_FP32 only.  0 (default): the exact-mass step where a wall moves
                            (some link has a nonzero wall velocity) or the lattice has no
                            boundary links (periodic, often uniform flow); 1: always; -1: never.
-                           The exact-mass step computes the collision change in FP64 and
-                           rounds f'_1..f'_8 to FP32 stochastically (unbiased), forms each
-                           boundary link's value (Eq. EqNewBDSC) in double-FP32 arithmetic
-                           (about 48 significant bits) and the rest population's mass closure
-                           in FP64, and keeps, per link and per node, what FP32 storage dropped
-                           from them, adding it to the next value: the stored mass then follows
-                           the exact trajectory instead of drifting by roundings that repeat
-                           every step.  It costs 4 B per link and 8 B per fluid node of extra
-                           traffic per step, and FP64 arithmetic per node. */
+                           The exact-mass step sums rho - 1 and j in twice the working
+                           precision, rounds f'_1..f'_8 to FP32 stochastically (unbiased),
+                           forms each boundary link's value (Eq. EqNewBDSC) in double-FP32
+                           arithmetic (about 48 significant bits) and the rest population's
+                           mass closure in twice the working precision, and keeps, per link
+                           and per node, what FP32 storage dropped from them, adding it to the
+                           next value: the stored mass then follows the exact trajectory
+                           instead of drifting by roundings that repeat every step.  It costs
+                           4 B per link and 8 B per fluid node of extra traffic per step and
+                           about 2.5x the plain step's time. */
   int32_t residual_mode; /* 0 (default): lbm_residual's residual is the one-step change
                             ||u^n - u^(n-1)|| / ||u^n||.  1: the interval change
                             ||u^n - u^m|| / ((n - m) ||u^n||), u^m the velocity field at the
@@ -406,8 +407,9 @@ int lbm_load(lbm_handle_t *h, const char *path);
  *     lbm_create takes them (collision must be MRT; residual_mode does not
  *     apply).  mass_mode as for lbm_create: by default FP32 takes the
  *     exact-mass step where a wall moves or the lattice has no boundary
- *     links (FP64 collision, stochastic rounding of f'_1..f'_18 to FP32,
- *     double-FP32 link values, per-link and per-node carries).  The lattice
+ *     links (d - d_eq in double-FP32, stochastic rounding of f'_1..f'_18 to
+ *     FP32, double-FP32 link values, per-link and per-node carries; about
+ *     4x the plain step's time).  The lattice
  *     is dense (every node has slots).  Calls synchronise the handle's
  *     stream, except lbm3d_step.
  * ------------------------------------------------------------------------- */

@@ -245,11 +245,12 @@ struct Warp3 {
 };
 
 // Double-FP32 numbers (about 48 significant bits from FP32 operations) with
-// the arithmetic operators, so that the collision template below runs in
-// them unchanged: the exact-mass variant's collision.  This GPU runs FP64 at
-// a small fraction of its FP32 rate; the operations are those of
-// lbm::dev::DF.  Its own namespace keeps its fma out of the ordinary lookup
-// of float and double code (argument-dependent lookup finds it for D2).
+// the arithmetic operators, so that the exact-mass variant's moments
+// (exact_moments3) read as the FP32 code does and mac3 serves them too.
+// This GPU runs FP64 at a small fraction of its FP32 rate; the operations
+// are those of lbm::dev::DF.  Its own namespace keeps its fma out of the
+// ordinary lookup of float and double code (argument-dependent lookup finds
+// it for D2).
 namespace df {
 struct D2 {
   float h, l;
@@ -847,7 +848,7 @@ __global__ void import3_kernel(const double *__restrict__ in, const uint32_t *__
 struct Const3Both {
   Const3<double> d;
   Const3<float> f;
-  Const3<D2> x;  // the FP32 exact-mass variant's collision constants
+  Const3<D2> x;  // the same as double-FP32 pairs (the exact-mass variant's body force)
   Const3<double> &get(double *) { return d; }
   Const3<float> &get(float *) { return f; }
   const Const3<double> &get(double *) const { return d; }
@@ -1080,7 +1081,7 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
                                static_cast<C>(cf[3])};
       }
       // the case's constants in each arithmetic type (the FP32 exact-mass
-      // variant collides in double-FP32)
+      // variant forms its moments in double-FP32)
       auto fill = [&](auto &kc) {
         using A = std::remove_reference_t<decltype(kc.ax)>;
         for (int a = 0; a < Q; a++) {

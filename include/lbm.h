@@ -439,6 +439,9 @@ int lbm3d_set_f(lbm3d_t *h, const double *f);
 int lbm3d_fields(lbm3d_t *h, double *rho, double *ux, double *uy, double *uz);
 /* Per-link r and l as used, in the order the links were given. */
 int lbm3d_link_params(const lbm3d_t *h, double *r, double *l);
+/* The case's sizes and parameters as lbm_get_info reports them (pitch = nx;
+ * exact_mass: 1 if the step runs the exact-mass variant). */
+int lbm3d_get_info(const lbm3d_t *h, lbm_info_t *info);
 void lbm3d_destroy(lbm3d_t *h);
 /* Last error of the handle; with h = NULL, of the last failed lbm3d_create. */
 const char *lbm3d_last_error(const lbm3d_t *h);

@@ -878,6 +878,7 @@ struct lbm3d {
   // the exact-mass variant (FP32): link coefficients as FP32 pairs and the
   // carries (one per link, then one per fluid node)
   int exact = 0;
+  int64_t dev_bytes = 0;  // device memory the handle holds
   lbm::LinkCoefDF *links_df = nullptr;
   float *carry = nullptr;
   void *links = nullptr;
@@ -1048,6 +1049,7 @@ int lbm3d_create(const lbm3d_domain_t *dom, const uint8_t *solid, size_t n_links
   const size_t es = p.precision == LBM_FP64 ? 8 : 4;
   const size_t fbytes = (19 * static_cast<size_t>(h->plane) + (n_links + 63) / 64 * 64) * es;
   auto alloc = [&](void **ptr, size_t bytes) {
+    h->dev_bytes += static_cast<int64_t>(std::max<size_t>(bytes, 16));
     return cudaMalloc(ptr, std::max<size_t>(bytes, 16));
   };
   if (e == cudaSuccess) e = alloc(&h->f[0], fbytes);
@@ -1262,6 +1264,27 @@ int lbm3d_link_params(const lbm3d_t *h, double *r, double *l) {
   if (!h) return LBM_EINVAL;
   if (r) std::copy(h->link_r.begin(), h->link_r.end(), r);
   if (l) std::copy(h->link_l.begin(), h->link_l.end(), l);
+  return LBM_OK;
+}
+
+int lbm3d_get_info(const lbm3d_t *h, lbm_info_t *info) {
+  if (!h || !info) return LBM_EINVAL;
+  *info = lbm_info_t{};
+  info->n_nodes = h->n_nodes;
+  info->n_fluid = h->n_fluid;
+  info->n_links = h->n_links;
+  info->steps = h->steps;
+  info->tau_s = h->cp.tau_s;
+  info->tau_q = h->cp.tau_q;
+  info->E = h->cp.E;
+  info->E_max = h->cp.E_max;
+  info->L1 = h->cp.L1;
+  info->L2 = h->cp.L2;
+  info->n_clamped = h->cp.n_clamped;
+  info->device_bytes = h->dev_bytes;
+  info->precision = h->precision;
+  info->pitch = h->nx;
+  info->exact_mass = h->exact;
   return LBM_OK;
 }
 

@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lbm3d_get_f.argtypes = [H, dp]
     lib.lbm3d_set_f.argtypes = [H, dp]
     lib.lbm3d_link_params.argtypes = [H, dp, dp]
+    lib.lbm3d_get_info.argtypes = [H, ctypes.POINTER(Info)]
     lib.lbm3d_fields.argtypes = [H, dp, dp, dp, dp]
     lib.lbm3d_destroy.argtypes = [H]
     lib.lbm3d_destroy.restype = None
@@ -718,6 +719,12 @@ class Solver3D:
         r, l = np.empty(n), np.empty(n)
         _check3(load().lbm3d_link_params(self.h, _dp(r), _dp(l)), self.h)
         return r, l
+
+    def info(self) -> Info:
+        """lbm3d_get_info: sizes, parameters, device bytes, exact_mass."""
+        info = Info()
+        _check3(load().lbm3d_get_info(self.h, ctypes.byref(info)), self.h)
+        return info
 
     def close(self):
         if getattr(self, "h", None):

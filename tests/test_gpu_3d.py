@@ -95,6 +95,9 @@ def test_fp32_velocity_and_mass_3d(name):
     carries."""
     c = CASES3[name]()
     o, g = _pair3(c, "fp32")
+    info = g.info()
+    assert info.exact_mass == (0 if name == "spheres" else 1)
+    assert (info.n_fluid, info.n_links) == (int((c.solid == 0).sum()), c.n_links)
     m0 = o.residual()[1]
     for n in (500, 1500):
         o.step(n)
@@ -112,6 +115,7 @@ def test_fp32_exact_mass_step_3d_meets_the_mass_target_at_static_walls():
     c = CASES3["spheres"]()
     o = oracle.OracleLBM3D(c, P.Parameters(c.Kn, c.H))
     g = lbm.Solver3D(c, precision="fp32", mass_mode=1)
+    assert g.info().exact_mass == 1
     m0 = o.residual()[1]
     o.step(2000)
     g.step(2000)
@@ -130,6 +134,7 @@ def test_fp32_exact_mass_step_3d_matches_the_plain_step_in_velocity():
     o = oracle.OracleLBM3D(c, P.Parameters(c.Kn, c.H))
     a = lbm.Solver3D(c, precision="fp32")
     b = lbm.Solver3D(c, precision="fp32", mass_mode=-1)
+    assert a.info().exact_mass == 1 and b.info().exact_mass == 0
     m0 = o.residual()[1]
     for s in (o, a, b):
         s.step(1000)

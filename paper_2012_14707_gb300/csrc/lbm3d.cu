@@ -416,15 +416,28 @@ __device__ __forceinline__ void exact_moments3(const float (&d)[Q], const Const3
   const float rf = rho.h, uaf = u[0].h * kd.ax.h + u[1].h * kd.ay.h + u[2].h * kd.az.h;
   n0 = to_f(D2(d[0], 0.0f) - wq3<D2>(0) * (drho - D2(1.5) * rho * uu));
   F0 = -3.0f * w3<float>(0) * rf * uaf;
-#pragma unroll
+  // one pair per iteration, not unrolled: the double-FP32 body is long, and
+  // nine copies of it would overflow the instruction cache
+#pragma unroll 1
   for (int pp = 0; pp < kPairs3; pp++) {
     const int q = rep3(pp);
-    const D2 cu = mac3(mac3(mac3(D2(0.0f, 0.0f), cvel3(q, 0), u[0]), cvel3(q, 1), u[1]),
-                       cvel3(q, 2), u[2]);
-    const float caf = mac3(mac3(mac3(0.0f, cvel3(q, 0), kd.ax.h), cvel3(q, 1), kd.ay.h),
-                           cvel3(q, 2), kd.az.h);
-    NS[pp] = to_f(S[pp] - D2(2.0) * wq3<D2>(q) * (drho + rho * (D2(4.5) * cu * cu - D2(1.5) * uu)));
-    NA[pp] = to_f(Dd[pp] - D2(6.0) * wq3<D2>(q) * rho * cu);
+    D2 cu(0.0f, 0.0f);
+    float caf = 0.0f;
+    const float ka[3] = {kd.ax.h, kd.ay.h, kd.az.h};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const int c = cvel3_rt(q, a);
+      if (c > 0) {
+        cu = cu + u[a];
+        caf += ka[a];
+      } else if (c < 0) {
+        cu = cu - u[a];
+        caf -= ka[a];
+      }
+    }
+    const D2 wq = wq3<D2>(q);
+    NS[pp] = to_f(S[pp] - D2(2.0) * wq * (drho + rho * (D2(4.5) * cu * cu - D2(1.5) * uu)));
+    NA[pp] = to_f(Dd[pp] - D2(6.0) * wq * rho * cu);
     const float wrf = w3<float>(q) * rf;
     FS[pp] = 2.0f * wrf * (9.0f * cu.h * caf - 3.0f * uaf);
     FA[pp] = 6.0f * wrf * caf;

@@ -470,8 +470,8 @@ ACCURACY_3D = {
              "mass_target": 1e-10,
              "mass": "the plain step this line times (walls at rest) misses it at static curved "
                      "walls after 2000 steps (4.6e-10 on the 20^3 sphere array; 1.2e-9 after 4000); "
-                     "met with mass_mode=1 (2.3e-11 after 2000 steps, at 4.3x the step time) and by "
-                     "default where walls move (1.0e-11 after 2000 steps on the moving-lid channel)"},
+                     "met with mass_mode=1 (2.4e-11 after 2000 steps, at 3.7x the step time) and by "
+                     "default where walls move (5.2e-11 after 2000 steps on the moving-lid channel)"},
     "fp64": {"populations": "within 1e-13 of the oracle, element by element"},
 }
 

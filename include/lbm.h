@@ -409,7 +409,7 @@ int lbm_load(lbm_handle_t *h, const char *path);
  *     exact-mass step where a wall moves or the lattice has no boundary
  *     links (d - d_eq in double-FP32, stochastic rounding of f'_1..f'_18 to
  *     FP32, double-FP32 link values, per-link and per-node carries; about
- *     4x the plain step's time).  The lattice
+ *     3.7x the plain step's time).  The lattice
  *     is dense (every node has slots).  Calls synchronise the handle's
  *     stream, except lbm3d_step.
  * ------------------------------------------------------------------------- */

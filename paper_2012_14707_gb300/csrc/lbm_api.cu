@@ -30,6 +30,7 @@ struct lbm_handle {
   uint2 *node = nullptr;  // per fluid node: flags, seam bits, row and link offsets
   int2 *grp = nullptr;    // per group of lbm::kGroup nodes: first row, first link
   uint32_t *jbslot = nullptr;  // per link: slot of f_jb(x, t) (lbm::link_jb_slots)
+  uint16_t *ldesc = nullptr;   // per link: (x mod 64) << 4 | j (lbm::link_descriptors)
   uint32_t pf_dist = 0;        // L2 prefetch distance of the step kernel, in CTAs
   int32_t *rowstart = nullptr;
   int32_t *index = nullptr;  // y * nx + x -> compacted index or -1
@@ -141,7 +142,7 @@ void release(lbm_handle_t *h) {
   cudaStream_t s = h->stream;
   cudaStreamSynchronize(s);
   for (void *p : {h->f[0], h->f[1], static_cast<void *>(h->node), static_cast<void *>(h->grp),
-                  static_cast<void *>(h->jbslot),
+                  static_cast<void *>(h->jbslot), static_cast<void *>(h->ldesc),
                   static_cast<void *>(h->rowstart), static_cast<void *>(h->index), h->links,
                   static_cast<void *>(h->links64), static_cast<void *>(h->carry), h->snap,
                   static_cast<void *>(h->partials), static_cast<void *>(h->result)})
@@ -167,6 +168,7 @@ lbm::PullGeom pull_geom(const lbm_handle_t *h) {
   g.grp = h->grp;
   g.rowstart = h->rowstart;
   g.jbslot = h->jbslot;
+  g.ldesc = h->ldesc;
   g.ny = h->ny;
   g.periodic_y = h->py;
   g.plane = static_cast<uint32_t>(h->plane);
@@ -574,6 +576,20 @@ std::vector<uint32_t> link_jb_slots(const CompactCase &cc, int ny, int periodic_
   return out;
 }
 
+std::vector<uint16_t> link_descriptors(const CompactCase &cc, int64_t n_links) {
+  std::vector<uint16_t> out(static_cast<size_t>(n_links), 0u);
+  parallel_for(cc.n_fluid, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; i++) {
+      const uint32_t fl = cc.node[static_cast<size_t>(i)].x & 0xFFu;
+      int64_t l = cc.lbase[static_cast<size_t>(i)];
+      for (int j = 1; j < 9; j++)
+        if (fl & (1u << (j - 1)))
+          out[static_cast<size_t>(l++)] = static_cast<uint16_t>(((i & 63) << 4) | j);
+    }
+  });
+  return out;
+}
+
 // Error text for handle-less calls, read back by lbm_last_error(NULL).
 const char *set_thread_error(const std::string &msg) {
   g_create_error = msg;
@@ -735,6 +751,9 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   const std::vector<uint32_t> jbs = lbm::link_jb_slots(cc, hc.ny, hc.py, hc.n_links);
   if (e == cudaSuccess)
     e = alloc(reinterpret_cast<void **>(&h->jbslot), std::max<size_t>(1, jbs.size()) * 4);
+  const std::vector<uint16_t> lds = lbm::link_descriptors(cc, hc.n_links);
+  if (e == cudaSuccess)
+    e = alloc(reinterpret_cast<void **>(&h->ldesc), std::max<size_t>(1, lds.size()) * 2);
   if (e == cudaSuccess) e = alloc(&h->links, lbytes);
   h->exact = lbm::exact_mass(hc) ? 1 : 0;
   // the exact-mass variant's link coefficients as FP32 pairs (alive until
@@ -771,6 +790,7 @@ int lbm_create(const lbm_domain_t *dom, const uint8_t *solid, size_t n_links,
   up(h->node, cc.node.data(), P * sizeof(uint2));
   up(h->grp, cc.grp.data(), cc.grp.size() * sizeof(int2));
   up(h->jbslot, jbs.data(), jbs.size() * 4);
+  up(h->ldesc, lds.data(), lds.size() * 2);
   up(h->rowstart, cc.rowstart.data(), cc.rowstart.size() * 4);
   up(h->index, cc.index.data(), cc.index.size() * 4);
   if (e == cudaSuccess)

@@ -57,12 +57,14 @@ __host__ __device__ inline PullGeom case_geom(const BatchCase<C> &bc, const uint
                                               const int2 *grp, const int32_t *rowstart,
                                               const uint32_t *jbslot,
                                               const LinkCoefDF *links64 = nullptr,
-                                              float *carry = nullptr, float *carry0 = nullptr) {
+                                              float *carry = nullptr, float *carry0 = nullptr,
+                                              const uint16_t *ldesc = nullptr) {
   PullGeom g;
   g.node = node + bc.node_off;
   g.grp = grp + bc.grp_off;
   g.rowstart = rowstart + bc.row_off;
   g.jbslot = jbslot ? jbslot + bc.link_off : nullptr;
+  g.ldesc = ldesc ? ldesc + bc.link_off : nullptr;
   g.ny = bc.k.ny;
   g.periodic_y = bc.k.periodic_y;
   g.plane = static_cast<uint32_t>(bc.k.plane);
@@ -381,6 +383,7 @@ struct lbm_batch {
   int64_t arena_nodes = 0;   // node-arena entries (cases padded to kChunk)
   int32_t *rowstart = nullptr;
   uint32_t *jbslot = nullptr;
+  uint16_t *ldesc = nullptr;  // per link: (x mod 64) << 4 | j (lbm::link_descriptors)
   int32_t *index = nullptr;
   void *links = nullptr;
   void *cases = nullptr;
@@ -528,7 +531,7 @@ void batch_release(lbm_batch_t *b) {
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (void *p : {b->f[0], b->f[1], static_cast<void *>(b->node), static_cast<void *>(b->grp),
-                  static_cast<void *>(b->jbslot), static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->ccase), static_cast<void *>(b->active),
+                  static_cast<void *>(b->jbslot), static_cast<void *>(b->ldesc), static_cast<void *>(b->rowstart), static_cast<void *>(b->index), b->links, b->cases, static_cast<void *>(b->ccase), static_cast<void *>(b->active),
                   static_cast<void *>(b->steps_done), static_cast<void *>(b->res),
                   static_cast<void *>(b->counter), static_cast<void *>(b->n_active),
                   static_cast<void *>(b->links64), static_cast<void *>(b->carry),
@@ -674,6 +677,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   std::vector<int2> grp(static_cast<size_t>(std::max<int64_t>(1, groups)), int2{0, 0});
   std::vector<int32_t> ccase(static_cast<size_t>(std::max<int64_t>(1, nodes / lbm::kChunk)), 0);
   std::vector<uint32_t> jbs(static_cast<size_t>(std::max<int64_t>(1, links)), 0u);
+  std::vector<uint16_t> lds(static_cast<size_t>(std::max<int64_t>(1, links)), 0u);
   std::vector<int32_t> rowstart(static_cast<size_t>(rows), 0), index(static_cast<size_t>(dense), -1);
   std::vector<unsigned char> lhost(std::max<int64_t>(1, links) * 4 * ces, 0);
   std::vector<double> l64;  // FP64 link records (filled if some case runs the exact variant)
@@ -713,6 +717,8 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
     std::fill(ccase.begin() + noff / lbm::kChunk, ccase.begin() + (noff + padded) / lbm::kChunk, c);
     const std::vector<uint32_t> kj = lbm::link_jb_slots(k, h.ny, h.py, h.n_links);
     std::copy(kj.begin(), kj.end(), jbs.begin() + loff);
+    const std::vector<uint16_t> kd = lbm::link_descriptors(k, h.n_links);
+    std::copy(kd.begin(), kd.end(), lds.begin() + loff);
     std::copy(k.rowstart.begin(), k.rowstart.end(), rowstart.begin() + roff);
     std::copy(k.index.begin(), k.index.end(), index.begin() + ioff);
     b->chunk_first.push_back(static_cast<int32_t>(noff / lbm::kChunk));
@@ -773,6 +779,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->grp), grp.size() * sizeof(int2));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->ccase), ccase.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->jbslot), jbs.size() * 4);
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->ldesc), lds.size() * 2);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->rowstart), rowstart.size() * 4);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->index), index.size() * 4);
   if (e == cudaSuccess) e = alloc(&b->links, lhost.size());
@@ -815,6 +822,7 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
               static_cast<size_t>(std::max<int64_t>(1, nodes / lbm::kChunk)) * 4);
   if (e == cudaSuccess) e = build_lists(b, nullptr);
   up(b->jbslot, jbs.data(), jbs.size() * 4);
+  up(b->ldesc, lds.data(), lds.size() * 2);
   if (e == cudaSuccess) {
     // every case's pull geometry inside the arenas (read by the step kernels)
     std::vector<lbm::PullGeom> gs(static_cast<size_t>(n_cases));
@@ -822,11 +830,11 @@ int lbm_batch_create(const lbm_case_t *cases, int32_t n_cases, int32_t precision
       if (precision == LBM_FP64)
         gs[c] = lbm::case_geom(reinterpret_cast<const lbm::BatchCase<double> *>(chost.data())[c],
                                b->node, b->grp, b->rowstart, b->jbslot, b->links64, b->carry,
-                               b->carry0);
+                               b->carry0, b->ldesc);
       else
         gs[c] = lbm::case_geom(reinterpret_cast<const lbm::BatchCase<float> *>(chost.data())[c],
                                b->node, b->grp, b->rowstart, b->jbslot, b->links64, b->carry,
-                               b->carry0);
+                               b->carry0, b->ldesc);
     }
     e = alloc(reinterpret_cast<void **>(&b->geoms), gs.size() * sizeof(lbm::PullGeom));
     if (e == cudaSuccess)

@@ -823,8 +823,10 @@ __device__ __forceinline__ float link_value_rt(const LinkCoef<float> &c, const i
 // links in the table; the warp spreads them over its lanes, one link per
 // lane at a time, each reading its node's values (f'_1..f'_8, drho, rho, u,
 // |u|^2 in the step's units, and the node's random word) from the warp's
-// shared record.  Each link value is rounded stochastically with the
-// random bits of its node and direction, as a node doing its own links
+// shared record.  The warp's nodes are one 64-aligned block, so each link's
+// entry of g.ldesc ((x mod 64) << 4 | j) names its node's column in the
+// record and its direction.  Each link value is rounded stochastically with
+// the random bits of its node and direction, as a node doing its own links
 // would.  The lanes whose pair is complete take part (a prefix of the
 // warp; a lone last node runs the one-node step instead).
 constexpr int kPairMaxWarps = 4;  // CTAs of up to 128 threads
@@ -840,14 +842,13 @@ __device__ __forceinline__ void pair_links_warp(const T *__restrict__ src, T *__
                                                 const uint32_t h0, const uint32_t h1) {
   __shared__ float pw_v[kPairMaxWarps][13][65];
   __shared__ uint32_t pw_h[kPairMaxWarps][64];
-  __shared__ uint32_t pw_ex[kPairMaxWarps][32], pw_fl[kPairMaxWarps][32];
   const int lane = static_cast<int>(threadIdx.x & 31u), w = static_cast<int>(threadIdx.x >> 5);
   const uint32_t first = i0 - 2u * static_cast<uint32_t>(lane);
   const uint32_t pairs = (g.n_fluid - first) / 2u;
   const int nact = pairs >= 32u ? 32 : static_cast<int>(pairs);
   const unsigned am = nact == 32 ? 0xFFFFFFFFu : ((1u << nact) - 1u);
   __syncwarp(am);
-  const uint32_t na = static_cast<uint32_t>(__popc(fl0)), nl = na + static_cast<uint32_t>(__popc(fl1));
+  const uint32_t nl = static_cast<uint32_t>(__popc(fl0)) + static_cast<uint32_t>(__popc(fl1));
   const unsigned anyl = __ballot_sync(am, nl != 0u);
   if (anyl == 0u) return;
   if (fl0) {
@@ -872,36 +873,17 @@ __device__ __forceinline__ void pair_links_warp(const T *__restrict__ src, T *__
     pw_v[w][12][n] = uu.v.y;
     pw_h[w][n] = h1;
   }
-  // exclusive prefix of the lanes' link counts: link t of the warp is link
-  // base + t of the table
-  uint32_t incl = nl;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t v = __shfl_up_sync(am, incl, off);
-    if (lane >= off) incl += v;
-  }
-  const uint32_t excl = incl - nl, total = __shfl_sync(am, incl, nact - 1);
+  // the warp's links are links base .. base + total - 1 of the table (its
+  // first lane with links holds the first of them)
+  const uint32_t total = __reduce_add_sync(am, nl);
   const uint32_t mine = fl0 ? li0 : li1;  // the lane's first link (where it has one)
-  const uint32_t base = __shfl_sync(am, mine - excl, __ffs(static_cast<int>(anyl)) - 1);
-  pw_ex[w][lane] = excl;
-  pw_fl[w][lane] = fl0 | (fl1 << 8);
+  const uint32_t base = __shfl_sync(am, mine, __ffs(static_cast<int>(anyl)) - 1);
   __syncwarp(am);
   const uint32_t tail = 9u * g.plane;
   for (uint32_t t = static_cast<uint32_t>(lane); t < total; t += static_cast<uint32_t>(nact)) {
-    int s = 0;
-#pragma unroll
-    for (int st = 16; st >= 1; st >>= 1)
-      if (s + st < nact && pw_ex[w][s + st] <= t) s += st;
-    uint32_t r = t - pw_ex[w][s];
-    const uint32_t f = pw_fl[w][s], fa = f & 0xFFu;
-    const uint32_t ca = static_cast<uint32_t>(__popc(fa));
-    const int half = r >= ca ? 1 : 0;
-    uint32_t m = half ? (f >> 8) : fa;
-    if (half) r -= ca;
-    for (; r; r--) m &= m - 1u;
-    const int j = __ffs(static_cast<int>(m)), jb = opp2(j);
-    const int n = 2 * s + half;
     const uint32_t lj = base + t;
+    const uint32_t dsc = g.ldesc[lj];
+    const int n = static_cast<int>(dsc >> 4), j = static_cast<int>(dsc & 15u), jb = opp2(j);
     const float v = link_value_rt<T>(links[lj], j, Stor<T>::ld_raw(src[g.jbslot[lj]]),
                                      pw_v[w][j - 1][n], pw_v[w][jb - 1][n], pw_v[w][8][n],
                                      pw_v[w][9][n], pw_v[w][10][n], pw_v[w][11][n],

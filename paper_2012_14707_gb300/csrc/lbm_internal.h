@@ -194,6 +194,7 @@ struct PullGeom {
   const int2 *grp = nullptr;        // group records (CompactCase::grp)
   const int32_t *rowstart = nullptr;
   const uint32_t *jbslot = nullptr; // per link (x, j): pull slot of f_jb(x) (link_jb_slots)
+  const uint16_t *ldesc = nullptr;  // per link (x, j): (x mod 64) << 4 | j (link_descriptors)
   int32_t ny = 0, periodic_y = 0;
   uint32_t plane = 0;               // P
   uint32_t n_fluid = 0;
@@ -287,6 +288,12 @@ std::string build_compact(const HostCase &hc, CompactCase *cc);
 // there instead of recomputing the neighbour's index.
 std::vector<uint32_t> link_jb_slots(const CompactCase &cc, int ny, int periodic_y,
                                     int64_t n_links);
+
+// For every link (node x, direction j) of a compacted case, in link-table
+// order: (x mod 64) << 4 | j.  A warp of the paired 16-bit step runs the 64
+// nodes of one 64-aligned block (x mod 64 is the node's place in it), so
+// each lane finds its link's node and direction from this one entry.
+std::vector<uint16_t> link_descriptors(const CompactCase &cc, int64_t n_links);
 
 // Kernel constants of one case in arithmetic type C.
 template <typename C>

@@ -53,6 +53,8 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
   const uint32_t P = (uint32_t)cc.plane;
   const std::vector<uint32_t> jbs = lbm::link_jb_slots(cc, ny, py, hc.n_links);
   if ((int64_t)jbs.size() != hc.n_links) bad++;
+  const std::vector<uint16_t> lds = lbm::link_descriptors(cc, hc.n_links);
+  if ((int64_t)lds.size() != hc.n_links) bad++;
   const uint64_t n_slots = 9ull * P + (uint64_t)hc.n_links;
   std::vector<uint8_t> slot_use(n_slots, 0);
   if (cc.grp.size() != (size_t)((cc.n_fluid + lbm::kGroup - 1) / lbm::kGroup)) bad++;
@@ -116,6 +118,9 @@ int check(const char *name, int nx, int ny, int px, int py, std::vector<uint8_t>
                                           __builtin_popcount(fl & ((1u << (ob - 1)) - 1u)));
           }
           if (jbs[link] != want_jb) bad++;
+          // the link's descriptor: its node's place in the node's 64-aligned
+          // block and its direction
+          if (lds[link] != (uint16_t)(((uint32_t)i & 63u) << 4 | (uint32_t)qd)) bad++;
           rank++;
         }
       }
